@@ -1,0 +1,262 @@
+"""FP64 CPU oracle for the SplatAD camera/lidar rasterizer (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The library's product path never does.
+
+The numerical work lives in ``splat_oracle.c`` (plain C, FP64, OpenMP over
+rays); this module only builds it with gcc and marshals numpy arrays through
+ctypes.  Functions and the paper passages they follow:
+
+* :func:`project`        -- Sec. 3.2 projection / AABB / tiles; Sec. 3.3 and
+                            App. A.1 for the lidar (spherical projection, J^S,
+                            azimuth wrap, elevation loop).
+* :func:`isect_list`     -- Sec. 3.2 / 3.3 tile duplication and depth (range)
+                            sort: pairs ordered by (tile, depth, id).
+* :func:`render`         -- Eq. (t_pix), (alpha blend), (alpha), (delta);
+                            Sec. 3.3 expected range (r + v_r t) and median range.
+* :func:`render_backward`-- reverse mode of the above, then the projection
+                            chain rule back to means, scales, quaternions,
+                            opacities, velocities and features.
+* :mod:`oracle.head`     -- the per-ray MLP decoder (Sec. 3.3, App. B).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+GUARD_PX = 1e-4     # camera tile-edge guard band, pixels
+GUARD_RAD = 2e-6    # lidar tile-edge guard band, radians
+
+
+def build(force: bool = False) -> str:
+    """Compile ``splat_oracle.c`` (and the head oracle) into ``liboracle.so``."""
+    srcs = [os.path.join(_HERE, "splat_oracle.c"), os.path.join(_HERE, "head_oracle.c")]
+    srcs = [s for s in srcs if os.path.exists(s)]
+    newest = max(os.path.getmtime(s) for s in srcs)
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-D_DEFAULT_SOURCE", "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = ctypes.CDLL(_LIB_PATH)
+        _declare(_lib)
+    return _lib
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+
+
+def _declare(L):
+    L.oracle_project.restype = ctypes.c_int
+    L.oracle_project.argtypes = [_I64] + [_P] * 7 + [ctypes.c_double] + [_P] * 6
+    L.oracle_isect_list.restype = _I64
+    L.oracle_isect_list.argtypes = [_I64, _P, _P, _P, _P, _I64, _P, _P]
+    L.oracle_render.restype = ctypes.c_int
+    L.oracle_render.argtypes = ([_I64] + [_P] * 6 + [ctypes.c_int] + [_P] * 3 + [ctypes.c_double, _I64] + [_P] * 7)
+    L.oracle_render_backward.restype = ctypes.c_int
+    L.oracle_render_backward.argtypes = ([_I64] + [_P] * 6 + [ctypes.c_int] + [_P] * 14)
+    L.oracle_projection_backward.restype = ctypes.c_int
+    L.oracle_projection_backward.argtypes = [_I64] + [_P] * 13
+    L.oracle_jacobian.restype = ctypes.c_int
+    L.oracle_jacobian.argtypes = [_P, _P, _P, ctypes.c_double, _P, _P, _P, _P, _P]
+    if hasattr(L, "head_forward"):
+        from . import head as _head
+        _head._declare(L)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f32(a):
+    """Input array as FP64.  FP32 arrays (what the library receives) are promoted
+    exactly; FP64 arrays pass unchanged, so finite-difference tests can perturb
+    parameters far below FP32 resolution."""
+    if a is None:
+        return None
+    a = np.asarray(a)
+    if a.dtype != np.float64:
+        a = a.astype(np.float32)
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _r32(x) -> float:
+    """Round a parameter through FP32, exactly as the library receives it."""
+    return float(np.float32(x))
+
+
+def sensor_params(s) -> np.ndarray:
+    """Flat FP64 parameter vector of a sensor (values rounded through FP32)."""
+    P = np.zeros(32, dtype=np.float64)
+    P[1:10] = np.asarray(s.R, dtype=np.float32).reshape(9)
+    P[10:13] = np.asarray(s.t, dtype=np.float32)
+    P[13:16] = np.asarray(s.lin_vel, dtype=np.float32)
+    P[16:19] = np.asarray(s.ang_vel, dtype=np.float32)
+    if s.kind == "camera":
+        P[0] = 0
+        P[19:31] = [s.width, s.height, _r32(s.fx), _r32(s.fy), _r32(s.cx), _r32(s.cy), _r32(s.rs_time),
+                    _r32(s.time_offset), _r32(s.eps2d), _r32(s.near), s.tile_w, s.tile_h]
+    else:
+        P[0] = 1
+        P[19:27] = [s.n_beams, s.n_az, _r32(s.az_res), _r32(s.sweep_time), _r32(s.eps2d), _r32(s.r_min),
+                    s.tile_az, s.tile_el]
+    return P
+
+
+def _sensor_array(a):
+    """Sensor-side arrays always reach the renderer in FP32; round them the same way."""
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float32), dtype=np.float64)
+
+
+def _elev(s):
+    return _sensor_array(s.beam_elev) if s.kind == "lidar" else None
+
+
+def _rays(s):
+    return _sensor_array(s.rays.reshape(-1, 3)) if (s.kind == "lidar" and s.rays is not None) else None
+
+
+def _g(g):
+    return [_f32(g["means"]), _f32(g["scales"]), _f32(g["quats"]), _f32(g["opacities"]), _f32(g.get("velocities"))]
+
+
+def guard_for(s) -> float:
+    return GUARD_PX if s.kind == "camera" else GUARD_RAD
+
+
+def n_tiles_of(s):
+    if s.kind == "camera":
+        return (-(-s.width // s.tile_w)) * (-(-s.height // s.tile_h))
+    return (-(-s.n_az // s.tile_az)) * (s.n_beams // s.tile_el)
+
+
+def project(g: dict, s, guard: float | None = None) -> dict:
+    """Per-Gaussian projection of one sensor (FP64).
+
+    Returns rec (n,16): [mean_a, mean_b, conic a, b, c, o', depth, v_a, v_b, v_r,
+    Sigma'_aa, Sigma'_ab, Sigma'_bb, compensation, extent_a, extent_b], rect (n,4),
+    outer rect, n_tiles, visible and marginal flags.
+    """
+    L = lib()
+    n = len(g["opacities"])
+    m = _g(g)
+    P = sensor_params(s)
+    guard = guard_for(s) if guard is None else guard
+    rec = np.zeros((n, 16)); rect = np.zeros((n, 4), np.int32); orect = np.zeros((n, 4), np.int32)
+    nt = np.zeros(n, np.int32); vis = np.zeros(n, np.uint8); marg = np.zeros(n, np.uint8)
+    el = _elev(s)
+    L.oracle_project(n, *[_ptr(a) for a in m], _ptr(P), _ptr(el), guard, _ptr(rec), _ptr(rect), _ptr(orect),
+                     _ptr(nt), _ptr(vis), _ptr(marg))
+    return {"rec": rec, "rect": rect, "orect": orect, "n_tiles": nt, "visible": vis.astype(bool),
+            "marginal": marg.astype(bool)}
+
+
+def isect_list(g: dict, s, proj: dict | None = None):
+    """Sorted (tile, gaussian id) intersection list of one sensor."""
+    L = lib()
+    proj = project(g, s) if proj is None else proj
+    n = len(g["opacities"])
+    P = sensor_params(s)
+    total = int(proj["n_tiles"].astype(np.int64).sum())
+    tiles = np.zeros(max(total, 1), np.int32); ids = np.zeros(max(total, 1), np.int32)
+    got = L.oracle_isect_list(n, _ptr(P), _ptr(proj["rec"]), _ptr(proj["rect"]), _ptr(proj["n_tiles"]), total,
+                              _ptr(tiles), _ptr(ids))
+    assert got == total
+    return tiles[:total], ids[:total]
+
+
+def render(g: dict, s, sel=None, guard: float | None = None) -> dict:
+    """Render the selected rays (indices into the sensor's ray grid; None: all).
+
+    Camera ray k is pixel (row, col) = divmod(k, width); lidar ray k is
+    (beam, azimuth bin) = divmod(k, n_az).
+    """
+    L = lib()
+    n = len(g["opacities"])
+    m = _g(g)
+    feat = _f32(g["features"])
+    C = feat.shape[1] if feat.ndim == 2 else 0
+    P = sensor_params(s)
+    guard = guard_for(s) if guard is None else guard
+    sel_arr = None if sel is None else np.ascontiguousarray(sel, dtype=np.int64)
+    nr = s.n_rays if sel is None else len(sel_arr)
+    F = np.zeros((nr, C)); T = np.zeros(nr); De = np.zeros(nr); Dm = np.zeros(nr)
+    mg = np.zeros(nr, np.uint8); cnt = np.zeros(nr, np.int32)
+    L.oracle_render(n, *[_ptr(a) for a in m], _ptr(feat), C, _ptr(P), _ptr(_elev(s)), _ptr(_rays(s)), guard,
+                    nr, _ptr(sel_arr), _ptr(F), _ptr(T), _ptr(De), _ptr(Dm), _ptr(mg), _ptr(cnt))
+    out = {"F": F, "T": T, "marginal": mg.astype(bool), "count": cnt}
+    if s.kind == "lidar":
+        out.update({"range_exp": De, "range_med": Dm, "alpha": 1.0 - T})
+    return out
+
+
+def render_backward(g: dict, s, gF, gT=None, gD=None, gA=None) -> dict:
+    """Gradients of sum(gF*F) + sum(gT*T) [+ sum(gD*range_exp) + sum(gA*alpha)]."""
+    L = lib()
+    n = len(g["opacities"])
+    m = _g(g)
+    feat = _f32(g["features"])
+    C = feat.shape[1]
+    P = sensor_params(s)
+    out = {"d2": np.zeros((n, 10)), "features": np.zeros((n, C)), "means": np.zeros((n, 3)),
+           "scales": np.zeros((n, 3)), "quats": np.zeros((n, 4)), "opacities": np.zeros(n),
+           "velocities": np.zeros((n, 3))}
+    L.oracle_render_backward(n, *[_ptr(a) for a in m], _ptr(feat), C, _ptr(P), _ptr(_elev(s)), _ptr(_rays(s)),
+                             _ptr(_f32(gF)), _ptr(_f32(gT)), _ptr(_f32(gD)), _ptr(_f32(gA)), _ptr(out["d2"]),
+                             _ptr(out["features"]), _ptr(out["means"]), _ptr(out["scales"]), _ptr(out["quats"]),
+                             _ptr(out["opacities"]), _ptr(out["velocities"]))
+    return out
+
+
+def projection_backward(g: dict, s, d2) -> dict:
+    L = lib()
+    n = len(g["opacities"])
+    m = _g(g)
+    P = sensor_params(s)
+    out = {"means": np.zeros((n, 3)), "scales": np.zeros((n, 3)), "quats": np.zeros((n, 4)),
+           "opacities": np.zeros(n), "velocities": np.zeros((n, 3))}
+    L.oracle_projection_backward(n, *[_ptr(a) for a in m], _ptr(P), _ptr(_elev(s)),
+                                 _ptr(np.ascontiguousarray(d2, dtype=np.float64)), _ptr(out["means"]),
+                                 _ptr(out["scales"]), _ptr(out["quats"]), _ptr(out["opacities"]),
+                                 _ptr(out["velocities"]))
+    return out
+
+
+def jacobian(mean, scale, quat, opac, s):
+    """(visible, J (3x3), sensor-frame covariance, relative velocity w) of one Gaussian."""
+    L = lib()
+    J = np.zeros(9); Sc = np.zeros(9); w = np.zeros(3)
+    vis = L.oracle_jacobian(_ptr(_f32(mean)), _ptr(_f32(scale)), _ptr(_f32(quat)), float(np.float32(opac)),
+                            _ptr(sensor_params(s)), _ptr(_elev(s)), _ptr(J), _ptr(Sc), _ptr(w))
+    return bool(vis), J.reshape(3, 3), Sc.reshape(3, 3), w
+
+
+def frame_isect_list(g: dict, sensors) -> tuple[np.ndarray, np.ndarray]:
+    """Concatenated list over a frame's sensors with global tile ids (sensor order)."""
+    tiles, ids, off = [], [], 0
+    for s in sensors:
+        t, i = isect_list(g, s)
+        tiles.append(t.astype(np.int64) + off)
+        ids.append(i)
+        off += n_tiles_of(s)
+    return np.concatenate(tiles), np.concatenate(ids)
