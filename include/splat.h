@@ -1,0 +1,239 @@
+/*
+ * splat.h -- C ABI of libsplat, a GB300 (sm_103a) implementation of SplatAD's
+ * differentiable tile-based Gaussian rasterizer for cameras and spinning lidars
+ * (arXiv 2411.16816).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every array argument is CALLER-OWNED DEVICE MEMORY unless stated otherwise; the
+ *    library never allocates, frees or synchronises.  All work is enqueued on `stream`
+ *    (a cudaStream_t passed as void*; NULL means the legacy default stream).
+ *  - All floating point is FP32.  Matrices are row-major.
+ *  - Host-detectable argument errors (null pointers, unsupported channel counts,
+ *    inconsistent tiling) return SPLAT_ERR_INVALID_ARG before anything is enqueued;
+ *    splat_last_error() then returns a message (thread-local).
+ *  - Errors found on the device (intersection capacity exceeded) are reported through
+ *    device-side counters described per function; nothing writes out of bounds.
+ *  - Gradient outputs are ACCUMULATED (+=) so that several sensors or frames can share
+ *    them; the caller zeroes them first.
+ *  - The library launches no kernel that waits on another block: there are no
+ *    inter-block spin waits anywhere, so no call can hang on a lost signal.
+ *
+ * Sensor model (paper Sec. 3.2, 3.3, App. A, App. D)
+ * --------------------------------------------------
+ *  World frame: any right-handed frame.  A sensor pose is the world->sensor rotation R
+ *  and translation t (x_s = R x_w + t) at the sensor's mid-capture time; lin_vel and
+ *  ang_vel are the sensor's own linear and angular velocity in its own frame.  Camera
+ *  frame: z forward, x right, y down; pixel centres at (col + 0.5, row + 0.5).  Lidar
+ *  frame: azimuth phi = atan2(y, x) in [0, 2 pi), elevation omega = asin(z / r).
+ */
+#ifndef SPLAT_H
+#define SPLAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t splat_status;
+#define SPLAT_OK 0
+#define SPLAT_ERR_INVALID_ARG 1
+#define SPLAT_ERR_CAPACITY 2
+#define SPLAT_ERR_CUDA 3
+#define SPLAT_ERR_TIMEOUT 4
+
+#define SPLAT_SENSOR_CAMERA 0
+#define SPLAT_SENSOR_LIDAR 1
+#define SPLAT_MAX_SENSORS 16
+
+/* 3D Gaussians (paper Sec. 3.1), structure of arrays, device memory, FP32.
+ *   means[n][3]       world-frame means mu
+ *   scales[n][3]      ACTIVATED scales S (already exponentiated, > 0)
+ *   quats[n][4]       rotation quaternion (w, x, y, z), need not be normalised
+ *   opacities[n]      ACTIVATED opacity o in (0, 1)
+ *   features[n][channels]  per-Gaussian features blended by the rasterizer (the
+ *                     paper's [f_rgb, f]); channels in {1,2,3,4,8,16,29,32}
+ *   velocities[n][3]  world-frame velocity of each Gaussian (v_dyn before rotation to
+ *                     the sensor frame); may be NULL for a static scene */
+typedef struct {
+    const float *means;
+    const float *scales;
+    const float *quats;
+    const float *opacities;
+    const float *features;
+    const float *velocities;
+    int64_t n;
+    int32_t channels;
+    int32_t reserved;
+} splat_gaussians;
+
+/* One sensor.  `kind` selects which block of fields is read.
+ * Camera (Sec. 3.2): pinhole width x height, fx, fy, cx, cy; rs_time is the rolling-
+ *   shutter readout time t_rs (first to last row, seconds; 0 = global shutter);
+ *   time_offset is the learnable offset between timestamp and mid-exposure (added to
+ *   every row time); eps2d is the blur s of Eq. (alpha) in px^2 (0.3 in the paper);
+ *   near_plane culls Gaussians with camera z below it; tile_w x tile_h is the tile
+ *   (16 x 16 in the paper; supported: 16x16, 8x8, 32x8, 16x32).
+ * Lidar (Sec. 3.3, App. A): n_beams elevation channels with ascending elevations
+ *   beam_elev[n_beams] (radians, DEVICE memory), n_az azimuth bins of az_res radians
+ *   (n_az * az_res must equal 2 pi), sweep_time is the spin period t_rs, eps2d is the
+ *   blur in rad^2, r_min culls Gaussians closer than it (metres); tile_w x tile_h =
+ *   N_phi azimuth bins x N_omega beams per tile (32 x 8 in the paper; n_beams must be
+ *   a multiple of tile_h and tile_w * tile_h must be 64, 128, 256 or 512).  rays, if
+ *   not NULL, is DEVICE memory [n_beams][n_az][3] of per-ray (phi, omega, t) that
+ *   replace the regular grid phi = (a + 0.5) az_res, omega = beam_elev[b],
+ *   t = ((a + 0.5) / n_az - 0.5) sweep_time; each ray stays in its grid cell's tile. */
+typedef struct {
+    int32_t kind;
+    int32_t reserved0;
+    float R[9];
+    float t[3];
+    float lin_vel[3];
+    float ang_vel[3];
+    /* camera */
+    int32_t width, height;
+    float fx, fy, cx, cy;
+    float rs_time, time_offset;
+    float eps2d;
+    float near_plane;
+    /* lidar */
+    int32_t n_beams, n_az;
+    const float *beam_elev;
+    const float *rays;
+    float az_res, sweep_time, r_min;
+    /* tiling (both kinds) */
+    int32_t tile_w, tile_h;
+    int32_t reserved1;
+} splat_sensor;
+
+/* Per-(sensor, Gaussian) projection results, caller-owned device buffers.
+ *   rec[n_sensors][3][n][4] floats:
+ *     rec[s][0][i] = (mean_a, mean_b, v_a, v_b)  2-D mean (pixels, or phi/omega in rad)
+ *                     and its sensor-space velocity (Eq. pixel velocity / v^S)
+ *     rec[s][1][i] = (conic_a, conic_b, conic_c, o')  (Sigma_2d + eps I)^-1 as
+ *                     [[a, b], [b, c]] and the compensated opacity of Eq. (alpha)
+ *     rec[s][2][i] = (depth, v_r, 0, 0)  camera z or lidar range r, and the range rate
+ *   rect[n_sensors][n][4] int16: tile rectangle (x0, y0, x1, y1), x1/y1 exclusive; for
+ *     a lidar x0 is in [0, M_phi) and x1 may exceed M_phi (columns wrap modulo M_phi)
+ *   n_tiles[n_sensors][n] int32: intersected tiles (0 = culled) */
+typedef struct {
+    float *rec;
+    int16_t *rect;
+    int32_t *n_tiles;
+} splat_projected;
+
+/* Sorted intersection lists of a frame (all sensors).
+ *   isect_ids[capacity]: Gaussian index of each (tile, Gaussian) pair, ordered by
+ *     global tile, then depth (camera z / lidar range), then Gaussian index.
+ *   tile_ranges[total_tiles][2]: [start, end) of each tile in isect_ids.  Global tile
+ *     ids number the sensors' tiles consecutively in sensor order, each sensor
+ *     row-major (camera: ty * tiles_x + tx; lidar: row * M_phi + column).
+ *   n_isect: one int64 on the device, written with the number of intersections found
+ *     (it may exceed `capacity`, in which case the lists are not valid). */
+typedef struct {
+    uint32_t *isect_ids;
+    int32_t *tile_ranges;
+    int64_t *n_isect;
+} splat_bins;
+
+/* Tiles of a frame: per-sensor tile counts, their total, and rays per sensor.
+ * tiles_out and rays_out are HOST arrays of n_sensors entries (may be NULL). */
+splat_status splat_frame_layout(int32_t n_sensors, const splat_sensor *sensors, int64_t *total_tiles,
+                                int64_t *tiles_out, int64_t *rays_out);
+
+/* Bytes of device workspace splat_bin_sort needs for n Gaussians, the given sensors and
+ * an intersection capacity. */
+splat_status splat_workspace_size(int64_t n, int32_t n_sensors, const splat_sensor *sensors, int64_t capacity,
+                                  size_t *bytes);
+
+/* Projection of every Gaussian into every sensor (Sec. 3.2 "Projection, tiling, and
+ * sorting", Eq. pixel velocity, App. D; Sec. 3.3 Eq. spherical projection, J^S, v^S,
+ * App. A.1 tile ranges).  Writes proj.rec (visible Gaussians only), proj.rect and
+ * proj.n_tiles for all n_sensors x n pairs. */
+splat_status splat_project(const splat_gaussians *g, int32_t n_sensors, const splat_sensor *sensors,
+                           splat_projected proj, void *stream);
+
+/* Tile duplication and sort (Sec. 3.2 tiling and depth sort; Sec. 3.3 range sort;
+ * App. A.1 wrapped identifiers).  Emits every (tile, Gaussian) pair of the frame,
+ * orders them by (tile, depth, Gaussian index) with an on-device stable radix sort and
+ * writes per-tile ranges.  `workspace` is device scratch of at least
+ * splat_workspace_size() bytes.  If more than `capacity` pairs exist, *bins.n_isect
+ * holds the required count, the lists are left undefined, and the call returns
+ * SPLAT_OK (the caller checks n_isect against capacity, grows its buffers and calls
+ * again). */
+splat_status splat_bin_sort(int64_t n, int32_t n_sensors, const splat_sensor *sensors, splat_projected proj,
+                            int64_t capacity, splat_bins bins, void *workspace, size_t workspace_bytes,
+                            void *stream);
+
+/* The sort has no gradient: this twin exists for symmetry and does nothing. */
+splat_status splat_bin_sort_backward(void);
+
+/* Camera rasterization (Eq. t_pix, alpha blend, alpha, delta) of every camera sensor in
+ * the frame, one CTA per tile.  Outputs are concatenated over the frame's cameras in
+ * sensor order, each row-major H x W:
+ *   out_feat[pixels][channels]  blended features
+ *   out_T[pixels]               final transmittance
+ *   out_last[pixels]            number of list entries up to and including the last
+ *                               Gaussian blended into the pixel (for the backward pass);
+ *                               out_T and out_last may be NULL. */
+splat_status splat_render_camera(const splat_gaussians *g, int32_t n_sensors, const splat_sensor *sensors,
+                                 splat_projected proj, splat_bins bins, float *out_feat, float *out_T,
+                                 int32_t *out_last, void *stream);
+
+/* Lidar rasterization (Sec. 3.3: blended features, expected range of the rolling-
+ * shutter ranges r + v_r t, median range = rolling-shutter range of the first Gaussian
+ * after which the transmittance is below 0.5, 0 if none).  Outputs are concatenated
+ * over the frame's lidars in sensor order, each [n_beams][n_az]:
+ *   out_feat[rays][channels], out_range_exp[rays], out_range_med[rays],
+ *   out_alpha[rays] (= 1 - T), out_T[rays], out_last[rays] (as for cameras);
+ *   out_range_med, out_T and out_last may be NULL. */
+splat_status splat_render_lidar(const splat_gaussians *g, int32_t n_sensors, const splat_sensor *sensors,
+                                splat_projected proj, splat_bins bins, float *out_feat, float *out_range_exp,
+                                float *out_range_med, float *out_alpha, float *out_T, int32_t *out_last,
+                                void *stream);
+
+/* Backward of splat_render_camera.  Inputs: the forward's out_T and out_last (or both
+ * NULL: the kernel then recomputes them per tile), dL_dfeat[pixels][channels] and
+ * dL_dT[pixels] (may be NULL).  Accumulates into
+ *   grad_proj[n_sensors][3][n][4]: gradients of proj.rec (same layout), and
+ *   dL_dfeatures[n][channels]. */
+splat_status splat_render_camera_backward(const splat_gaussians *g, int32_t n_sensors, const splat_sensor *sensors,
+                                          splat_projected proj, splat_bins bins, const float *out_T,
+                                          const int32_t *out_last, const float *dL_dfeat, const float *dL_dT,
+                                          float *grad_proj, float *dL_dfeatures, void *stream);
+
+/* Backward of splat_render_lidar for dL_dfeat[rays][channels], dL_drange_exp[rays] and
+ * dL_dalpha[rays] (the latter two may be NULL).  The median range has no gradient.
+ * out_T/out_last as for cameras (both NULL: recomputed).  Accumulates like the camera
+ * twin. */
+splat_status splat_render_lidar_backward(const splat_gaussians *g, int32_t n_sensors, const splat_sensor *sensors,
+                                         splat_projected proj, splat_bins bins, const float *out_T,
+                                         const int32_t *out_last, const float *dL_dfeat,
+                                         const float *dL_drange_exp, const float *dL_dalpha, float *grad_proj,
+                                         float *dL_dfeatures, void *stream);
+
+/* Chain rule from grad_proj to the Gaussian parameters, summed over sensors (one thread
+ * per Gaussian, no atomics).  Accumulates into dL_dmeans[n][3], dL_dscales[n][3],
+ * dL_dquats[n][4], dL_dopacities[n], dL_dvelocities[n][3] (may be NULL).  Gradients
+ * are with respect to the ACTIVATED scales and opacities and the unnormalised
+ * quaternion. */
+splat_status splat_project_backward(const splat_gaussians *g, int32_t n_sensors, const splat_sensor *sensors,
+                                    splat_projected proj, const float *grad_proj, float *dL_dmeans,
+                                    float *dL_dscales, float *dL_dquats, float *dL_dopacities,
+                                    float *dL_dvelocities, void *stream);
+
+/* L1 term of the training loss (Eq. loss_fn, lambda_r L1): adds scale * sum |pred - target|
+ * over `count` floats to *loss (device float, accumulated) and, if grad is not NULL,
+ * writes grad[i] = scale * sign(pred[i] - target[i]).  loss may be NULL. */
+splat_status splat_l1_loss(const float *pred, const float *target, int64_t count, float scale, float *grad,
+                           float *loss, void *stream);
+
+/* Message of the last non-OK status on this host thread ("" if none). */
+const char *splat_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SPLAT_H */

@@ -1,0 +1,108 @@
+"""ctypes binding of libsplat's C ABI (include/splat.h): the same entry points and
+structs, argument marshalling only.  Every computation runs in the library's CUDA
+kernels; if the library cannot be loaded this module raises instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+c_int32, c_int64, c_float, c_void_p, c_size_t = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p, ctypes.c_size_t
+
+SPLAT_OK = 0
+SPLAT_ERR_INVALID_ARG = 1
+SPLAT_ERR_CAPACITY = 2
+SPLAT_ERR_CUDA = 3
+SPLAT_ERR_TIMEOUT = 4
+SPLAT_SENSOR_CAMERA = 0
+SPLAT_SENSOR_LIDAR = 1
+SPLAT_MAX_SENSORS = 16
+
+EXPORTS = [
+    "splat_frame_layout", "splat_workspace_size", "splat_project", "splat_bin_sort", "splat_bin_sort_backward",
+    "splat_render_camera", "splat_render_lidar", "splat_render_camera_backward", "splat_render_lidar_backward",
+    "splat_project_backward", "splat_l1_loss", "splat_last_error",
+]
+
+
+class splat_gaussians(ctypes.Structure):
+    _fields_ = [("means", c_void_p), ("scales", c_void_p), ("quats", c_void_p), ("opacities", c_void_p),
+                ("features", c_void_p), ("velocities", c_void_p), ("n", c_int64), ("channels", c_int32),
+                ("reserved", c_int32)]
+
+
+class splat_sensor(ctypes.Structure):
+    _fields_ = [("kind", c_int32), ("reserved0", c_int32), ("R", c_float * 9), ("t", c_float * 3),
+                ("lin_vel", c_float * 3), ("ang_vel", c_float * 3), ("width", c_int32), ("height", c_int32),
+                ("fx", c_float), ("fy", c_float), ("cx", c_float), ("cy", c_float), ("rs_time", c_float),
+                ("time_offset", c_float), ("eps2d", c_float), ("near_plane", c_float), ("n_beams", c_int32),
+                ("n_az", c_int32), ("beam_elev", c_void_p), ("rays", c_void_p), ("az_res", c_float),
+                ("sweep_time", c_float), ("r_min", c_float), ("tile_w", c_int32), ("tile_h", c_int32),
+                ("reserved1", c_int32)]
+
+
+class splat_projected(ctypes.Structure):
+    _fields_ = [("rec", c_void_p), ("rect", c_void_p), ("n_tiles", c_void_p)]
+
+
+class splat_bins(ctypes.Structure):
+    _fields_ = [("isect_ids", c_void_p), ("tile_ranges", c_void_p), ("n_isect", c_void_p)]
+
+
+_lib = None
+
+
+class SplatError(RuntimeError):
+    pass
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libsplat.so (building it in-tree if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise SplatError(f"libsplat.so not found at {path}; run paper_2411_16816_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    P, S = ctypes.POINTER, c_int32
+    G, SE = P(splat_gaussians), P(splat_sensor)
+    L.splat_frame_layout.argtypes = [c_int32, SE, P(c_int64), P(c_int64), P(c_int64)]
+    L.splat_workspace_size.argtypes = [c_int64, c_int32, SE, c_int64, P(c_size_t)]
+    L.splat_project.argtypes = [G, c_int32, SE, splat_projected, c_void_p]
+    L.splat_bin_sort.argtypes = [c_int64, c_int32, SE, splat_projected, c_int64, splat_bins, c_void_p, c_size_t,
+                                 c_void_p]
+    L.splat_bin_sort_backward.argtypes = []
+    L.splat_render_camera.argtypes = [G, c_int32, SE, splat_projected, splat_bins, c_void_p, c_void_p, c_void_p,
+                                      c_void_p]
+    L.splat_render_lidar.argtypes = [G, c_int32, SE, splat_projected, splat_bins] + [c_void_p] * 7
+    L.splat_render_camera_backward.argtypes = [G, c_int32, SE, splat_projected, splat_bins] + [c_void_p] * 7
+    L.splat_render_lidar_backward.argtypes = [G, c_int32, SE, splat_projected, splat_bins] + [c_void_p] * 8
+    L.splat_project_backward.argtypes = [G, c_int32, SE, splat_projected] + [c_void_p] * 7
+    L.splat_l1_loss.argtypes = [c_void_p, c_void_p, c_int64, c_float, c_void_p, c_void_p, c_void_p]
+    L.splat_last_error.argtypes = []
+    L.splat_last_error.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name != "splat_last_error":
+            getattr(L, name).restype = S
+    _lib = L
+    return L
+
+
+def check(status: int, what: str = "") -> None:
+    if status != SPLAT_OK:
+        msg = load().splat_last_error().decode()
+        raise SplatError(f"{what} failed with status {status}: {msg}")
+
+
+def call(name: str, *args) -> None:
+    """Call a libsplat entry point and raise on a non-OK status."""
+    check(getattr(load(), name)(*args), name)

@@ -1,0 +1,349 @@
+// api.cu -- the extern "C" entry points of libsplat (declared in include/splat.h):
+// argument checks on the host, the per-frame sensor table, and kernel launches.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "types.cuh"
+
+using namespace splat;
+
+static thread_local std::string g_err;
+
+static splat_status fail(splat_status code, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+static splat_status fail(splat_status code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+static splat_status check_launch(const char* what) {
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(SPLAT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+    g_err.clear();
+    return SPLAT_OK;
+}
+
+static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Per-sensor constants and the frame's tile / block / ray numbering.
+static splat_status build_frame(int32_t n_sensors, const splat_sensor* sensors, Frame& fr, int64_t* total_tiles) {
+    if (n_sensors < 1 || n_sensors > kMaxSensors)
+        return fail(SPLAT_ERR_INVALID_ARG, "n_sensors must be in [1, %d], got %d", kMaxSensors, n_sensors);
+    if (!sensors) return fail(SPLAT_ERR_INVALID_ARG, "sensors is NULL");
+    memset(&fr, 0, sizeof fr);
+    fr.n_sensors = n_sensors;
+    int64_t tile_base = 0, cam_blocks = 0, lid_blocks = 0, cam_rays = 0, lid_rays = 0;
+    for (int s = 0; s < n_sensors; s++) {
+        const splat_sensor& in = sensors[s];
+        SensorDev& d = fr.s[s];
+        d.kind = in.kind;
+        memcpy(d.R, in.R, sizeof d.R);
+        memcpy(d.t, in.t, sizeof d.t);
+        memcpy(d.v, in.lin_vel, sizeof d.v);
+        memcpy(d.w, in.ang_vel, sizeof d.w);
+        d.tile_w = in.tile_w;
+        d.tile_h = in.tile_h;
+        d.eps = in.eps2d;
+        if (!(in.eps2d >= 0.f)) return fail(SPLAT_ERR_INVALID_ARG, "sensor %d: eps2d must be >= 0", s);
+        const bool lidar = in.kind == SPLAT_SENSOR_LIDAR;
+        if (in.kind != SPLAT_SENSOR_CAMERA && !lidar) return fail(SPLAT_ERR_INVALID_ARG, "sensor %d: bad kind", s);
+        if (!raster_shape_supported(lidar, in.tile_w, in.tile_h))
+            return fail(SPLAT_ERR_INVALID_ARG, "sensor %d: unsupported tile %dx%d", s, in.tile_w, in.tile_h);
+        int64_t rays;
+        if (!lidar) {
+            if (in.width < 1 || in.height < 1 || !(in.fx > 0.f) || !(in.fy > 0.f))
+                return fail(SPLAT_ERR_INVALID_ARG, "camera %d: bad size or focal length", s);
+            d.width = in.width;
+            d.height = in.height;
+            d.fx = in.fx;
+            d.fy = in.fy;
+            d.cx = in.cx;
+            d.cy = in.cy;
+            d.rs = in.rs_time;
+            d.dt = in.time_offset;
+            d.near_plane = in.near_plane;
+            d.lim_x = 1.3f * 0.5f * (float)in.width / in.fx;
+            d.lim_y = 1.3f * 0.5f * (float)in.height / in.fy;
+            d.tiles_x = (in.width + in.tile_w - 1) / in.tile_w;
+            d.tiles_y = (in.height + in.tile_h - 1) / in.tile_h;
+            rays = (int64_t)in.width * in.height;
+        } else {
+            if (in.n_beams < 2 || in.n_az < 1 || !in.beam_elev || !(in.az_res > 0.f))
+                return fail(SPLAT_ERR_INVALID_ARG, "lidar %d: bad beams/azimuth/elevations", s);
+            if (in.n_beams % in.tile_h != 0)
+                return fail(SPLAT_ERR_INVALID_ARG, "lidar %d: n_beams %d not a multiple of tile_h %d", s, in.n_beams,
+                            in.tile_h);
+            if (std::fabs((double)in.n_az * in.az_res - 2.0 * M_PI) > 1e-3)
+                return fail(SPLAT_ERR_INVALID_ARG, "lidar %d: n_az * az_res must cover 2 pi", s);
+            d.nb = in.n_beams;
+            d.naz = in.n_az;
+            d.elev = in.beam_elev;
+            d.rays = in.rays;
+            d.az_res = in.az_res;
+            d.sweep = in.sweep_time;
+            d.rmin = in.r_min;
+            d.tiles_x = (in.n_az + in.tile_w - 1) / in.tile_w;
+            d.tiles_y = in.n_beams / in.tile_h;
+            d.wphi = (float)in.tile_w * in.az_res;
+            d.phimax = (float)d.tiles_x * d.wphi;
+            rays = (int64_t)in.n_beams * in.n_az;
+        }
+        const int64_t tiles = (int64_t)d.tiles_x * d.tiles_y;
+        d.tile_base = (int)tile_base;
+        tile_base += tiles;
+        if (!lidar) {
+            d.block_base = (int)cam_blocks;
+            d.ray_base = (int)cam_rays;
+            cam_blocks += tiles;
+            cam_rays += rays;
+            fr.cam_sensors[fr.n_cams++] = s;
+        } else {
+            d.block_base = (int)lid_blocks;
+            d.ray_base = (int)lid_rays;
+            lid_blocks += tiles;
+            lid_rays += rays;
+            fr.lid_sensors[fr.n_lids++] = s;
+        }
+        if (tile_base > (int64_t)1 << 30 || cam_rays > (int64_t)1 << 31 || lid_rays > (int64_t)1 << 31)
+            return fail(SPLAT_ERR_INVALID_ARG, "frame too large");
+    }
+    fr.n_cam_blocks = (int)cam_blocks;
+    fr.n_lid_blocks = (int)lid_blocks;
+    if (total_tiles) *total_tiles = tile_base;
+    return SPLAT_OK;
+}
+
+static splat_status check_gaussians(const splat_gaussians* g, bool need_features) {
+    if (!g) return fail(SPLAT_ERR_INVALID_ARG, "gaussians is NULL");
+    if (g->n < 0) return fail(SPLAT_ERR_INVALID_ARG, "n < 0");
+    if (g->n > 0 && (!g->means || !g->scales || !g->quats || !g->opacities))
+        return fail(SPLAT_ERR_INVALID_ARG, "gaussian parameter pointer is NULL");
+    if (g->n > 0 && !aligned16(g->quats)) return fail(SPLAT_ERR_INVALID_ARG, "quats must be 16-byte aligned");
+    if (need_features) {
+        if (!raster_channels_supported(g->channels))
+            return fail(SPLAT_ERR_INVALID_ARG, "channels must be in [1, 32], got %d", g->channels);
+        if (g->n > 0 && !g->features) return fail(SPLAT_ERR_INVALID_ARG, "features is NULL");
+        if ((g->channels & 3) == 0 && !aligned16(g->features))
+            return fail(SPLAT_ERR_INVALID_ARG, "features must be 16-byte aligned");
+    }
+    return SPLAT_OK;
+}
+
+static splat_status check_proj(const splat_projected& p) {
+    if (!p.rec || !p.rect || !p.n_tiles) return fail(SPLAT_ERR_INVALID_ARG, "projected buffer is NULL");
+    if (!aligned16(p.rec) || ((uintptr_t)p.rect & 7u)) return fail(SPLAT_ERR_INVALID_ARG, "projected misaligned");
+    return SPLAT_OK;
+}
+
+static GaussIn gauss_in(const splat_gaussians* g) {
+    return GaussIn{g->means, g->scales, g->quats, g->opacities, g->velocities, g->n};
+}
+
+extern "C" {
+
+splat_status splat_frame_layout(int32_t n_sensors, const splat_sensor* sensors, int64_t* total_tiles,
+                                int64_t* tiles_out, int64_t* rays_out) {
+    Frame fr;
+    const splat_status st = build_frame(n_sensors, sensors, fr, total_tiles);
+    if (st != SPLAT_OK) return st;
+    for (int s = 0; s < n_sensors; s++) {
+        const SensorDev& d = fr.s[s];
+        if (tiles_out) tiles_out[s] = (int64_t)d.tiles_x * d.tiles_y;
+        if (rays_out) rays_out[s] = d.kind == SPLAT_SENSOR_CAMERA ? (int64_t)d.width * d.height : (int64_t)d.nb * d.naz;
+    }
+    return SPLAT_OK;
+}
+
+splat_status splat_workspace_size(int64_t n, int32_t n_sensors, const splat_sensor* sensors, int64_t capacity,
+                                  size_t* bytes) {
+    Frame fr;
+    const splat_status st = build_frame(n_sensors, sensors, fr, nullptr);
+    if (st != SPLAT_OK) return st;
+    if (!bytes || n < 0 || capacity < 0) return fail(SPLAT_ERR_INVALID_ARG, "bad workspace query");
+    *bytes = carve_workspace(nullptr, (int64_t)n_sensors * n, capacity).bytes;
+    return SPLAT_OK;
+}
+
+splat_status splat_project(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
+                           splat_projected proj, void* stream) {
+    splat_status st = check_gaussians(g, false);
+    if (st != SPLAT_OK) return st;
+    Frame fr;
+    if ((st = build_frame(n_sensors, sensors, fr, nullptr)) != SPLAT_OK) return st;
+    if ((st = check_proj(proj)) != SPLAT_OK) return st;
+    if ((int64_t)n_sensors * g->n >= ((int64_t)1 << 32))
+        return fail(SPLAT_ERR_INVALID_ARG, "n_sensors * n must be below 2^32");
+    launch_project(gauss_in(g), fr, ProjOut{(float4*)proj.rec, (short4*)proj.rect, proj.n_tiles},
+                   (cudaStream_t)stream);
+    return check_launch("splat_project");
+}
+
+splat_status splat_bin_sort(int64_t n, int32_t n_sensors, const splat_sensor* sensors, splat_projected proj,
+                            int64_t capacity, splat_bins bins, void* workspace, size_t workspace_bytes,
+                            void* stream) {
+    Frame fr;
+    int64_t total_tiles = 0;
+    splat_status st = build_frame(n_sensors, sensors, fr, &total_tiles);
+    if (st != SPLAT_OK) return st;
+    if ((st = check_proj(proj)) != SPLAT_OK) return st;
+    if (n < 0 || capacity < 0 || capacity >= ((int64_t)1 << 31))
+        return fail(SPLAT_ERR_INVALID_ARG, "capacity must be in [0, 2^31)");
+    if ((int64_t)n_sensors * n >= ((int64_t)1 << 32))
+        return fail(SPLAT_ERR_INVALID_ARG, "n_sensors * n must be below 2^32");
+    if (!bins.isect_ids || !bins.tile_ranges || !bins.n_isect || !workspace)
+        return fail(SPLAT_ERR_INVALID_ARG, "bins or workspace pointer is NULL");
+    if (((uintptr_t)bins.tile_ranges & 7u) || ((uintptr_t)bins.n_isect & 7u) || ((uintptr_t)workspace & 255u))
+        return fail(SPLAT_ERR_INVALID_ARG, "bins or workspace misaligned");
+    const size_t need = carve_workspace(nullptr, (int64_t)n_sensors * n, capacity).bytes;
+    if (workspace_bytes < need)
+        return fail(SPLAT_ERR_INVALID_ARG, "workspace too small: %zu < %zu bytes", workspace_bytes, need);
+    launch_bin_sort(fr, n, (const float4*)proj.rec, (const short4*)proj.rect, proj.n_tiles, capacity, bins.isect_ids,
+                    (int2*)bins.tile_ranges, total_tiles, bins.n_isect, workspace, (cudaStream_t)stream);
+    return check_launch("splat_bin_sort");
+}
+
+splat_status splat_bin_sort_backward(void) { return SPLAT_OK; }
+
+static splat_status render_common(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
+                                  splat_projected proj, splat_bins bins, Frame& fr, bool lidar, int& tw, int& th) {
+    splat_status st = check_gaussians(g, true);
+    if (st != SPLAT_OK) return st;
+    if ((st = build_frame(n_sensors, sensors, fr, nullptr)) != SPLAT_OK) return st;
+    if ((st = check_proj(proj)) != SPLAT_OK) return st;
+    if (!bins.isect_ids || !bins.tile_ranges) return fail(SPLAT_ERR_INVALID_ARG, "bins pointer is NULL");
+    tw = th = 0;
+    const int nk = lidar ? fr.n_lids : fr.n_cams;
+    const int* list = lidar ? fr.lid_sensors : fr.cam_sensors;
+    for (int k = 0; k < nk; k++) {
+        const SensorDev& d = fr.s[list[k]];
+        if (k == 0) {
+            tw = d.tile_w;
+            th = d.tile_h;
+        } else if (d.tile_w != tw || d.tile_h != th) {
+            return fail(SPLAT_ERR_INVALID_ARG, "all %s sensors of a frame must share one tile shape",
+                        lidar ? "lidar" : "camera");
+        }
+    }
+    return SPLAT_OK;
+}
+
+splat_status splat_render_camera(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
+                                 splat_projected proj, splat_bins bins, float* out_feat, float* out_T,
+                                 int32_t* out_last, void* stream) {
+    Frame fr;
+    int tw, th;
+    splat_status st = render_common(g, n_sensors, sensors, proj, bins, fr, false, tw, th);
+    if (st != SPLAT_OK) return st;
+    if (fr.n_cams == 0) return SPLAT_OK;
+    if (!out_feat) return fail(SPLAT_ERR_INVALID_ARG, "out_feat is NULL");
+    if ((g->channels & 3) == 0 && !aligned16(out_feat)) return fail(SPLAT_ERR_INVALID_ARG, "out_feat misaligned");
+    RasterIn in{(const float4*)proj.rec, bins.isect_ids, (const int2*)bins.tile_ranges, g->features, g->n,
+                g->channels};
+    RasterOut out{out_feat, out_T, out_last, nullptr, nullptr, nullptr};
+    if (!launch_raster_fwd(false, g->channels, tw, th, fr, fr.n_cam_blocks, in, out, (cudaStream_t)stream))
+        return fail(SPLAT_ERR_INVALID_ARG, "unsupported camera configuration");
+    return check_launch("splat_render_camera");
+}
+
+splat_status splat_render_lidar(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
+                                splat_projected proj, splat_bins bins, float* out_feat, float* out_range_exp,
+                                float* out_range_med, float* out_alpha, float* out_T, int32_t* out_last,
+                                void* stream) {
+    Frame fr;
+    int tw, th;
+    splat_status st = render_common(g, n_sensors, sensors, proj, bins, fr, true, tw, th);
+    if (st != SPLAT_OK) return st;
+    if (fr.n_lids == 0) return SPLAT_OK;
+    if (!out_feat || !out_range_exp || !out_alpha)
+        return fail(SPLAT_ERR_INVALID_ARG, "out_feat, out_range_exp and out_alpha are required");
+    if ((g->channels & 3) == 0 && !aligned16(out_feat)) return fail(SPLAT_ERR_INVALID_ARG, "out_feat misaligned");
+    RasterIn in{(const float4*)proj.rec, bins.isect_ids, (const int2*)bins.tile_ranges, g->features, g->n,
+                g->channels};
+    RasterOut out{out_feat, out_T, out_last, out_range_exp, out_range_med, out_alpha};
+    if (!launch_raster_fwd(true, g->channels, tw, th, fr, fr.n_lid_blocks, in, out, (cudaStream_t)stream))
+        return fail(SPLAT_ERR_INVALID_ARG, "unsupported lidar configuration");
+    return check_launch("splat_render_lidar");
+}
+
+splat_status splat_render_camera_backward(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
+                                          splat_projected proj, splat_bins bins, const float* out_T,
+                                          const int32_t* out_last, const float* dL_dfeat, const float* dL_dT,
+                                          float* grad_proj, float* dL_dfeatures, void* stream) {
+    Frame fr;
+    int tw, th;
+    splat_status st = render_common(g, n_sensors, sensors, proj, bins, fr, false, tw, th);
+    if (st != SPLAT_OK) return st;
+    if (fr.n_cams == 0) return SPLAT_OK;
+    if (!dL_dfeat || !grad_proj || !dL_dfeatures) return fail(SPLAT_ERR_INVALID_ARG, "gradient pointer is NULL");
+    if ((out_T == nullptr) != (out_last == nullptr))
+        return fail(SPLAT_ERR_INVALID_ARG, "out_T and out_last must both be given or both be NULL");
+    if (!aligned16(grad_proj) || ((g->channels & 3) == 0 && !aligned16(dL_dfeatures)))
+        return fail(SPLAT_ERR_INVALID_ARG, "gradient buffers misaligned");
+    RasterIn in{(const float4*)proj.rec, bins.isect_ids, (const int2*)bins.tile_ranges, g->features, g->n,
+                g->channels};
+    RasterGrad gr{out_T, out_last, dL_dfeat, dL_dT, nullptr, nullptr, (float4*)grad_proj, dL_dfeatures};
+    if (!launch_raster_bwd(false, g->channels, tw, th, fr, fr.n_cam_blocks, in, gr, out_T == nullptr,
+                           (cudaStream_t)stream))
+        return fail(SPLAT_ERR_INVALID_ARG, "unsupported camera configuration");
+    return check_launch("splat_render_camera_backward");
+}
+
+splat_status splat_render_lidar_backward(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
+                                         splat_projected proj, splat_bins bins, const float* out_T,
+                                         const int32_t* out_last, const float* dL_dfeat,
+                                         const float* dL_drange_exp, const float* dL_dalpha, float* grad_proj,
+                                         float* dL_dfeatures, void* stream) {
+    Frame fr;
+    int tw, th;
+    splat_status st = render_common(g, n_sensors, sensors, proj, bins, fr, true, tw, th);
+    if (st != SPLAT_OK) return st;
+    if (fr.n_lids == 0) return SPLAT_OK;
+    if (!dL_dfeat || !grad_proj || !dL_dfeatures) return fail(SPLAT_ERR_INVALID_ARG, "gradient pointer is NULL");
+    if ((out_T == nullptr) != (out_last == nullptr))
+        return fail(SPLAT_ERR_INVALID_ARG, "out_T and out_last must both be given or both be NULL");
+    if (!aligned16(grad_proj) || ((g->channels & 3) == 0 && !aligned16(dL_dfeatures)))
+        return fail(SPLAT_ERR_INVALID_ARG, "gradient buffers misaligned");
+    RasterIn in{(const float4*)proj.rec, bins.isect_ids, (const int2*)bins.tile_ranges, g->features, g->n,
+                g->channels};
+    RasterGrad gr{out_T, out_last, dL_dfeat, nullptr, dL_drange_exp, dL_dalpha, (float4*)grad_proj, dL_dfeatures};
+    if (!launch_raster_bwd(true, g->channels, tw, th, fr, fr.n_lid_blocks, in, gr, out_T == nullptr,
+                           (cudaStream_t)stream))
+        return fail(SPLAT_ERR_INVALID_ARG, "unsupported lidar configuration");
+    return check_launch("splat_render_lidar_backward");
+}
+
+splat_status splat_project_backward(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
+                                    splat_projected proj, const float* grad_proj, float* dL_dmeans,
+                                    float* dL_dscales, float* dL_dquats, float* dL_dopacities,
+                                    float* dL_dvelocities, void* stream) {
+    splat_status st = check_gaussians(g, false);
+    if (st != SPLAT_OK) return st;
+    Frame fr;
+    if ((st = build_frame(n_sensors, sensors, fr, nullptr)) != SPLAT_OK) return st;
+    if ((st = check_proj(proj)) != SPLAT_OK) return st;
+    if (!grad_proj || !dL_dmeans || !dL_dscales || !dL_dquats || !dL_dopacities)
+        return fail(SPLAT_ERR_INVALID_ARG, "gradient pointer is NULL");
+    if (!aligned16(grad_proj)) return fail(SPLAT_ERR_INVALID_ARG, "grad_proj misaligned");
+    launch_project_backward(gauss_in(g), fr, proj.n_tiles, (const float4*)grad_proj,
+                            GradOut{dL_dmeans, dL_dscales, dL_dquats, dL_dopacities, dL_dvelocities},
+                            (cudaStream_t)stream);
+    return check_launch("splat_project_backward");
+}
+
+splat_status splat_l1_loss(const float* pred, const float* target, int64_t count, float scale, float* grad,
+                           float* loss, void* stream) {
+    if (count < 0 || (count > 0 && (!pred || !target))) return fail(SPLAT_ERR_INVALID_ARG, "bad L1 arguments");
+    launch_l1(pred, target, count, scale, grad, loss, (cudaStream_t)stream);
+    return check_launch("splat_l1_loss");
+}
+
+const char* splat_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

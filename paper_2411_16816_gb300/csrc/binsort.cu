@@ -1,0 +1,397 @@
+// binsort.cu -- tile duplication and sorting (paper Sec. 3.2 "Projection, tiling, and
+// sorting": Gaussians are duplicated into every tile they intersect and sorted by
+// depth; Sec. 3.3 / App. A.1: lidar Gaussians sorted by range, azimuth tile ids wrapped
+// into [0, M_phi) before the identifier is formed).
+//
+// Order of the lists: (global tile, depth, Gaussian index).  It is produced in two
+// stable stages instead of one 48-bit key sort:
+//   1. compact the visible (sensor, Gaussian) pairs and radix-sort them by the FP32 bit
+//      pattern of their depth (32-bit key, stable, so equal depths keep index order);
+//   2. emit every pair's tiles in that depth order and stable radix-sort the
+//      intersections by tile id only (16 bits for a 6-camera + lidar frame).
+// Stage 2 touches each intersection in ceil(bits(tiles)/8) passes instead of six.
+//
+// Every device-wide step is reduce -> scan -> apply with no inter-block waiting, so
+// nothing in this file can spin.  Counts that only the device knows (visible pairs,
+// intersections) are read by the kernels from device memory; grids are sized from host
+// upper bounds and surplus blocks do no work.
+#include "types.cuh"
+
+namespace splat {
+
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;  // 2048
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096
+
+__device__ __forceinline__ int64_t eff_count(const int64_t* count_ptr, int64_t max_count, int64_t capacity) {
+    if (!count_ptr) return max_count;
+    const int64_t c = *count_ptr;
+    if (c > capacity) return 0;  // over capacity: the lists are invalid, touch nothing
+    return c < max_count ? c : max_count;
+}
+
+// Exclusive scan of one value per thread across a 256-thread block.
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t* total, int64_t* sm /*[9]*/) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) sm[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t run = 0;
+        for (int w = 0; w < kScanThreads / 32; w++) {
+            const int64_t t = sm[w];
+            sm[w] = run;
+            run += t;
+        }
+        sm[8] = run;
+    }
+    __syncthreads();
+    const int64_t res = x - v + sm[warp];
+    if (total) *total = sm[8];
+    __syncthreads();
+    return res;
+}
+
+template <typename In>
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(In in, int64_t max_count, const int64_t* count_ptr,
+                                                              int64_t capacity, int64_t* partials) {
+    __shared__ int64_t sm[9];
+    const int64_t count = eff_count(count_ptr, max_count, capacity);
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++)
+        if (base + k < count) s += in(base + k);
+    int64_t total;
+    block_exclusive_scan(s, &total, sm);
+    if (threadIdx.x == 0) partials[blockIdx.x] = total;
+}
+
+// Single block: exclusive scan of the block partials in place; writes the grand total.
+__global__ void __launch_bounds__(1024) k_scan_top(int64_t* partials, int64_t nparts, int64_t* total) {
+    __shared__ int64_t sm[33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t carry = 0;
+    for (int64_t base = 0; base < nparts; base += 1024) {
+        const int64_t idx = base + threadIdx.x;
+        const int64_t v = idx < nparts ? partials[idx] : 0;
+        int64_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) sm[warp] = x;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int64_t run = 0;
+            for (int w = 0; w < 32; w++) {
+                const int64_t t = sm[w];
+                sm[w] = run;
+                run += t;
+            }
+            sm[32] = run;
+        }
+        __syncthreads();
+        if (idx < nparts) partials[idx] = carry + x - v + sm[warp];
+        carry += sm[32];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
+template <typename In, typename Out>
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(In in, Out out, int64_t max_count,
+                                                             const int64_t* count_ptr, int64_t capacity,
+                                                             const int64_t* partials) {
+    __shared__ int64_t sm[9];
+    const int64_t count = eff_count(count_ptr, max_count, capacity);
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int64_t v[kScanItems];
+    int64_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        v[k] = base + k < count ? in(base + k) : 0;
+        s += v[k];
+    }
+    int64_t run = block_exclusive_scan(s, nullptr, sm) + partials[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        if (base + k < count) out(base + k, run, v[k]);
+        run += v[k];
+    }
+}
+
+template <typename In, typename Out>
+void device_scan(In in, Out out, int64_t max_count, const int64_t* count_ptr, int64_t capacity, int64_t* partials,
+                 int64_t* total, cudaStream_t st) {
+    const int64_t nblocks = (max_count + kScanTile - 1) / kScanTile;
+    if (nblocks == 0) {
+        if (total) cudaMemsetAsync(total, 0, sizeof(int64_t), st);
+        return;
+    }
+    k_scan_reduce<<<(unsigned)nblocks, kScanThreads, 0, st>>>(in, max_count, count_ptr, capacity, partials);
+    k_scan_top<<<1, 1024, 0, st>>>(partials, nblocks, total);
+    k_scan_apply<<<(unsigned)nblocks, kScanThreads, 0, st>>>(in, out, max_count, count_ptr, capacity, partials);
+}
+
+// ---------------------------------------------------------------------------------
+// Stable LSD radix sort pass (8-bit digit) of (key, value) pairs.
+// ---------------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ keys,
+                                                             const int64_t* count_ptr, int64_t max_count,
+                                                             int64_t capacity, int shift, uint32_t* hist,
+                                                             int64_t nblocks) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t count = eff_count(count_ptr, max_count, capacity);
+    const int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll 4
+    for (int k = 0; k < kSortItems; k++) {
+        const int64_t idx = base + k * kSortThreads + threadIdx.x;
+        if (idx < count) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+struct HistIn {
+    const uint32_t* h;
+    __device__ int64_t operator()(int64_t i) const { return h[i]; }
+};
+struct HistOut {
+    uint32_t* h;
+    __device__ void operator()(int64_t i, int64_t prefix, int64_t) const { h[i] = (uint32_t)prefix; }
+};
+
+// Each warp ranks 512 consecutive keys in order (32 at a time, __match_any_sync groups
+// equal digits); warps' digit counts are then scanned in warp order, so the block's
+// ranking -- and with the digit-major global scan, the whole pass -- is stable.
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* __restrict__ kin,
+                                                                const uint32_t* __restrict__ vin,
+                                                                uint32_t* __restrict__ kout,
+                                                                uint32_t* __restrict__ vout,
+                                                                const int64_t* count_ptr, int64_t max_count,
+                                                                int64_t capacity, int shift,
+                                                                const uint32_t* __restrict__ hist_scan,
+                                                                int64_t nblocks) {
+    constexpr int kWarps = kSortThreads / 32;
+    __shared__ uint32_t wh[kWarps][256];
+    __shared__ uint32_t bd[256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = threadIdx.x; k < kWarps * 256; k += kSortThreads) (&wh[0][0])[k] = 0;
+    const int64_t count = eff_count(count_ptr, max_count, capacity);
+    const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * (kSortItems * 32);
+    if (base - (int64_t)warp * (kSortItems * 32) >= count) return;  // whole block empty (uniform)
+    __syncthreads();
+    uint32_t kk[kSortItems], vv[kSortItems], rr[kSortItems];
+#pragma unroll
+    for (int it = 0; it < kSortItems; it++) {
+        const int64_t idx = base + it * 32 + lane;
+        const bool valid = idx < count;
+        kk[it] = valid ? kin[idx] : 0u;
+        vv[it] = valid ? vin[idx] : 0u;
+        const uint32_t d = valid ? ((kk[it] >> shift) & 255u) : 256u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t cnt = valid ? wh[warp][d] : 0u;
+        rr[it] = cnt + __popc(peers & ((1u << lane) - 1u));
+        __syncwarp();
+        if (valid && lane == 31 - __clz(peers)) wh[warp][d] = cnt + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        const int d = threadIdx.x;  // 256 threads, one per digit
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; w++) {
+            const uint32_t c = wh[w][d];
+            wh[w][d] = run;
+            run += c;
+        }
+        bd[d] = hist_scan[(int64_t)d * nblocks + blockIdx.x];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kSortItems; it++) {
+        const int64_t idx = base + it * 32 + lane;
+        if (idx < count) {
+            const uint32_t d = (kk[it] >> shift) & 255u;
+            const uint32_t pos = bd[d] + wh[warp][d] + rr[it];
+            kout[pos] = kk[it];
+            vout[pos] = vv[it];
+        }
+    }
+}
+
+// Sorts by bits [0, 8*passes) of the keys.  Buffers ping-pong: pass p reads buffer
+// p % 2 and writes buffer (p + 1) % 2; the result is in buffer passes % 2.
+void radix_sort(uint32_t* keys[2], uint32_t* vals[2], int passes, int64_t max_count, const int64_t* count_ptr,
+                int64_t capacity, uint32_t* hist, int64_t* partials, cudaStream_t st) {
+    const int64_t nblocks = (max_count + kSortTile - 1) / kSortTile;
+    if (nblocks == 0) return;
+    for (int p = 0; p < passes; p++) {
+        const int a = p & 1, b = a ^ 1;
+        k_radix_hist<<<(unsigned)nblocks, kSortThreads, 0, st>>>(keys[a], count_ptr, max_count, capacity, 8 * p, hist,
+                                                                nblocks);
+        device_scan(HistIn{hist}, HistOut{hist}, 256 * nblocks, nullptr, INT64_MAX, partials, nullptr, st);
+        k_radix_scatter<<<(unsigned)nblocks, kSortThreads, 0, st>>>(keys[a], vals[a], keys[b], vals[b], count_ptr,
+                                                                   max_count, capacity, 8 * p, hist, nblocks);
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// Frame-level binning
+// ---------------------------------------------------------------------------------
+
+struct VisIn {
+    const int32_t* n_tiles;
+    __device__ int64_t operator()(int64_t p) const { return n_tiles[p] > 0 ? 1 : 0; }
+};
+struct VisOut {  // compact visible pairs with their depth bits as keys
+    const float4* rec;
+    int64_t n;
+    uint32_t* keys;
+    uint32_t* vals;
+    __device__ void operator()(int64_t p, int64_t prefix, int64_t v) const {
+        if (!v) return;
+        const int64_t s = p / n, i = p - s * n;
+        const float depth = rec[rec_index((int)s, 2, n, i)].x;
+        keys[prefix] = __float_as_uint(depth);
+        vals[prefix] = (uint32_t)p;
+    }
+};
+
+struct EmitIn {
+    const uint32_t* sorted_pairs;
+    const int32_t* n_tiles;
+    __device__ int64_t operator()(int64_t j) const { return n_tiles[sorted_pairs[j]]; }
+};
+
+struct EmitOut {
+    const uint32_t* sorted_pairs;
+    const short4* rect;
+    int64_t n;
+    int64_t capacity;
+    uint32_t* keys;
+    uint32_t* vals;
+    int tile_base[kMaxSensors];
+    int tiles_x[kMaxSensors];
+    int is_lidar[kMaxSensors];
+    __device__ void operator()(int64_t j, int64_t prefix, int64_t cnt) const {
+        const uint32_t p = sorted_pairs[j];
+        const int s = (int)(p / (uint64_t)n);
+        const uint32_t i = (uint32_t)(p - (uint64_t)s * n);
+        const short4 rc = rect[p];
+        const int tx = tiles_x[s], tb = tile_base[s];
+        const int w = rc.z - rc.x;
+        int64_t o = prefix;
+        for (int ty = rc.y; ty < rc.w; ty++) {
+            for (int k = 0; k < w; k++, o++) {
+                if (o >= capacity) return;
+                int col = rc.x + k;
+                if (is_lidar[s] && col >= tx) col -= tx;
+                keys[o] = (uint32_t)(tb + ty * tx + col);
+                vals[o] = i;
+            }
+        }
+        (void)cnt;
+    }
+};
+
+__global__ void k_tile_ranges(const uint32_t* __restrict__ keys, const int64_t* count_ptr, int64_t capacity,
+                              int2* ranges) {
+    const int64_t count = eff_count(count_ptr, capacity, capacity);
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= count) return;
+    const uint32_t t = keys[j];
+    if (j == 0 || keys[j - 1] != t) ranges[t].x = (int)j;
+    if (j == count - 1 || keys[j + 1] != t) ranges[t].y = (int)(j + 1);
+}
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Workspace carving; with base == nullptr only computes the size.
+BinWorkspace carve_workspace(void* base, int64_t pairs, int64_t capacity) {
+    BinWorkspace w{};
+    char* p = (char*)base;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void* {
+        void* r = p ? (void*)(p + off) : nullptr;
+        off += align_up(bytes);
+        return r;
+    };
+    const int64_t vp = pairs > 0 ? pairs : 1, cp = capacity > 0 ? capacity : 1;
+    w.vkeys[0] = (uint32_t*)take(4 * vp);
+    w.vkeys[1] = (uint32_t*)take(4 * vp);
+    w.vvals[0] = (uint32_t*)take(4 * vp);
+    w.vvals[1] = (uint32_t*)take(4 * vp);
+    w.vis_count = (int64_t*)take(8);
+    w.ikeys[0] = (uint32_t*)take(4 * cp);
+    w.ikeys[1] = (uint32_t*)take(4 * cp);
+    w.ivals_tmp = (uint32_t*)take(4 * cp);
+    const int64_t maxn = vp > cp ? vp : cp;
+    const int64_t sort_blocks = (maxn + kSortTile - 1) / kSortTile;
+    w.hist = (uint32_t*)take(4 * 256 * sort_blocks);
+    const int64_t scan_items = (256 * sort_blocks > maxn ? 256 * sort_blocks : maxn);
+    w.partials = (int64_t*)take(8 * ((scan_items + kScanTile - 1) / kScanTile + 1));
+    w.bytes = off;
+    return w;
+}
+
+static int bits_for(int64_t v) {
+    int b = 0;
+    while (b < 62 && ((int64_t)1 << b) < v) b++;
+    return b;
+}
+
+void launch_bin_sort(const Frame& fr, int64_t n, const float4* rec, const short4* rect, const int32_t* n_tiles,
+                     int64_t capacity, uint32_t* isect_ids, int2* tile_ranges, int64_t total_tiles,
+                     int64_t* n_isect, void* workspace, cudaStream_t st) {
+    BinWorkspace w = carve_workspace(workspace, (int64_t)fr.n_sensors * n, capacity);
+    const int64_t pairs = (int64_t)fr.n_sensors * n;
+    cudaMemsetAsync(tile_ranges, 0, sizeof(int2) * (size_t)total_tiles, st);
+    // 1. compact visible pairs (stable), keyed by depth bits
+    device_scan(VisIn{n_tiles}, VisOut{rec, n, w.vkeys[0], w.vvals[0]}, pairs, nullptr, INT64_MAX, w.partials,
+                w.vis_count, st);
+    // 2. stable depth sort of the visible pairs (32-bit keys)
+    radix_sort(w.vkeys, w.vvals, 4, pairs, w.vis_count, INT64_MAX, w.hist, w.partials, st);
+    const uint32_t* sorted_pairs = w.vvals[0];  // 4 passes: result back in buffer 0
+    // 3. emit (tile, id) in depth order; n_isect = total
+    const int passes = (bits_for(total_tiles) + 7) / 8 > 0 ? (bits_for(total_tiles) + 7) / 8 : 1;
+    uint32_t* vals_buf[2];
+    // the result lands in buffer passes % 2: make that buffer the caller's isect_ids
+    vals_buf[passes & 1] = isect_ids;
+    vals_buf[(passes & 1) ^ 1] = w.ivals_tmp;
+    EmitOut eo{};
+    eo.sorted_pairs = sorted_pairs;
+    eo.rect = rect;
+    eo.n = n;
+    eo.capacity = capacity;
+    eo.keys = w.ikeys[0];
+    eo.vals = vals_buf[0];
+    for (int s = 0; s < fr.n_sensors; s++) {
+        eo.tile_base[s] = fr.s[s].tile_base;
+        eo.tiles_x[s] = fr.s[s].tiles_x;
+        eo.is_lidar[s] = fr.s[s].kind == SPLAT_SENSOR_LIDAR;
+    }
+    device_scan(EmitIn{sorted_pairs, n_tiles}, eo, pairs, w.vis_count, INT64_MAX, w.partials, n_isect, st);
+    // 4. stable sort of the intersections by tile id
+    radix_sort(w.ikeys, vals_buf, passes, capacity, n_isect, capacity, w.hist, w.partials, st);
+    // 5. per-tile ranges
+    const int64_t blocks = (capacity + 255) / 256;
+    if (blocks > 0)
+        k_tile_ranges<<<(unsigned)blocks, 256, 0, st>>>(w.ikeys[passes & 1], n_isect, capacity, tile_ranges);
+}
+
+}  // namespace splat

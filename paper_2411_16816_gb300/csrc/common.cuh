@@ -1,0 +1,121 @@
+// common.cuh -- device-side frame descriptor and small math shared by the kernels of
+// libsplat.  Everything here is FP32; constants follow the 3DGS conventions the paper
+// builds on (alpha threshold 1/255, alpha clamp 0.999, early stop below T = 1e-4).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/splat.h"
+
+namespace splat {
+
+constexpr float kAlphaMin = 1.0f / 255.0f;
+constexpr float kAlphaMax = 0.999f;
+constexpr float kTEps = 1e-4f;
+constexpr float kTwoPi = 6.283185307179586f;
+constexpr float kPi = 3.14159265358979f;
+constexpr int kMaxSensors = SPLAT_MAX_SENSORS;
+
+// Per-sensor constants, derived once on the host and passed by value in kernel params.
+struct SensorDev {
+    int kind;
+    int tiles_x, tiles_y;
+    int tile_w, tile_h;
+    int tile_base;   // first global tile id of this sensor
+    int block_base;  // first block of this sensor in its kind's raster launch
+    int ray_base;    // first output ray (pixel) of this sensor in its kind's outputs
+    float R[9], t[3], v[3], w[3];
+    // camera
+    int width, height;
+    float fx, fy, cx, cy, rs, dt, eps, near_plane, lim_x, lim_y;
+    // lidar
+    int nb, naz;
+    const float* elev;
+    const float* rays;
+    float az_res, sweep, rmin, wphi, phimax;
+};
+
+struct Frame {
+    int n_sensors;
+    int n_cam_blocks, n_lid_blocks;
+    int cam_sensors[kMaxSensors];  // sensor indices of the cameras, in order
+    int lid_sensors[kMaxSensors];
+    int n_cams, n_lids;
+    SensorDev s[kMaxSensors];
+};
+
+// The frame table travels by value in every launch; keep it inside the classic 4 KB
+// kernel-parameter space together with the other arguments.
+static_assert(sizeof(Frame) + 512 <= 4096, "frame table too large for kernel parameters");
+
+// Projected record and gradient layout: [sensor][3][n] float4.
+__host__ __device__ inline size_t rec_index(int s, int k, int64_t n, int64_t i) {
+    return ((size_t)s * 3 + k) * (size_t)n + (size_t)i;
+}
+
+struct Mat3 {
+    float m[9];
+};
+
+__device__ __forceinline__ void quat_to_rot(float w, float x, float y, float z, float* R) {
+    R[0] = 1.f - 2.f * (y * y + z * z);
+    R[1] = 2.f * (x * y - w * z);
+    R[2] = 2.f * (x * z + w * y);
+    R[3] = 2.f * (x * y + w * z);
+    R[4] = 1.f - 2.f * (x * x + z * z);
+    R[5] = 2.f * (y * z - w * x);
+    R[6] = 2.f * (x * z - w * y);
+    R[7] = 2.f * (y * z + w * x);
+    R[8] = 1.f - 2.f * (x * x + y * y);
+}
+
+// Symmetric 3x3 stored as (xx, xy, xz, yy, yz, zz).
+struct Sym3 {
+    float xx, xy, xz, yy, yz, zz;
+};
+
+// R S R^T for symmetric S.
+__device__ __forceinline__ Sym3 rotate_sym(const float* R, const Sym3& S) {
+    // T = R S (3x3)
+    float T[9];
+#pragma unroll
+    for (int i = 0; i < 3; i++) {
+        float r0 = R[3 * i], r1 = R[3 * i + 1], r2 = R[3 * i + 2];
+        T[3 * i + 0] = r0 * S.xx + r1 * S.xy + r2 * S.xz;
+        T[3 * i + 1] = r0 * S.xy + r1 * S.yy + r2 * S.yz;
+        T[3 * i + 2] = r0 * S.xz + r1 * S.yz + r2 * S.zz;
+    }
+    Sym3 o;
+    o.xx = T[0] * R[0] + T[1] * R[1] + T[2] * R[2];
+    o.xy = T[0] * R[3] + T[1] * R[4] + T[2] * R[5];
+    o.xz = T[0] * R[6] + T[1] * R[7] + T[2] * R[8];
+    o.yy = T[3] * R[3] + T[4] * R[4] + T[5] * R[5];
+    o.yz = T[3] * R[6] + T[4] * R[7] + T[5] * R[8];
+    o.zz = T[6] * R[6] + T[7] * R[7] + T[8] * R[8];
+    return o;
+}
+
+__device__ __forceinline__ float sym_get(const Sym3& S, int i, int j) {
+    const int a = i < j ? i : j, b = i < j ? j : i;
+    if (a == 0) return b == 0 ? S.xx : (b == 1 ? S.xy : S.xz);
+    if (a == 1) return b == 1 ? S.yy : S.yz;
+    return S.zz;
+}
+
+// Azimuth difference wrapped to [-pi, pi).
+__device__ __forceinline__ float wrap_pi(float d) {
+    return d - kTwoPi * floorf(d * (1.0f / kTwoPi) + 0.5f);
+}
+
+__device__ __forceinline__ int sensor_of_block(const Frame& fr, int block, bool lidar) {
+    const int n = lidar ? fr.n_lids : fr.n_cams;
+    const int* list = lidar ? fr.lid_sensors : fr.cam_sensors;
+    int s = list[0];
+    for (int k = 1; k < n; k++) {
+        if (fr.s[list[k]].block_base <= block) s = list[k];
+    }
+    return s;
+}
+
+}  // namespace splat

@@ -1,0 +1,87 @@
+// types.cuh -- argument structs shared by the kernels and the C-ABI layer, and the
+// launcher declarations of every translation unit.
+#pragma once
+#include "common.cuh"
+
+namespace splat {
+
+struct GaussIn {
+    const float* means;
+    const float* scales;
+    const float* quats;
+    const float* opac;
+    const float* vel;
+    int64_t n;
+};
+
+struct ProjOut {
+    float4* rec;
+    short4* rect;
+    int32_t* n_tiles;
+};
+
+struct GradOut {
+    float* means;
+    float* scales;
+    float* quats;
+    float* opac;
+    float* vel;
+};
+
+struct RasterIn {
+    const float4* rec;      // [S][3][n]
+    const uint32_t* ids;    // sorted Gaussian indices
+    const int2* ranges;     // [total_tiles]
+    const float* feat;      // [n][C]
+    int64_t n;
+    int C;                  // channels (<= the kernel's compile-time maximum CM)
+};
+
+struct RasterOut {
+    float* feat;
+    float* T;
+    int32_t* last;
+    float* range_exp;   // lidar
+    float* range_med;   // lidar
+    float* alpha;       // lidar
+};
+
+struct RasterGrad {
+    const float* T;
+    const int32_t* last;
+    const float* dfeat;
+    const float* dT;       // camera: dL/dT
+    const float* drange;   // lidar: dL/d expected range
+    const float* dalpha;   // lidar: dL/d (1 - T)
+    float4* grad_proj;     // [S][3][n]
+    float* dfeatures;      // [n][C]
+};
+
+struct BinWorkspace {
+    uint32_t* vkeys[2];
+    uint32_t* vvals[2];
+    int64_t* vis_count;
+    uint32_t* ikeys[2];
+    uint32_t* ivals_tmp;
+    uint32_t* hist;
+    int64_t* partials;
+    size_t bytes;
+};
+
+void launch_project(const GaussIn& g, const Frame& fr, const ProjOut& out, cudaStream_t st);
+void launch_project_backward(const GaussIn& g, const Frame& fr, const int32_t* n_tiles, const float4* grad,
+                             const GradOut& out, cudaStream_t st);
+BinWorkspace carve_workspace(void* base, int64_t pairs, int64_t capacity);
+void launch_bin_sort(const Frame& fr, int64_t n, const float4* rec, const short4* rect, const int32_t* n_tiles,
+                     int64_t capacity, uint32_t* isect_ids, int2* tile_ranges, int64_t total_tiles,
+                     int64_t* n_isect, void* workspace, cudaStream_t st);
+bool launch_raster_fwd(bool lidar, int C, int tw, int th, const Frame& fr, int blocks, const RasterIn& in,
+                       const RasterOut& out, cudaStream_t st);
+bool launch_raster_bwd(bool lidar, int C, int tw, int th, const Frame& fr, int blocks, const RasterIn& in,
+                       const RasterGrad& g, bool recompute, cudaStream_t st);
+bool raster_shape_supported(bool lidar, int tw, int th);
+bool raster_channels_supported(int C);
+void launch_l1(const float* pred, const float* target, int64_t count, float scale, float* grad, float* loss,
+               cudaStream_t st);
+
+}  // namespace splat

@@ -1,0 +1,325 @@
+"""Torch-facing wrapper of libsplat: device buffers, the per-frame call sequence and
+the autograd function.
+
+PyTorch only provides device memory and the stream here; every step of the
+projection, binning, rasterization and backward runs in libsplat's CUDA kernels
+(called through :mod:`._lib`).  There is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+_PARAMS = ("means", "scales", "quats", "opacities", "features", "velocities")
+
+
+def _vp(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p(0)
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _f32(a, device):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device=device)
+
+
+def gaussians_to_device(g: dict, device="cuda") -> dict:
+    """Copy a dict of numpy arrays (see scenes.py) to contiguous FP32 device tensors."""
+    out = {}
+    for k in _PARAMS:
+        v = g.get(k)
+        out[k] = None if v is None else _f32(v, device)
+    return out
+
+
+class Frame:
+    """A fixed set of sensors rendered together (one projection, one sort, one raster
+    launch per sensor kind).  Holds the library's per-frame device buffers for a
+    scene of `n` Gaussians with `channels` features.
+
+    `capacity` is the intersection buffer size; `forward(..., check=True)` grows it
+    and re-runs the binning when the frame needs more."""
+
+    def __init__(self, sensors, n: int, channels: int, device="cuda", capacity: int | None = None):
+        if not 1 <= len(sensors) <= L.SPLAT_MAX_SENSORS:
+            raise ValueError(f"a frame holds 1..{L.SPLAT_MAX_SENSORS} sensors")
+        self.lib = L.load()
+        self.device = torch.device(device)
+        self.sensors = list(sensors)
+        self.n, self.channels = int(n), int(channels)
+        S = len(self.sensors)
+        self._keep = []
+        self.c_sensors = (L.splat_sensor * S)()
+        for k, s in enumerate(self.sensors):
+            self._fill_sensor(self.c_sensors[k], s)
+        total = ctypes.c_int64()
+        tiles = (ctypes.c_int64 * S)()
+        rays = (ctypes.c_int64 * S)()
+        L.call("splat_frame_layout", S, self.c_sensors, ctypes.byref(total), tiles, rays)
+        self.total_tiles = total.value
+        self.tiles = list(tiles)
+        self.rays = list(rays)
+        self.cam_idx = [k for k, s in enumerate(self.sensors) if s.kind == "camera"]
+        self.lid_idx = [k for k, s in enumerate(self.sensors) if s.kind == "lidar"]
+        self.cam_rays = sum(self.rays[k] for k in self.cam_idx)
+        self.lid_rays = sum(self.rays[k] for k in self.lid_idx)
+        dev = self.device
+        self.rec = torch.empty((S, 3, max(self.n, 1), 4), dtype=torch.float32, device=dev)
+        self.rect = torch.empty((S, max(self.n, 1), 4), dtype=torch.int16, device=dev)
+        self.n_tiles = torch.empty((S, max(self.n, 1)), dtype=torch.int32, device=dev)
+        self.ranges = torch.empty((max(self.total_tiles, 1), 2), dtype=torch.int32, device=dev)
+        self.n_isect = torch.zeros(1, dtype=torch.int64, device=dev)
+        self.capacity = 0
+        self._alloc_capacity(capacity if capacity is not None else max(1 << 16, 8 * self.n))
+        self.grad_proj = None
+        self.version = 0
+
+    # -- set-up ------------------------------------------------------------------------
+    def _fill_sensor(self, c, s):
+        c.R[:] = [float(x) for x in np.asarray(s.R, dtype=np.float32).reshape(9)]
+        c.t[:] = [float(x) for x in np.asarray(s.t, dtype=np.float32)]
+        c.lin_vel[:] = [float(x) for x in np.asarray(s.lin_vel, dtype=np.float32)]
+        c.ang_vel[:] = [float(x) for x in np.asarray(s.ang_vel, dtype=np.float32)]
+        c.tile_w, c.tile_h = s.tile_w if s.kind == "camera" else s.tile_az, s.tile_h if s.kind == "camera" else s.tile_el
+        c.eps2d = s.eps2d
+        if s.kind == "camera":
+            c.kind = L.SPLAT_SENSOR_CAMERA
+            c.width, c.height = s.width, s.height
+            c.fx, c.fy, c.cx, c.cy = s.fx, s.fy, s.cx, s.cy
+            c.rs_time, c.time_offset, c.near_plane = s.rs_time, s.time_offset, s.near
+        else:
+            c.kind = L.SPLAT_SENSOR_LIDAR
+            c.n_beams, c.n_az = s.n_beams, s.n_az
+            elev = _f32(s.beam_elev, self.device)
+            self._keep.append(elev)
+            c.beam_elev = elev.data_ptr()
+            if s.rays is not None:
+                rays = _f32(np.asarray(s.rays).reshape(s.n_beams, s.n_az, 3), self.device)
+                self._keep.append(rays)
+                c.rays = rays.data_ptr()
+            c.az_res, c.sweep_time, c.r_min = s.az_res, s.sweep_time, s.r_min
+
+    def _alloc_capacity(self, capacity: int):
+        capacity = int(max(capacity, 1))
+        self.capacity = capacity
+        self.isect_ids = torch.empty(capacity, dtype=torch.int32, device=self.device)
+        ws = ctypes.c_size_t()
+        L.call("splat_workspace_size", self.n, len(self.sensors), self.c_sensors, capacity, ctypes.byref(ws))
+        self.workspace = torch.empty(max(ws.value, 256), dtype=torch.uint8, device=self.device)
+
+    def c_gaussians(self, g: dict) -> L.splat_gaussians:
+        for k in ("means", "scales", "quats", "opacities", "features"):
+            t = g[k]
+            if t.dtype != torch.float32 or not t.is_contiguous() or t.device != self.device:
+                raise ValueError(f"{k} must be a contiguous float32 tensor on {self.device}")
+        if g["means"].shape[0] != self.n or g["features"].shape[1] != self.channels:
+            raise ValueError("scene size does not match the frame")
+        vel = g.get("velocities")
+        return L.splat_gaussians(g["means"].data_ptr(), g["scales"].data_ptr(), g["quats"].data_ptr(),
+                                 g["opacities"].data_ptr(), g["features"].data_ptr(),
+                                 vel.data_ptr() if vel is not None else None, self.n, self.channels, 0)
+
+    def c_proj(self):
+        return L.splat_projected(self.rec.data_ptr(), self.rect.data_ptr(), self.n_tiles.data_ptr())
+
+    def c_bins(self):
+        return L.splat_bins(self.isect_ids.data_ptr(), self.ranges.data_ptr(), self.n_isect.data_ptr())
+
+    # -- forward ------------------------------------------------------------------------
+    def project(self, cg, stream=None):
+        L.call("splat_project", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(), _stream(stream))
+
+    def bin_sort(self, stream=None):
+        L.call("splat_bin_sort", self.n, len(self.sensors), self.c_sensors, self.c_proj(), self.capacity,
+               self.c_bins(), _vp(self.workspace), self.workspace.numel(), _stream(stream))
+
+    def ensure_capacity(self, stream=None) -> bool:
+        """Reads the intersection count (one sync); grows and re-bins if it overflowed.
+        Returns True if the lists had to be rebuilt."""
+        need = int(self.n_isect.item())
+        if need <= self.capacity:
+            return False
+        self._alloc_capacity(int(need * 1.25) + 1024)
+        self.bin_sort(stream)
+        return True
+
+    def alloc_outputs(self, keep_state: bool = True) -> dict:
+        dev, C = self.device, self.channels
+        out = {}
+        if self.cam_idx:
+            out["cam_feat"] = torch.empty((self.cam_rays, C), dtype=torch.float32, device=dev)
+            out["cam_T"] = torch.empty(self.cam_rays, dtype=torch.float32, device=dev)
+            out["cam_last"] = torch.empty(self.cam_rays, dtype=torch.int32, device=dev) if keep_state else None
+        if self.lid_idx:
+            R = self.lid_rays
+            out["lid_feat"] = torch.empty((R, C), dtype=torch.float32, device=dev)
+            out["lid_range_exp"] = torch.empty(R, dtype=torch.float32, device=dev)
+            out["lid_range_med"] = torch.empty(R, dtype=torch.float32, device=dev)
+            out["lid_alpha"] = torch.empty(R, dtype=torch.float32, device=dev)
+            out["lid_T"] = torch.empty(R, dtype=torch.float32, device=dev) if keep_state else None
+            out["lid_last"] = torch.empty(R, dtype=torch.int32, device=dev) if keep_state else None
+        return out
+
+    def rasterize(self, cg, out: dict, stream=None):
+        st = _stream(stream)
+        if self.cam_idx:
+            L.call("splat_render_camera", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
+                   self.c_bins(), _vp(out["cam_feat"]), _vp(out["cam_T"]), _vp(out.get("cam_last")), st)
+        if self.lid_idx:
+            L.call("splat_render_lidar", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
+                   self.c_bins(), _vp(out["lid_feat"]), _vp(out["lid_range_exp"]), _vp(out["lid_range_med"]),
+                   _vp(out["lid_alpha"]), _vp(out.get("lid_T")), _vp(out.get("lid_last")), st)
+
+    def forward(self, g: dict, keep_state: bool = True, check: bool = True, out: dict | None = None,
+                stream=None) -> dict:
+        """Project, bin and rasterize every sensor.  With keep_state the per-ray final
+        transmittance and last index are kept for the backward pass; without it the
+        backward recomputes them per tile."""
+        cg = self.c_gaussians(g)
+        self.project(cg, stream)
+        self.bin_sort(stream)
+        if check:
+            self.ensure_capacity(stream)
+        out = self.alloc_outputs(keep_state) if out is None else out
+        self.rasterize(cg, out, stream)
+        self.version += 1
+        return out
+
+    def split(self, flat: torch.Tensor, kind: str):
+        """Per-sensor views of a concatenated output (cameras H x W [x C], lidars B x A [x C])."""
+        idx = self.cam_idx if kind == "camera" else self.lid_idx
+        views, off = [], 0
+        for k in idx:
+            s = self.sensors[k]
+            shape = (s.height, s.width) if kind == "camera" else (s.n_beams, s.n_az)
+            n = self.rays[k]
+            v = flat[off:off + n]
+            views.append(v.reshape(*shape, *flat.shape[1:]))
+            off += n
+        return views
+
+    # -- backward -----------------------------------------------------------------------
+    def backward(self, g: dict, out: dict, grads: dict, param_grads: dict | None = None, stream=None) -> dict:
+        """Gradients with respect to the Gaussian parameters (activated scales and
+        opacities, unnormalised quaternions) for upstream gradients
+        grads = {cam_feat, cam_T, lid_feat, lid_range_exp, lid_alpha} (any may be absent)."""
+        cg = self.c_gaussians(g)
+        st = _stream(stream)
+        dev = self.device
+        if self.grad_proj is None:
+            self.grad_proj = torch.zeros_like(self.rec)
+        else:
+            self.grad_proj.zero_()
+        if param_grads is None:
+            param_grads = {k: torch.zeros_like(g[k]) for k in _PARAMS if g.get(k) is not None}
+        else:
+            for v in param_grads.values():
+                v.zero_()
+        if self.cam_idx:
+            dF = grads.get("cam_feat")
+            if dF is None:
+                dF = torch.zeros((self.cam_rays, self.channels), dtype=torch.float32, device=dev)
+            L.call("splat_render_camera_backward", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
+                   self.c_bins(), _vp(out.get("cam_T") if out.get("cam_last") is not None else None),
+                   _vp(out.get("cam_last")), _vp(dF.contiguous()), _vp(grads.get("cam_T")), _vp(self.grad_proj),
+                   _vp(param_grads["features"]), st)
+        if self.lid_idx:
+            dF = grads.get("lid_feat")
+            if dF is None:
+                dF = torch.zeros((self.lid_rays, self.channels), dtype=torch.float32, device=dev)
+            keep = out.get("lid_last") is not None
+            L.call("splat_render_lidar_backward", ctypes.byref(cg), len(self.sensors), self.c_sensors,
+                   self.c_proj(), self.c_bins(), _vp(out.get("lid_T") if keep else None),
+                   _vp(out.get("lid_last") if keep else None), _vp(dF.contiguous()),
+                   _vp(grads.get("lid_range_exp")), _vp(grads.get("lid_alpha")), _vp(self.grad_proj),
+                   _vp(param_grads["features"]), st)
+        L.call("splat_project_backward", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
+               _vp(self.grad_proj), _vp(param_grads["means"]), _vp(param_grads["scales"]),
+               _vp(param_grads["quats"]), _vp(param_grads["opacities"]), _vp(param_grads.get("velocities")), st)
+        return param_grads
+
+    # -- inspection ---------------------------------------------------------------------
+    def intersections(self):
+        """(global tile, Gaussian index) of every intersection, sorted (host arrays)."""
+        n = int(self.n_isect.item())
+        if n > self.capacity:
+            raise RuntimeError("intersection capacity exceeded")
+        ranges = self.ranges.cpu().numpy()
+        ids = self.isect_ids[:n].cpu().numpy().astype(np.int64)
+        tiles = np.zeros(n, np.int64)
+        for t in np.nonzero(ranges[:, 1] > ranges[:, 0])[0]:
+            tiles[ranges[t, 0]:ranges[t, 1]] = t
+        return tiles, ids
+
+
+def l1_loss(pred: torch.Tensor, target: torch.Tensor, scale: float, grad: torch.Tensor | None,
+            loss: torch.Tensor | None, stream=None):
+    """Accumulates scale * sum|pred - target| into loss (1-element device tensor) and
+    writes grad = scale * sign(pred - target) (both through libsplat)."""
+    L.call("splat_l1_loss", _vp(pred), _vp(target), pred.numel(), float(scale), _vp(grad), _vp(loss),
+           _stream(stream))
+
+
+class RenderFrame(torch.autograd.Function):
+    """Differentiable render of a Frame: inputs are the activated Gaussian parameters,
+    outputs (camera features, camera T, lidar features, expected range, median range,
+    lidar alpha).  With recompute=True the forward keeps no per-ray state and the
+    backward recomputes it tile by tile."""
+
+    @staticmethod
+    def forward(ctx, frame: Frame, recompute: bool, means, scales, quats, opacities, features, velocities):
+        g = {"means": means.detach().contiguous(), "scales": scales.detach().contiguous(),
+             "quats": quats.detach().contiguous(), "opacities": opacities.detach().contiguous(),
+             "features": features.detach().contiguous(),
+             "velocities": velocities.detach().contiguous() if velocities is not None else None}
+        out = frame.forward(g, keep_state=not recompute)
+        ctx.frame, ctx.g, ctx.out, ctx.version = frame, g, out, frame.version
+        ctx.has_vel = velocities is not None
+        empty = torch.zeros(0, device=frame.device)
+        res = (out.get("cam_feat", empty), out.get("cam_T", empty), out.get("lid_feat", empty),
+               out.get("lid_range_exp", empty), out.get("lid_range_med", empty), out.get("lid_alpha", empty))
+        ctx.mark_non_differentiable(res[4])
+        return res
+
+    @staticmethod
+    def backward(ctx, d_cf, d_cT, d_lf, d_lr, d_lm, d_la):
+        frame = ctx.frame
+        if frame.version != ctx.version:
+            raise RuntimeError("the Frame rendered again before this backward; use one Frame per pending graph")
+        grads = {}
+        if frame.cam_idx:
+            grads["cam_feat"] = d_cf.contiguous() if d_cf is not None else None
+            grads["cam_T"] = d_cT.contiguous() if d_cT is not None else None
+        if frame.lid_idx:
+            grads["lid_feat"] = d_lf.contiguous() if d_lf is not None else None
+            grads["lid_range_exp"] = d_lr.contiguous() if d_lr is not None else None
+            grads["lid_alpha"] = d_la.contiguous() if d_la is not None else None
+        pg = frame.backward(ctx.g, ctx.out, grads)
+        return (None, None, pg["means"], pg["scales"], pg["quats"], pg["opacities"], pg["features"],
+                pg.get("velocities") if ctx.has_vel else None)
+
+
+def render(frame: Frame, means, scales, quats, opacities, features, velocities=None, recompute=False):
+    """Differentiable frame render (activated parameters).  Returns a dict of outputs."""
+    cf, cT, lf, lr, lm, la = RenderFrame.apply(frame, recompute, means, scales, quats, opacities, features,
+                                               velocities)
+    out = {}
+    if frame.cam_idx:
+        out.update(cam_feat=cf, cam_T=cT)
+    if frame.lid_idx:
+        out.update(lid_feat=lf, lid_range_exp=lr, lid_range_med=lm, lid_alpha=la)
+    return out
+
+
+def render_raw(frame: Frame, means, log_scales, quats, opacity_logits, features, velocities=None, recompute=False):
+    """Differentiable render from unconstrained parameters (exp scales, sigmoid opacity)."""
+    return render(frame, means, torch.exp(log_scales), quats, torch.sigmoid(opacity_logits), features, velocities,
+                  recompute)
