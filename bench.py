@@ -1,0 +1,428 @@
+#!/usr/bin/env python
+"""Benchmark: fwd+bwd rendered rays/sec (camera + lidar) of one training step on the
+500k-Gaussian driving frame (six 1920x1080 rolling-shutter cameras + a 32 x 1080 lidar,
+L1 loss against a seeded target render), with the roofline of the dominant kernel and
+the FP64 CPU oracle timed on a bounded sample of the same workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One JSON line is printed by rank 0.  With N > 1 (torchrun), every rank renders its own
+copy of the frame (independent problems, no collective): weak scaling.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2411_16816_gb300 import scenes  # noqa: E402
+
+METRIC = "fwd+bwd rendered rays/sec (camera+lidar) at 500k Gaussians"
+UNIT = "rays/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=["driving", "lidar_heavy"], default="driving")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--profile-only", action="store_true", help="a few untimed steps (for ncu captures)")
+    return p.parse_args()
+
+
+def workload(name):
+    if name == "driving":
+        g, sensors = scenes.driving_frame()
+        desc = {"workload": "driving frame: 500k Gaussians (100x100x10 m box, 20% dynamic), 6 x 1920x1080 "
+                            "rolling-shutter cameras (30 ms) + 32-beam x 1080 lidar (100 ms sweep), 16 channels, "
+                            "L1 vs seeded target render",
+                "gaussians": len(g["opacities"]), "rays_per_step": sum(s.n_rays for s in sensors),
+                "cameras": "6x1920x1080", "lidar": "32x1080"}
+    else:
+        g, sensors = scenes.lidar_heavy_frame()
+        desc = {"workload": "lidar-heavy frame: 1M Gaussians, 128-beam non-uniform x 2048 lidar, 100 ms sweep",
+                "gaussians": len(g["opacities"]), "rays_per_step": sum(s.n_rays for s in sensors)}
+    target = scenes.target_like(g, seed=1003)
+    return g, sensors, target, desc
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------------------------
+# CPU oracle on a bounded sample (the reference arm and the cpu_baseline field)
+# ------------------------------------------------------------------------------------
+
+def oracle_sample_step(g, sensors, rays_per_sensor, seed):
+    """One oracle fwd+bwd over a strided sample of every sensor's rays.  Returns
+    (sampled rays, seconds)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    total = 0
+    C = g["features"].shape[1]
+    for s in sensors:
+        k = min(rays_per_sensor, s.n_rays)
+        stride = s.n_rays // k
+        sel = (np.arange(k) * stride + int(rng.integers(stride))).astype(np.int64)
+        r = oracle.render(g, s, sel=sel)
+        gF = np.sign(r["F"] - 0.1) / max(1, k * C)
+        if s.kind == "camera":
+            oracle.render_backward(g, s, gF, None, sel=sel)
+        else:
+            oracle.render_backward(g, s, gF, None, np.sign(r["range_exp"]) / k, None, sel=sel)
+        total += k
+    return total, time.perf_counter() - t0
+
+
+def cpu_baseline(g, sensors, budget_s=20.0):
+    import oracle
+    oracle.build()
+    n_s, dt = oracle_sample_step(g, sensors, 32, seed=0)          # calibration
+    per_ray = dt / n_s
+    rays = int(max(32, min(4096, budget_s / max(per_ray, 1e-6) / len(sensors))))
+    n_s, dt = oracle_sample_step(g, sensors, rays, seed=1)
+    return {"value": n_s / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"{rays} strided rays per sensor ({n_s} total) of the same frame, FP64 fwd+bwd incl. "
+                      f"full per-Gaussian projection of all {len(g['opacities'])} Gaussians per sensor; "
+                      f"{dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    g, sensors, _, desc = workload(args.workload)
+    import oracle
+    oracle.build()
+    n_s, dt0 = oracle_sample_step(g, sensors, 16, seed=0)
+    rays = int(max(16, min(2048, 8.0 / max(dt0 / n_s, 1e-6) / len(sensors))))
+    for w in range(args.warmup):
+        oracle_sample_step(g, sensors, max(16, rays // 8), seed=100 + w)
+    times, counts = [], []
+    for k in range(args.steps):
+        n_s, dt = oracle_sample_step(g, sensors, rays, seed=k)
+        times.append(dt)
+        counts.append(n_s)
+    value = sum(counts) / sum(times)
+    cores = cpu_cores()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": desc,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{rays} strided rays per sensor per step, FP64 fwd+bwd with full "
+                                       f"per-Gaussian projection"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.file,
+                                         stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.file.flush()
+        self.file.seek(0)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.file.read().strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1", "0x1") or v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"hbm_gbs": d["hbm_gbs"], "sm_max_mhz": d.get("sm_max_mhz", 2070.0), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+def fp32_peak_tflops(sm_mhz):
+    """Dense FP32 FMA peak: 152 SMs x 128 FP32 lanes x 2 flops x clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def launches_per_step(fr, n_l1):
+    """Kernels libsplat launches in one training step (counted from the call sequence)."""
+    total_tiles = fr.total_tiles
+    bits = max(1, int(math.ceil(math.log2(max(total_tiles, 2)))))
+    passes = max(1, (bits + 7) // 8)
+    scan = 3
+    radix_pass = 1 + scan + 1
+    bin_sort = scan + 4 * radix_pass + scan + passes * radix_pass + 1
+    raster = (1 if fr.cam_idx else 0) + (1 if fr.lid_idx else 0)
+    return 1 + bin_sort + raster + n_l1 + raster + 1
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2411_16816_gb300 import _lib
+    from paper_2411_16816_gb300.render import Frame, gaussians_to_device, l1_loss
+    _lib.load()
+
+    g, sensors, target, desc = workload(args.workload)
+    n, C = len(g["opacities"]), g["features"].shape[1]
+    gd = gaussians_to_device(g, dev)
+    td = gaussians_to_device(target, dev)
+    fr = Frame(sensors, n, C, dev)
+    # target render (an input of the loss, made once outside the timed region)
+    tout = fr.forward(td, keep_state=False)
+    tgt = {k: tout[k].clone() for k in ("cam_feat", "lid_feat", "lid_range_exp") if k in tout}
+    out = fr.forward(gd)
+    need = int(fr.n_isect.item())
+    if need * 1.05 > fr.capacity:
+        fr._alloc_capacity(int(need * 1.1))
+    out = fr.forward(gd, check=True)
+    grads = {"cam_feat": torch.empty_like(out["cam_feat"]), "lid_feat": torch.empty_like(out["lid_feat"]),
+             "lid_range_exp": torch.empty_like(out["lid_range_exp"])}
+    pgrads = {k: torch.zeros_like(v) for k, v in gd.items() if v is not None}
+    loss = torch.zeros(1, device=dev)
+    l1_terms = [("cam_feat", 1.0 / out["cam_feat"].numel()), ("lid_feat", 1.0 / out["lid_feat"].numel()),
+                ("lid_range_exp", 1.0 / out["lid_range_exp"].numel())]
+    stream = torch.cuda.current_stream()
+
+    def step(src=None):
+        loss.zero_()
+        fr.forward(src if src is not None else gd, keep_state=True, check=False, out=out)
+        for key, sc in l1_terms:
+            l1_loss(out[key], tgt[key], sc, grads[key], loss)
+        fr.backward(src if src is not None else gd, out, grads, param_grads=pgrads)
+
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    if args.profile_only:
+        for _ in range(max(1, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        return
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if int(fr.n_isect.item()) > fr.capacity:
+        raise RuntimeError("intersection capacity exceeded during warm-up")
+
+    # ---- timed region: K steps, each bracketed by events; L2 flushed between steps ----
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.fill_(float(k))
+            starts[k].record(stream)
+            step()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        wall = time.perf_counter() - wall0
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = statistics.mean(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    overflow = int(fr.n_isect.item()) > fr.capacity
+    rays = desc["rays_per_step"]
+    value = world * rays / (ms * 1e-3)
+
+    # ---- end to end through the public API with host buffers ----
+    host_g = {k: v.cpu().pin_memory() for k, v in gd.items() if v is not None}
+    host_t = {k: v.cpu().pin_memory() for k, v in tgt.items()}
+    host_loss = torch.empty(1, dtype=torch.float32).pin_memory()
+    dev_g = {k: torch.empty_like(v) for k, v in gd.items() if v is not None}
+    h2d = sum(v.numel() * v.element_size() for v in host_g.values()) + \
+        sum(v.numel() * v.element_size() for v in host_t.values())
+    e2e_times = []
+    for k in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for key, v in host_g.items():
+            dev_g[key].copy_(v, non_blocking=True)
+        for key, v in host_t.items():
+            tgt[key].copy_(v, non_blocking=True)
+        step(dev_g)
+        host_loss.copy_(loss, non_blocking=True)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e = {"value": world * rays / statistics.mean(e2e_times), "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": 4}
+
+    # ---- per-kernel timing (events around each library call) and work counters ----
+    import ctypes
+    evaluated = torch.zeros(2, dtype=torch.int64, device=dev)
+    cg = fr.c_gaussians(gd)
+    fr.project(cg)
+    fr.bin_sort()
+    fr.rasterize(cg, out, evaluated=evaluated)
+    torch.cuda.synchronize()
+    ev_cam, ev_lid = (int(x) for x in evaluated.cpu())
+    n_isect = int(fr.n_isect.item())
+    visible = int((fr.n_tiles > 0).sum().item())
+    parts = {}
+
+    def timed(name, fn, reps=5):
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        parts[name] = statistics.mean(ts)
+
+    from paper_2411_16816_gb300 import _lib as L
+    from paper_2411_16816_gb300.render import _stream, _vp
+    st = _stream()
+    S = len(fr.sensors)
+    timed("project", lambda: fr.project(cg))
+    timed("bin_sort", lambda: fr.bin_sort())
+    timed("raster_camera_fwd", lambda: L.call("splat_render_camera", ctypes.byref(cg), S, fr.c_sensors, fr.c_proj(),
+                                                fr.c_bins(), _vp(out["cam_feat"]), _vp(out["cam_T"]),
+                                                _vp(out["cam_last"]), None, st))
+    timed("raster_lidar_fwd", lambda: L.call("splat_render_lidar", ctypes.byref(cg), S, fr.c_sensors, fr.c_proj(),
+                                               fr.c_bins(), _vp(out["lid_feat"]), _vp(out["lid_range_exp"]),
+                                               _vp(out["lid_range_med"]), _vp(out["lid_alpha"]), _vp(out["lid_T"]),
+                                               _vp(out["lid_last"]), None, st))
+    fr.grad_proj.zero_()
+    timed("raster_camera_bwd", lambda: L.call("splat_render_camera_backward", ctypes.byref(cg), S, fr.c_sensors,
+                                                fr.c_proj(), fr.c_bins(), _vp(out["cam_T"]), _vp(out["cam_last"]),
+                                                _vp(grads["cam_feat"]), None, _vp(fr.grad_proj),
+                                                _vp(pgrads["features"]), st))
+    timed("raster_lidar_bwd", lambda: L.call("splat_render_lidar_backward", ctypes.byref(cg), S, fr.c_sensors,
+                                               fr.c_proj(), fr.c_bins(), _vp(out["lid_T"]), _vp(out["lid_last"]),
+                                               _vp(grads["lid_feat"]), _vp(grads["lid_range_exp"]), None,
+                                               _vp(fr.grad_proj), _vp(pgrads["features"]), st))
+    timed("project_bwd", lambda: L.call("splat_project_backward", ctypes.byref(cg), S, fr.c_sensors, fr.c_proj(),
+                                          _vp(fr.grad_proj), _vp(pgrads["means"]), _vp(pgrads["scales"]),
+                                          _vp(pgrads["quats"]), _vp(pgrads["opacities"]),
+                                          _vp(pgrads["velocities"]), st))
+
+    peaks = measured_peaks()
+    clocks = clk.summary()
+    fp32_peak = fp32_peak_tflops(peaks["sm_max_mhz"])
+    # algorithmic work per launch (see the design notes for the per-unit figures)
+    work = {
+        "raster_camera_fwd": ("alu", ev_cam * (22 + 2 * C) / 1e12, "TFLOP/s"),
+        "raster_camera_bwd": ("alu", ev_cam * (50 + 7 * C) / 1e12, "TFLOP/s"),
+        "raster_lidar_fwd": ("alu", ev_lid * (30 + 2 * C) / 1e12, "TFLOP/s"),
+        "raster_lidar_bwd": ("alu", ev_lid * (56 + 7 * C) / 1e12, "TFLOP/s"),
+        "project": ("hbm", (n * 56 + S * n * 8 + visible * 56) / 1e9, "GB/s"),
+        "project_bwd": ("hbm", (n * 56 + S * n * 4 + visible * 48 + n * 56) / 1e9, "GB/s"),
+        "bin_sort": ("hbm", (S * n * 4 + visible * 64 + n_isect * (8 + 2 * 20) + fr.total_tiles * 8) / 1e9, "GB/s"),
+    }
+    dom = max(parts, key=parts.get)
+    bound, amount, unit = work[dom]
+    achieved = amount / (parts[dom] * 1e-3)
+    peak = fp32_peak if bound == "alu" else peaks["hbm_gbs"]
+    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": (f"FP32 FMA 152x128x2 at {peaks['sm_max_mhz']:.0f} MHz" if bound == "alu"
+                                else f"{peaks['source']} HBM copy"),
+                "kernel_ms": parts,
+                "per_kernel_frac": {k: (work[k][1] / (parts[k] * 1e-3)) /
+                                    (fp32_peak if work[k][0] == "alu" else peaks["hbm_gbs"]) for k in parts}}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(desc, l2="explicit 258 MB flush between timed steps (per-step CUDA events)",
+                           intersections=n_isect, evaluated_pairs={"camera": ev_cam, "lidar": ev_lid},
+                           parallelism=f"replicas x{world}"),
+            "e2e": e2e, "gpu_launches": launches_per_step(fr, len(l1_terms)) * args.steps,
+            "roofline": roofline, "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
+            "wall_s": wall, "overflow": overflow}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(g, sensors)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

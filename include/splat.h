@@ -177,10 +177,12 @@ splat_status splat_bin_sort_backward(void);
  *   out_T[pixels]               final transmittance
  *   out_last[pixels]            number of list entries up to and including the last
  *                               Gaussian blended into the pixel (for the backward pass);
- *                               out_T and out_last may be NULL. */
+ *                               out_T and out_last may be NULL.
+ *   evaluated                   optional device uint64 to which the number of (pixel,
+ *                               Gaussian) pairs examined is added (work accounting). */
 splat_status splat_render_camera(const splat_gaussians *g, int32_t n_sensors, const splat_sensor *sensors,
                                  splat_projected proj, splat_bins bins, float *out_feat, float *out_T,
-                                 int32_t *out_last, void *stream);
+                                 int32_t *out_last, uint64_t *evaluated, void *stream);
 
 /* Lidar rasterization (Sec. 3.3: blended features, expected range of the rolling-
  * shutter ranges r + v_r t, median range = rolling-shutter range of the first Gaussian
@@ -188,11 +190,11 @@ splat_status splat_render_camera(const splat_gaussians *g, int32_t n_sensors, co
  * over the frame's lidars in sensor order, each [n_beams][n_az]:
  *   out_feat[rays][channels], out_range_exp[rays], out_range_med[rays],
  *   out_alpha[rays] (= 1 - T), out_T[rays], out_last[rays] (as for cameras);
- *   out_range_med, out_T and out_last may be NULL. */
+ *   out_range_med, out_T and out_last may be NULL; evaluated as for cameras. */
 splat_status splat_render_lidar(const splat_gaussians *g, int32_t n_sensors, const splat_sensor *sensors,
                                 splat_projected proj, splat_bins bins, float *out_feat, float *out_range_exp,
                                 float *out_range_med, float *out_alpha, float *out_T, int32_t *out_last,
-                                void *stream);
+                                uint64_t *evaluated, void *stream);
 
 /* Backward of splat_render_camera.  Inputs: the forward's out_T and out_last (or both
  * NULL: the kernel then recomputes them per tile), dL_dfeat[pixels][channels] and

@@ -64,13 +64,13 @@ _I64 = ctypes.c_int64
 
 def _declare(L):
     L.oracle_project.restype = ctypes.c_int
-    L.oracle_project.argtypes = [_I64] + [_P] * 7 + [ctypes.c_double] + [_P] * 6
+    L.oracle_project.argtypes = [_I64] + [_P] * 7 + [ctypes.c_double] + [_P] * 7
     L.oracle_isect_list.restype = _I64
     L.oracle_isect_list.argtypes = [_I64, _P, _P, _P, _P, _I64, _P, _P]
     L.oracle_render.restype = ctypes.c_int
     L.oracle_render.argtypes = ([_I64] + [_P] * 6 + [ctypes.c_int] + [_P] * 3 + [ctypes.c_double, _I64] + [_P] * 7)
     L.oracle_render_backward.restype = ctypes.c_int
-    L.oracle_render_backward.argtypes = ([_I64] + [_P] * 6 + [ctypes.c_int] + [_P] * 14)
+    L.oracle_render_backward.argtypes = ([_I64] + [_P] * 6 + [ctypes.c_int] + [_P] * 3 + [_I64] + [_P] * 12)
     L.oracle_projection_backward.restype = ctypes.c_int
     L.oracle_projection_backward.argtypes = [_I64] + [_P] * 13
     L.oracle_jacobian.restype = ctypes.c_int
@@ -155,7 +155,8 @@ def project(g: dict, s, guard: float | None = None) -> dict:
 
     Returns rec (n,16): [mean_a, mean_b, conic a, b, c, o', depth, v_a, v_b, v_r,
     Sigma'_aa, Sigma'_ab, Sigma'_bb, compensation, extent_a, extent_b], rect (n,4),
-    outer rect, n_tiles, visible and marginal flags.
+    outer and inner rects of marginal Gaussians (tiles whose membership FP32 rounding
+    could change lie between the two), n_tiles, visible and marginal flags.
     """
     L = lib()
     n = len(g["opacities"])
@@ -163,11 +164,12 @@ def project(g: dict, s, guard: float | None = None) -> dict:
     P = sensor_params(s)
     guard = guard_for(s) if guard is None else guard
     rec = np.zeros((n, 16)); rect = np.zeros((n, 4), np.int32); orect = np.zeros((n, 4), np.int32)
+    irect = np.zeros((n, 4), np.int32)
     nt = np.zeros(n, np.int32); vis = np.zeros(n, np.uint8); marg = np.zeros(n, np.uint8)
     el = _elev(s)
     L.oracle_project(n, *[_ptr(a) for a in m], _ptr(P), _ptr(el), guard, _ptr(rec), _ptr(rect), _ptr(orect),
-                     _ptr(nt), _ptr(vis), _ptr(marg))
-    return {"rec": rec, "rect": rect, "orect": orect, "n_tiles": nt, "visible": vis.astype(bool),
+                     _ptr(irect), _ptr(nt), _ptr(vis), _ptr(marg))
+    return {"rec": rec, "rect": rect, "orect": orect, "irect": irect, "n_tiles": nt, "visible": vis.astype(bool),
             "marginal": marg.astype(bool)}
 
 
@@ -204,14 +206,15 @@ def render(g: dict, s, sel=None, guard: float | None = None) -> dict:
     mg = np.zeros(nr, np.uint8); cnt = np.zeros(nr, np.int32)
     L.oracle_render(n, *[_ptr(a) for a in m], _ptr(feat), C, _ptr(P), _ptr(_elev(s)), _ptr(_rays(s)), guard,
                     nr, _ptr(sel_arr), _ptr(F), _ptr(T), _ptr(De), _ptr(Dm), _ptr(mg), _ptr(cnt))
-    out = {"F": F, "T": T, "marginal": mg.astype(bool), "count": cnt}
+    out = {"F": F, "T": T, "marginal": mg.astype(bool), "marginal_bits": mg, "count": cnt}
     if s.kind == "lidar":
         out.update({"range_exp": De, "range_med": Dm, "alpha": 1.0 - T})
     return out
 
 
-def render_backward(g: dict, s, gF, gT=None, gD=None, gA=None) -> dict:
-    """Gradients of sum(gF*F) + sum(gT*T) [+ sum(gD*range_exp) + sum(gA*alpha)]."""
+def render_backward(g: dict, s, gF, gT=None, gD=None, gA=None, sel=None) -> dict:
+    """Gradients of sum(gF*F) + sum(gT*T) [+ sum(gD*range_exp) + sum(gA*alpha)] over the
+    selected rays (None: all rays; the upstream arrays then hold one row per selected ray)."""
     L = lib()
     n = len(g["opacities"])
     m = _g(g)
@@ -221,8 +224,10 @@ def render_backward(g: dict, s, gF, gT=None, gD=None, gA=None) -> dict:
     out = {"d2": np.zeros((n, 10)), "features": np.zeros((n, C)), "means": np.zeros((n, 3)),
            "scales": np.zeros((n, 3)), "quats": np.zeros((n, 4)), "opacities": np.zeros(n),
            "velocities": np.zeros((n, 3))}
+    sel_arr = None if sel is None else np.ascontiguousarray(sel, dtype=np.int64)
     L.oracle_render_backward(n, *[_ptr(a) for a in m], _ptr(feat), C, _ptr(P), _ptr(_elev(s)), _ptr(_rays(s)),
-                             _ptr(_f32(gF)), _ptr(_f32(gT)), _ptr(_f32(gD)), _ptr(_f32(gA)), _ptr(out["d2"]),
+                             0 if sel_arr is None else len(sel_arr), _ptr(sel_arr),
+                             _ptr(_f64(gF)), _ptr(_f64(gT)), _ptr(_f64(gD)), _ptr(_f64(gA)), _ptr(out["d2"]),
                              _ptr(out["features"]), _ptr(out["means"]), _ptr(out["scales"]), _ptr(out["quats"]),
                              _ptr(out["opacities"]), _ptr(out["velocities"]))
     return out

@@ -181,6 +181,7 @@ static int camera_rect(const double *P, const double *rec, double extra, int rec
     int tw = (int)P[P_TW], th = (int)P[P_TH];
     int ntx = ((int)W + tw - 1) / tw, nty = ((int)H + th - 1) / th;
     double ea = rec[R_EXA] + extra, eb = rec[R_EXB] + extra;
+    if (ea < 0 || eb < 0) { rect[0] = rect[1] = rect[2] = rect[3] = 0; return 0; }
     double xl = (rec[R_MA] - ea) / tw, xh = (rec[R_MA] + ea) / tw;
     double yl = (rec[R_MB] - eb) / th, yh = (rec[R_MB] + eb) / th;
     double gx = guard / tw, gy = guard / th;
@@ -200,11 +201,12 @@ static int camera_rect(const double *P, const double *rec, double extra, int rec
  * ------------------------------------------------------------------------------- */
 static int project_camera(const double *P, const double *mean, const double *scale, const double *quat,
                           double opac, const double *vel, proj_state *st, double *rec, int rect[4],
-                          int orect[4], double guard_px, int *marg) {
+                          int orect[4], int irect[4], double guard_px, int *marg) {
     common_state(P, mean, scale, quat, vel, st);
     memset(rec, 0, sizeof(double) * REC);
-    for (int k = 0; k < 4; k++) rect[k] = orect[k] = 0;
+    for (int k = 0; k < 4; k++) rect[k] = orect[k] = irect[k] = 0;
     *marg = 0;
+    int cull_marg = 0;
     double x = st->m[0], y = st->m[1], z = st->m[2];
     double nearp = P[P_NEAR];
     if (fabs(z - nearp) <= 1e-6 * fmax(fabs(nearp), 1e-3)) *marg = 1;
@@ -225,7 +227,7 @@ static int project_camera(const double *P, const double *mean, const double *sca
     if (!cov2d(st, P[P_EPS], cv)) return 0;
     double A = cv[0], B = cv[1], C = cv[2], comp = cv[3], det1 = cv[4];
     double op = opac * comp;
-    if (fabs(op - ALPHA_MIN) <= 5e-5 * ALPHA_MIN) *marg = 1;
+    if (fabs(op - ALPHA_MIN) <= 5e-5 * ALPHA_MIN) cull_marg = 1;
     rec[R_MA] = fx * ux + P[P_CX];
     rec[R_MB] = fy * uy + P[P_CY];
     rec[R_CA] = C / det1; rec[R_CB] = -B / det1; rec[R_CC] = A / det1;
@@ -242,7 +244,12 @@ static int project_camera(const double *P, const double *mean, const double *sca
     rec[R_EXA] = 3.0 * sqrt(A) + fabs(rec[R_VA]) * tspan;
     rec[R_EXB] = 3.0 * sqrt(C) + fabs(rec[R_VB]) * tspan;
     if (camera_rect(P, rec, 0.0, rect, guard_px)) *marg = 1;
-    if (*marg) camera_rect(P, rec, guard_px, orect, 0.0);
+    if (cull_marg) *marg = 1;
+    if (*marg) {
+        camera_rect(P, rec, guard_px, orect, 0.0);
+        /* tiles inside the shrunk box belong to the Gaussian whatever the rounding */
+        if (!cull_marg) camera_rect(P, rec, -guard_px, irect, 0.0);
+    }
     if (op < ALPHA_MIN) return 0;
     return rect[2] > rect[0] && rect[3] > rect[1];
 }
@@ -278,6 +285,8 @@ static int lidar_rect(const double *P, const double *elev, const double *rec, do
     int mphi = (naz + taz - 1) / taz, mw = nb / tel;
     double wphi = taz * P[P_AZRES], phimax = mphi * wphi;
     double ea = rec[R_EXA] + extra, eb = rec[R_EXB] + extra;
+    rect[0] = rect[1] = rect[2] = rect[3] = 0;
+    if (ea < 0 || eb < 0) return 0;
     double plo = rec[R_MA] - ea, phi_hi = rec[R_MA] + ea;
     double olo = rec[R_MB] - eb, ohi = rec[R_MB] + eb;
     double bnd[1025];
@@ -313,11 +322,12 @@ static int lidar_rect(const double *P, const double *elev, const double *rec, do
  * ------------------------------------------------------------------------------- */
 static int project_lidar(const double *P, const double *elev, const double *mean, const double *scale,
                          const double *quat, double opac, const double *vel, proj_state *st, double *rec,
-                         int rect[4], int orect[4], double guard_rad, int *marg) {
+                         int rect[4], int orect[4], int irect[4], double guard_rad, int *marg) {
     common_state(P, mean, scale, quat, vel, st);
     memset(rec, 0, sizeof(double) * REC);
-    for (int k = 0; k < 4; k++) rect[k] = orect[k] = 0;
+    for (int k = 0; k < 4; k++) rect[k] = orect[k] = irect[k] = 0;
     *marg = 0;
+    int cull_marg = 0;
     double x = st->m[0], y = st->m[1], z = st->m[2];
     double rho2 = x * x + y * y, rho = sqrt(rho2), r2 = rho2 + z * z, r = sqrt(r2);
     double rmin = P[P_RMIN];
@@ -337,7 +347,7 @@ static int project_lidar(const double *P, const double *elev, const double *mean
     if (!cov2d(st, P[P_LEPS], cv)) return 0;
     double A = cv[0], B = cv[1], C = cv[2], comp = cv[3], det1 = cv[4];
     double op = opac * comp;
-    if (fabs(op - ALPHA_MIN) <= 5e-5 * ALPHA_MIN) *marg = 1;
+    if (fabs(op - ALPHA_MIN) <= 5e-5 * ALPHA_MIN) cull_marg = 1;
     rec[R_MA] = phi; rec[R_MB] = om;
     rec[R_CA] = C / det1; rec[R_CB] = -B / det1; rec[R_CC] = A / det1;
     rec[R_OP] = op;
@@ -351,7 +361,12 @@ static int project_lidar(const double *P, const double *elev, const double *mean
     rec[R_EXA] = 3.0 * sqrt(A) + fabs(rec[R_VA]) * half;
     rec[R_EXB] = 3.0 * sqrt(C) + fabs(rec[R_VB]) * half;
     int nt = lidar_rect(P, elev, rec, 0.0, rect, guard_rad, marg);
-    if (*marg) { int dummy = 0; lidar_rect(P, elev, rec, guard_rad, orect, 0.0, &dummy); }
+    if (cull_marg) *marg = 1;
+    if (*marg) {
+        int dummy = 0;
+        lidar_rect(P, elev, rec, guard_rad, orect, 0.0, &dummy);
+        if (!cull_marg) lidar_rect(P, elev, rec, -guard_rad, irect, 0.0, &dummy);
+    }
     if (op < ALPHA_MIN) return 0;
     return nt > 0;
 }
@@ -380,24 +395,24 @@ static int rect_contains(const double *P, const int rect[4], int tx, int ty) {
 
 static int project_one(const double *P, const double *elev, int64_t i, const double *means, const double *scales,
                        const double *quats, const double *opac, const double *vel, proj_state *st, double *rec,
-                       int rect[4], int orect[4], double guard, int *marg) {
+                       int rect[4], int orect[4], int irect[4], double guard, int *marg) {
     if ((int)P[P_KIND] == 0)
         return project_camera(P, means + 3 * i, scales + 3 * i, quats + 4 * i, opac[i], vel ? vel + 3 * i : NULL,
-                              st, rec, rect, orect, guard, marg);
+                              st, rec, rect, orect, irect, guard, marg);
     return project_lidar(P, elev, means + 3 * i, scales + 3 * i, quats + 4 * i, opac[i], vel ? vel + 3 * i : NULL,
-                         st, rec, rect, orect, guard, marg);
+                         st, rec, rect, orect, irect, guard, marg);
 }
 
 /* Public: per-Gaussian projection for one sensor. */
 int oracle_project(int64_t n, const double *means, const double *scales, const double *quats, const double *opac,
                    const double *vel, const double *P, const double *elev, double guard, double *rec, int32_t *rect,
-                   int32_t *orect, int32_t *ntiles, uint8_t *visible, uint8_t *marginal) {
+                   int32_t *orect, int32_t *irect, int32_t *ntiles, uint8_t *visible, uint8_t *marginal) {
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) {
         proj_state st;
-        int rc[4], orc[4], mg;
-        int vis = project_one(P, elev, i, means, scales, quats, opac, vel, &st, rec + REC * i, rc, orc, guard, &mg);
-        for (int k = 0; k < 4; k++) { rect[4 * i + k] = rc[k]; orect[4 * i + k] = orc[k]; }
+        int rc[4], orc[4], irc[4], mg;
+        int vis = project_one(P, elev, i, means, scales, quats, opac, vel, &st, rec + REC * i, rc, orc, irc, guard, &mg);
+        for (int k = 0; k < 4; k++) { rect[4 * i + k] = rc[k]; orect[4 * i + k] = orc[k]; irect[4 * i + k] = irc[k]; }
         ntiles[i] = vis ? (rc[2] - rc[0]) * (rc[3] - rc[1]) : 0;
         visible[i] = (uint8_t)vis;
         marginal[i] = (uint8_t)mg;
@@ -495,7 +510,8 @@ static double wrap_pi(double d) { return d - TWO_PI * floor((d + M_PI) / TWO_PI)
 
 /* Render one ray: returns the number of blended Gaussians (written to cb if non-null). */
 static int render_ray(const double *P, const double *elev, const double *rays, int64_t n, const double *rec,
-                      const int32_t *rect, const int32_t *orect, const uint8_t *vis, const uint8_t *gmarg,
+                      const int32_t *rect, const int32_t *orect, const int32_t *irect, const uint8_t *vis,
+                      const uint8_t *gmarg,
                       const double *feat, int C,
                       int64_t k, cand_t *cands, double *F, double *Tout, double *Dexp, double *Dmed,
                       int *marginal, contrib_t *cb, int cb_cap) {
@@ -505,7 +521,16 @@ static int render_ray(const double *P, const double *elev, const double *rays, i
     ray_setup(P, elev, rays, k, &tx, &ty, &pa, &pb, &t);
     int nc = 0, mg = 0;
     for (int64_t i = 0; i < n; i++) {
-        if (gmarg && gmarg[i] && rect_contains(P, orect + 4 * i, tx, ty)) mg = 1;
+        /* a marginal Gaussian's membership is uncertain between its inner and outer boxes;
+         * it matters only where it would be blended (alpha at or above the threshold) */
+        if (gmarg && gmarg[i] && rect_contains(P, orect + 4 * i, tx, ty) &&
+            !rect_contains(P, irect + 4 * i, tx, ty)) {
+            const double *g = rec + REC * i;
+            double dx = pa - (g[R_MA] + g[R_VA] * t), dy = pb - (g[R_MB] + g[R_VB] * t);
+            if ((int)P[P_KIND] == 1) dx = wrap_pi(dx);
+            double sig = 0.5 * (g[R_CA] * dx * dx + g[R_CC] * dy * dy) + g[R_CB] * dx * dy;
+            if (sig >= 0 && g[R_OP] * exp(-sig) >= ALPHA_MIN * (1 - 1e-4)) mg |= 1;
+        }
         if (!vis[i]) continue;
         if (!rect_contains(P, rect + 4 * i, tx, ty)) continue;
         cands[nc].id = (int32_t)i;
@@ -526,21 +551,22 @@ static int render_ray(const double *P, const double *elev, const double *rays, i
         if (sig < 0) continue;
         double G = exp(-sig);
         double a = g[R_OP] * G;
-        if (fabs(a - ALPHA_MIN) <= 5e-5 * ALPHA_MIN || fabs(a - ALPHA_MAX) <= 5e-5 * ALPHA_MAX) mg = 1;
+        if (fabs(a - ALPHA_MIN) <= 5e-5 * ALPHA_MIN) mg |= 2;
+        if (fabs(a - ALPHA_MAX) <= 5e-5 * ALPHA_MAX) mg |= 4;
         int clamped = 0;
         if (a > ALPHA_MAX) { a = ALPHA_MAX; clamped = 1; }
         if (a < ALPHA_MIN) continue;
         /* two blended Gaussians this close in depth may swap order in FP32 */
-        if (cands[j].depth - last_depth < 1e-6 * cands[j].depth) mg = 1;
+        if (cands[j].depth - last_depth < 1e-6 * cands[j].depth) mg |= 32;
         last_depth = cands[j].depth;
         double Tn = T * (1 - a);
-        if (fabs(Tn - T_EPS) <= 2e-3 * T_EPS) mg = 1;
+        if (fabs(Tn - T_EPS) <= 2e-3 * T_EPS) mg |= 8;
         if (Tn < T_EPS) break;
         double rrs = g[R_DEPTH] + g[R_VR] * t; /* r_rs = r + v_r t_l */
         const double *f = feat + (int64_t)C * cands[j].id;
         for (int c = 0; c < C; c++) F[c] += f[c] * a * T;
         de += rrs * a * T;
-        if (fabs(Tn - 0.5) <= 1e-3 * 0.5) mg = 1;
+        if (fabs(Tn - 0.5) <= 1e-3 * 0.5) mg |= 16;
         if (!med && Tn < 0.5) { dm = rrs; med = 1; }
         if (cb && nb < cb_cap) {
             contrib_t *e = cb + nb;
@@ -562,14 +588,14 @@ static int render_ray(const double *P, const double *elev, const double *rays, i
  * every tile an FP32 evaluation could assign them to. */
 static void project_all(int64_t n, const double *means, const double *scales, const double *quats, const double *opac,
                         const double *vel, const double *P, const double *elev, double guard, double *rec,
-                        int32_t *rect, int32_t *orect, uint8_t *vis, uint8_t *marg) {
+                        int32_t *rect, int32_t *orect, int32_t *irect, uint8_t *vis, uint8_t *marg) {
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; i++) {
         proj_state st;
-        int rc[4], orc[4], mg;
-        vis[i] = (uint8_t)project_one(P, elev, i, means, scales, quats, opac, vel, &st, rec + REC * i, rc, orc, guard,
-                                      &mg);
-        for (int q = 0; q < 4; q++) { rect[4 * i + q] = rc[q]; orect[4 * i + q] = orc[q]; }
+        int rc[4], orc[4], irc[4], mg;
+        vis[i] = (uint8_t)project_one(P, elev, i, means, scales, quats, opac, vel, &st, rec + REC * i, rc, orc, irc,
+                                      guard, &mg);
+        for (int q = 0; q < 4; q++) { rect[4 * i + q] = rc[q]; orect[4 * i + q] = orc[q]; irect[4 * i + q] = irc[q]; }
         marg[i] = (uint8_t)mg;
     }
 }
@@ -589,9 +615,10 @@ int oracle_render(int64_t n, const double *means, const double *scales, const do
     double *rec = (double *)malloc(sizeof(double) * REC * (size_t)(n > 0 ? n : 1));
     int32_t *rect = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)(n > 0 ? n : 1));
     int32_t *orect = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)(n > 0 ? n : 1));
+    int32_t *irect = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)(n > 0 ? n : 1));
     uint8_t *vis = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
     uint8_t *marg = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
-    project_all(n, means, scales, quats, opac, vel, P, elev, guard, rec, rect, orect, vis, marg);
+    project_all(n, means, scales, quats, opac, vel, P, elev, guard, rec, rect, orect, irect, vis, marg);
     int64_t nr = sel ? n_sel : sensor_rays(P);
 #pragma omp parallel
     {
@@ -601,7 +628,7 @@ int oracle_render(int64_t n, const double *means, const double *scales, const do
             int64_t k = sel ? sel[j] : j;
             double T, de, dm;
             int mg;
-            int cnt = render_ray(P, elev, rays, n, rec, rect, orect, vis, marg, feat, C, k, cands,
+            int cnt = render_ray(P, elev, rays, n, rec, rect, orect, irect, vis, marg, feat, C, k, cands,
                                  outF + (int64_t)C * j, &T, &de, &dm, &mg, NULL, 0);
             outT[j] = T;
             if (outDexp) outDexp[j] = de;
@@ -611,7 +638,7 @@ int oracle_render(int64_t n, const double *means, const double *scales, const do
         }
         free(cands);
     }
-    free(rec); free(rect); free(orect); free(vis); free(marg);
+    free(rec); free(rect); free(orect); free(irect); free(vis); free(marg);
     return 0;
 }
 
@@ -732,8 +759,8 @@ static void projection_backward(const double *P, const double *elev, int64_t i, 
                                 double *dvel) {
     proj_state st;
     double rec[REC];
-    int rc[4], orc[4], mg;
-    if (!project_one(P, elev, i, means, scales, quats, opac, vel, &st, rec, rc, orc, 0.0, &mg)) return;
+    int rc[4], orc[4], irc[4], mg;
+    if (!project_one(P, elev, i, means, scales, quats, opac, vel, &st, rec, rc, orc, irc, 0.0, &mg)) return;
     int lidar = (int)P[P_KIND] == 1;
     const double *J = st.J;
     double dm[3] = {0, 0, 0};
@@ -818,24 +845,26 @@ static void projection_backward(const double *P, const double *elev, int64_t i, 
     for (int k = 0; k < 4; k++) dquat[4 * i + k] += (dqh[k] - qh[k] * dot) / st.qn;
 }
 
-/* Public: full backward for one sensor.  Upstream gradients for every ray:
+/* Public: full backward for one sensor over the selected rays (sel == NULL: all rays).
+ * Upstream gradients, one entry per selected ray:
  * gF[nrays][C], gT[nrays] (d/d final transmittance), gD[nrays] (expected range, lidar
  * only, may be NULL), gA[nrays] (accumulated alpha = 1 - T, lidar, may be NULL).
  * Accumulates (+=) into d2 (n x 10, projected-quantity gradients), dfeat and the
  * parameter gradients. */
 int oracle_render_backward(int64_t n, const double *means, const double *scales, const double *quats,
                            const double *opac, const double *vel, const double *feat, int C, const double *P,
-                           const double *elev, const double *rays, const double *gF, const double *gT, const double *gD,
-                           const double *gA, double *d2, double *dfeat, double *dmean, double *dscale,
-                           double *dquat, double *dopac, double *dvel) {
+                           const double *elev, const double *rays, int64_t n_sel, const int64_t *sel,
+                           const double *gF, const double *gT, const double *gD, const double *gA, double *d2,
+                           double *dfeat, double *dmean, double *dscale, double *dquat, double *dopac, double *dvel) {
     if (C > 64) return -1;
     double *rec = (double *)malloc(sizeof(double) * REC * (size_t)(n > 0 ? n : 1));
     int32_t *rect = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)(n > 0 ? n : 1));
     int32_t *orect = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)(n > 0 ? n : 1));
+    int32_t *irect = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)(n > 0 ? n : 1));
     uint8_t *vis = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
     uint8_t *marg = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
-    project_all(n, means, scales, quats, opac, vel, P, elev, 0.0, rec, rect, orect, vis, marg);
-    int64_t nr = sensor_rays(P);
+    project_all(n, means, scales, quats, opac, vel, P, elev, 0.0, rec, rect, orect, irect, vis, marg);
+    int64_t nr = sel ? n_sel : sensor_rays(P);
     double *loc2 = (double *)calloc((size_t)(n > 0 ? n : 1) * 10, sizeof(double));
 #pragma omp parallel
     {
@@ -843,13 +872,14 @@ int oracle_render_backward(int64_t n, const double *means, const double *scales,
         contrib_t *cb = (contrib_t *)malloc(sizeof(contrib_t) * (size_t)(n > 0 ? n : 1));
         double F[64];
 #pragma omp for schedule(dynamic, 16)
-        for (int64_t k = 0; k < nr; k++) {
+        for (int64_t j = 0; j < nr; j++) {
+            const int64_t k = sel ? sel[j] : j;   /* ray index; upstream gradients are indexed by j */
             double T, de, dm;
-            int nb = render_ray(P, elev, rays, n, rec, rect, orect, vis, NULL, feat, C, k, cands, F, &T, &de, &dm,
+            int nb = render_ray(P, elev, rays, n, rec, rect, orect, irect, vis, NULL, feat, C, k, cands, F, &T, &de, &dm,
                                 NULL, cb, (int)(n > 0 ? n : 1));
-            double gt = gT ? gT[k] : 0;
-            if (gA) gt -= gA[k]; /* alpha_acc = 1 - T */
-            ray_backward(P, C, feat, rec, cb, nb, T, gF + (int64_t)C * k, gt, gD ? gD[k] : 0, loc2, dfeat);
+            double gt = gT ? gT[j] : 0;
+            if (gA) gt -= gA[j]; /* alpha_acc = 1 - T */
+            ray_backward(P, C, feat, rec, cb, nb, T, gF + (int64_t)C * j, gt, gD ? gD[j] : 0, loc2, dfeat);
         }
         free(cands); free(cb);
     }
@@ -860,7 +890,7 @@ int oracle_render_backward(int64_t n, const double *means, const double *scales,
         projection_backward(P, elev, i, means, scales, quats, opac, vel, loc2 + 10 * i, dmean, dscale, dquat, dopac,
                             dvel);
     }
-    free(loc2); free(rec); free(rect); free(orect); free(vis); free(marg);
+    free(loc2); free(rec); free(rect); free(orect); free(irect); free(vis); free(marg);
     return 0;
 }
 
@@ -881,12 +911,12 @@ int oracle_jacobian(const double *mean, const double *scale, const double *quat,
                     const double *elev, double *J, double *Sc, double *w) {
     proj_state st;
     double rec[REC];
-    int rc[4], orc[4], mg;
+    int rc[4], orc[4], irc[4], mg;
     int vis;
     if ((int)P[P_KIND] == 0)
-        vis = project_camera(P, mean, scale, quat, opac, NULL, &st, rec, rc, orc, 0.0, &mg);
+        vis = project_camera(P, mean, scale, quat, opac, NULL, &st, rec, rc, orc, irc, 0.0, &mg);
     else
-        vis = project_lidar(P, elev, mean, scale, quat, opac, NULL, &st, rec, rc, orc, 0.0, &mg);
+        vis = project_lidar(P, elev, mean, scale, quat, opac, NULL, &st, rec, rc, orc, irc, 0.0, &mg);
     memcpy(J, st.J, sizeof(double) * 9);
     memcpy(Sc, st.Sc, sizeof(double) * 9);
     memcpy(w, st.w, sizeof(double) * 3);

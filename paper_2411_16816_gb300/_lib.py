@@ -81,9 +81,8 @@ def load(build_if_missing: bool = True):
     L.splat_bin_sort.argtypes = [c_int64, c_int32, SE, splat_projected, c_int64, splat_bins, c_void_p, c_size_t,
                                  c_void_p]
     L.splat_bin_sort_backward.argtypes = []
-    L.splat_render_camera.argtypes = [G, c_int32, SE, splat_projected, splat_bins, c_void_p, c_void_p, c_void_p,
-                                      c_void_p]
-    L.splat_render_lidar.argtypes = [G, c_int32, SE, splat_projected, splat_bins] + [c_void_p] * 7
+    L.splat_render_camera.argtypes = [G, c_int32, SE, splat_projected, splat_bins] + [c_void_p] * 5
+    L.splat_render_lidar.argtypes = [G, c_int32, SE, splat_projected, splat_bins] + [c_void_p] * 8
     L.splat_render_camera_backward.argtypes = [G, c_int32, SE, splat_projected, splat_bins] + [c_void_p] * 7
     L.splat_render_lidar_backward.argtypes = [G, c_int32, SE, splat_projected, splat_bins] + [c_void_p] * 8
     L.splat_project_backward.argtypes = [G, c_int32, SE, splat_projected] + [c_void_p] * 7

@@ -236,7 +236,7 @@ static splat_status render_common(const splat_gaussians* g, int32_t n_sensors, c
 
 splat_status splat_render_camera(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
                                  splat_projected proj, splat_bins bins, float* out_feat, float* out_T,
-                                 int32_t* out_last, void* stream) {
+                                 int32_t* out_last, uint64_t* evaluated, void* stream) {
     Frame fr;
     int tw, th;
     splat_status st = render_common(g, n_sensors, sensors, proj, bins, fr, false, tw, th);
@@ -246,7 +246,7 @@ splat_status splat_render_camera(const splat_gaussians* g, int32_t n_sensors, co
     if ((g->channels & 3) == 0 && !aligned16(out_feat)) return fail(SPLAT_ERR_INVALID_ARG, "out_feat misaligned");
     RasterIn in{(const float4*)proj.rec, bins.isect_ids, (const int2*)bins.tile_ranges, g->features, g->n,
                 g->channels};
-    RasterOut out{out_feat, out_T, out_last, nullptr, nullptr, nullptr};
+    RasterOut out{out_feat, out_T, out_last, nullptr, nullptr, nullptr, (unsigned long long*)evaluated};
     if (!launch_raster_fwd(false, g->channels, tw, th, fr, fr.n_cam_blocks, in, out, (cudaStream_t)stream))
         return fail(SPLAT_ERR_INVALID_ARG, "unsupported camera configuration");
     return check_launch("splat_render_camera");
@@ -255,7 +255,7 @@ splat_status splat_render_camera(const splat_gaussians* g, int32_t n_sensors, co
 splat_status splat_render_lidar(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
                                 splat_projected proj, splat_bins bins, float* out_feat, float* out_range_exp,
                                 float* out_range_med, float* out_alpha, float* out_T, int32_t* out_last,
-                                void* stream) {
+                                uint64_t* evaluated, void* stream) {
     Frame fr;
     int tw, th;
     splat_status st = render_common(g, n_sensors, sensors, proj, bins, fr, true, tw, th);
@@ -266,7 +266,8 @@ splat_status splat_render_lidar(const splat_gaussians* g, int32_t n_sensors, con
     if ((g->channels & 3) == 0 && !aligned16(out_feat)) return fail(SPLAT_ERR_INVALID_ARG, "out_feat misaligned");
     RasterIn in{(const float4*)proj.rec, bins.isect_ids, (const int2*)bins.tile_ranges, g->features, g->n,
                 g->channels};
-    RasterOut out{out_feat, out_T, out_last, out_range_exp, out_range_med, out_alpha};
+    RasterOut out{out_feat, out_T, out_last, out_range_exp, out_range_med, out_alpha,
+                  (unsigned long long*)evaluated};
     if (!launch_raster_fwd(true, g->channels, tw, th, fr, fr.n_lid_blocks, in, out, (cudaStream_t)stream))
         return fail(SPLAT_ERR_INVALID_ARG, "unsupported lidar configuration");
     return check_launch("splat_render_lidar");

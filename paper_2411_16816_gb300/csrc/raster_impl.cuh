@@ -122,6 +122,7 @@ __device__ __forceinline__ bool eval_alpha(const float4 g0, const float4 g1, con
 struct FwdState {
     float T;
     int last;
+    int evals;   // list entries examined (blended, skipped or terminating)
     float de, dm;
     bool med, done;
 };
@@ -133,6 +134,7 @@ __device__ __forceinline__ void forward_tile(Stage<CM, B, LIDAR>& sm, const Rast
                                              FwdState& st, float* F) {
     st.T = 1.f;
     st.last = 0;
+    st.evals = 0;
     st.de = 0.f;
     st.dm = 0.f;
     st.med = false;
@@ -147,6 +149,7 @@ __device__ __forceinline__ void forward_tile(Stage<CM, B, LIDAR>& sm, const Rast
             for (int k = 0; k < nb; k++) {
                 float dx, dy, G, a;
                 bool cl;
+                st.evals++;
                 if (!eval_alpha<LIDAR>(sm.g0[k], sm.g1[k], r, dx, dy, G, a, cl)) continue;
                 const float Tn = st.T * (1.f - a);
                 if (Tn < kTEps) {
@@ -185,6 +188,12 @@ __global__ void __launch_bounds__(TW* TH) k_raster_fwd(const __grid_constant__ F
     for (int c = 0; c < CM; c++) F[c] = 0.f;
     FwdState st;
     forward_tile<CM, B, LIDAR, true>(sm, in, r, range, st, F);
+    if (out.evaluated) {
+        unsigned long long e = (unsigned long long)st.evals;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(out.evaluated, e);
+    }
     if (!r.inside) return;
     const int C = in.C;
     float* fo = out.feat + r.o * C;

@@ -44,6 +44,7 @@ struct RasterOut {
     float* range_exp;   // lidar
     float* range_med;   // lidar
     float* alpha;       // lidar
+    unsigned long long* evaluated;  // optional: number of (ray, Gaussian) pairs examined
 };
 
 struct RasterGrad {

@@ -168,15 +168,20 @@ class Frame:
             out["lid_last"] = torch.empty(R, dtype=torch.int32, device=dev) if keep_state else None
         return out
 
-    def rasterize(self, cg, out: dict, stream=None):
+    def rasterize(self, cg, out: dict, stream=None, evaluated: torch.Tensor | None = None):
+        """Camera and lidar raster launches.  `evaluated` (optional int64[2] device tensor)
+        accumulates the examined (ray, Gaussian) pairs of the camera and lidar launch."""
         st = _stream(stream)
+        ev_c = ev_l = None
+        if evaluated is not None:
+            ev_c, ev_l = evaluated[0:1], evaluated[1:2]
         if self.cam_idx:
             L.call("splat_render_camera", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
-                   self.c_bins(), _vp(out["cam_feat"]), _vp(out["cam_T"]), _vp(out.get("cam_last")), st)
+                   self.c_bins(), _vp(out["cam_feat"]), _vp(out["cam_T"]), _vp(out.get("cam_last")), _vp(ev_c), st)
         if self.lid_idx:
             L.call("splat_render_lidar", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
                    self.c_bins(), _vp(out["lid_feat"]), _vp(out["lid_range_exp"]), _vp(out["lid_range_med"]),
-                   _vp(out["lid_alpha"]), _vp(out.get("lid_T")), _vp(out.get("lid_last")), st)
+                   _vp(out["lid_alpha"]), _vp(out.get("lid_T")), _vp(out.get("lid_last")), _vp(ev_l), st)
 
     def forward(self, g: dict, keep_state: bool = True, check: bool = True, out: dict | None = None,
                 stream=None) -> dict:

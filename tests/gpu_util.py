@@ -69,14 +69,14 @@ def upstream(fr, sensors, g, seed, with_T=True):
         ref = oracle.render(g, s)
         keep = (~ref["marginal"]).astype(np.float64)
         n = s.n_rays
-        gF = rng.normal(size=(n, C)) * keep[:, None]
-        gT = rng.normal(size=n) * keep if with_T else np.zeros(n)
+        gF = (rng.normal(size=(n, C)) * keep[:, None]).astype(np.float32)
+        gT = (rng.normal(size=n) * keep).astype(np.float32) if with_T else np.zeros(n, np.float32)
         if s.kind == "camera":
             cam_F.append(gF)
             cam_T.append(gT)
             per.append({"gF": gF, "gT": gT})
         else:
-            gD = rng.normal(size=n) * keep * 0.05
+            gD = (rng.normal(size=n) * keep * 0.05).astype(np.float32)
             lid_F.append(gF)
             lid_D.append(gD)
             lid_A.append(gT)
