@@ -36,10 +36,10 @@ L2_BYTES = 129 * 1024 * 1024
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
-    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=10)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", choices=["driving", "lidar_heavy"], default="driving")
+    p.add_argument("--workload", choices=["driving", "lidar_heavy", "profile"], default="driving")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--profile-only", action="store_true", help="a few untimed steps (for ncu captures)")
     return p.parse_args()
@@ -53,6 +53,12 @@ def workload(name):
                             "L1 vs seeded target render",
                 "gaussians": len(g["opacities"]), "rays_per_step": sum(s.n_rays for s in sensors),
                 "cameras": "6x1920x1080", "lidar": "32x1080"}
+    elif name == "profile":
+        # the driving scene seen by one camera and the lidar: a small case for ncu captures
+        g, sensors = scenes.driving_frame()
+        sensors = [sensors[0], sensors[-1]]
+        desc = {"workload": "profiling case: driving scene, 1 x 1920x1080 camera + 32x1080 lidar",
+                "gaussians": len(g["opacities"]), "rays_per_step": sum(s.n_rays for s in sensors)}
     else:
         g, sensors = scenes.lidar_heavy_frame()
         desc = {"workload": "lidar-heavy frame: 1M Gaussians, 128-beam non-uniform x 2048 lidar, 100 ms sweep",

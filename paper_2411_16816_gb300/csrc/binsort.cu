@@ -176,7 +176,10 @@ struct HistOut {
 
 // Each warp ranks 512 consecutive keys in order (32 at a time, __match_any_sync groups
 // equal digits); warps' digit counts are then scanned in warp order, so the block's
-// ranking -- and with the digit-major global scan, the whole pass -- is stable.
+// ranking -- and with the digit-major global scan, the whole pass -- is stable.  The
+// block first writes its keys in sorted order to shared memory and then copies each
+// digit's run to its global position, so consecutive threads write consecutive
+// addresses.
 __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* __restrict__ kin,
                                                                 const uint32_t* __restrict__ vin,
                                                                 uint32_t* __restrict__ kout,
@@ -187,12 +190,18 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
                                                                 int64_t nblocks) {
     constexpr int kWarps = kSortThreads / 32;
     __shared__ uint32_t wh[kWarps][256];
-    __shared__ uint32_t bd[256];
+    __shared__ uint32_t bd[256];      // global start of each digit's run for this block
+    __shared__ uint32_t dstart[256];  // start of each digit's run within the block
+    __shared__ uint32_t sk[kSortTile];
+    __shared__ uint32_t sv[kSortTile];
+    __shared__ int64_t scan_sm[9];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int k = threadIdx.x; k < kWarps * 256; k += kSortThreads) (&wh[0][0])[k] = 0;
     const int64_t count = eff_count(count_ptr, max_count, capacity);
-    const int64_t base = (int64_t)blockIdx.x * kSortTile + (int64_t)warp * (kSortItems * 32);
-    if (base - (int64_t)warp * (kSortItems * 32) >= count) return;  // whole block empty (uniform)
+    const int64_t block0 = (int64_t)blockIdx.x * kSortTile;
+    if (block0 >= count) return;  // whole block empty (uniform)
+    const int nvalid = (int)min((int64_t)kSortTile, count - block0);
+    const int64_t base = block0 + (int64_t)warp * (kSortItems * 32);
     __syncthreads();
     uint32_t kk[kSortItems], vv[kSortItems], rr[kSortItems];
 #pragma unroll
@@ -210,6 +219,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
         __syncwarp();
     }
     __syncthreads();
+    uint32_t total;
     {
         const int d = threadIdx.x;  // 256 threads, one per digit
         uint32_t run = 0;
@@ -219,18 +229,29 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
             wh[w][d] = run;
             run += c;
         }
+        total = run;
         bd[d] = hist_scan[(int64_t)d * nblocks + blockIdx.x];
     }
+    const int64_t ds = block_exclusive_scan((int64_t)total, nullptr, scan_sm);
+    dstart[threadIdx.x] = (uint32_t)ds;
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < kSortItems; it++) {
         const int64_t idx = base + it * 32 + lane;
         if (idx < count) {
             const uint32_t d = (kk[it] >> shift) & 255u;
-            const uint32_t pos = bd[d] + wh[warp][d] + rr[it];
-            kout[pos] = kk[it];
-            vout[pos] = vv[it];
+            const uint32_t lp = dstart[d] + wh[warp][d] + rr[it];
+            sk[lp] = kk[it];
+            sv[lp] = vv[it];
         }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nvalid; i += kSortThreads) {
+        const uint32_t key = sk[i];
+        const uint32_t d = (key >> shift) & 255u;
+        const uint32_t pos = bd[d] + (uint32_t)i - dstart[d];
+        kout[pos] = key;
+        vout[pos] = sv[i];
     }
 }
 
@@ -278,45 +299,91 @@ struct EmitIn {
     __device__ int64_t operator()(int64_t j) const { return n_tiles[sorted_pairs[j]]; }
 };
 
-struct EmitOut {
-    const uint32_t* sorted_pairs;
-    const short4* rect;
-    int64_t n;
-    int64_t capacity;
-    uint32_t* keys;
-    uint32_t* vals;
+struct OffsetOut {  // exclusive prefix of the tile counts, in depth order
+    int64_t* offsets;
+    __device__ void operator()(int64_t j, int64_t prefix, int64_t) const { offsets[j] = prefix; }
+};
+
+struct EmitTables {
     int tile_base[kMaxSensors];
     int tiles_x[kMaxSensors];
     int is_lidar[kMaxSensors];
-    __device__ void operator()(int64_t j, int64_t prefix, int64_t cnt) const {
-        const uint32_t p = sorted_pairs[j];
+};
+
+constexpr int kEmitThreads = 256;
+constexpr int kEmitItems = 8;
+constexpr int kEmitTile = kEmitThreads * kEmitItems;  // output slots per block
+
+// Writes intersections [b*2048, (b+1)*2048): each block binary-searches the first
+// visible pair that owns one of its slots, stages the owners' offsets in shared memory
+// and every thread then writes one (tile, Gaussian) pair per slot it owns.  Work per
+// block is fixed whatever the size of the Gaussians, and the writes are contiguous.
+__global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restrict__ sorted_pairs,
+                                                      const int64_t* __restrict__ offsets,
+                                                      const int64_t* vis_count, const int64_t* n_isect,
+                                                      int64_t capacity, const short4* __restrict__ rect, int64_t n,
+                                                      const __grid_constant__ EmitTables tab,
+                                                      uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    __shared__ int64_t s_off[kEmitTile + 1];
+    __shared__ int64_t s_lo;
+    const int64_t total = *n_isect;
+    if (total > capacity) return;   // over capacity: write nothing
+    const int64_t o0 = (int64_t)blockIdx.x * kEmitTile;
+    if (o0 >= total) return;
+    const int64_t V = *vis_count;
+    const int64_t o1 = min(o0 + (int64_t)kEmitTile, total);
+    if (threadIdx.x == 0) {
+        // last j with offsets[j] <= o0 (exists: offsets[0] == 0)
+        int64_t lo = 0, hi = V - 1;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (offsets[mid] <= o0) lo = mid;
+            else hi = mid - 1;
+        }
+        s_lo = lo;
+    }
+    __syncthreads();
+    const int64_t jlo = s_lo;
+    // owners of this block's slots are jlo .. jlo + count - 1 with count <= kEmitTile
+    // (every visible pair owns at least one slot)
+    const int64_t nown = min((int64_t)kEmitTile, V - jlo);
+    for (int q = threadIdx.x; q < nown; q += kEmitThreads) s_off[q] = offsets[jlo + q];
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < kEmitItems; it++) {
+        const int64_t o = o0 + it * kEmitThreads + threadIdx.x;
+        if (o >= o1) break;
+        // last local owner with s_off <= o
+        int lo = 0, hi = (int)nown - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= o) lo = mid;
+            else hi = mid - 1;
+        }
+        const uint32_t p = sorted_pairs[jlo + lo];
         const int s = (int)(p / (uint64_t)n);
         const uint32_t i = (uint32_t)(p - (uint64_t)s * n);
         const short4 rc = rect[p];
-        const int tx = tiles_x[s], tb = tile_base[s];
         const int w = rc.z - rc.x;
-        int64_t o = prefix;
-        for (int ty = rc.y; ty < rc.w; ty++) {
-            for (int k = 0; k < w; k++, o++) {
-                if (o >= capacity) return;
-                int col = rc.x + k;
-                if (is_lidar[s] && col >= tx) col -= tx;
-                keys[o] = (uint32_t)(tb + ty * tx + col);
-                vals[o] = i;
-            }
-        }
-        (void)cnt;
+        const int q = (int)(o - s_off[lo]);
+        const int ty = rc.y + q / w;
+        int col = rc.x + q % w;
+        const int tx = tab.tiles_x[s];
+        if (tab.is_lidar[s] && col >= tx) col -= tx;
+        keys[o] = (uint32_t)(tab.tile_base[s] + ty * tx + col);
+        vals[o] = i;
     }
-};
+}
 
-__global__ void k_tile_ranges(const uint32_t* __restrict__ keys, const int64_t* count_ptr, int64_t capacity,
-                              int2* ranges) {
+__global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict__ keys, const int64_t* count_ptr,
+                                                      int64_t capacity, int2* ranges) {
     const int64_t count = eff_count(count_ptr, capacity, capacity);
-    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= count) return;
-    const uint32_t t = keys[j];
-    if (j == 0 || keys[j - 1] != t) ranges[t].x = (int)j;
-    if (j == count - 1 || keys[j + 1] != t) ranges[t].y = (int)(j + 1);
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < count;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t t = keys[j];
+        if (j == 0 || keys[j - 1] != t) ranges[t].x = (int)j;
+        if (j == count - 1 || keys[j + 1] != t) ranges[t].y = (int)(j + 1);
+    }
 }
 
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -337,6 +404,7 @@ BinWorkspace carve_workspace(void* base, int64_t pairs, int64_t capacity) {
     w.vvals[0] = (uint32_t*)take(4 * vp);
     w.vvals[1] = (uint32_t*)take(4 * vp);
     w.vis_count = (int64_t*)take(8);
+    w.offsets = (int64_t*)take(8 * vp);
     w.ikeys[0] = (uint32_t*)take(4 * cp);
     w.ikeys[1] = (uint32_t*)take(4 * cp);
     w.ivals_tmp = (uint32_t*)take(4 * cp);
@@ -373,23 +441,23 @@ void launch_bin_sort(const Frame& fr, int64_t n, const float4* rec, const short4
     // the result lands in buffer passes % 2: make that buffer the caller's isect_ids
     vals_buf[passes & 1] = isect_ids;
     vals_buf[(passes & 1) ^ 1] = w.ivals_tmp;
-    EmitOut eo{};
-    eo.sorted_pairs = sorted_pairs;
-    eo.rect = rect;
-    eo.n = n;
-    eo.capacity = capacity;
-    eo.keys = w.ikeys[0];
-    eo.vals = vals_buf[0];
+    device_scan(EmitIn{sorted_pairs, n_tiles}, OffsetOut{w.offsets}, pairs, w.vis_count, INT64_MAX, w.partials,
+                n_isect, st);
+    EmitTables tab{};
     for (int s = 0; s < fr.n_sensors; s++) {
-        eo.tile_base[s] = fr.s[s].tile_base;
-        eo.tiles_x[s] = fr.s[s].tiles_x;
-        eo.is_lidar[s] = fr.s[s].kind == SPLAT_SENSOR_LIDAR;
+        tab.tile_base[s] = fr.s[s].tile_base;
+        tab.tiles_x[s] = fr.s[s].tiles_x;
+        tab.is_lidar[s] = fr.s[s].kind == SPLAT_SENSOR_LIDAR;
     }
-    device_scan(EmitIn{sorted_pairs, n_tiles}, eo, pairs, w.vis_count, INT64_MAX, w.partials, n_isect, st);
+    const int64_t emit_blocks = (capacity + kEmitTile - 1) / kEmitTile;
+    if (emit_blocks > 0)
+        k_emit<<<(unsigned)emit_blocks, kEmitThreads, 0, st>>>(sorted_pairs, w.offsets, w.vis_count, n_isect, capacity,
+                                                               rect, n, tab, w.ikeys[0], vals_buf[0]);
     // 4. stable sort of the intersections by tile id
     radix_sort(w.ikeys, vals_buf, passes, capacity, n_isect, capacity, w.hist, w.partials, st);
     // 5. per-tile ranges
-    const int64_t blocks = (capacity + 255) / 256;
+    int64_t blocks = (capacity + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks > 0)
         k_tile_ranges<<<(unsigned)blocks, 256, 0, st>>>(w.ikeys[passes & 1], n_isect, capacity, tile_ranges);
 }

@@ -1,52 +1,77 @@
-// raster.cu -- tile rasterization of cameras and lidars, forward and backward.
+// raster_impl.cuh -- tile rasterization of cameras and lidars, forward and backward.
 //
-// Camera (paper Sec. 3.2 "Rasterization"): one CTA per tile, one thread per pixel, row
-// time t_pix = ((row + 0.5) / H - 0.5) t_rs (+ time offset) (Eq. t_pix), Gaussians
-// blended front to back (Eq. alpha blend) with the EWA-blurred alpha of Eq. (alpha) at the
-// rolling-shutter shifted mean of Eq. (delta).
+// Camera (paper Sec. 3.2 "Rasterization"): one CTA per tile, row time
+// t_pix = ((row + 0.5) / H - 0.5) t_rs (+ time offset) (Eq. t_pix), Gaussians blended front
+// to back (Eq. alpha blend) with the EWA-blurred alpha of Eq. (alpha) at the rolling-
+// shutter shifted mean of Eq. (delta).
 // Lidar (Sec. 3.3 "Rasterization", App. A.2): one CTA per lidar tile (N_phi azimuth bins x
-// N_omega beams), one thread per ray with its own (phi, omega, t); the expected range
-// blends r + v_r t and the median range is the rolling-shutter range of the first
-// Gaussian after which the transmittance is below 0.5.  Threads without a ray (the
-// ragged last azimuth column) only help stage Gaussians, as in App. A.2.
+// N_omega beams), each ray with its own (phi, omega, t); the expected range blends
+// r + v_r t and the median range is the rolling-shutter range of the first Gaussian
+// after which the transmittance is below 0.5.  Slots without a ray (the ragged last
+// azimuth column) only help stage Gaussians, as in App. A.2.
 //
-// Gaussians are staged through shared memory a batch of one-per-thread at a time; the
-// block stops as soon as every thread is done (__syncthreads_count vote).
-// The backward walks each tile's list back to front, rebuilding transmittance by
-// division, sums each Gaussian's gradient over the warp's 32 rays with shuffles and
-// issues one vector atomic per warp and Gaussian.  With `out_T`/`out_last` absent it first
-// recomputes them for its tile (no per-pixel forward state kept).
+// Each thread owns PX rays of the tile (rays t, t + NT, ... for NT = tile / PX threads),
+// so one shared-memory read of a Gaussian serves PX rays and, in the backward, one warp
+// reduction of a Gaussian's gradient covers 32 * PX rays.  Gaussians are staged through
+// shared memory a tile-sized batch at a time and the block stops once every ray is done
+// (__syncthreads_count vote).  The backward walks the list back to front, rebuilding the
+// transmittance by division, evaluates each (ray, Gaussian) term branch-free (a ray that
+// does not blend the Gaussian gets alpha = 0, which zeroes every term), sums the terms
+// over the warp with one transpose reduction, over the CTA in shared memory, and issues
+// one set of vector atomics per (tile, Gaussian).  With `out_T`/`out_last` absent it first
+// recomputes them for its tile (no per-ray forward state kept).
 #pragma once
 #include "types.cuh"
 
 namespace splat {
 
+// Rays per thread.  The backward takes two rays per thread for up to 16 channels, so one
+// warp reduction of a Gaussian's gradient covers 64 rays; the forward keeps one ray per
+// thread (its per-Gaussian cost is small and occupancy matters more); wide channel counts
+// keep one ray per thread for register room.
+template <int CM, bool BWD>
+struct RaysPerThread {
+    static constexpr int value = (BWD && CM <= 16) ? 2 : 1;
+};
+
 struct RayCtx {
     bool inside;
     float pa, pb, t;
     int64_t o;      // output index
-    int s;          // sensor
-    int gtile;
 };
 
-template <int TW, int TH, bool LIDAR>
-__device__ __forceinline__ RayCtx ray_setup(const Frame& fr) {
-    RayCtx r;
-    r.s = sensor_of_block(fr, blockIdx.x, LIDAR);
-    const SensorDev& S = fr.s[r.s];
+struct TileCtx {
+    int s;          // sensor
+    int gtile;      // global tile id
+    int tx, ty;     // tile coordinates
+};
+
+template <bool LIDAR>
+__device__ __forceinline__ TileCtx tile_setup(const Frame& fr) {
+    TileCtx c;
+    c.s = sensor_of_block(fr, blockIdx.x, LIDAR);
+    const SensorDev& S = fr.s[c.s];
     const int lt = blockIdx.x - S.block_base;
-    const int tx = lt % S.tiles_x, ty = lt / S.tiles_x;
-    r.gtile = S.tile_base + lt;
-    const int lx = threadIdx.x % TW, ly = threadIdx.x / TW;
+    c.tx = lt % S.tiles_x;
+    c.ty = lt / S.tiles_x;
+    c.gtile = S.tile_base + lt;
+    return c;
+}
+
+template <int TW, int TH, bool LIDAR>
+__device__ __forceinline__ RayCtx ray_setup(const Frame& fr, const TileCtx& tc, int p /* ray slot in tile */) {
+    RayCtx r;
+    const SensorDev& S = fr.s[tc.s];
+    const int lx = p % TW, ly = p / TW;
     if (!LIDAR) {
-        const int col = tx * TW + lx, row = ty * TH + ly;
+        const int col = tc.tx * TW + lx, row = tc.ty * TH + ly;
         r.inside = col < S.width && row < S.height;
         r.pa = col + 0.5f;
         r.pb = row + 0.5f;
         r.t = ((row + 0.5f) / (float)S.height - 0.5f) * S.rs + S.dt;
         r.o = (int64_t)S.ray_base + (int64_t)row * S.width + col;
     } else {
-        const int a = tx * TW + lx, b = ty * TH + ly;
+        const int a = tc.tx * TW + lx, b = tc.ty * TH + ly;
         r.inside = a < S.naz;
         r.o = (int64_t)S.ray_base + (int64_t)b * S.naz + a;
         if (r.inside) {
@@ -111,244 +136,356 @@ __device__ __forceinline__ bool eval_alpha(const float4 g0, const float4 g1, con
     dy = r.pb - (g0.y + g0.w * r.t);
     if (LIDAR) dx = wrap_pi(dx);
     const float sig = 0.5f * (g1.x * dx * dx + g1.z * dy * dy) + g1.y * dx * dy;
-    if (sig < 0.f) return false;
     G = __expf(-sig);
     const float a = g1.w * G;
     clamped = a > kAlphaMax;
     alpha = clamped ? kAlphaMax : a;
-    return alpha >= kAlphaMin;
+    return sig >= 0.f && alpha >= kAlphaMin;
 }
 
 struct FwdState {
     float T;
     int last;
-    int evals;   // list entries examined (blended, skipped or terminating)
     float de, dm;
     bool med, done;
 };
 
-// Front-to-back blend of the tile's list for this thread's ray.  F may be null when
-// only the transmittance and the last index are wanted (recomputation).
-template <int CM, int B, bool LIDAR, bool WANT_F>
-__device__ __forceinline__ void forward_tile(Stage<CM, B, LIDAR>& sm, const RasterIn& in, const RayCtx& r, int2 range,
-                                             FwdState& st, float* F) {
-    st.T = 1.f;
-    st.last = 0;
-    st.evals = 0;
-    st.de = 0.f;
-    st.dm = 0.f;
-    st.med = false;
-    st.done = !r.inside;
+// Front-to-back blend of the tile's list for this thread's PX rays.  F may be null when
+// only the transmittance and last index are wanted (recomputation).
+template <int CM, int TW, int TH, bool LIDAR, int PX, bool WANT_F>
+__device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, const RasterIn& in,
+                                            const TileCtx& tc, const RayCtx (&r)[PX], int2 range,
+                                            FwdState (&st)[PX], float (*F)[CM]) {
+    constexpr int NT = TW * TH / PX, B = NT;   // one staged Gaussian per thread and batch
+    int evals = 0;
+    bool all_done = true;
+#pragma unroll
+    for (int q = 0; q < PX; q++) {
+        st[q].T = 1.f;
+        st[q].last = 0;
+        st[q].de = 0.f;
+        st[q].dm = 0.f;
+        st[q].med = false;
+        st[q].done = !r[q].inside;
+        all_done &= st[q].done;
+    }
     for (int start = range.x; start < range.y; start += B) {
-        if (__syncthreads_count(st.done) == B) break;
-        const int j = start + threadIdx.x;
-        if (j < range.y) stage_load<CM, B, LIDAR>(sm, in, r.s, j, threadIdx.x);
+        if (__syncthreads_count(all_done) == NT) break;
+        if (start + (int)threadIdx.x < range.y) stage_load<CM, B, LIDAR>(sm, in, tc.s, start + threadIdx.x, threadIdx.x);
         __syncthreads();
-        if (!st.done) {
+        if (!all_done) {
             const int nb = min(B, range.y - start);
             for (int k = 0; k < nb; k++) {
-                float dx, dy, G, a;
-                bool cl;
-                st.evals++;
-                if (!eval_alpha<LIDAR>(sm.g0[k], sm.g1[k], r, dx, dy, G, a, cl)) continue;
-                const float Tn = st.T * (1.f - a);
-                if (Tn < kTEps) {
-                    st.done = true;
-                    break;
-                }
-                const float wgt = a * st.T;
-                if (WANT_F) {
+                const float4 g0 = sm.g0[k], g1 = sm.g1[k];
+                all_done = true;
 #pragma unroll
-                    for (int c = 0; c < CM; c++) F[c] += sm.f[k * CM + c] * wgt;
-                }
-                if (LIDAR) {
-                    const float rrs = sm.g2[k].x + sm.g2[k].y * r.t;
-                    st.de += rrs * wgt;
-                    if (!st.med && Tn < 0.5f) {
-                        st.dm = rrs;
-                        st.med = true;
+                for (int q = 0; q < PX; q++) {
+                    if (st[q].done) continue;
+                    evals++;
+                    float dx, dy, G, a;
+                    bool cl;
+                    if (eval_alpha<LIDAR>(g0, g1, r[q], dx, dy, G, a, cl)) {
+                        const float Tn = st[q].T * (1.f - a);
+                        if (Tn < kTEps) {
+                            st[q].done = true;
+                            continue;
+                        }
+                        const float wgt = a * st[q].T;
+                        if (WANT_F) {
+#pragma unroll
+                            for (int c = 0; c < CM; c++) F[q][c] += sm.f[k * CM + c] * wgt;
+                        }
+                        if (LIDAR) {
+                            const float rrs = sm.g2[k].x + sm.g2[k].y * r[q].t;
+                            st[q].de += rrs * wgt;
+                            if (!st[q].med && Tn < 0.5f) {
+                                st[q].dm = rrs;
+                                st[q].med = true;
+                            }
+                        }
+                        st[q].T = Tn;
+                        st[q].last = start + k - range.x + 1;
                     }
+                    all_done = false;
                 }
-                st.T = Tn;
-                st.last = start + k - range.x + 1;
+                if (all_done) break;
             }
         }
     }
+    return evals;
 }
 
 template <int CM, int TW, int TH, bool LIDAR>
-__global__ void __launch_bounds__(TW* TH) k_raster_fwd(const __grid_constant__ Frame fr, RasterIn in, RasterOut out) {
-    constexpr int B = TW * TH;
+__global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, false>::value)
+    k_raster_fwd(const __grid_constant__ Frame fr, RasterIn in, RasterOut out) {
+    constexpr int PX = RaysPerThread<CM, false>::value;
+    constexpr int NT = TW * TH / PX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Stage<CM, B, LIDAR>& sm = *reinterpret_cast<Stage<CM, B, LIDAR>*>(smem_raw);
-    const RayCtx r = ray_setup<TW, TH, LIDAR>(fr);
-    const int2 range = in.ranges[r.gtile];
-    float F[CM];
+    Stage<CM, NT, LIDAR>& sm = *reinterpret_cast<Stage<CM, NT, LIDAR>*>(smem_raw);
+    const TileCtx tc = tile_setup<LIDAR>(fr);
+    RayCtx r[PX];
 #pragma unroll
-    for (int c = 0; c < CM; c++) F[c] = 0.f;
-    FwdState st;
-    forward_tile<CM, B, LIDAR, true>(sm, in, r, range, st, F);
+    for (int q = 0; q < PX; q++) r[q] = ray_setup<TW, TH, LIDAR>(fr, tc, threadIdx.x + q * NT);
+    const int2 range = in.ranges[tc.gtile];
+    float F[PX][CM];
+#pragma unroll
+    for (int q = 0; q < PX; q++)
+#pragma unroll
+        for (int c = 0; c < CM; c++) F[q][c] = 0.f;
+    FwdState st[PX];
+    const int evals = forward_tile<CM, TW, TH, LIDAR, PX, true>(sm, in, tc, r, range, st, F);
     if (out.evaluated) {
-        unsigned long long e = (unsigned long long)st.evals;
+        unsigned long long e = (unsigned long long)evals;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
         if ((threadIdx.x & 31) == 0) atomicAdd(out.evaluated, e);
     }
-    if (!r.inside) return;
     const int C = in.C;
-    float* fo = out.feat + r.o * C;
-    if ((C & 3) == 0) {
 #pragma unroll
-        for (int c = 0; c < CM; c += 4)
-            if (c < C) *reinterpret_cast<float4*>(fo + c) = make_float4(F[c], F[c + 1], F[c + 2], F[c + 3]);
-    } else {
+    for (int q = 0; q < PX; q++) {
+        if (!r[q].inside) continue;
+        float* fo = out.feat + r[q].o * C;
+        if ((C & 3) == 0) {
 #pragma unroll
-        for (int c = 0; c < CM; c++)
-            if (c < C) fo[c] = F[c];
-    }
-    if (out.T) out.T[r.o] = st.T;
-    if (out.last) out.last[r.o] = st.last;
-    if (LIDAR) {
-        out.range_exp[r.o] = st.de;
-        if (out.range_med) out.range_med[r.o] = st.dm;
-        out.alpha[r.o] = 1.f - st.T;
+            for (int c = 0; c < CM; c += 4)
+                if (c < C)
+                    *reinterpret_cast<float4*>(fo + c) = make_float4(F[q][c], F[q][c + 1], F[q][c + 2], F[q][c + 3]);
+        } else {
+#pragma unroll
+            for (int c = 0; c < CM; c++)
+                if (c < C) fo[c] = F[q][c];
+        }
+        if (out.T) out.T[r[q].o] = st[q].T;
+        if (out.last) out.last[r[q].o] = st[q].last;
+        if (LIDAR) {
+            out.range_exp[r[q].o] = st[q].de;
+            if (out.range_med) out.range_med[r[q].o] = st[q].dm;
+            out.alpha[r[q].o] = 1.f - st[q].T;
+        }
     }
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Sum of VP per-lane values over the warp by recursive halving: at each of the five
+// steps a lane keeps half of its values and receives the partner's copy of that half, so
+// the warp exchanges VP - VP/32 values instead of 5 VP.  Afterwards lane l holds the
+// totals of value indices [l * VP / 32, (l + 1) * VP / 32) (VP >= 32), or index l / 2
+// (VP == 16, even and odd lanes holding the same total).
+template <int VP>
+__device__ __forceinline__ void warp_transpose_reduce(float (&v)[VP], int lane) {
+    int n = VP;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int o = 16; o >= 1; o >>= 1) {
+        const bool upper = (lane & o) != 0;
+        if (n >= 2) {
+            const int h = n / 2;
+#pragma unroll
+            for (int i = 0; i < VP / 2; i++) {
+                if (i < h) {
+                    const float send = upper ? v[i] : v[i + h];
+                    const float keep = upper ? v[i + h] : v[i];
+                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                }
+            }
+            n = h;
+        } else {
+            v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+        }
+    }
 }
+
+template <int CM, bool LIDAR>
+struct BwdLayout {
+    static constexpr int kOffF = LIDAR ? 12 : 8;          // first feature slot (16-byte aligned)
+    static constexpr int kV = kOffF + CM;                 // values per (ray, Gaussian)
+    static constexpr int kVP = kV <= 16 ? 16 : (kV <= 32 ? 32 : 64);
+    static constexpr int kRow = (kV + 3) & ~3;            // shared accumulator row (float4 aligned)
+};
 
 template <int CM, int TW, int TH, bool LIDAR, bool RECOMPUTE>
-__global__ void __launch_bounds__(TW* TH) k_raster_bwd(const __grid_constant__ Frame fr, RasterIn in, RasterGrad gr) {
-    constexpr int B = TW * TH;
-    constexpr int C = CM;   // register arrays sized by the maximum; lanes beyond in.C stay zero
+__global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true>::value)
+    k_raster_bwd(const __grid_constant__ Frame fr, RasterIn in, RasterGrad gr) {
+    constexpr int PX = RaysPerThread<CM, true>::value;
+    constexpr int NT = TW * TH / PX;
+    constexpr int B = NT;   // one staged Gaussian per thread and batch
+    using LY = BwdLayout<CM, LIDAR>;
+    constexpr int OFF = LY::kOffF, VP = LY::kVP, ROW = LY::kRow;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Stage<CM, B, LIDAR>& sm = *reinterpret_cast<Stage<CM, B, LIDAR>*>(smem_raw);
-    __shared__ int s_max_last[B / 32];
+    float* acc = reinterpret_cast<float*>(smem_raw + sizeof(Stage<CM, B, LIDAR>));   // [B][ROW]
+    __shared__ int s_max_last[NT / 32 > 0 ? NT / 32 : 1];
     const int Crt = in.C;
-    const RayCtx r = ray_setup<TW, TH, LIDAR>(fr);
-    const int2 range = in.ranges[r.gtile];
-    float Tfin;
-    int last;
-    if (RECOMPUTE) {
-        FwdState st;
-        forward_tile<CM, B, LIDAR, false>(sm, in, r, range, st, nullptr);
-        Tfin = st.T;
-        last = st.last;
-    } else {
-        Tfin = r.inside ? gr.T[r.o] : 1.f;
-        last = r.inside ? gr.last[r.o] : 0;
-    }
-    float gF[C], Bc[C];
-    float gT = 0.f, gD = 0.f;
-    if (r.inside) {
+    const int V = OFF + Crt;
+    const TileCtx tc = tile_setup<LIDAR>(fr);
+    RayCtx r[PX];
 #pragma unroll
-        for (int c = 0; c < C; c++) gF[c] = c < Crt ? gr.dfeat[r.o * Crt + c] : 0.f;
-        if (!LIDAR) {
-            gT = gr.dT ? gr.dT[r.o] : 0.f;
-        } else {
-            gT = gr.dalpha ? -gr.dalpha[r.o] : 0.f;
-            gD = gr.drange ? gr.drange[r.o] : 0.f;
+    for (int q = 0; q < PX; q++) r[q] = ray_setup<TW, TH, LIDAR>(fr, tc, threadIdx.x + q * NT);
+    const int2 range = in.ranges[tc.gtile];
+    const int len = range.y - range.x;
+    for (int q = threadIdx.x; q < B * ROW; q += NT) acc[q] = 0.f;
+    float Tfin[PX];
+    int last[PX];
+    if (RECOMPUTE) {
+        FwdState st[PX];
+        forward_tile<CM, TW, TH, LIDAR, PX, false>(sm, in, tc, r, range, st, nullptr);
+#pragma unroll
+        for (int q = 0; q < PX; q++) {
+            Tfin[q] = st[q].T;
+            last[q] = min(st[q].last, len);
         }
     } else {
 #pragma unroll
-        for (int c = 0; c < C; c++) gF[c] = 0.f;
+        for (int q = 0; q < PX; q++) {
+            Tfin[q] = r[q].inside ? gr.T[r[q].o] : 1.f;
+            last[q] = r[q].inside ? min(gr.last[r[q].o], len) : 0;   // never past this tile's list
+        }
     }
+    float gF[PX][CM], gTT[PX], gD[PX], T[PX], S[PX], SD[PX];
+    int my_last = 0;
 #pragma unroll
-    for (int c = 0; c < C; c++) Bc[c] = 0.f;
-    float BD = 0.f;
-    // tile-wide maximum of the last blended index
-    const int wl = __reduce_max_sync(0xffffffffu, (unsigned)last);
+    for (int q = 0; q < PX; q++) {
+#pragma unroll
+        for (int c = 0; c < CM; c++) gF[q][c] = (r[q].inside && c < Crt) ? gr.dfeat[r[q].o * Crt + c] : 0.f;
+        float gT = 0.f;
+        gD[q] = 0.f;
+        if (r[q].inside) {
+            if (!LIDAR) {
+                gT = gr.dT ? gr.dT[r[q].o] : 0.f;
+            } else {
+                gT = gr.dalpha ? -gr.dalpha[r[q].o] : 0.f;
+                gD[q] = gr.drange ? gr.drange[r[q].o] : 0.f;
+            }
+        }
+        gTT[q] = gT * Tfin[q];
+        T[q] = Tfin[q];
+        S[q] = 0.f;    // sum_c gF_c B_c, B = normalised blend of everything behind
+        SD[q] = 0.f;   // its counterpart for the range
+        my_last = max(my_last, last[q]);
+    }
+    const int wl = __reduce_max_sync(0xffffffffu, (unsigned)my_last);
     if ((threadIdx.x & 31) == 0) s_max_last[threadIdx.x >> 5] = wl;
     __syncthreads();
     int max_last = 0;
 #pragma unroll
-    for (int w = 0; w < B / 32; w++) max_last = max(max_last, s_max_last[w]);
-    max_last = min(max_last, range.y - range.x);   // never walk past this tile's list
-    last = min(last, range.y - range.x);
-    float T = Tfin;
+    for (int w = 0; w < (NT + 31) / 32; w++) max_last = max(max_last, s_max_last[w]);
     const int lane = threadIdx.x & 31;
-    float4* gp0 = gr.grad_proj + rec_index(r.s, 0, in.n, 0);
-    float4* gp1 = gr.grad_proj + rec_index(r.s, 1, in.n, 0);
-    float4* gp2 = gr.grad_proj + rec_index(r.s, 2, in.n, 0);
+    float4* gp0 = gr.grad_proj + rec_index(tc.s, 0, in.n, 0);
+    float4* gp1 = gr.grad_proj + rec_index(tc.s, 1, in.n, 0);
+    float4* gp2 = gr.grad_proj + rec_index(tc.s, 2, in.n, 0);
     for (int end = range.x + max_last; end > range.x; end -= B) {
         const int cnt = min(B, end - range.x);
         __syncthreads();
-        if (threadIdx.x < cnt) stage_load<CM, B, LIDAR>(sm, in, r.s, end - 1 - threadIdx.x, threadIdx.x);
+        if ((int)threadIdx.x < cnt) stage_load<CM, B, LIDAR>(sm, in, tc.s, end - 1 - threadIdx.x, threadIdx.x);
         __syncthreads();
         for (int k = 0; k < cnt; k++) {
             const int idx = end - 1 - k - range.x;
-            float dx = 0.f, dy = 0.f, G = 0.f, a = 0.f;
-            bool cl = false;
-            bool contrib = r.inside && idx < last;
-            if (contrib) contrib = eval_alpha<LIDAR>(sm.g0[k], sm.g1[k], r, dx, dy, G, a, cl);
-            if (!__any_sync(0xffffffffu, contrib)) continue;
-            float v[10 + C];
+            const float4 g0 = sm.g0[k], g1 = sm.g1[k];
+            float dx[PX], dy[PX], G[PX], a[PX];
+            bool cl[PX], on[PX];
+            bool any = false;
 #pragma unroll
-            for (int q = 0; q < 10 + C; q++) v[q] = 0.f;
-            if (contrib) {
-                const float Ti = T / (1.f - a);
-                const float wgt = a * Ti;
-                float dot = 0.f;
+            for (int q = 0; q < PX; q++) {
+                on[q] = eval_alpha<LIDAR>(g0, g1, r[q], dx[q], dy[q], G[q], a[q], cl[q]) && idx < last[q];
+                any |= on[q];
+            }
+            if (!__any_sync(0xffffffffu, any)) continue;
+            float v[VP];
 #pragma unroll
-                for (int c = 0; c < C; c++) {
-                    const float f = sm.f[k * CM + c];
-                    v[10 + c] = wgt * gF[c];
-                    dot += gF[c] * (f - Bc[c]);
-                    Bc[c] = f * a + (1.f - a) * Bc[c];
-                }
-                float dalpha = Ti * dot - gT * Tfin / (1.f - a);
+            for (int q = 0; q < PX; q++) {
+                // a ray that does not blend this Gaussian gets alpha = 0: every term vanishes
+                const float aq = on[q] ? a[q] : 0.f;
+                const float Gq = on[q] ? G[q] : 0.f;
+                const float inv = __frcp_rn(1.f - aq);
+                const float Ti = T[q] * inv;
+                const float wgt = aq * Ti;
+                float Gf = 0.f;
+#pragma unroll
+                for (int c = 0; c < CM; c++) Gf += gF[q][c] * sm.f[k * CM + c];
+                float dalpha = Ti * (Gf - S[q]) - gTT[q] * inv;
+                S[q] += aq * (Gf - S[q]);
+                float drrs = 0.f, tq = r[q].t;
                 if (LIDAR) {
-                    const float rrs = sm.g2[k].x + sm.g2[k].y * r.t;
-                    dalpha += Ti * gD * (rrs - BD);
-                    BD = rrs * a + (1.f - a) * BD;
-                    const float drrs = gD * wgt;
-                    v[8] = drrs;          // d range
-                    v[9] = drrs * r.t;    // d v_r
+                    const float rrs = sm.g2[k].x + sm.g2[k].y * tq;
+                    dalpha += Ti * gD[q] * (rrs - SD[q]);
+                    SD[q] += aq * (rrs - SD[q]);
+                    drrs = gD[q] * wgt;
                 }
-                if (!cl) {
-                    const float4 g1 = sm.g1[k];
-                    const float dsig = -dalpha * a;
-                    v[7] = dalpha * G;                        // d o'
-                    v[4] = dsig * 0.5f * dx * dx;              // d conic a
-                    v[5] = dsig * dx * dy;                     // d conic b
-                    v[6] = dsig * 0.5f * dy * dy;              // d conic c
-                    const float ddx = dsig * (g1.x * dx + g1.y * dy);
-                    const float ddy = dsig * (g1.y * dx + g1.z * dy);
-                    v[0] = -ddx;                               // d mean a
-                    v[1] = -ddy;                               // d mean b
-                    v[2] = -ddx * r.t;                         // d v_a
-                    v[3] = -ddy * r.t;                         // d v_b
-                }
-                T = Ti;
-            }
+                // clamped alpha (o' G > 0.999) passes no gradient to o' and the exponent
+                const float dg = (on[q] && !cl[q]) ? dalpha : 0.f;
+                const float dsig = -dg * aq;
+                const float ddx = dsig * (g1.x * dx[q] + g1.y * dy[q]);
+                const float ddy = dsig * (g1.y * dx[q] + g1.z * dy[q]);
+                const float t0[8] = {-ddx, -ddy, -ddx * tq, -ddy * tq, dsig * 0.5f * dx[q] * dx[q],
+                                     dsig * dx[q] * dy[q], dsig * 0.5f * dy[q] * dy[q], dg * Gq};
+                if (q == 0) {
 #pragma unroll
-            for (int q = 0; q < 10 + C; q++) {
-                if (!LIDAR && (q == 8 || q == 9)) continue;
-                if (q >= 10 + Crt) continue;
-                v[q] = warp_sum(v[q]);
-            }
-            if (lane == 0) {
-                const uint32_t id = sm.id[k];
-                atomicAdd(gp0 + id, make_float4(v[0], v[1], v[2], v[3]));
-                atomicAdd(gp1 + id, make_float4(v[4], v[5], v[6], v[7]));
-                if (LIDAR) atomicAdd(reinterpret_cast<float2*>(gp2 + id), make_float2(v[8], v[9]));
-                float* df = gr.dfeatures + (int64_t)id * Crt;
-                if ((Crt & 3) == 0) {
+                    for (int j = 0; j < 8; j++) v[j] = t0[j];
 #pragma unroll
-                    for (int c = 0; c < C; c += 4)
-                        if (c < Crt)
-                            atomicAdd(reinterpret_cast<float4*>(df + c),
-                                      make_float4(v[10 + c], v[11 + c], v[12 + c], v[13 + c]));
+                    for (int j = 8; j < OFF; j++) v[j] = 0.f;
+#pragma unroll
+                    for (int c = 0; c < CM; c++) v[OFF + c] = wgt * gF[q][c];
+#pragma unroll
+                    for (int j = OFF + CM; j < VP; j++) v[j] = 0.f;
+                    if (LIDAR) {
+                        v[8] = drrs;
+                        v[9] = drrs * tq;
+                    }
                 } else {
 #pragma unroll
-                    for (int c = 0; c < C; c++)
-                        if (c < Crt) atomicAdd(df + c, v[10 + c]);
+                    for (int j = 0; j < 8; j++) v[j] += t0[j];
+#pragma unroll
+                    for (int c = 0; c < CM; c++) v[OFF + c] += wgt * gF[q][c];
+                    if (LIDAR) {
+                        v[8] += drrs;
+                        v[9] += drrs * tq;
+                    }
+                }
+                T[q] = Ti;
+            }
+            warp_transpose_reduce<VP>(v, lane);
+            constexpr int M = VP >= 32 ? VP / 32 : 1;
+            const int j0 = VP >= 32 ? lane * M : (lane >> 1);
+            if (VP >= 32 || (lane & 1) == 0) {
+#pragma unroll
+                for (int q = 0; q < M; q++) {
+                    const int j = j0 + q;
+                    if (j < V && v[q] != 0.f) atomicAdd(&acc[k * ROW + j], v[q]);
                 }
             }
+        }
+        __syncthreads();
+        // one set of vector atomics per (tile, Gaussian): flush this batch's sums
+        if ((int)threadIdx.x < cnt) {
+            const int slot = threadIdx.x;
+            float* a_row = acc + slot * ROW;
+            const uint32_t id = sm.id[slot];
+            const float4 s0 = *reinterpret_cast<float4*>(a_row);
+            const float4 s1 = *reinterpret_cast<float4*>(a_row + 4);
+            if (s0.x != 0.f || s0.y != 0.f || s0.z != 0.f || s0.w != 0.f || s1.x != 0.f || s1.y != 0.f ||
+                s1.z != 0.f || s1.w != 0.f) {
+                atomicAdd(gp0 + id, s0);
+                atomicAdd(gp1 + id, s1);
+            }
+            if (LIDAR) {
+                const float2 s2 = make_float2(a_row[8], a_row[9]);
+                if (s2.x != 0.f || s2.y != 0.f) atomicAdd(reinterpret_cast<float2*>(gp2 + id), s2);
+            }
+            float* df = gr.dfeatures + (int64_t)id * Crt;
+            if ((Crt & 3) == 0) {
+#pragma unroll
+                for (int c = 0; c < CM; c += 4) {
+                    if (c < Crt) {
+                        const float4 f4 = *reinterpret_cast<float4*>(a_row + OFF + c);
+                        if (f4.x != 0.f || f4.y != 0.f || f4.z != 0.f || f4.w != 0.f)
+                            atomicAdd(reinterpret_cast<float4*>(df + c), f4);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < CM; c++)
+                    if (c < Crt && a_row[OFF + c] != 0.f) atomicAdd(df + c, a_row[OFF + c]);
+            }
+#pragma unroll
+            for (int q = 0; q < ROW; q += 4) *reinterpret_cast<float4*>(a_row + q) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
 }
@@ -364,24 +501,26 @@ static void set_smem(K kernel, size_t bytes) {
 
 template <int CM, int TW, int TH, bool LIDAR>
 static void launch_fwd_t(const Frame& fr, int blocks, const RasterIn& in, const RasterOut& out, cudaStream_t st) {
-    const size_t sm = sizeof(Stage<CM, TW * TH, LIDAR>);
+    constexpr int NT = TW * TH / RaysPerThread<CM, false>::value;
+    const size_t sm = sizeof(Stage<CM, NT, LIDAR>);
     auto k = k_raster_fwd<CM, TW, TH, LIDAR>;
     set_smem(k, sm);
-    k<<<blocks, TW * TH, sm, st>>>(fr, in, out);
+    k<<<blocks, NT, sm, st>>>(fr, in, out);
 }
 
 template <int CM, int TW, int TH, bool LIDAR>
 static void launch_bwd_t(const Frame& fr, int blocks, const RasterIn& in, const RasterGrad& g, bool recompute,
                          cudaStream_t st) {
-    const size_t sm = sizeof(Stage<CM, TW * TH, LIDAR>);
+    constexpr int NT = TW * TH / RaysPerThread<CM, true>::value;
+    const size_t sm = sizeof(Stage<CM, NT, LIDAR>) + sizeof(float) * NT * BwdLayout<CM, LIDAR>::kRow;
     if (recompute) {
         auto k = k_raster_bwd<CM, TW, TH, LIDAR, true>;
         set_smem(k, sm);
-        k<<<blocks, TW * TH, sm, st>>>(fr, in, g);
+        k<<<blocks, NT, sm, st>>>(fr, in, g);
     } else {
         auto k = k_raster_bwd<CM, TW, TH, LIDAR, false>;
         set_smem(k, sm);
-        k<<<blocks, TW * TH, sm, st>>>(fr, in, g);
+        k<<<blocks, NT, sm, st>>>(fr, in, g);
     }
 }
 

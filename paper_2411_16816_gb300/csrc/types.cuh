@@ -62,6 +62,7 @@ struct BinWorkspace {
     uint32_t* vkeys[2];
     uint32_t* vvals[2];
     int64_t* vis_count;
+    int64_t* offsets;
     uint32_t* ikeys[2];
     uint32_t* ivals_tmp;
     uint32_t* hist;
