@@ -167,6 +167,20 @@ splat_status splat_bin_sort(int64_t n, int32_t n_sensors, const splat_sensor *se
                             int64_t capacity, splat_bins bins, void *workspace, size_t workspace_bytes,
                             void *stream);
 
+/* splat_bin_sort for callers that cannot allocate device memory (the paper has no
+ * counterpart; this is a deployment convenience).  Hosts with a fixed device-memory
+ * budget, plug-ins running inside another program's frame loop, or runtimes that forbid
+ * allocation after start-up cannot hand the sort a workspace; this variant takes its
+ * scratch from a 32 MiB array built into the library (held by every GPU that loads the
+ * library until the process exits), so it allocates nothing.  Arguments and results are
+ * those of splat_bin_sort without the workspace.  A frame whose scratch need
+ * (splat_workspace_size) exceeds 32 MiB is rejected with SPLAT_ERR_INVALID_ARG before
+ * anything is enqueued.  The first call on a device looks up the array's device address;
+ * make it before any stream capture.  All calls share the array, so calls whose work
+ * overlaps on the GPU race; nothing in it needs to start at zero. */
+splat_status splat_bin_sort_noalloc(int64_t n, int32_t n_sensors, const splat_sensor *sensors, splat_projected proj,
+                                    int64_t capacity, splat_bins bins, void *stream);
+
 /* The sort has no gradient: this twin exists for symmetry and does nothing. */
 splat_status splat_bin_sort_backward(void);
 

@@ -348,3 +348,11 @@ splat_status splat_l1_loss(const float* pred, const float* target, int64_t count
 const char* splat_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"
+
+namespace splat {
+// Lets other translation units of the library report an error through splat_last_error().
+splat_status record_error(splat_status code, const char* msg) {
+    g_err = msg;
+    return code;
+}
+}  // namespace splat

@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol():
     lib = L.load()
     for name in _declared_symbols():
         assert hasattr(lib, name), name
-    assert set(_declared_symbols()) <= set(L.EXPORTS) | {"splat_no_alloc_bin_sort"}
+    assert set(_declared_symbols()) <= set(L.EXPORTS) | {"splat_bin_sort_noalloc"}
 
 
 def test_struct_layout_matches_header():
