@@ -246,6 +246,44 @@ splat_status splat_project_backward(const splat_gaussians *g, int32_t n_sensors,
 splat_status splat_l1_loss(const float *pred, const float *target, int64_t count, float scale, float *grad,
                            float *loss, void *stream);
 
+/* ---------------------------------------------------------------------------------
+ * Per-ray lidar decoder (paper Sec. 3.3: the rendered features concatenated with the
+ * ray direction are decoded to intensity and ray-drop probability by a small MLP;
+ * App. B: two hidden layers, loss weights lambda_intens = 1 and lambda_raydrop = 0.1).
+ * Network: x[32] -> relu(64) -> relu(64) -> (intensity logit, drop logit).
+ * Parameters, flattened in this order (splat_head_param_count() = 6402 values):
+ *   W1[32][64], b1[64], W2[64][64], b2[64], W3[64][2], b3[2]   (row-major [in][out]).
+ * The decoder reads BF16 weights w_bf16 = W1 | W2 | W3 (6272 values) and FP32 biases
+ * bias = b1 | b2 | b3 (130 values); products are accumulated in FP32 with FP32
+ * activations.  All arrays are device memory.
+ * --------------------------------------------------------------------------------- */
+int32_t splat_head_param_count(void);
+
+/* x[r] = [feat[r][0..channels), unit ray direction (cos w cos p, cos w sin p, sin w)] for
+ * every ray of one lidar ([n_beams][n_az] order, grid or explicit rays); channels must be
+ * 29 so that x is 32 wide.  x must be 16-byte aligned. */
+splat_status splat_head_inputs(const splat_sensor *lidar, const float *feat, int32_t channels, float *x,
+                               void *stream);
+
+/* out[r] = (intensity logit, drop logit) for R rays; intensity = sigmoid(out[r][0]) and the
+ * ray-drop probability = sigmoid(out[r][1]). */
+splat_status splat_head_forward(const float *x, int64_t R, const uint16_t *w_bf16, const float *bias, float *out,
+                                void *stream);
+
+/* Training pass over R rays: loss = lam_i mean (sigmoid(o0) - y_int)^2 + lam_d mean
+ * BCE(o1, y_drop), added to *loss (device float; may be NULL); its gradients with respect to
+ * the 6402 parameters are ADDED to grad (FP32, caller zeroes); dx[R][32], if not NULL,
+ * receives dL/dx (to continue the backward into the rasterizer's features). */
+splat_status splat_head_train(const float *x, int64_t R, const uint16_t *w_bf16, const float *bias,
+                              const float *y_int, const float *y_drop, float lam_i, float lam_d, float *grad,
+                              float *loss, float *dx, void *stream);
+
+/* One Adam step (bias-corrected, epsilon outside the square root) on the FP32 master
+ * parameters `params` (6402 values) with moments m, v; then refreshes the decoder's BF16
+ * weights (round to nearest even) and FP32 biases.  step counts from 1. */
+splat_status splat_head_adam(float *params, const float *grad, float *m, float *v, float lr, float beta1,
+                             float beta2, float eps, int64_t step, uint16_t *w_bf16, float *bias, void *stream);
+
 /* Message of the last non-OK status on this host thread ("" if none). */
 const char *splat_last_error(void);
 

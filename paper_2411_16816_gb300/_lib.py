@@ -23,7 +23,8 @@ SPLAT_MAX_SENSORS = 16
 EXPORTS = [
     "splat_frame_layout", "splat_workspace_size", "splat_project", "splat_bin_sort", "splat_bin_sort_backward",
     "splat_render_camera", "splat_render_lidar", "splat_render_camera_backward", "splat_render_lidar_backward",
-    "splat_project_backward", "splat_l1_loss", "splat_last_error",
+    "splat_project_backward", "splat_l1_loss", "splat_last_error", "splat_head_param_count", "splat_head_inputs",
+    "splat_head_forward", "splat_head_train", "splat_head_adam",
 ]
 
 
@@ -87,6 +88,13 @@ def load(build_if_missing: bool = True):
     L.splat_render_lidar_backward.argtypes = [G, c_int32, SE, splat_projected, splat_bins] + [c_void_p] * 8
     L.splat_project_backward.argtypes = [G, c_int32, SE, splat_projected] + [c_void_p] * 7
     L.splat_l1_loss.argtypes = [c_void_p, c_void_p, c_int64, c_float, c_void_p, c_void_p, c_void_p]
+    L.splat_head_param_count.argtypes = []
+    L.splat_head_inputs.argtypes = [SE, c_void_p, c_int32, c_void_p, c_void_p]
+    L.splat_head_forward.argtypes = [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p]
+    L.splat_head_train.argtypes = [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_float,
+                                   c_void_p, c_void_p, c_void_p, c_void_p]
+    L.splat_head_adam.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_float, c_float, c_float,
+                                  c_int64, c_void_p, c_void_p, c_void_p]
     L.splat_last_error.argtypes = []
     L.splat_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:

@@ -345,6 +345,54 @@ splat_status splat_l1_loss(const float* pred, const float* target, int64_t count
     return check_launch("splat_l1_loss");
 }
 
+int32_t splat_head_param_count(void) { return head_param_count(); }
+
+splat_status splat_head_inputs(const splat_sensor* lidar, const float* feat, int32_t channels, float* x,
+                               void* stream) {
+    Frame fr;
+    splat_status st = build_frame(1, lidar, fr, nullptr);
+    if (st != SPLAT_OK) return st;
+    if (fr.s[0].kind != SPLAT_SENSOR_LIDAR) return fail(SPLAT_ERR_INVALID_ARG, "splat_head_inputs needs a lidar");
+    if (channels + 3 != 32) return fail(SPLAT_ERR_INVALID_ARG, "head input is 32 wide: channels must be 29");
+    if (!feat || !x || !aligned16(x)) return fail(SPLAT_ERR_INVALID_ARG, "bad feature or input pointer");
+    launch_head_inputs(fr.s[0], feat, channels, x, (cudaStream_t)stream);
+    return check_launch("splat_head_inputs");
+}
+
+static splat_status check_head(const float* x, int64_t R, const uint16_t* w, const float* b) {
+    if (R < 0) return fail(SPLAT_ERR_INVALID_ARG, "R < 0");
+    if (R > 0 && (!x || !w || !b)) return fail(SPLAT_ERR_INVALID_ARG, "head pointer is NULL");
+    if (!aligned16(x)) return fail(SPLAT_ERR_INVALID_ARG, "head inputs must be 16-byte aligned");
+    return SPLAT_OK;
+}
+
+splat_status splat_head_forward(const float* x, int64_t R, const uint16_t* w_bf16, const float* bias, float* out,
+                                void* stream) {
+    splat_status st = check_head(x, R, w_bf16, bias);
+    if (st != SPLAT_OK) return st;
+    if (R > 0 && (!out || ((uintptr_t)out & 7u))) return fail(SPLAT_ERR_INVALID_ARG, "bad output pointer");
+    launch_head_fwd(x, R, HeadW{w_bf16, bias}, out, (cudaStream_t)stream);
+    return check_launch("splat_head_forward");
+}
+
+splat_status splat_head_train(const float* x, int64_t R, const uint16_t* w_bf16, const float* bias,
+                              const float* y_int, const float* y_drop, float lam_i, float lam_d, float* grad,
+                              float* loss, float* dx, void* stream) {
+    splat_status st = check_head(x, R, w_bf16, bias);
+    if (st != SPLAT_OK) return st;
+    if (R > 0 && (!y_int || !y_drop || !grad)) return fail(SPLAT_ERR_INVALID_ARG, "bad target or gradient pointer");
+    launch_head_train(x, R, HeadW{w_bf16, bias}, y_int, y_drop, lam_i, lam_d, grad, loss, dx, (cudaStream_t)stream);
+    return check_launch("splat_head_train");
+}
+
+splat_status splat_head_adam(float* params, const float* grad, float* m, float* v, float lr, float beta1, float beta2,
+                             float eps, int64_t step, uint16_t* w_bf16, float* bias, void* stream) {
+    if (!params || !grad || !m || !v || !w_bf16 || !bias || step < 1)
+        return fail(SPLAT_ERR_INVALID_ARG, "bad Adam arguments");
+    launch_head_adam(params, grad, m, v, lr, beta1, beta2, eps, step, w_bf16, bias, (cudaStream_t)stream);
+    return check_launch("splat_head_adam");
+}
+
 const char* splat_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"

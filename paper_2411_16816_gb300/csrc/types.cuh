@@ -86,4 +86,16 @@ bool raster_channels_supported(int C);
 void launch_l1(const float* pred, const float* target, int64_t count, float scale, float* grad, float* loss,
                cudaStream_t st);
 
+struct HeadW {
+    const uint16_t* w;   // BF16 W1 | W2 | W3 (row-major [in][out])
+    const float* b;      // FP32 b1 | b2 | b3
+};
+void launch_head_fwd(const float* x, int64_t R, const HeadW& hw, float* out, cudaStream_t st);
+void launch_head_train(const float* x, int64_t R, const HeadW& hw, const float* y_int, const float* y_drop, float lam_i,
+                       float lam_d, float* grad, float* loss, float* dx, cudaStream_t st);
+void launch_head_adam(float* p, const float* g, float* m, float* v, float lr, float beta1, float beta2, float eps,
+                      int64_t step, uint16_t* wbf, float* bias, cudaStream_t st);
+void launch_head_inputs(const SensorDev& S, const float* feat, int C, float* x, cudaStream_t st);
+int head_param_count();
+
 }  // namespace splat

@@ -241,3 +241,50 @@ def target_like(g: dict, seed: int) -> dict:
 
 def subset(g: dict, idx) -> dict:
     return {k: np.ascontiguousarray(v[idx]) for k, v in g.items()}
+
+
+# ----------------------------------------------------------------------------------------
+# Learned ray head inputs: initial weights and a seeded ground-truth "teacher"
+# ----------------------------------------------------------------------------------------
+
+HEAD_SHAPES = {"W1": (32, 64), "b1": (64,), "W2": (64, 64), "b2": (64,), "W3": (64, 2), "b3": (2,)}
+HEAD_ORDER = ("W1", "b1", "W2", "b2", "W3", "b3")
+
+
+def head_init_params(seed: int) -> dict:
+    """Seeded initial weights of the 32 -> 64 -> 64 -> 2 head (uniform, fan-in scaled; zero
+    biases), FP32 masters."""
+    rng = _rng(seed)
+    p = {}
+    for k in HEAD_ORDER:
+        shape = HEAD_SHAPES[k]
+        if len(shape) == 2:
+            b = 1.0 / math.sqrt(shape[0])
+            p[k] = rng.uniform(-b, b, size=shape).astype(F32)
+        else:
+            p[k] = np.zeros(shape, F32)
+    return p
+
+
+def teacher_params(seed: int, n_feat: int = 29) -> dict:
+    """A frozen random network that defines the synthetic lidar ground truth: its two
+    outputs depend non-linearly on the rendered features and on the ray direction, so a
+    view-independent per-Gaussian channel cannot reproduce them."""
+    rng = _rng(seed)
+    return {"A": rng.normal(0, 1.0 / math.sqrt(n_feat + 3), size=(n_feat + 3, 24)),
+            "a": rng.normal(0, 0.3, size=24),
+            "B": rng.normal(0, 1.2 / math.sqrt(24), size=(24, 2)),
+            "D": rng.normal(0, 1.0, size=(3, 2)), "c": np.array([0.2, -0.8])}
+
+
+def teacher_labels(feat: np.ndarray, dirs: np.ndarray, tp: dict, seed: int):
+    """Ground-truth intensity in [0, 1] and Bernoulli ray-drop labels for rays with
+    rendered features `feat` (R x F) and unit directions `dirs` (R x 3)."""
+    x = np.concatenate([feat, dirs], axis=1).astype(np.float64)
+    h = np.tanh(x @ tp["A"] + tp["a"])
+    z = h @ tp["B"] + (dirs ** 2) @ tp["D"] + tp["c"]
+    intensity = 1.0 / (1.0 + np.exp(-z[:, 0]))
+    p_drop = 1.0 / (1.0 + np.exp(-z[:, 1]))
+    drop = (_rng(seed).uniform(size=len(p_drop)) < p_drop).astype(F32)
+    return intensity.astype(F32), drop, p_drop.astype(F32)
+
