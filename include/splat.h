@@ -247,6 +247,57 @@ splat_status splat_l1_loss(const float *pred, const float *target, int64_t count
                            float *loss, void *stream);
 
 /* ---------------------------------------------------------------------------------
+ * Batched rendering: many camera views and lidar sweeps of different sizes, over several
+ * scenes, rasterized by ONE persistent launch (forward only, for serving).  The paper
+ * renders one sensor at a time; this is the serving form of its rasterization
+ * (Sec. 3.2, 3.3).
+ *
+ * Each request names a sensor that was projected and binned as part of a group (a frame
+ * passed to splat_project / splat_bin_sort), the group's buffers, its scene's features
+ * and its own outputs (layouts as for splat_render_camera / splat_render_lidar of a single
+ * sensor).  Every request's tile must hold 256 rays (tile_w * tile_h == 256).
+ * --------------------------------------------------------------------------------- */
+typedef struct {
+    const splat_sensor *group_sensors;  /* HOST array: the group's sensors, as binned */
+    int32_t group_n_sensors;
+    int32_t group_sensor_index;         /* this request's sensor within the group */
+    splat_projected proj;               /* the group's projection buffers */
+    splat_bins bins;                    /* the group's sorted lists */
+    const float *features;              /* the scene's features [n][channels] */
+    int64_t n;
+    int32_t channels;
+    int32_t reserved;
+    float *out_feat;                    /* [rays][channels] */
+    float *out_T;                       /* [rays] or NULL */
+    float *out_range_exp;               /* lidar: [rays] */
+    float *out_range_med;               /* lidar: [rays] or NULL */
+    float *out_alpha;                   /* lidar: [rays] */
+} splat_batch_request;
+
+/* Bytes of the request table for n requests (1..1024). */
+size_t splat_batch_table_bytes(int32_t n_requests);
+
+/* Writes the request table into `table` (HOST memory of splat_batch_table_bytes bytes)
+ * and the number of work items (tiles over all requests) into *total_items.  The caller
+ * copies the table to device memory once; it stays valid while the buffers it names do.
+ * Requests are processed in table order (put the largest first for throughput). */
+splat_status splat_batch_build(const splat_batch_request *reqs, int32_t n_requests, void *table, size_t table_bytes,
+                               int64_t *total_items);
+
+/* Renders every request of a DEVICE copy of the table in one persistent launch.
+ * counters: device int32[n_requests + 1] (reset by this call); stamps, if not NULL:
+ * device uint64[n_requests + 1] receiving the global-timer nanoseconds at which each
+ * request's last tile finished, and in stamps[n_requests] the time the batch started.
+ * max_channels is the largest channel count of the requests (<= 32).  Safe to capture
+ * in a CUDA graph (it enqueues a memset and two kernels). */
+splat_status splat_render_batch(const void *table, int32_t n_requests, int64_t total_items, int32_t max_channels,
+                                int32_t *counters, uint64_t *stamps, void *stream);
+
+/* Writes the device global timer (nanoseconds) to the device uint64 *at when the stream
+ * reaches this point (latency bookkeeping for batches). */
+splat_status splat_stamp(uint64_t *at, void *stream);
+
+/* ---------------------------------------------------------------------------------
  * Per-ray lidar decoder (paper Sec. 3.3: the rendered features concatenated with the
  * ray direction are decoded to intensity and ray-drop probability by a small MLP;
  * App. B: two hidden layers, loss weights lambda_intens = 1 and lambda_raydrop = 0.1).

@@ -24,7 +24,8 @@ EXPORTS = [
     "splat_frame_layout", "splat_workspace_size", "splat_project", "splat_bin_sort", "splat_bin_sort_backward",
     "splat_render_camera", "splat_render_lidar", "splat_render_camera_backward", "splat_render_lidar_backward",
     "splat_project_backward", "splat_l1_loss", "splat_last_error", "splat_head_param_count", "splat_head_inputs",
-    "splat_head_forward", "splat_head_train", "splat_head_adam",
+    "splat_head_forward", "splat_head_train", "splat_head_adam", "splat_batch_table_bytes", "splat_batch_build",
+    "splat_render_batch", "splat_stamp",
 ]
 
 
@@ -50,6 +51,14 @@ class splat_projected(ctypes.Structure):
 
 class splat_bins(ctypes.Structure):
     _fields_ = [("isect_ids", c_void_p), ("tile_ranges", c_void_p), ("n_isect", c_void_p)]
+
+
+class splat_batch_request(ctypes.Structure):
+    _fields_ = [("group_sensors", ctypes.POINTER(splat_sensor)), ("group_n_sensors", c_int32),
+                ("group_sensor_index", c_int32), ("proj", splat_projected), ("bins", splat_bins),
+                ("features", c_void_p), ("n", c_int64), ("channels", c_int32), ("reserved", c_int32),
+                ("out_feat", c_void_p), ("out_T", c_void_p), ("out_range_exp", c_void_p),
+                ("out_range_med", c_void_p), ("out_alpha", c_void_p)]
 
 
 _lib = None
@@ -95,11 +104,17 @@ def load(build_if_missing: bool = True):
                                    c_void_p, c_void_p, c_void_p, c_void_p]
     L.splat_head_adam.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_float, c_float, c_float, c_float,
                                   c_int64, c_void_p, c_void_p, c_void_p]
+    L.splat_batch_table_bytes.argtypes = [c_int32]
+    L.splat_batch_table_bytes.restype = c_size_t
+    L.splat_batch_build.argtypes = [P(splat_batch_request), c_int32, c_void_p, c_size_t, P(c_int64)]
+    L.splat_render_batch.argtypes = [c_void_p, c_int32, c_int64, c_int32, c_void_p, c_void_p, c_void_p]
+    L.splat_stamp.argtypes = [c_void_p, c_void_p]
     L.splat_last_error.argtypes = []
     L.splat_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name != "splat_last_error":
+        if name not in ("splat_last_error", "splat_batch_table_bytes", "splat_head_param_count"):
             getattr(L, name).restype = S
+    L.splat_head_param_count.restype = c_int32
     _lib = L
     return L
 

@@ -32,6 +32,15 @@ static splat_status check_launch(const char* what) {
 
 static bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
+// Tiles the binning supports: 64 to 512 rays, both sides powers of two.  The per-frame
+// raster entry points have kernels for a subset (raster_shape_supported); the batched
+// persistent launch takes any 256-ray tile.
+static bool tile_shape_ok(int tw, int th) {
+    auto pow2 = [](int v) { return v >= 1 && (v & (v - 1)) == 0; };
+    const int r = tw * th;
+    return pow2(tw) && pow2(th) && r >= 64 && r <= 512;
+}
+
 // Per-sensor constants and the frame's tile / block / ray numbering.
 static splat_status build_frame(int32_t n_sensors, const splat_sensor* sensors, Frame& fr, int64_t* total_tiles) {
     if (n_sensors < 1 || n_sensors > kMaxSensors)
@@ -54,7 +63,7 @@ static splat_status build_frame(int32_t n_sensors, const splat_sensor* sensors, 
         if (!(in.eps2d >= 0.f)) return fail(SPLAT_ERR_INVALID_ARG, "sensor %d: eps2d must be >= 0", s);
         const bool lidar = in.kind == SPLAT_SENSOR_LIDAR;
         if (in.kind != SPLAT_SENSOR_CAMERA && !lidar) return fail(SPLAT_ERR_INVALID_ARG, "sensor %d: bad kind", s);
-        if (!raster_shape_supported(lidar, in.tile_w, in.tile_h))
+        if (!tile_shape_ok(in.tile_w, in.tile_h))
             return fail(SPLAT_ERR_INVALID_ARG, "sensor %d: unsupported tile %dx%d", s, in.tile_w, in.tile_h);
         int64_t rays;
         if (!lidar) {
@@ -398,6 +407,16 @@ const char* splat_last_error(void) { return g_err.c_str(); }
 }  // extern "C"
 
 namespace splat {
+// Per-sensor constants of sensor `which` within a frame (its tile numbering included).
+splat_status frame_sensor_constants(int32_t n_sensors, const splat_sensor* sensors, int32_t which, SensorDev* out) {
+    Frame fr;
+    const splat_status st = build_frame(n_sensors, sensors, fr, nullptr);
+    if (st != SPLAT_OK) return st;
+    if (which < 0 || which >= n_sensors) return fail(SPLAT_ERR_INVALID_ARG, "sensor index out of range");
+    *out = fr.s[which];
+    return SPLAT_OK;
+}
+
 // Lets other translation units of the library report an error through splat_last_error().
 splat_status record_error(splat_status code, const char* msg) {
     g_err = msg;

@@ -58,20 +58,20 @@ __device__ __forceinline__ TileCtx tile_setup(const Frame& fr) {
     return c;
 }
 
-template <int TW, int TH, bool LIDAR>
-__device__ __forceinline__ RayCtx ray_setup(const Frame& fr, const TileCtx& tc, int p /* ray slot in tile */) {
+// Ray `p` of tile (tx, ty) for a tile of tw x th rays (runtime shape).
+template <bool LIDAR>
+__device__ __forceinline__ RayCtx ray_setup_rt(const SensorDev& S, int tx, int ty, int p, int tw, int th) {
     RayCtx r;
-    const SensorDev& S = fr.s[tc.s];
-    const int lx = p % TW, ly = p / TW;
+    const int lx = p % tw, ly = p / tw;
     if (!LIDAR) {
-        const int col = tc.tx * TW + lx, row = tc.ty * TH + ly;
+        const int col = tx * tw + lx, row = ty * th + ly;
         r.inside = col < S.width && row < S.height;
         r.pa = col + 0.5f;
         r.pb = row + 0.5f;
         r.t = ((row + 0.5f) / (float)S.height - 0.5f) * S.rs + S.dt;
         r.o = (int64_t)S.ray_base + (int64_t)row * S.width + col;
     } else {
-        const int a = tc.tx * TW + lx, b = tc.ty * TH + ly;
+        const int a = tx * tw + lx, b = ty * th + ly;
         r.inside = a < S.naz;
         r.o = (int64_t)S.ray_base + (int64_t)b * S.naz + a;
         if (r.inside) {
@@ -90,6 +90,11 @@ __device__ __forceinline__ RayCtx ray_setup(const Frame& fr, const TileCtx& tc, 
         }
     }
     return r;
+}
+
+template <int TW, int TH, bool LIDAR>
+__device__ __forceinline__ RayCtx ray_setup(const Frame& fr, const TileCtx& tc, int p /* ray slot in tile */) {
+    return ray_setup_rt<LIDAR>(fr.s[tc.s], tc.tx, tc.ty, p, TW, TH);
 }
 
 template <int CM, int B, bool LIDAR>

@@ -53,6 +53,8 @@ class Frame:
             raise ValueError(f"a frame holds 1..{L.SPLAT_MAX_SENSORS} sensors")
         self.lib = L.load()
         self.device = torch.device(device)
+        if self.device.type == "cuda" and self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
         self.sensors = list(sensors)
         self.n, self.channels = int(n), int(channels)
         S = len(self.sensors)

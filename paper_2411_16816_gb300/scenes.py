@@ -288,3 +288,38 @@ def teacher_labels(feat: np.ndarray, dirs: np.ndarray, tp: dict, seed: int):
     drop = (_rng(seed).uniform(size=len(p_drop)) < p_drop).astype(F32)
     return intensity.astype(F32), drop, p_drop.astype(F32)
 
+
+
+# ----------------------------------------------------------------------------------------
+# Serving batch: 64 mixed requests over three scenes
+# ----------------------------------------------------------------------------------------
+
+def serving_batch(seed: int = 1005, sizes=(200_000, 800_000, 2_000_000), channels: int = 16):
+    """Three driving scenes (200k / 800k / 2M Gaussians) and 64 requests assigned to them
+    round-robin: 12 x 640x480, 12 x 1280x720, 12 x 1920x1080 rolling-shutter cameras (60-
+    degree field of view), 14 x 32-beam x 1080 and 14 x 128-beam x 2048 lidar sweeps, each
+    at a random heading of a rig moving at 15 m/s.  Returns (scenes, [(scene, sensor)])."""
+    rng = _rng(seed)
+    scene_list = [driving_gaussians(n, seed + 10 * k, channels=channels) for k, n in enumerate(sizes)]
+    kinds = ([("cam", 640, 480)] * 12 + [("cam", 1280, 720)] * 12 + [("cam", 1920, 1080)] * 12 +
+             [("lid", 32, 1080)] * 14 + [("lid", 128, 2048)] * 14)
+    requests = []
+    for q, kind in enumerate(kinds):
+        yaw = float(rng.uniform(0, 2 * math.pi))
+        if kind[0] == "cam":
+            w, h = kind[1], kind[2]
+            R = camera_rotation(yaw)
+            v, om = ego_motion(R, 15.0, 0.05)
+            f = (w / 2) / math.tan(math.radians(30.0))
+            s = Camera(R=R, t=np.zeros(3), width=w, height=h, fx=f, fy=f, cx=w / 2, cy=h / 2, lin_vel=v,
+                       ang_vel=om, rs_time=0.03)
+        else:
+            nb, naz = kind[1], kind[2]
+            elev = np.deg2rad(np.linspace(-25.0, 15.0, nb)) if nb == 32 else nonuniform_elevations(nb)
+            R = yaw_matrix(yaw).T
+            v, om = ego_motion(R, 15.0, 0.05)
+            res = 2 * math.pi / naz
+            s = Lidar(R=R, t=np.zeros(3), beam_elev=elev, n_az=naz, az_res=res, sweep_time=0.1,
+                      eps2d=lidar_blur(elev, res), lin_vel=v, ang_vel=om)
+        requests.append((q % len(sizes), s))
+    return scene_list, requests
