@@ -42,6 +42,9 @@ def parse():
     p.add_argument("--workload", choices=["driving", "lidar_heavy", "profile"], default="driving")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--profile-only", action="store_true", help="a few untimed steps (for ncu captures)")
+    p.add_argument("--no-serving", action="store_true", help="skip the batched-serving measurement")
+    p.add_argument("--no-head", action="store_true", help="skip the learned ray-head measurement")
+    p.add_argument("--serving-replays", type=int, default=200)
     return p.parse_args()
 
 
@@ -416,10 +419,112 @@ def run_ours(args):
             "wall_s": wall, "overflow": overflow}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, sensors)
+    if rank == 0 and world == 1:
+        del fr, out, grads, pgrads, flush, dev_g, host_g, host_t
+        torch.cuda.empty_cache()
+        if not args.no_serving:
+            line["serving"] = serving_bench(args, dev)
+            torch.cuda.empty_cache()
+        if not args.no_head:
+            line["head"] = head_bench(args, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def serving_bench(args, dev):
+    """64 mixed requests over 200k / 800k / 2M-Gaussian scenes in one graph-captured
+    persistent launch; tile shapes from the autotuner; latency over replays."""
+    import torch
+    from paper_2411_16816_gb300.batch import autotune, time_replays
+    from paper_2411_16816_gb300.render import gaussians_to_device
+    sc, reqs = scenes.serving_batch()
+    gd = [gaussians_to_device(g, dev) for g in sc]
+    t0 = time.perf_counter()
+    br, table = autotune(gd, reqs, reps=3, device=dev)
+    tune_s = time.perf_counter() - t0
+    for _ in range(3):
+        br.replay()
+    torch.cuda.synchronize()
+    ms, lat = time_replays(br, args.serving_replays)
+    overflow = br.overflowed()
+    best = min(table, key=table.get)
+    return {"workload": "64 requests (12x640x480, 12x1280x720, 12x1920x1080 RS cameras, 14x 32x1080 and "
+                        "14x 128x2048 lidar sweeps) over 200k/800k/2M-Gaussian scenes, forward, 16 channels",
+            "rays_per_batch": br.rays, "replays": args.serving_replays,
+            "batch_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+            "request_latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+            "rays_per_s": br.rays / (float(np.median(ms)) * 1e-3),
+            "tiles": {"camera": list(best[0]), "lidar": list(best[1])},
+            "autotune_ms_per_batch": {f"cam{c[0]}x{c[1]}_lid{l[0]}x{l[1]}": v for (c, l), v in table.items()},
+            "autotune_s": tune_s, "gpu_launches_per_batch": br.launches(), "overflow": overflow}
+
+
+def head_bench(args, dev):
+    """Learned ray head: one training epoch over 10M lidar rays rendered from a
+    500k-Gaussian scene (29 channels) at 38 poses along a 15 m/s trajectory, and inference."""
+    import torch
+    from paper_2411_16816_gb300.head import RayHead, head_inputs
+    from paper_2411_16816_gb300.render import Frame, gaussians_to_device
+    g = scenes.driving_gaussians(500_000, 1004, channels=29)
+    gd = gaussians_to_device(g, dev)
+    elev = scenes.nonuniform_elevations(128)
+    res = 2 * math.pi / 2048
+    tp = scenes.teacher_params(77)
+    xs, yi, yd = [], [], []
+    total = 0
+    k = 0
+    while total < 10_000_000:
+        v, w = scenes.ego_motion(np.eye(3), 15.0, 0.0)
+        lid = scenes.Lidar(R=np.eye(3), t=np.array([-1.5 * k, 0.0, 0.0]), beam_elev=elev, n_az=2048, az_res=res,
+                           sweep_time=0.1, eps2d=scenes.lidar_blur(elev, res), lin_vel=v, ang_vel=w)
+        fr = Frame([lid], len(g["opacities"]), 29, dev)
+        out = fr.forward(gd, keep_state=False)
+        x = head_inputs(fr, 0, out["lid_feat"])
+        take = min(x.shape[0], 10_000_000 - total)
+        x = x[:take]
+        xn = x.cpu().numpy()
+        a, b, _ = scenes.teacher_labels(xn[:, :29], xn[:, 29:], tp, seed=200 + k)
+        xs.append(x)
+        yi.append(torch.as_tensor(a, device=dev))
+        yd.append(torch.as_tensor(b, device=dev))
+        total += take
+        k += 1
+        del fr, out
+    X, YI, YD = torch.cat(xs), torch.cat(yi), torch.cat(yd)
+    del xs, yi, yd
+    head = RayHead(scenes.head_init_params(21), dev, lr=3e-3)
+    B = 65536
+    starts = list(range(0, X.shape[0], B))
+    for i in starts[:3]:
+        head.train_step(X[i:i + B], YI[i:i + B], YD[i:i + B])
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for i in starts:
+        head.train_step(X[i:i + B], YI[i:i + B], YD[i:i + B])
+    b.record(stream)
+    torch.cuda.synchronize()
+    epoch_ms = a.elapsed_time(b)
+    loss = float(head.loss.item())
+    out = torch.empty((X.shape[0], 2), dtype=torch.float32, device=dev)
+    head.forward(X, out)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(5):
+        head.forward(X, out)
+    b.record(stream)
+    torch.cuda.synchronize()
+    infer_ms = a.elapsed_time(b) / 5
+    flop_train = 2 * (32 * 64 + 64 * 64 + 64 * 2) * 3
+    return {"workload": f"{X.shape[0]} lidar rays (128x2048 sweeps at {k} poses) of a 500k-Gaussian scene, "
+                        "29 rendered channels + ray direction -> 64 -> 64 -> 2, BF16 weights, FP32 accumulate",
+            "train_epoch_ms": epoch_ms, "train_rays_per_s": X.shape[0] / (epoch_ms * 1e-3),
+            "minibatch": B, "steps": len(starts), "last_loss": loss,
+            "infer_ms": infer_ms, "infer_rays_per_s": X.shape[0] / (infer_ms * 1e-3),
+            "train_tflops": X.shape[0] * flop_train / (epoch_ms * 1e-3) / 1e12}
 
 
 def main():
