@@ -25,13 +25,15 @@
 
 namespace splat {
 
-// Rays per thread.  The backward takes two rays per thread for up to 16 channels, so one
-// warp reduction of a Gaussian's gradient covers 64 rays; the forward keeps one ray per
-// thread (its per-Gaussian cost is small and occupancy matters more); wide channel counts
-// keep one ray per thread for register room.
-template <int CM, bool BWD>
+// Rays per thread.  The camera backward takes four rays per thread for up to 16 channels
+// (two for the lidar), so one warp reduction of a Gaussian's gradient covers 128 (64)
+// rays; the forward keeps one ray per thread (its per-Gaussian cost is small and occupancy
+// matters more); wide channel counts keep one ray per thread for register room.  A block
+// always keeps at least one full warp.
+template <int CM, bool BWD, bool LIDAR, int RAYS>
 struct RaysPerThread {
-    static constexpr int value = (BWD && CM <= 16) ? 2 : 1;
+    static constexpr int want = (BWD && CM <= 16) ? (LIDAR ? 2 : 4) : 1;
+    static constexpr int value = want * 32 <= RAYS ? want : (2 * 32 <= RAYS ? 2 : 1);
 };
 
 struct RayCtx {
@@ -221,9 +223,9 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
 }
 
 template <int CM, int TW, int TH, bool LIDAR>
-__global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, false>::value)
+__global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, false, LIDAR, TW * TH>::value)
     k_raster_fwd(const __grid_constant__ Frame fr, RasterIn in, RasterOut out) {
-    constexpr int PX = RaysPerThread<CM, false>::value;
+    constexpr int PX = RaysPerThread<CM, false, LIDAR, TW * TH>::value;
     constexpr int NT = TW * TH / PX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Stage<CM, NT, LIDAR>& sm = *reinterpret_cast<Stage<CM, NT, LIDAR>*>(smem_raw);
@@ -307,9 +309,9 @@ struct BwdLayout {
 };
 
 template <int CM, int TW, int TH, bool LIDAR, bool RECOMPUTE>
-__global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true>::value)
+__global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * TH>::value)
     k_raster_bwd(const __grid_constant__ Frame fr, RasterIn in, RasterGrad gr) {
-    constexpr int PX = RaysPerThread<CM, true>::value;
+    constexpr int PX = RaysPerThread<CM, true, LIDAR, TW * TH>::value;
     constexpr int NT = TW * TH / PX;
     constexpr int B = NT;   // one staged Gaussian per thread and batch
     using LY = BwdLayout<CM, LIDAR>;
@@ -366,7 +368,7 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true>::value)
         SD[q] = 0.f;   // its counterpart for the range
         my_last = max(my_last, last[q]);
     }
-    const int wl = __reduce_max_sync(0xffffffffu, (unsigned)my_last);
+    const int wl = __reduce_max_sync(0xffffffffu, (unsigned)my_last);   // this warp's deepest entry
     if ((threadIdx.x & 31) == 0) s_max_last[threadIdx.x >> 5] = wl;
     __syncthreads();
     int max_last = 0;
@@ -383,6 +385,7 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true>::value)
         __syncthreads();
         for (int k = 0; k < cnt; k++) {
             const int idx = end - 1 - k - range.x;
+            if (idx >= wl) continue;   // warp-uniform: no ray of this warp blended this deep
             const float4 g0 = sm.g0[k], g1 = sm.g1[k];
             float dx[PX], dy[PX], G[PX], a[PX];
             bool cl[PX], on[PX];
@@ -506,7 +509,7 @@ static void set_smem(K kernel, size_t bytes) {
 
 template <int CM, int TW, int TH, bool LIDAR>
 static void launch_fwd_t(const Frame& fr, int blocks, const RasterIn& in, const RasterOut& out, cudaStream_t st) {
-    constexpr int NT = TW * TH / RaysPerThread<CM, false>::value;
+    constexpr int NT = TW * TH / RaysPerThread<CM, false, LIDAR, TW * TH>::value;
     const size_t sm = sizeof(Stage<CM, NT, LIDAR>);
     auto k = k_raster_fwd<CM, TW, TH, LIDAR>;
     set_smem(k, sm);
@@ -516,7 +519,7 @@ static void launch_fwd_t(const Frame& fr, int blocks, const RasterIn& in, const 
 template <int CM, int TW, int TH, bool LIDAR>
 static void launch_bwd_t(const Frame& fr, int blocks, const RasterIn& in, const RasterGrad& g, bool recompute,
                          cudaStream_t st) {
-    constexpr int NT = TW * TH / RaysPerThread<CM, true>::value;
+    constexpr int NT = TW * TH / RaysPerThread<CM, true, LIDAR, TW * TH>::value;
     const size_t sm = sizeof(Stage<CM, NT, LIDAR>) + sizeof(float) * NT * BwdLayout<CM, LIDAR>::kRow;
     if (recompute) {
         auto k = k_raster_bwd<CM, TW, TH, LIDAR, true>;
