@@ -60,12 +60,14 @@ __device__ __forceinline__ void batch_tile(const BatchReqDev& B, int lt, unsigne
     r[0] = ray_setup_rt<LIDAR>(S, tc.tx, tc.ty, threadIdx.x, S.tile_w, S.tile_h);
     const RasterIn in{B.rec, B.ids, B.ranges, B.feat, B.n, B.C};
     const int2 range = in.ranges[tc.gtile];
+    TileBox box{};
+    if (!LIDAR) box = camera_tile_box(S, tc.tx, tc.ty, S.tile_w, S.tile_h);
     float F[1][CM];
 #pragma unroll
     for (int c = 0; c < CM; c++) F[0][c] = 0.f;
     FwdState st[1];
     // 16 x 16 only fixes the 256-ray batch size here; the ray layout comes from r[].
-    forward_tile<CM, 16, 16, LIDAR, 1, true>(sm, in, tc, r, range, st, F);
+    forward_tile<CM, 16, 16, LIDAR, 1, true>(sm, in, tc, box, r, range, st, F);
     if (!r[0].inside) return;
     const int64_t o = r[0].o;
     const int C = B.C;

@@ -105,15 +105,67 @@ struct Stage {
     float4 g1[B];
     float2 g2[LIDAR ? B : 1];
     uint32_t id[B];
+    int live[LIDAR ? 1 : B];   // camera: the Gaussian can reach alpha >= 1/255 somewhere in this tile
     alignas(16) float f[B * CM];
 };
 
+// Pixel-centre rectangle of a camera tile (clipped to the image) and its row-time range.
+struct TileBox {
+    float x0, x1, y0, y1, t0, t1;
+};
+
+__device__ __forceinline__ TileBox camera_tile_box(const SensorDev& S, int tx, int ty, int tw, int th) {
+    TileBox b;
+    const int c1 = min(tx * tw + tw, S.width) - 1, r1 = min(ty * th + th, S.height) - 1;
+    b.x0 = tx * tw + 0.5f;
+    b.x1 = c1 + 0.5f;
+    b.y0 = ty * th + 0.5f;
+    b.y1 = r1 + 0.5f;
+    b.t0 = ((ty * th + 0.5f) / (float)S.height - 0.5f) * S.rs + S.dt;
+    b.t1 = ((r1 + 0.5f) / (float)S.height - 0.5f) * S.rs + S.dt;
+    return b;
+}
+
+// Can the Gaussian reach alpha >= 1/255 at some pixel centre of the tile, at that pixel's
+// row time?  alpha >= 1/255 needs d^T K d <= 2 ln(255 o') (K the conic).  The mean moves by
+// v t; relative to the mean at mid-time, a pixel at time t acts as a pixel displaced by at
+// most |v| (t1 - t0) / 2, so the test grows the rectangle by that sweep and takes the
+// minimum of the quadratic form over it (centre inside, else the minimum along an edge).
+// Conservative by a small margin: it never calls a tile dead where an FP32 evaluation
+// could still blend the Gaussian.
+__device__ __forceinline__ bool tile_live(const float4 g0, const float4 g1, const TileBox& b) {
+    const float a = g1.x, bb = g1.y, c = g1.z;
+    const float thr = 2.f * logf(255.f * g1.w) * 1.001f + 1e-3f;
+    if (!(thr >= 0.f)) return false;
+    const float tm = 0.5f * (b.t0 + b.t1), ht = 0.5f * fabsf(b.t1 - b.t0);
+    const float cx = g0.x + g0.z * tm, cy = g0.y + g0.w * tm;
+    const float gx = fabsf(g0.z) * ht + 1e-3f, gy = fabsf(g0.w) * ht + 1e-3f;
+    const float u0 = b.x0 - gx - cx, u1 = b.x1 + gx - cx;
+    const float v0 = b.y0 - gy - cy, v1 = b.y1 + gy - cy;
+    if (u0 <= 0.f && u1 >= 0.f && v0 <= 0.f && v1 >= 0.f) return true;
+    auto q = [&](float u, float v) { return a * u * u + 2.f * bb * u * v + c * v * v; };
+    auto edge_u = [&](float u) {   // u fixed, v in [v0, v1]
+        const float v = fminf(fmaxf(-bb * u / c, v0), v1);
+        return q(u, v);
+    };
+    auto edge_v = [&](float v) {   // v fixed, u in [u0, u1]
+        const float u = fminf(fmaxf(-bb * v / a, u0), u1);
+        return q(u, v);
+    };
+    const float m = fminf(fminf(edge_u(u0), edge_u(u1)), fminf(edge_v(v0), edge_v(v1)));
+    return !(m > thr);
+}
+
 template <int CM, int B, bool LIDAR>
-__device__ __forceinline__ void stage_load(Stage<CM, B, LIDAR>& sm, const RasterIn& in, int s, int64_t j, int slot) {
+__device__ __forceinline__ void stage_load(Stage<CM, B, LIDAR>& sm, const RasterIn& in, int s, int64_t j, int slot,
+                                           const TileBox& box) {
     const uint32_t id = in.ids[j];
     sm.id[slot] = id;
-    sm.g0[slot] = in.rec[rec_index(s, 0, in.n, id)];
-    sm.g1[slot] = in.rec[rec_index(s, 1, in.n, id)];
+    const float4 g0 = in.rec[rec_index(s, 0, in.n, id)];
+    const float4 g1 = in.rec[rec_index(s, 1, in.n, id)];
+    sm.g0[slot] = g0;
+    sm.g1[slot] = g1;
+    if (!LIDAR) sm.live[slot] = tile_live(g0, g1, box);
     if (LIDAR) {
         const float4 r2 = in.rec[rec_index(s, 2, in.n, id)];
         sm.g2[slot] = make_float2(r2.x, r2.y);
@@ -161,8 +213,8 @@ struct FwdState {
 // only the transmittance and last index are wanted (recomputation).
 template <int CM, int TW, int TH, bool LIDAR, int PX, bool WANT_F>
 __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, const RasterIn& in,
-                                            const TileCtx& tc, const RayCtx (&r)[PX], int2 range,
-                                            FwdState (&st)[PX], float (*F)[CM]) {
+                                            const TileCtx& tc, const TileBox& box, const RayCtx (&r)[PX],
+                                            int2 range, FwdState (&st)[PX], float (*F)[CM]) {
     constexpr int NT = TW * TH / PX, B = NT;   // one staged Gaussian per thread and batch
     int evals = 0;
     bool all_done = true;
@@ -178,11 +230,13 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
     }
     for (int start = range.x; start < range.y; start += B) {
         if (__syncthreads_count(all_done) == NT) break;
-        if (start + (int)threadIdx.x < range.y) stage_load<CM, B, LIDAR>(sm, in, tc.s, start + threadIdx.x, threadIdx.x);
+        if (start + (int)threadIdx.x < range.y)
+            stage_load<CM, B, LIDAR>(sm, in, tc.s, start + threadIdx.x, threadIdx.x, box);
         __syncthreads();
         if (!all_done) {
             const int nb = min(B, range.y - start);
             for (int k = 0; k < nb; k++) {
+                if (!LIDAR && !sm.live[k]) continue;   // alpha < 1/255 at every pixel of the tile
                 const float4 g0 = sm.g0[k], g1 = sm.g1[k];
                 all_done = true;
 #pragma unroll
@@ -234,13 +288,15 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, false, LIDAR, TW * 
 #pragma unroll
     for (int q = 0; q < PX; q++) r[q] = ray_setup<TW, TH, LIDAR>(fr, tc, threadIdx.x + q * NT);
     const int2 range = in.ranges[tc.gtile];
+    TileBox box{};
+    if (!LIDAR) box = camera_tile_box(fr.s[tc.s], tc.tx, tc.ty, TW, TH);
     float F[PX][CM];
 #pragma unroll
     for (int q = 0; q < PX; q++)
 #pragma unroll
         for (int c = 0; c < CM; c++) F[q][c] = 0.f;
     FwdState st[PX];
-    const int evals = forward_tile<CM, TW, TH, LIDAR, PX, true>(sm, in, tc, r, range, st, F);
+    const int evals = forward_tile<CM, TW, TH, LIDAR, PX, true>(sm, in, tc, box, r, range, st, F);
     if (out.evaluated) {
         unsigned long long e = (unsigned long long)evals;
 #pragma unroll
@@ -328,12 +384,14 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
     for (int q = 0; q < PX; q++) r[q] = ray_setup<TW, TH, LIDAR>(fr, tc, threadIdx.x + q * NT);
     const int2 range = in.ranges[tc.gtile];
     const int len = range.y - range.x;
+    TileBox box{};
+    if (!LIDAR) box = camera_tile_box(fr.s[tc.s], tc.tx, tc.ty, TW, TH);
     for (int q = threadIdx.x; q < B * ROW; q += NT) acc[q] = 0.f;
     float Tfin[PX];
     int last[PX];
     if (RECOMPUTE) {
         FwdState st[PX];
-        forward_tile<CM, TW, TH, LIDAR, PX, false>(sm, in, tc, r, range, st, nullptr);
+        forward_tile<CM, TW, TH, LIDAR, PX, false>(sm, in, tc, box, r, range, st, nullptr);
 #pragma unroll
         for (int q = 0; q < PX; q++) {
             Tfin[q] = st[q].T;
@@ -381,11 +439,12 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
     for (int end = range.x + max_last; end > range.x; end -= B) {
         const int cnt = min(B, end - range.x);
         __syncthreads();
-        if ((int)threadIdx.x < cnt) stage_load<CM, B, LIDAR>(sm, in, tc.s, end - 1 - threadIdx.x, threadIdx.x);
+        if ((int)threadIdx.x < cnt) stage_load<CM, B, LIDAR>(sm, in, tc.s, end - 1 - threadIdx.x, threadIdx.x, box);
         __syncthreads();
         for (int k = 0; k < cnt; k++) {
             const int idx = end - 1 - k - range.x;
             if (idx >= wl) continue;   // warp-uniform: no ray of this warp blended this deep
+            if (!LIDAR && !sm.live[k]) continue;   // no pixel of the tile can blend it
             const float4 g0 = sm.g0[k], g1 = sm.g1[k];
             float dx[PX], dy[PX], G[PX], a[PX];
             bool cl[PX], on[PX];
