@@ -62,9 +62,9 @@ __device__ __forceinline__ void batch_tile(const BatchReqDev& B, int lt, unsigne
     const int2 range = in.ranges[tc.gtile];
     TileBox box{};
     if (!LIDAR) box = camera_tile_box(S, tc.tx, tc.ty, S.tile_w, S.tile_h);
-    float F[1][CM];
+    float2 F[1][CM / 2];
 #pragma unroll
-    for (int c = 0; c < CM; c++) F[0][c] = 0.f;
+    for (int c = 0; c < CM / 2; c++) F[0][c] = make_float2(0.f, 0.f);
     FwdState st[1];
     // 16 x 16 only fixes the 256-ray batch size here; the ray layout comes from r[].
     forward_tile<CM, 16, 16, LIDAR, 1, true>(sm, in, tc, box, r, range, st, F);
@@ -75,11 +75,13 @@ __device__ __forceinline__ void batch_tile(const BatchReqDev& B, int lt, unsigne
     if ((C & 3) == 0) {
 #pragma unroll
         for (int c = 0; c < CM; c += 4)
-            if (c < C) *reinterpret_cast<float4*>(fo + c) = make_float4(F[0][c], F[0][c + 1], F[0][c + 2], F[0][c + 3]);
+            if (c < C)
+                *reinterpret_cast<float4*>(fo + c) =
+                    make_float4(F[0][c / 2].x, F[0][c / 2].y, F[0][c / 2 + 1].x, F[0][c / 2 + 1].y);
     } else {
 #pragma unroll
         for (int c = 0; c < CM; c++)
-            if (c < C) fo[c] = F[0][c];
+            if (c < C) fo[c] = (c & 1) ? F[0][c / 2].y : F[0][c / 2].x;
     }
     if (B.out_T) B.out_T[o] = st[0].T;
     if (LIDAR) {

@@ -214,7 +214,7 @@ struct FwdState {
 template <int CM, int TW, int TH, bool LIDAR, int PX, bool WANT_F>
 __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, const RasterIn& in,
                                             const TileCtx& tc, const TileBox& box, const RayCtx (&r)[PX],
-                                            int2 range, FwdState (&st)[PX], float (*F)[CM]) {
+                                            int2 range, FwdState (&st)[PX], float2 (*F)[CM / 2]) {
     constexpr int NT = TW * TH / PX, B = NT;   // one staged Gaussian per thread and batch
     int evals = 0;
     bool all_done = true;
@@ -252,9 +252,11 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
                             continue;
                         }
                         const float wgt = a * st[q].T;
-                        if (WANT_F) {
+                        if (WANT_F) {   // packed FP32 pairs: each lane is the same fused multiply-add
+                            const float2* f2 = reinterpret_cast<const float2*>(sm.f + k * CM);
+                            const float2 w2 = make_float2(wgt, wgt);
 #pragma unroll
-                            for (int c = 0; c < CM; c++) F[q][c] += sm.f[k * CM + c] * wgt;
+                            for (int c = 0; c < CM / 2; c++) F[q][c] = __ffma2_rn(f2[c], w2, F[q][c]);
                         }
                         if (LIDAR) {
                             const float rrs = sm.g2[k].x + sm.g2[k].y * r[q].t;
@@ -290,11 +292,11 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, false, LIDAR, TW * 
     const int2 range = in.ranges[tc.gtile];
     TileBox box{};
     if (!LIDAR) box = camera_tile_box(fr.s[tc.s], tc.tx, tc.ty, TW, TH);
-    float F[PX][CM];
+    float2 F[PX][CM / 2];
 #pragma unroll
     for (int q = 0; q < PX; q++)
 #pragma unroll
-        for (int c = 0; c < CM; c++) F[q][c] = 0.f;
+        for (int c = 0; c < CM / 2; c++) F[q][c] = make_float2(0.f, 0.f);
     FwdState st[PX];
     const int evals = forward_tile<CM, TW, TH, LIDAR, PX, true>(sm, in, tc, box, r, range, st, F);
     if (out.evaluated) {
@@ -312,11 +314,12 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, false, LIDAR, TW * 
 #pragma unroll
             for (int c = 0; c < CM; c += 4)
                 if (c < C)
-                    *reinterpret_cast<float4*>(fo + c) = make_float4(F[q][c], F[q][c + 1], F[q][c + 2], F[q][c + 3]);
+                    *reinterpret_cast<float4*>(fo + c) =
+                        make_float4(F[q][c / 2].x, F[q][c / 2].y, F[q][c / 2 + 1].x, F[q][c / 2 + 1].y);
         } else {
 #pragma unroll
             for (int c = 0; c < CM; c++)
-                if (c < C) fo[c] = F[q][c];
+                if (c < C) fo[c] = (c & 1) ? F[q][c / 2].y : F[q][c / 2].x;
         }
         if (out.T) out.T[r[q].o] = st[q].T;
         if (out.last) out.last[r[q].o] = st[q].last;
@@ -328,18 +331,60 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, false, LIDAR, TW * 
     }
 }
 
-// Sum of VP per-lane values over the warp by recursive halving: at each of the five
-// steps a lane keeps half of its values and receives the partner's copy of that half, so
-// the warp exchanges VP - VP/32 values instead of 5 VP.  Afterwards lane l holds the
-// totals of value indices [l * VP / 32, (l + 1) * VP / 32) (VP >= 32), or index l / 2
-// (VP == 16, even and odd lanes holding the same total).
+// Sum of VP per-lane values over the warp.  At each of the five butterfly steps
+// (lane offsets 16, 8, 4, 2, 1) an even count n is halved: a lane keeps one half of its
+// values and receives the partner's copy of that half; an odd count is summed whole.
+// Afterwards lane l holds the totals of the value indices
+// [reduce_first<VP>(l), reduce_first<VP>(l) + reduce_left<VP>()); the lanes of a replica
+// group share them out for reporting, one value per lane per round.
+__host__ __device__ constexpr int reduce_left_n(int n, int step) {
+    return step == 5 ? n : reduce_left_n((n >= 2 && n % 2 == 0) ? n / 2 : n, step + 1);
+}
+template <int VP>
+__host__ __device__ constexpr int reduce_left() { return reduce_left_n(VP, 0); }
+
+// Issue cost of the reduction (shuffles, selects and adds) for a padded count VP.
+__host__ __device__ constexpr int reduce_cost(int n, int step = 0) {
+    return step == 5 ? 0
+                     : ((n >= 2 && n % 2 == 0) ? 2 * n + reduce_cost(n / 2, step + 1)
+                                               : 2 * n + reduce_cost(n, step + 1));
+}
+// Cheapest padded count >= v (halving steps move half the values at 4 instructions each;
+// whole sums move every value at 2).
+__host__ __device__ constexpr int reduce_pad(int v, int best = 0, int p = 0) {
+    return p == 0 ? reduce_pad(v, v, v + 1)
+                  : (p > 64 ? best : reduce_pad(v, reduce_cost(p) < reduce_cost(best) ? p : best, p + 1));
+}
+
+// Number of trailing whole-sum steps: lanes that differ only in those low bits hold the
+// same totals afterwards (a replica group of 1 << reduce_plain() lanes).
+__host__ __device__ constexpr int reduce_plain_n(int n, int step) {
+    return step == 5 ? 0
+                     : ((n >= 2 && n % 2 == 0) ? reduce_plain_n(n / 2, step + 1) : 1 + reduce_plain_n(n, step + 1));
+}
+template <int VP>
+__host__ __device__ constexpr int reduce_plain() { return reduce_plain_n(VP, 0); }
+
+template <int VP>
+__device__ __forceinline__ int reduce_first(int lane) {
+    int n = VP, j0 = 0;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        if (n >= 2 && n % 2 == 0) {
+            n /= 2;
+            if (lane & o) j0 += n;
+        }
+    }
+    return j0;
+}
+
 template <int VP>
 __device__ __forceinline__ void warp_transpose_reduce(float (&v)[VP], int lane) {
     int n = VP;
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
         const bool upper = (lane & o) != 0;
-        if (n >= 2) {
+        if (n >= 2 && n % 2 == 0) {
             const int h = n / 2;
 #pragma unroll
             for (int i = 0; i < VP / 2; i++) {
@@ -351,7 +396,9 @@ __device__ __forceinline__ void warp_transpose_reduce(float (&v)[VP], int lane) 
             }
             n = h;
         } else {
-            v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+#pragma unroll
+            for (int i = 0; i < VP; i++)
+                if (i < n) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
         }
     }
 }
@@ -360,7 +407,7 @@ template <int CM, bool LIDAR>
 struct BwdLayout {
     static constexpr int kOffF = LIDAR ? 12 : 8;          // first feature slot (16-byte aligned)
     static constexpr int kV = kOffF + CM;                 // values per (ray, Gaussian)
-    static constexpr int kVP = kV <= 16 ? 16 : (kV <= 32 ? 32 : 64);
+    static constexpr int kVP = reduce_pad(kV);            // padded count for the warp reduction
     static constexpr int kRow = (kV + 3) & ~3;            // shared accumulator row (float4 aligned)
 };
 
@@ -509,14 +556,15 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
                 T[q] = Ti;
             }
             warp_transpose_reduce<VP>(v, lane);
-            constexpr int M = VP >= 32 ? VP / 32 : 1;
-            const int j0 = VP >= 32 ? lane * M : (lane >> 1);
-            if (VP >= 32 || (lane & 1) == 0) {
+            constexpr int M = reduce_left<VP>(), RG = 1 << reduce_plain<VP>();
+            const int j0 = reduce_first<VP>(lane), rank = lane & (RG - 1);
 #pragma unroll
-                for (int q = 0; q < M; q++) {
-                    const int j = j0 + q;
-                    if (j < V && v[q] != 0.f) atomicAdd(&acc[k * ROW + j], v[q]);
-                }
+            for (int q0 = 0; q0 < M; q0 += RG) {
+                float val = v[q0];
+#pragma unroll
+                for (int q = q0 + 1; q < q0 + RG && q < M; q++) val = (rank == q - q0) ? v[q] : val;
+                const int j = j0 + q0 + rank;
+                if (q0 + rank < M && j < V && val != 0.f) atomicAdd(&acc[k * ROW + j], val);
             }
         }
         __syncthreads();
