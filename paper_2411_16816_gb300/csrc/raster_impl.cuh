@@ -409,6 +409,9 @@ struct BwdLayout {
     static constexpr int kV = kOffF + CM;                 // values per (ray, Gaussian)
     static constexpr int kVP = reduce_pad(kV);            // padded count for the warp reduction
     static constexpr int kRow = (kV + 3) & ~3;            // shared accumulator row (float4 aligned)
+    // With at most two warps per tile each warp keeps its own accumulator slice and stores
+    // its per-Gaussian totals without atomics; the flush adds the slices.
+    __host__ __device__ static constexpr int slices(int warps) { return warps <= 2 ? warps : 1; }
 };
 
 template <int CM, int TW, int TH, bool LIDAR, bool RECOMPUTE>
@@ -419,9 +422,10 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
     constexpr int B = NT;   // one staged Gaussian per thread and batch
     using LY = BwdLayout<CM, LIDAR>;
     constexpr int OFF = LY::kOffF, VP = LY::kVP, ROW = LY::kRow;
+    constexpr int NSL = LY::slices(NT / 32);   // accumulator slices (1: shared by all warps, atomics)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Stage<CM, B, LIDAR>& sm = *reinterpret_cast<Stage<CM, B, LIDAR>*>(smem_raw);
-    float* acc = reinterpret_cast<float*>(smem_raw + sizeof(Stage<CM, B, LIDAR>));   // [B][ROW]
+    float* acc = reinterpret_cast<float*>(smem_raw + sizeof(Stage<CM, B, LIDAR>));   // [NSL][B][ROW]
     __shared__ int s_max_last[NT / 32 > 0 ? NT / 32 : 1];
     const int Crt = in.C;
     const int V = OFF + Crt;
@@ -433,7 +437,7 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
     const int len = range.y - range.x;
     TileBox box{};
     if (!LIDAR) box = camera_tile_box(fr.s[tc.s], tc.tx, tc.ty, TW, TH);
-    for (int q = threadIdx.x; q < B * ROW; q += NT) acc[q] = 0.f;
+    for (int q = threadIdx.x; q < NSL * B * ROW; q += NT) acc[q] = 0.f;
     float Tfin[PX];
     int last[PX];
     if (RECOMPUTE) {
@@ -564,7 +568,11 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
 #pragma unroll
                 for (int q = q0 + 1; q < q0 + RG && q < M; q++) val = (rank == q - q0) ? v[q] : val;
                 const int j = j0 + q0 + rank;
-                if (q0 + rank < M && j < V && val != 0.f) atomicAdd(&acc[k * ROW + j], val);
+                if (NSL > 1) {
+                    if (q0 + rank < M && j < V) acc[((threadIdx.x >> 5) * B + k) * ROW + j] = val;
+                } else if (q0 + rank < M && j < V && val != 0.f) {
+                    atomicAdd(&acc[k * ROW + j], val);
+                }
             }
         }
         __syncthreads();
@@ -572,6 +580,21 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
         if ((int)threadIdx.x < cnt) {
             const int slot = threadIdx.x;
             float* a_row = acc + slot * ROW;
+#pragma unroll
+            for (int w = 1; w < NSL; w++) {   // fold the other warps' slices into the first
+                float* o_row = acc + (w * B + slot) * ROW;
+#pragma unroll
+                for (int q = 0; q < ROW; q += 4) {
+                    float4 x = *reinterpret_cast<float4*>(a_row + q);
+                    const float4 y = *reinterpret_cast<float4*>(o_row + q);
+                    x.x += y.x;
+                    x.y += y.y;
+                    x.z += y.z;
+                    x.w += y.w;
+                    *reinterpret_cast<float4*>(a_row + q) = x;
+                    *reinterpret_cast<float4*>(o_row + q) = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
             const uint32_t id = sm.id[slot];
             const float4 s0 = *reinterpret_cast<float4*>(a_row);
             const float4 s1 = *reinterpret_cast<float4*>(a_row + 4);
@@ -627,7 +650,8 @@ template <int CM, int TW, int TH, bool LIDAR>
 static void launch_bwd_t(const Frame& fr, int blocks, const RasterIn& in, const RasterGrad& g, bool recompute,
                          cudaStream_t st) {
     constexpr int NT = TW * TH / RaysPerThread<CM, true, LIDAR, TW * TH>::value;
-    const size_t sm = sizeof(Stage<CM, NT, LIDAR>) + sizeof(float) * NT * BwdLayout<CM, LIDAR>::kRow;
+    using LY = BwdLayout<CM, LIDAR>;
+    const size_t sm = sizeof(Stage<CM, NT, LIDAR>) + sizeof(float) * LY::slices(NT / 32) * NT * LY::kRow;
     if (recompute) {
         auto k = k_raster_bwd<CM, TW, TH, LIDAR, true>;
         set_smem(k, sm);
