@@ -188,6 +188,7 @@ __global__ void __launch_bounds__(kHeadTile) k_head_train(const float* __restric
         {
             const int i = t >> 1, k = t & 1;   // 128 threads <-> 64 x 2 entries
             float acc = 0.f;
+#pragma unroll 8
             for (int rr = 0; rr < kHeadTile; rr++) acc += s.A[rr][i] * s.DO[rr][k];
             gW3 += acc;
         }
@@ -223,6 +224,7 @@ __global__ void __launch_bounds__(kHeadTile) k_head_train(const float* __restric
         for (int k = 0; k < kW1 / kHeadTile; k++) {
             const int e = t + kHeadTile * k, i = e / kHHid, j = e % kHHid;
             float acc = 0.f;
+#pragma unroll 8
             for (int rr = 0; rr < kHeadTile; rr++) acc += s.X[rr][i] * s.A[rr][j];
             gW1[k] += acc;
         }
@@ -230,6 +232,7 @@ __global__ void __launch_bounds__(kHeadTile) k_head_train(const float* __restric
         for (int k = 0; k < kW2 / kHeadTile; k++) {
             const int e = t + kHeadTile * k, i = e / kHHid, j = e % kHHid;
             float acc = 0.f;
+#pragma unroll 8
             for (int rr = 0; rr < kHeadTile; rr++) acc += s.H1[rr][i] * s.DZ2[rr][j];
             gW2[k] += acc;
         }
@@ -237,9 +240,11 @@ __global__ void __launch_bounds__(kHeadTile) k_head_train(const float* __restric
         {
             float acc = 0.f;
             if (t < kHHid)
-                for (int rr = 0; rr < kHeadTile; rr++) acc += s.A[rr][t];
+#pragma unroll 8
+            for (int rr = 0; rr < kHeadTile; rr++) acc += s.A[rr][t];
             else
-                for (int rr = 0; rr < kHeadTile; rr++) acc += s.DZ2[rr][t - kHHid];
+#pragma unroll 8
+            for (int rr = 0; rr < kHeadTile; rr++) acc += s.DZ2[rr][t - kHHid];
             gb += acc;
         }
     }

@@ -187,6 +187,13 @@ __device__ __forceinline__ void stage_load(Stage<CM, B, LIDAR>& sm, const Raster
     }
 }
 
+// Hardware reciprocal (at most 1 ulp from the rounded result).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // alpha of one staged Gaussian at the ray; returns false if it is skipped.
 template <bool LIDAR>
 __device__ __forceinline__ bool eval_alpha(const float4 g0, const float4 g1, const RayCtx& r, float& dx, float& dy,
@@ -211,7 +218,7 @@ struct FwdState {
 
 // Front-to-back blend of the tile's list for this thread's PX rays.  F may be null when
 // only the transmittance and last index are wanted (recomputation).
-template <int CM, int TW, int TH, bool LIDAR, int PX, bool WANT_F>
+template <int CM, int TW, int TH, bool LIDAR, int PX, bool WANT_F, bool COUNT = false>
 __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, const RasterIn& in,
                                             const TileCtx& tc, const TileBox& box, const RayCtx (&r)[PX],
                                             int2 range, FwdState (&st)[PX], float2 (*F)[CM / 2]) {
@@ -242,7 +249,7 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
 #pragma unroll
                 for (int q = 0; q < PX; q++) {
                     if (st[q].done) continue;
-                    evals++;
+                    if (COUNT) evals++;
                     float dx, dy, G, a;
                     bool cl;
                     if (eval_alpha<LIDAR>(g0, g1, r[q], dx, dy, G, a, cl)) {
@@ -278,7 +285,7 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
     return evals;
 }
 
-template <int CM, int TW, int TH, bool LIDAR>
+template <int CM, int TW, int TH, bool LIDAR, bool COUNT>
 __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, false, LIDAR, TW * TH>::value)
     k_raster_fwd(const __grid_constant__ Frame fr, RasterIn in, RasterOut out) {
     constexpr int PX = RaysPerThread<CM, false, LIDAR, TW * TH>::value;
@@ -298,8 +305,8 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, false, LIDAR, TW * 
 #pragma unroll
         for (int c = 0; c < CM / 2; c++) F[q][c] = make_float2(0.f, 0.f);
     FwdState st[PX];
-    const int evals = forward_tile<CM, TW, TH, LIDAR, PX, true>(sm, in, tc, box, r, range, st, F);
-    if (out.evaluated) {
+    const int evals = forward_tile<CM, TW, TH, LIDAR, PX, true, COUNT>(sm, in, tc, box, r, range, st, F);
+    if (COUNT) {
         unsigned long long e = (unsigned long long)evals;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
@@ -512,7 +519,7 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
                 // a ray that does not blend this Gaussian gets alpha = 0: every term vanishes
                 const float aq = on[q] ? a[q] : 0.f;
                 const float Gq = on[q] ? G[q] : 0.f;
-                const float inv = __frcp_rn(1.f - aq);
+                const float inv = rcp_approx(1.f - aq);   // 1 - alpha >= 0.001: no special cases
                 const float Ti = T[q] * inv;
                 const float wgt = aq * Ti;
                 float Gf = 0.f;
@@ -641,7 +648,8 @@ template <int CM, int TW, int TH, bool LIDAR>
 static void launch_fwd_t(const Frame& fr, int blocks, const RasterIn& in, const RasterOut& out, cudaStream_t st) {
     constexpr int NT = TW * TH / RaysPerThread<CM, false, LIDAR, TW * TH>::value;
     const size_t sm = sizeof(Stage<CM, NT, LIDAR>);
-    auto k = k_raster_fwd<CM, TW, TH, LIDAR>;
+    // the evaluated-pair counter is compiled in only when it is asked for
+    auto k = out.evaluated ? k_raster_fwd<CM, TW, TH, LIDAR, true> : k_raster_fwd<CM, TW, TH, LIDAR, false>;
     set_smem(k, sm);
     k<<<blocks, NT, sm, st>>>(fr, in, out);
 }
