@@ -23,8 +23,8 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;  // 2048
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;  // 4096
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 2048
 
 __device__ __forceinline__ int64_t eff_count(const int64_t* count_ptr, int64_t max_count, int64_t capacity) {
     if (!count_ptr) return max_count;
@@ -204,12 +204,19 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
     const int64_t base = block0 + (int64_t)warp * (kSortItems * 32);
     __syncthreads();
     uint32_t kk[kSortItems], vv[kSortItems], rr[kSortItems];
+    // all loads first, so that they are in flight together (the ranking below orders
+    // shared-memory accesses with warp barriers, which loads cannot be moved across)
 #pragma unroll
     for (int it = 0; it < kSortItems; it++) {
         const int64_t idx = base + it * 32 + lane;
         const bool valid = idx < count;
         kk[it] = valid ? kin[idx] : 0u;
         vv[it] = valid ? vin[idx] : 0u;
+    }
+#pragma unroll
+    for (int it = 0; it < kSortItems; it++) {
+        const int64_t idx = base + it * 32 + lane;
+        const bool valid = idx < count;
         const uint32_t d = valid ? ((kk[it] >> shift) & 255u) : 256u;
         const uint32_t peers = __match_any_sync(0xffffffffu, d);
         const uint32_t cnt = valid ? wh[warp][d] : 0u;
@@ -299,9 +306,22 @@ struct EmitIn {
     __device__ int64_t operator()(int64_t j) const { return n_tiles[sorted_pairs[j]]; }
 };
 
-struct OffsetOut {  // exclusive prefix of the tile counts, in depth order
+constexpr int kEmitThreads = 256;
+constexpr int kEmitItems = 8;
+constexpr int kEmitTile = kEmitThreads * kEmitItems;  // output slots per block
+
+// Exclusive prefix of the tile counts, in depth order.  It also records, for every emit
+// block, the visible pair that owns the block's first slot (the pair whose slot range
+// [prefix, prefix + count) holds b * kEmitTile), so that no block has to search for it.
+struct OffsetOut {
     int64_t* offsets;
-    __device__ void operator()(int64_t j, int64_t prefix, int64_t) const { offsets[j] = prefix; }
+    uint32_t* first_owner;
+    int64_t nblocks;
+    __device__ void operator()(int64_t j, int64_t prefix, int64_t v) const {
+        offsets[j] = prefix;
+        for (int64_t b = (prefix + kEmitTile - 1) / kEmitTile; b < nblocks && b * kEmitTile < prefix + v; b++)
+            first_owner[b] = (uint32_t)j;
+    }
 };
 
 struct EmitTables {
@@ -310,68 +330,65 @@ struct EmitTables {
     int is_lidar[kMaxSensors];
 };
 
-constexpr int kEmitThreads = 256;
-constexpr int kEmitItems = 8;
-constexpr int kEmitTile = kEmitThreads * kEmitItems;  // output slots per block
-
 // Writes intersections [b*2048, (b+1)*2048): each block binary-searches the first
 // visible pair that owns one of its slots, stages the owners' offsets in shared memory
 // and every thread then writes one (tile, Gaussian) pair per slot it owns.  Work per
 // block is fixed whatever the size of the Gaussians, and the writes are contiguous.
 __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restrict__ sorted_pairs,
                                                       const int64_t* __restrict__ offsets,
+                                                      const uint32_t* __restrict__ first_owner,
                                                       const int64_t* vis_count, const int64_t* n_isect,
                                                       int64_t capacity, const short4* __restrict__ rect, int64_t n,
-                                                      const __grid_constant__ EmitTables tab,
+                                                      float inv_n, const __grid_constant__ EmitTables tab,
                                                       uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-    __shared__ int64_t s_off[kEmitTile + 1];
-    __shared__ int64_t s_lo;
+    __shared__ int s_off[kEmitTile];   // owners' first slots relative to the block (the first may be < 0)
     const int64_t total = *n_isect;
     if (total > capacity) return;   // over capacity: write nothing
     const int64_t o0 = (int64_t)blockIdx.x * kEmitTile;
     if (o0 >= total) return;
     const int64_t V = *vis_count;
-    const int64_t o1 = min(o0 + (int64_t)kEmitTile, total);
-    if (threadIdx.x == 0) {
-        // last j with offsets[j] <= o0 (exists: offsets[0] == 0)
-        int64_t lo = 0, hi = V - 1;
-        while (lo < hi) {
-            const int64_t mid = (lo + hi + 1) >> 1;
-            if (offsets[mid] <= o0) lo = mid;
-            else hi = mid - 1;
-        }
-        s_lo = lo;
-    }
-    __syncthreads();
-    const int64_t jlo = s_lo;
-    // owners of this block's slots are jlo .. jlo + count - 1 with count <= kEmitTile
-    // (every visible pair owns at least one slot)
-    const int64_t nown = min((int64_t)kEmitTile, V - jlo);
-    for (int q = threadIdx.x; q < nown; q += kEmitThreads) s_off[q] = offsets[jlo + q];
+    const int nslot = (int)min((int64_t)kEmitTile, total - o0);
+    const int64_t jlo = first_owner[blockIdx.x];
+    // owners of this block's slots are jlo .. jlo + nown - 1 (every visible pair owns a slot)
+    const int nown = (int)min((int64_t)kEmitTile, V - jlo);
+    for (int q = threadIdx.x; q < nown; q += kEmitThreads) s_off[q] = (int)(offsets[jlo + q] - o0);
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < kEmitItems; it++) {
-        const int64_t o = o0 + it * kEmitThreads + threadIdx.x;
-        if (o >= o1) break;
+        const int o = it * kEmitThreads + threadIdx.x;
+        if (o >= nslot) break;
         // last local owner with s_off <= o
-        int lo = 0, hi = (int)nown - 1;
+        int lo = 0, hi = nown - 1;
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (s_off[mid] <= o) lo = mid;
             else hi = mid - 1;
         }
         const uint32_t p = sorted_pairs[jlo + lo];
-        const int s = (int)(p / (uint64_t)n);
-        const uint32_t i = (uint32_t)(p - (uint64_t)s * n);
+        // sensor s = floor(p / n) and row / column in the rectangle, each from a float
+        // estimate that is within one of the quotient, then corrected exactly
+        int s = (int)((float)p * inv_n);
+        if ((uint64_t)s * (uint64_t)n > p) s--;
+        else if ((uint64_t)(s + 1) * (uint64_t)n <= p) s++;
+        const uint32_t i = (uint32_t)(p - (uint64_t)s * (uint64_t)n);
         const short4 rc = rect[p];
         const int w = rc.z - rc.x;
-        const int q = (int)(o - s_off[lo]);
-        const int ty = rc.y + q / w;
-        int col = rc.x + q % w;
+        const int q = o - s_off[lo];
+        int dy = (int)__fdividef((float)q + 0.5f, (float)w);
+        int dx = q - dy * w;
+        if (dx < 0) {
+            dy--;
+            dx += w;
+        } else if (dx >= w) {
+            dy++;
+            dx -= w;
+        }
+        const int ty = rc.y + dy;
+        int col = rc.x + dx;
         const int tx = tab.tiles_x[s];
         if (tab.is_lidar[s] && col >= tx) col -= tx;
-        keys[o] = (uint32_t)(tab.tile_base[s] + ty * tx + col);
-        vals[o] = i;
+        keys[o0 + o] = (uint32_t)(tab.tile_base[s] + ty * tx + col);
+        vals[o0 + o] = i;
     }
 }
 
@@ -408,6 +425,7 @@ BinWorkspace carve_workspace(void* base, int64_t pairs, int64_t capacity) {
     w.ikeys[0] = (uint32_t*)take(4 * cp);
     w.ikeys[1] = (uint32_t*)take(4 * cp);
     w.ivals_tmp = (uint32_t*)take(4 * cp);
+    w.first_owner = (uint32_t*)take(4 * ((cp + kEmitTile - 1) / kEmitTile));
     const int64_t maxn = vp > cp ? vp : cp;
     const int64_t sort_blocks = (maxn + kSortTile - 1) / kSortTile;
     w.hist = (uint32_t*)take(4 * 256 * sort_blocks);
@@ -441,18 +459,19 @@ void launch_bin_sort(const Frame& fr, int64_t n, const float4* rec, const short4
     // the result lands in buffer passes % 2: make that buffer the caller's isect_ids
     vals_buf[passes & 1] = isect_ids;
     vals_buf[(passes & 1) ^ 1] = w.ivals_tmp;
-    device_scan(EmitIn{sorted_pairs, n_tiles}, OffsetOut{w.offsets}, pairs, w.vis_count, INT64_MAX, w.partials,
-                n_isect, st);
+    const int64_t emit_blocks = (capacity + kEmitTile - 1) / kEmitTile;
+    device_scan(EmitIn{sorted_pairs, n_tiles}, OffsetOut{w.offsets, w.first_owner, emit_blocks}, pairs, w.vis_count,
+                INT64_MAX, w.partials, n_isect, st);
     EmitTables tab{};
     for (int s = 0; s < fr.n_sensors; s++) {
         tab.tile_base[s] = fr.s[s].tile_base;
         tab.tiles_x[s] = fr.s[s].tiles_x;
         tab.is_lidar[s] = fr.s[s].kind == SPLAT_SENSOR_LIDAR;
     }
-    const int64_t emit_blocks = (capacity + kEmitTile - 1) / kEmitTile;
     if (emit_blocks > 0)
-        k_emit<<<(unsigned)emit_blocks, kEmitThreads, 0, st>>>(sorted_pairs, w.offsets, w.vis_count, n_isect, capacity,
-                                                               rect, n, tab, w.ikeys[0], vals_buf[0]);
+        k_emit<<<(unsigned)emit_blocks, kEmitThreads, 0, st>>>(sorted_pairs, w.offsets, w.first_owner, w.vis_count,
+                                                               n_isect, capacity, rect, n, (float)(1.0 / (double)n),
+                                                               tab, w.ikeys[0], vals_buf[0]);
     // 4. stable sort of the intersections by tile id
     radix_sort(w.ikeys, vals_buf, passes, capacity, n_isect, capacity, w.hist, w.partials, st);
     // 5. per-tile ranges

@@ -65,6 +65,7 @@ struct BinWorkspace {
     int64_t* offsets;
     uint32_t* ikeys[2];
     uint32_t* ivals_tmp;
+    uint32_t* first_owner;   // visible pair owning each emit block's first slot
     uint32_t* hist;
     int64_t* partials;
     size_t bytes;
