@@ -327,6 +327,7 @@ struct OffsetOut {
 struct EmitTables {
     int tile_base[kMaxSensors];
     int tiles_x[kMaxSensors];
+    int tiles_y[kMaxSensors];
     int is_lidar[kMaxSensors];
 };
 
@@ -374,6 +375,12 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
         const short4 rc = rect[p];
         const int w = rc.z - rc.x;
         const int q = o - s_off[lo];
+        if (!(rc.x >= 0 && rc.x < tab.tiles_x[s] && w > 0 && w <= tab.tiles_x[s] && rc.y >= 0 && rc.w > rc.y &&
+              rc.w <= tab.tiles_y[s])) {   // malformed projection: an id past every tile, never ranged
+            keys[o0 + o] = 0xffffffffu;
+            vals[o0 + o] = i;
+            continue;
+        }
         int dy = (int)__fdividef((float)q + 0.5f, (float)w);
         int dx = q - dy * w;
         if (dx < 0) {
@@ -393,11 +400,12 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
 }
 
 __global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict__ keys, const int64_t* count_ptr,
-                                                      int64_t capacity, int2* ranges) {
+                                                      int64_t capacity, int64_t total_tiles, int2* ranges) {
     const int64_t count = eff_count(count_ptr, capacity, capacity);
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < count;
          j += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t t = keys[j];
+        if ((int64_t)t >= total_tiles) continue;   // never a tile: left out of every range
         if (j == 0 || keys[j - 1] != t) ranges[t].x = (int)j;
         if (j == count - 1 || keys[j + 1] != t) ranges[t].y = (int)(j + 1);
     }
@@ -466,6 +474,7 @@ void launch_bin_sort(const Frame& fr, int64_t n, const float4* rec, const short4
     for (int s = 0; s < fr.n_sensors; s++) {
         tab.tile_base[s] = fr.s[s].tile_base;
         tab.tiles_x[s] = fr.s[s].tiles_x;
+        tab.tiles_y[s] = fr.s[s].tiles_y;
         tab.is_lidar[s] = fr.s[s].kind == SPLAT_SENSOR_LIDAR;
     }
     if (emit_blocks > 0)
@@ -478,7 +487,8 @@ void launch_bin_sort(const Frame& fr, int64_t n, const float4* rec, const short4
     int64_t blocks = (capacity + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
     if (blocks > 0)
-        k_tile_ranges<<<(unsigned)blocks, 256, 0, st>>>(w.ikeys[passes & 1], n_isect, capacity, tile_ranges);
+        k_tile_ranges<<<(unsigned)blocks, 256, 0, st>>>(w.ikeys[passes & 1], n_isect, capacity, total_tiles,
+                                                        tile_ranges);
 }
 
 }  // namespace splat

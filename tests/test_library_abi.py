@@ -67,8 +67,10 @@ def test_frame_layout_counts_tiles_and_rays():
     assert lib.splat_frame_layout(2, arr, ctypes.byref(total), tiles, rays) == 0
     assert list(tiles) == [8 * 6, 8 * 2] and total.value == 64
     assert list(rays) == [128 * 96, 16 * 256]
-    ws = ctypes.c_size_t()
-    assert lib.splat_workspace_size(2000, 2, arr, 100000, ctypes.byref(ws)) == 0 and ws.value > 100000 * 12
+    ws, ws2 = ctypes.c_size_t(), ctypes.c_size_t()
+    # visible-pair keys and values, double-buffered: at least 16 bytes per (sensor, Gaussian)
+    assert lib.splat_workspace_size(2000, 2, arr, 100000, ctypes.byref(ws)) == 0 and ws.value >= 16 * 2 * 2000
+    assert lib.splat_workspace_size(4000, 2, arr, 100000, ctypes.byref(ws2)) == 0 and ws2.value > ws.value
 
 
 @pytest.mark.parametrize("mutate, msg", [

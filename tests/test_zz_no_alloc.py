@@ -68,8 +68,11 @@ def test_noalloc_bin_sort_equals_workspace_bin_sort_on_repeated_calls():
 
 def test_noalloc_rejects_a_frame_beyond_its_scratch():
     entry = _entry()
-    g, sensors = scenes.driving_frame(n=200_000)
+    # 2M Gaussians x 7 sensors: the visible-pair buffers alone are far above 32 MiB
+    g, sensors = scenes.driving_frame(n=2_000_000)
     fr = Frame(sensors, len(g["opacities"]), g["features"].shape[1], DEV, capacity=1 << 22)
+    fr.project(fr.c_gaussians(gaussians_to_device(g, DEV)))   # valid inputs even though it must refuse
+    torch.cuda.synchronize()
     bins = L.splat_bins(fr.isect_ids.data_ptr(), fr.ranges.data_ptr(), fr.n_isect.data_ptr())
     st = entry(fr.n, len(fr.sensors), fr.c_sensors, fr.c_proj(), fr.capacity, bins, _stream())
     assert st == L.SPLAT_ERR_INVALID_ARG
