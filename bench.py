@@ -217,7 +217,7 @@ def launches_per_step(fr, n_l1):
     passes = max(1, (bits + 7) // 8)
     scan = 3
     radix_pass = 1 + scan + 1
-    bin_sort = scan + 4 * radix_pass + scan + passes * radix_pass + 1
+    bin_sort = scan + 4 * radix_pass + scan + 1 + passes * radix_pass + 1   # ... emit ... tile ranges
     raster = (1 if fr.cam_idx else 0) + (1 if fr.lid_idx else 0)
     return 1 + bin_sort + raster + n_l1 + raster + 1
 
@@ -255,13 +255,15 @@ def run_ours(args):
              "lid_range_exp": torch.empty_like(out["lid_range_exp"])}
     pgrads = {k: torch.zeros_like(v) for k, v in gd.items() if v is not None}
     loss = torch.zeros(1, device=dev)
-    l1_terms = [("cam_feat", 1.0 / out["cam_feat"].numel()), ("lid_feat", 1.0 / out["lid_feat"].numel()),
-                ("lid_range_exp", 1.0 / out["lid_range_exp"].numel())]
+    # the camera L1 term is fused into the camera raster launch; the lidar terms run as
+    # separate element-wise launches
+    cam_l1 = (tgt["cam_feat"], 1.0 / out["cam_feat"].numel(), grads["cam_feat"], loss) if "cam_feat" in tgt else None
+    l1_terms = [("lid_feat", 1.0 / out["lid_feat"].numel()), ("lid_range_exp", 1.0 / out["lid_range_exp"].numel())]
     stream = torch.cuda.current_stream()
 
     def step(src=None):
         loss.zero_()
-        fr.forward(src if src is not None else gd, keep_state=True, check=False, out=out)
+        fr.forward(src if src is not None else gd, keep_state=True, check=False, out=out, cam_l1=cam_l1)
         for key, sc in l1_terms:
             l1_loss(out[key], tgt[key], sc, grads[key], loss)
         fr.backward(src if src is not None else gd, out, grads, param_grads=pgrads)
@@ -361,9 +363,10 @@ def run_ours(args):
     S = len(fr.sensors)
     timed("project", lambda: fr.project(cg))
     timed("bin_sort", lambda: fr.bin_sort())
-    timed("raster_camera_fwd", lambda: L.call("splat_render_camera", ctypes.byref(cg), S, fr.c_sensors, fr.c_proj(),
-                                                fr.c_bins(), _vp(out["cam_feat"]), _vp(out["cam_T"]),
-                                                _vp(out["cam_last"]), None, st))
+    timed("raster_camera_fwd", lambda: L.call("splat_render_camera_l1", ctypes.byref(cg), S, fr.c_sensors,
+                                                fr.c_proj(), fr.c_bins(), _vp(tgt["cam_feat"]), float(cam_l1[1]),
+                                                _vp(out["cam_feat"]), _vp(out["cam_T"]), _vp(out["cam_last"]),
+                                                _vp(grads["cam_feat"]), _vp(loss), None, st))
     timed("raster_lidar_fwd", lambda: L.call("splat_render_lidar", ctypes.byref(cg), S, fr.c_sensors, fr.c_proj(),
                                                fr.c_bins(), _vp(out["lid_feat"]), _vp(out["lid_range_exp"]),
                                                _vp(out["lid_range_med"]), _vp(out["lid_alpha"]), _vp(out["lid_T"]),

@@ -198,6 +198,21 @@ splat_status splat_render_camera(const splat_gaussians *g, int32_t n_sensors, co
                                  splat_projected proj, splat_bins bins, float *out_feat, float *out_T,
                                  int32_t *out_last, uint64_t *evaluated, void *stream);
 
+/* Camera rasterization with the L1 photometric term (Eq. loss_fn, lambda_r L1) fused into
+ * its epilogue: the same render as splat_render_camera, then, per ray and channel,
+ * loss += scale * |F - target| and grad_feat = scale * sign(F - target) (the upstream
+ * gradient of splat_render_camera_backward), without a separate pass over the images.
+ *   target[rays][C]     device, the reference image(s) in out_feat's layout; 16-byte
+ *                       aligned when C % 4 == 0 (so are grad_feat and out_feat)
+ *   grad_feat[rays][C]  device, written (not accumulated)
+ *   loss                device float, accumulated (the caller zeroes it)
+ *   out_feat            may be NULL when the rendered image itself is not wanted;
+ *                       out_T, out_last and evaluated as for splat_render_camera. */
+splat_status splat_render_camera_l1(const splat_gaussians *g, int32_t n_sensors, const splat_sensor *sensors,
+                                    splat_projected proj, splat_bins bins, const float *target, float scale,
+                                    float *out_feat, float *out_T, int32_t *out_last, float *grad_feat,
+                                    float *loss, uint64_t *evaluated, void *stream);
+
 /* Lidar rasterization (Sec. 3.3: blended features, expected range of the rolling-
  * shutter ranges r + v_r t, median range = rolling-shutter range of the first Gaussian
  * after which the transmittance is below 0.5, 0 if none).  Outputs are concatenated
@@ -337,6 +352,11 @@ splat_status splat_head_adam(float *params, const float *grad, float *m, float *
 
 /* Message of the last non-OK status on this host thread ("" if none). */
 const char *splat_last_error(void);
+
+/* Waits for the stream and reports a CUDA error raised by anything enqueued on it as
+ * SPLAT_ERR_CUDA (message in splat_last_error).  The library keeps no device status word:
+ * capacity overflow is reported through bins.n_isect, and no kernel waits on a flag. */
+splat_status splat_sync_status(void *stream);
 
 #ifdef __cplusplus
 }

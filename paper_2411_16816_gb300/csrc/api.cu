@@ -261,6 +261,36 @@ splat_status splat_render_camera(const splat_gaussians* g, int32_t n_sensors, co
     return check_launch("splat_render_camera");
 }
 
+splat_status splat_render_camera_l1(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
+                                    splat_projected proj, splat_bins bins, const float* target, float scale,
+                                    float* out_feat, float* out_T, int32_t* out_last, float* grad_feat, float* loss,
+                                    uint64_t* evaluated, void* stream) {
+    Frame fr;
+    int tw, th;
+    splat_status st = render_common(g, n_sensors, sensors, proj, bins, fr, false, tw, th);
+    if (st != SPLAT_OK) return st;
+    if (fr.n_cams == 0) return SPLAT_OK;
+    if (!target || !grad_feat || !loss) return fail(SPLAT_ERR_INVALID_ARG, "target, grad_feat and loss are required");
+    if ((g->channels & 3) == 0 &&
+        !(aligned16(target) && aligned16(grad_feat) && (!out_feat || aligned16(out_feat))))
+        return fail(SPLAT_ERR_INVALID_ARG, "target, grad_feat or out_feat misaligned");
+    RasterIn in{(const float4*)proj.rec, bins.isect_ids, (const int2*)bins.tile_ranges, g->features, g->n,
+                g->channels};
+    RasterOut out{out_feat, out_T, out_last, nullptr, nullptr, nullptr, (unsigned long long*)evaluated,
+                  target, grad_feat, loss, scale};
+    if (!launch_raster_fwd(false, g->channels, tw, th, fr, fr.n_cam_blocks, in, out, (cudaStream_t)stream))
+        return fail(SPLAT_ERR_INVALID_ARG, "unsupported camera configuration");
+    return check_launch("splat_render_camera_l1");
+}
+
+splat_status splat_sync_status(void* stream) {
+    const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return fail(SPLAT_ERR_CUDA, "%s", cudaGetErrorString(e));
+    const cudaError_t e2 = cudaGetLastError();
+    if (e2 != cudaSuccess) return fail(SPLAT_ERR_CUDA, "%s", cudaGetErrorString(e2));
+    return SPLAT_OK;
+}
+
 splat_status splat_render_lidar(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
                                 splat_projected proj, splat_bins bins, float* out_feat, float* out_range_exp,
                                 float* out_range_med, float* out_alpha, float* out_T, int32_t* out_last,

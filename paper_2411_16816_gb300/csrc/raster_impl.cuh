@@ -313,9 +313,53 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, false, LIDAR, TW * 
         if ((threadIdx.x & 31) == 0) atomicAdd(out.evaluated, e);
     }
     const int C = in.C;
+    if (!LIDAR && out.l1_grad) {
+        // fused L1 term (Eq. loss_fn): the gradient image and one loss atomic per block
+        float acc = 0.f;
+        const float sc = out.l1_scale;
+        auto sg = [sc](float d) { return d > 0.f ? sc : (d < 0.f ? -sc : 0.f); };
+#pragma unroll
+        for (int q = 0; q < PX; q++) {
+            if (!r[q].inside) continue;
+            const float* tg = out.l1_target + r[q].o * C;
+            float* gd = out.l1_grad + r[q].o * C;
+            if ((C & 3) == 0) {
+#pragma unroll
+                for (int c = 0; c < CM; c += 4) {
+                    if (c < C) {
+                        const float4 t = *reinterpret_cast<const float4*>(tg + c);
+                        const float d0 = F[q][c / 2].x - t.x, d1 = F[q][c / 2].y - t.y;
+                        const float d2 = F[q][c / 2 + 1].x - t.z, d3 = F[q][c / 2 + 1].y - t.w;
+                        acc += fabsf(d0) + fabsf(d1) + fabsf(d2) + fabsf(d3);
+                        *reinterpret_cast<float4*>(gd + c) = make_float4(sg(d0), sg(d1), sg(d2), sg(d3));
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < CM; c++) {
+                    if (c < C) {
+                        const float d = ((c & 1) ? F[q][c / 2].y : F[q][c / 2].x) - tg[c];
+                        acc += fabsf(d);
+                        gd[c] = sg(d);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        __shared__ float s_l1[NT / 32 > 0 ? NT / 32 : 1];
+        if ((threadIdx.x & 31) == 0) s_l1[threadIdx.x >> 5] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float tot = 0.f;
+            for (int w = 0; w < NT / 32; w++) tot += s_l1[w];
+            if (tot != 0.f) atomicAdd(out.l1_loss, tot * sc);
+        }
+    }
 #pragma unroll
     for (int q = 0; q < PX; q++) {
         if (!r[q].inside) continue;
+        if (!out.feat) continue;
         float* fo = out.feat + r[q].o * C;
         if ((C & 3) == 0) {
 #pragma unroll

@@ -45,6 +45,11 @@ struct RasterOut {
     float* range_med;   // lidar
     float* alpha;       // lidar
     unsigned long long* evaluated;  // optional: number of (ray, Gaussian) pairs examined
+    // optional camera L1 epilogue: loss += scale * sum |F - target|, l1_grad = scale * sign(F - target)
+    const float* l1_target;
+    float* l1_grad;
+    float* l1_loss;
+    float l1_scale;
 };
 
 struct RasterGrad {

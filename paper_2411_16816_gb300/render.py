@@ -170,14 +170,21 @@ class Frame:
             out["lid_last"] = torch.empty(R, dtype=torch.int32, device=dev) if keep_state else None
         return out
 
-    def rasterize(self, cg, out: dict, stream=None, evaluated: torch.Tensor | None = None):
+    def rasterize(self, cg, out: dict, stream=None, evaluated: torch.Tensor | None = None, cam_l1=None):
         """Camera and lidar raster launches.  `evaluated` (optional int64[2] device tensor)
-        accumulates the examined (ray, Gaussian) pairs of the camera and lidar launch."""
+        accumulates the examined (ray, Gaussian) pairs of the camera and lidar launch.
+        `cam_l1` = (target, scale, grad, loss) fuses the camera L1 term into the camera
+        launch: loss += scale * sum |F - target| and grad = scale * sign(F - target)."""
         st = _stream(stream)
         ev_c = ev_l = None
         if evaluated is not None:
             ev_c, ev_l = evaluated[0:1], evaluated[1:2]
-        if self.cam_idx:
+        if self.cam_idx and cam_l1 is not None:
+            target, scale, grad, loss = cam_l1
+            L.call("splat_render_camera_l1", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
+                   self.c_bins(), _vp(target), float(scale), _vp(out["cam_feat"]), _vp(out["cam_T"]),
+                   _vp(out.get("cam_last")), _vp(grad), _vp(loss), _vp(ev_c), st)
+        elif self.cam_idx:
             L.call("splat_render_camera", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
                    self.c_bins(), _vp(out["cam_feat"]), _vp(out["cam_T"]), _vp(out.get("cam_last")), _vp(ev_c), st)
         if self.lid_idx:
@@ -186,17 +193,17 @@ class Frame:
                    _vp(out["lid_alpha"]), _vp(out.get("lid_T")), _vp(out.get("lid_last")), _vp(ev_l), st)
 
     def forward(self, g: dict, keep_state: bool = True, check: bool = True, out: dict | None = None,
-                stream=None) -> dict:
+                stream=None, cam_l1=None) -> dict:
         """Project, bin and rasterize every sensor.  With keep_state the per-ray final
         transmittance and last index are kept for the backward pass; without it the
-        backward recomputes them per tile."""
+        backward recomputes them per tile.  cam_l1 as for rasterize()."""
         cg = self.c_gaussians(g)
         self.project(cg, stream)
         self.bin_sort(stream)
         if check:
             self.ensure_capacity(stream)
         out = self.alloc_outputs(keep_state) if out is None else out
-        self.rasterize(cg, out, stream)
+        self.rasterize(cg, out, stream, cam_l1=cam_l1)
         self.version += 1
         return out
 

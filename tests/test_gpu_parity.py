@@ -313,3 +313,38 @@ def test_l1_loss_kernel():
     torch.cuda.synchronize()
     assert abs(loss.item() - 0.5 * np.abs(a.astype(np.float64) - b).sum()) < 1e-4 * 0.5 * np.abs(a - b).sum()
     assert np.array_equal(grad.cpu().numpy(), 0.5 * np.sign(a - b))
+
+
+@pytest.mark.parametrize("channels", [3, 16])
+def test_fused_camera_l1_equals_render_then_l1(channels):
+    """splat_render_camera_l1 renders exactly what splat_render_camera renders and writes
+    the gradient of splat_l1_loss bit for bit; the loss agrees up to summation order."""
+    from paper_2411_16816_gb300.render import l1_loss
+    g, sensors = _dynamic_tiny()
+    if channels != g["features"].shape[1]:
+        g = dict(g)
+        g["features"] = np.random.default_rng(5).normal(size=(len(g["opacities"]), channels)).astype(np.float32)
+    gd = gaussians_to_device(g, U.DEV)
+    fr = Frame(sensors, len(g["opacities"]), g["features"].shape[1], U.DEV)
+    out = fr.forward(gd)
+    target = torch.rand_like(out["cam_feat"])
+    scale = 1.0 / out["cam_feat"].numel()
+    grad_ref = torch.empty_like(target)
+    loss_ref = torch.zeros(1, device=U.DEV)
+    l1_loss(out["cam_feat"], target, scale, grad_ref, loss_ref)
+    out2 = fr.alloc_outputs(True)
+    grad = torch.full_like(target, 7.0)
+    loss = torch.zeros(1, device=U.DEV)
+    fr.rasterize(fr.c_gaussians(gd), out2, cam_l1=(target, scale, grad, loss))
+    torch.cuda.synchronize()
+    assert torch.equal(out2["cam_feat"], out["cam_feat"])
+    assert torch.equal(out2["cam_T"], out["cam_T"]) and torch.equal(out2["cam_last"], out["cam_last"])
+    assert torch.equal(grad, grad_ref)
+    assert loss.item() == pytest.approx(loss_ref.item(), rel=1e-5)
+
+
+def test_sync_status_reports_ok_on_a_clean_stream():
+    from paper_2411_16816_gb300 import _lib as L
+    from paper_2411_16816_gb300.render import _stream
+    torch.zeros(16, device=U.DEV).add_(1.0)
+    assert L.load().splat_sync_status(_stream()) == L.SPLAT_OK
