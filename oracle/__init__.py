@@ -68,9 +68,11 @@ def _declare(L):
     L.oracle_isect_list.restype = _I64
     L.oracle_isect_list.argtypes = [_I64, _P, _P, _P, _P, _I64, _P, _P]
     L.oracle_render.restype = ctypes.c_int
-    L.oracle_render.argtypes = ([_I64] + [_P] * 6 + [ctypes.c_int] + [_P] * 3 + [ctypes.c_double, _I64] + [_P] * 7)
+    L.oracle_render.argtypes = ([_I64] + [_P] * 6 + [ctypes.c_int] + [_P] * 3 + [ctypes.c_double, _I64] + [_P] * 8 +
+                                [ctypes.c_double, _P])
     L.oracle_render_backward.restype = ctypes.c_int
-    L.oracle_render_backward.argtypes = ([_I64] + [_P] * 6 + [ctypes.c_int] + [_P] * 3 + [_I64] + [_P] * 12)
+    L.oracle_render_backward.argtypes = ([_I64] + [_P] * 6 + [ctypes.c_int] + [_P] * 3 + [_I64] + [_P] * 13 +
+                                         [ctypes.c_double, _P])
     L.oracle_projection_backward.restype = ctypes.c_int
     L.oracle_projection_backward.argtypes = [_I64] + [_P] * 13
     L.oracle_jacobian.restype = ctypes.c_int
@@ -187,11 +189,14 @@ def isect_list(g: dict, s, proj: dict | None = None):
     return tiles[:total], ids[:total]
 
 
-def render(g: dict, s, sel=None, guard: float | None = None) -> dict:
+def render(g: dict, s, sel=None, guard: float | None = None, los_range=None, los_eps: float = 0.8) -> dict:
     """Render the selected rays (indices into the sensor's ray grid; None: all).
 
     Camera ray k is pixel (row, col) = divmod(k, width); lidar ray k is
-    (beam, azimuth bin) = divmod(k, n_az).
+    (beam, azimuth bin) = divmod(k, n_az).  With los_range (one return range per
+    selected lidar ray; <= 0: no return) the line-of-sight term of App. B is returned
+    as out["los"]: the summed alpha of the blended Gaussians whose range r_rs lies
+    before los_range - los_eps.
     """
     L = lib()
     n = len(g["opacities"])
@@ -204,17 +209,24 @@ def render(g: dict, s, sel=None, guard: float | None = None) -> dict:
     nr = s.n_rays if sel is None else len(sel_arr)
     F = np.zeros((nr, C)); T = np.zeros(nr); De = np.zeros(nr); Dm = np.zeros(nr)
     mg = np.zeros(nr, np.uint8); cnt = np.zeros(nr, np.int32)
+    lr = None if los_range is None else _f64(los_range)
+    los = np.zeros(nr) if lr is not None else None
     L.oracle_render(n, *[_ptr(a) for a in m], _ptr(feat), C, _ptr(P), _ptr(_elev(s)), _ptr(_rays(s)), guard,
-                    nr, _ptr(sel_arr), _ptr(F), _ptr(T), _ptr(De), _ptr(Dm), _ptr(mg), _ptr(cnt))
+                    nr, _ptr(sel_arr), _ptr(F), _ptr(T), _ptr(De), _ptr(Dm), _ptr(mg), _ptr(cnt), _ptr(lr),
+                    float(los_eps), _ptr(los))
     out = {"F": F, "T": T, "marginal": mg.astype(bool), "marginal_bits": mg, "count": cnt}
+    if los is not None:
+        out["los"] = los
     if s.kind == "lidar":
         out.update({"range_exp": De, "range_med": Dm, "alpha": 1.0 - T})
     return out
 
 
-def render_backward(g: dict, s, gF, gT=None, gD=None, gA=None, sel=None) -> dict:
-    """Gradients of sum(gF*F) + sum(gT*T) [+ sum(gD*range_exp) + sum(gA*alpha)] over the
-    selected rays (None: all rays; the upstream arrays then hold one row per selected ray)."""
+def render_backward(g: dict, s, gF, gT=None, gD=None, gA=None, sel=None, gL=None, los_range=None,
+                    los_eps: float = 0.8) -> dict:
+    """Gradients of sum(gF*F) + sum(gT*T) [+ sum(gD*range_exp) + sum(gA*alpha)
+    + sum(gL*los)] over the selected rays (None: all rays; the upstream arrays then hold
+    one row per selected ray)."""
     L = lib()
     n = len(g["opacities"])
     m = _g(g)
@@ -229,7 +241,8 @@ def render_backward(g: dict, s, gF, gT=None, gD=None, gA=None, sel=None) -> dict
                              0 if sel_arr is None else len(sel_arr), _ptr(sel_arr),
                              _ptr(_f64(gF)), _ptr(_f64(gT)), _ptr(_f64(gD)), _ptr(_f64(gA)), _ptr(out["d2"]),
                              _ptr(out["features"]), _ptr(out["means"]), _ptr(out["scales"]), _ptr(out["quats"]),
-                             _ptr(out["opacities"]), _ptr(out["velocities"]))
+                             _ptr(out["opacities"]), _ptr(out["velocities"]),
+                             _ptr(None if los_range is None else _f64(los_range)), float(los_eps), _ptr(_f64(gL)))
     return out
 
 

@@ -514,7 +514,7 @@ static int render_ray(const double *P, const double *elev, const double *rays, i
                       const uint8_t *gmarg,
                       const double *feat, int C,
                       int64_t k, cand_t *cands, double *F, double *Tout, double *Dexp, double *Dmed,
-                      int *marginal, contrib_t *cb, int cb_cap) {
+                      int *marginal, contrib_t *cb, int cb_cap, double rp, double los_eps, double *los) {
     int lidar = (int)P[P_KIND] == 1;
     int tx, ty;
     double pa, pb, t;
@@ -539,7 +539,7 @@ static int render_ray(const double *P, const double *elev, const double *rays, i
     }
     qsort(cands, (size_t)nc, sizeof(cand_t), cmp_cand);
     for (int c = 0; c < C; c++) F[c] = 0;
-    double T = 1, de = 0, dm = 0, last_depth = -1e300;
+    double T = 1, de = 0, dm = 0, last_depth = -1e300, lsum = 0;
     int med = 0, nb = 0;
     for (int j = 0; j < nc; j++) {
         const double *g = rec + REC * cands[j].id;
@@ -568,6 +568,12 @@ static int render_ray(const double *P, const double *elev, const double *rays, i
         de += rrs * a * T;
         if (fabs(Tn - 0.5) <= 1e-3 * 0.5) mg |= 16;
         if (!med && Tn < 0.5) { dm = rrs; med = 1; }
+        /* line-of-sight term (App. B): alpha of every blended Gaussian in front of the
+         * return by more than eps; a range within the guard band of the cut is marginal */
+        if (los) {
+            if (rrs < rp - los_eps) lsum += a;
+            if (fabs(rrs - (rp - los_eps)) <= 1e-5 * fabs(rp)) mg |= 64;
+        }
         if (cb && nb < cb_cap) {
             contrib_t *e = cb + nb;
             e->id = cands[j].id; e->alpha = a; e->T = T; e->G = G; e->dx = dx; e->dy = dy; e->t = t;
@@ -577,6 +583,7 @@ static int render_ray(const double *P, const double *elev, const double *rays, i
         T = Tn;
     }
     *Tout = T;
+    if (los) *los = lsum;
     if (Dexp) *Dexp = de;
     if (Dmed) *Dmed = dm;
     if (marginal) *marginal = mg;
@@ -611,7 +618,8 @@ static int64_t sensor_rays(const double *P) {
 int oracle_render(int64_t n, const double *means, const double *scales, const double *quats, const double *opac,
                   const double *vel, const double *feat, int C, const double *P, const double *elev,
                   const double *rays, double guard, int64_t n_sel, const int64_t *sel, double *outF, double *outT,
-                  double *outDexp, double *outDmed, uint8_t *outMarg, int32_t *outCount) {
+                  double *outDexp, double *outDmed, uint8_t *outMarg, int32_t *outCount, const double *los_range,
+                  double los_eps, double *outLos) {
     double *rec = (double *)malloc(sizeof(double) * REC * (size_t)(n > 0 ? n : 1));
     int32_t *rect = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)(n > 0 ? n : 1));
     int32_t *orect = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)(n > 0 ? n : 1));
@@ -628,8 +636,11 @@ int oracle_render(int64_t n, const double *means, const double *scales, const do
             int64_t k = sel ? sel[j] : j;
             double T, de, dm;
             int mg;
+            double lsum = 0;
             int cnt = render_ray(P, elev, rays, n, rec, rect, orect, irect, vis, marg, feat, C, k, cands,
-                                 outF + (int64_t)C * j, &T, &de, &dm, &mg, NULL, 0);
+                                 outF + (int64_t)C * j, &T, &de, &dm, &mg, NULL, 0, los_range ? los_range[j] : 0,
+                                 los_eps, los_range ? &lsum : NULL);
+            if (outLos) outLos[j] = lsum;
             outT[j] = T;
             if (outDexp) outDexp[j] = de;
             if (outDmed) outDmed[j] = dm;
@@ -649,7 +660,8 @@ int oracle_render(int64_t n, const double *means, const double *scales, const do
  * d depth, d va, d vb, d vr), and of the features.
  * ------------------------------------------------------------------------------- */
 static void ray_backward(const double *P, int C, const double *feat, const double *rec, const contrib_t *cb, int nb,
-                         double Tfinal, const double *gF, double gT, double gD, double *d2, double *dfeat) {
+                         double Tfinal, const double *gF, double gT, double gD, double gL, double rp, double los_eps,
+                         double *d2, double *dfeat) {
     double B[64];
     double BD = 0;
     for (int c = 0; c < C; c++) B[c] = 0;
@@ -666,6 +678,8 @@ static void ray_backward(const double *P, int C, const double *feat, const doubl
             dot += gF[c] * (f[c] - B[c]);
         }
         double dalpha = T * (dot + gD * (e->rrs - BD)) - gT * Tfinal / (1 - a);
+        /* line-of-sight term: d/d alpha_i of sum alpha_i over r_rs,i < r_p - eps */
+        if (gL != 0 && e->rrs < rp - los_eps) dalpha += gL;
         /* range channel: r_rs = r + v_r t */
         double drrs = gD * w;
         for (int c = 0; c < C; c++) B[c] = f[c] * a + (1 - a) * B[c];
@@ -855,7 +869,8 @@ int oracle_render_backward(int64_t n, const double *means, const double *scales,
                            const double *opac, const double *vel, const double *feat, int C, const double *P,
                            const double *elev, const double *rays, int64_t n_sel, const int64_t *sel,
                            const double *gF, const double *gT, const double *gD, const double *gA, double *d2,
-                           double *dfeat, double *dmean, double *dscale, double *dquat, double *dopac, double *dvel) {
+                           double *dfeat, double *dmean, double *dscale, double *dquat, double *dopac, double *dvel,
+                           const double *los_range, double los_eps, const double *gL) {
     if (C > 64) return -1;
     double *rec = (double *)malloc(sizeof(double) * REC * (size_t)(n > 0 ? n : 1));
     int32_t *rect = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)(n > 0 ? n : 1));
@@ -876,10 +891,11 @@ int oracle_render_backward(int64_t n, const double *means, const double *scales,
             const int64_t k = sel ? sel[j] : j;   /* ray index; upstream gradients are indexed by j */
             double T, de, dm;
             int nb = render_ray(P, elev, rays, n, rec, rect, orect, irect, vis, NULL, feat, C, k, cands, F, &T, &de, &dm,
-                                NULL, cb, (int)(n > 0 ? n : 1));
+                                NULL, cb, (int)(n > 0 ? n : 1), 0, 0, NULL);
             double gt = gT ? gT[j] : 0;
             if (gA) gt -= gA[j]; /* alpha_acc = 1 - T */
-            ray_backward(P, C, feat, rec, cb, nb, T, gF + (int64_t)C * j, gt, gD ? gD[j] : 0, loc2, dfeat);
+            ray_backward(P, C, feat, rec, cb, nb, T, gF + (int64_t)C * j, gt, gD ? gD[j] : 0,
+                         (gL && los_range) ? gL[j] : 0, los_range ? los_range[j] : 0, los_eps, loc2, dfeat);
         }
         free(cands); free(cb);
     }

@@ -406,11 +406,13 @@ def test_isect_list_is_sorted_by_tile_depth_id():
 # Gradients: analytic reverse mode vs central finite differences of the forward
 # ----------------------------------------------------------------------------------
 
-def _loss(g, s, w):
-    r = oracle.render(g, s, guard=0.0)
+def _loss(g, s, w, los_range=None):
+    r = oracle.render(g, s, guard=0.0, los_range=los_range)
     L = (w["F"] * r["F"]).sum() + (w["T"] * r["T"]).sum()
     if s.kind == "lidar":
         L += (w["D"] * r["range_exp"]).sum() + (w["A"] * r["alpha"]).sum()
+    if los_range is not None:
+        L += (w["L"] * r["los"]).sum()
     return L, r["count"]
 
 
@@ -418,15 +420,15 @@ def _weights(s, C, seed):
     rng = np.random.default_rng(seed)
     n = s.n_rays
     return {"F": rng.normal(size=(n, C)), "T": rng.normal(size=n), "D": rng.normal(size=n) * 0.1,
-            "A": rng.normal(size=n)}
+            "A": rng.normal(size=n), "L": rng.normal(size=n)}
 
 
-def _fd_check(g, s, seed, h=1e-6):
+def _fd_check(g, s, seed, h=1e-6, los_range=None):
     C = g["features"].shape[1]
     w = _weights(s, C, seed)
     an = oracle.render_backward(g, s, w["F"], w["T"], w["D"] if s.kind == "lidar" else None,
-                                w["A"] if s.kind == "lidar" else None)
-    _, c0 = _loss(g, s, w)
+                                w["A"] if s.kind == "lidar" else None, gL=w["L"], los_range=los_range)
+    _, c0 = _loss(g, s, w, los_range)
     checked = 0
     for key in ("means", "scales", "quats", "opacities", "velocities", "features"):
         arr = g[key]
@@ -437,8 +439,8 @@ def _fd_check(g, s, seed, h=1e-6):
             step = h * max(1.0, abs(arr[idx]))
             gp[key][idx] += step
             gm[key][idx] -= step
-            Lp, cp = _loss(gp, s, w)
-            Lm, cm = _loss(gm, s, w)
+            Lp, cp = _loss(gp, s, w, los_range)
+            Lm, cm = _loss(gm, s, w, los_range)
             assert np.array_equal(cp, c0) and np.array_equal(cm, c0), f"discontinuity at {key}{idx}"
             num[idx] = (Lp - Lm) / (2 * step)
         scale = max(np.abs(num).max(), 1e-8)
@@ -466,6 +468,41 @@ def test_lidar_gradients_match_finite_differences():
     g = random_small_scene(33, 6, (-6.0, -6.0, -1.0), (6.0, 6.0, 1.0), channels=2, log_scale=(-1.2, 0.3))
     g["means"][0] = (5.0, -0.05, 0.0)     # straddles the azimuth wrap
     assert _fd_check(g, lid, seed=2) > 40
+
+
+def test_line_of_sight_gradients_match_finite_differences():
+    """App. B line-of-sight term: its gradient (1 on every alpha in front of the return)
+    through the alpha chain, against central differences; returns are placed between the
+    Gaussians' ranges so that no perturbation moves a Gaussian across the cut."""
+    vs, ws = np.array([12.0, 0.5, 0.0]), np.array([0.0, 0.02, 0.1])
+    lid = small_lidar(n_beams=8, n_az=96, lo=-12, hi=10, R=rodrigues([0, 0, 0.2]), lin_vel=vs, ang_vel=ws,
+                      sweep_time=0.1, eps2d=2e-5, tile_el=4, tile_az=16)
+    g = random_small_scene(33, 6, (-6.0, -6.0, -1.0), (6.0, 6.0, 1.0), channels=2, log_scale=(-1.2, 0.3))
+    g["means"][0] = (5.0, -0.05, 0.0)
+    # ranges of the Gaussians at the rays' times span at most a few cm around |mean|;
+    # cuts halfway between consecutive ranges keep a margin of centimetres
+    r = np.sort(np.linalg.norm(g["means"].astype(np.float64), axis=1))
+    cuts = np.concatenate([[0.5 * r[0]], 0.5 * (r[1:] + r[:-1]), [r[-1] + 1.0]])
+    rng = np.random.default_rng(9)
+    los_range = rng.choice(cuts, size=lid.n_rays) + 0.8
+    assert _fd_check(g, lid, seed=3, los_range=los_range) > 40
+
+
+def test_line_of_sight_term_sums_alphas_in_front_of_the_return():
+    lid = small_lidar()
+    near = one_gaussian((6.0, 0.0, 0.0), (0.3, 0.3, 0.3), opacity=0.45, feature=(1.0,))
+    mid = one_gaussian((9.0, 0.0, 0.0), (0.3, 0.45, 0.45), opacity=0.8, feature=(1.0,))
+    far = one_gaussian((12.0, 0.0, 0.0), (0.3, 0.6, 0.6), opacity=0.7, feature=(1.0,))
+    k = 7 * 256 + 0       # beam 7 (-1 deg), azimuth bin 0
+    a = [oracle.render(x, lid)["alpha"][k] for x in (near, mid, far)]
+    assert min(a) > 0.05
+    both = stack(far, near, mid)
+    for rp, want in ((10.5, a[0] + a[1]), (9.5, a[0]), (6.5, 0.0), (0.0, 0.0), (100.0, sum(a))):
+        out = oracle.render(both, lid, sel=[k], los_range=[rp])
+        assert out["los"][0] == pytest.approx(want, rel=1e-12, abs=1e-15), rp
+    # a return 0.8 m behind a Gaussian's range: the cut falls on it and the ray is marginal
+    out = oracle.render(both, lid, sel=[k], los_range=[9.0 + 0.8])
+    assert out["marginal"][0]
 
 
 # ----------------------------------------------------------------------------------
