@@ -225,6 +225,26 @@ splat_status splat_render_lidar(const splat_gaussians *g, int32_t n_sensors, con
                                 float *out_range_med, float *out_alpha, float *out_T, int32_t *out_last,
                                 uint64_t *evaluated, void *stream);
 
+/* Line-of-sight term of the training loss (App. B, lambda_los L_los): for a lidar ray p
+ * with a measured return at range r_p, L_los,p = sum of alpha_i over the Gaussians the
+ * ray blends whose rolling-shutter range r_rs,i = r_i + v_r,i t_p lies before
+ * r_p - eps.  The term rides on the lidar traversal.
+ *   target_range[lidar rays]  device, in out_feat's ray order; <= 0 marks a ray without
+ *                             a return (its term is 0)
+ *   eps                       metres (the paper uses 0.8), >= 0 */
+typedef struct {
+    const float *target_range;
+    float eps;
+    int32_t reserved;
+} splat_los;
+
+/* splat_render_lidar plus the line-of-sight term of every lidar ray in out_los[rays]
+ * (device, written).  The other outputs are exactly those of splat_render_lidar. */
+splat_status splat_render_lidar_los(const splat_gaussians *g, int32_t n_sensors, const splat_sensor *sensors,
+                                    splat_projected proj, splat_bins bins, float *out_feat, float *out_range_exp,
+                                    float *out_range_med, float *out_alpha, float *out_T, int32_t *out_last,
+                                    splat_los los, float *out_los, uint64_t *evaluated, void *stream);
+
 /* Backward of splat_render_camera.  Inputs: the forward's out_T and out_last (or both
  * NULL: the kernel then recomputes them per tile), dL_dfeat[pixels][channels] and
  * dL_dT[pixels] (may be NULL).  Accumulates into
@@ -244,6 +264,16 @@ splat_status splat_render_lidar_backward(const splat_gaussians *g, int32_t n_sen
                                          const int32_t *out_last, const float *dL_dfeat,
                                          const float *dL_drange_exp, const float *dL_dalpha, float *grad_proj,
                                          float *dL_dfeatures, void *stream);
+
+/* splat_render_lidar_backward plus the gradient of sum_p dL_dlos[p] * L_los,p (the
+ * line-of-sight term above, same los): each blended alpha_i in front of the cut gets
+ * dL_dlos[p] added to its upstream gradient.  dL_dlos[lidar rays] is device memory. */
+splat_status splat_render_lidar_backward_los(const splat_gaussians *g, int32_t n_sensors,
+                                             const splat_sensor *sensors, splat_projected proj, splat_bins bins,
+                                             const float *out_T, const int32_t *out_last, const float *dL_dfeat,
+                                             const float *dL_drange_exp, const float *dL_dalpha, splat_los los,
+                                             const float *dL_dlos, float *grad_proj, float *dL_dfeatures,
+                                             void *stream);
 
 /* Chain rule from grad_proj to the Gaussian parameters, summed over sensors (one thread
  * per Gaussian, no atomics).  Accumulates into dL_dmeans[n][3], dL_dscales[n][3],

@@ -291,10 +291,11 @@ splat_status splat_sync_status(void* stream) {
     return SPLAT_OK;
 }
 
-splat_status splat_render_lidar(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
-                                splat_projected proj, splat_bins bins, float* out_feat, float* out_range_exp,
-                                float* out_range_med, float* out_alpha, float* out_T, int32_t* out_last,
-                                uint64_t* evaluated, void* stream) {
+static splat_status render_lidar_impl(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
+                                      splat_projected proj, splat_bins bins, float* out_feat, float* out_range_exp,
+                                      float* out_range_med, float* out_alpha, float* out_T, int32_t* out_last,
+                                      const splat_los* los, float* out_los, uint64_t* evaluated, void* stream,
+                                      const char* name) {
     Frame fr;
     int tw, th;
     splat_status st = render_common(g, n_sensors, sensors, proj, bins, fr, true, tw, th);
@@ -303,13 +304,33 @@ splat_status splat_render_lidar(const splat_gaussians* g, int32_t n_sensors, con
     if (!out_feat || !out_range_exp || !out_alpha)
         return fail(SPLAT_ERR_INVALID_ARG, "out_feat, out_range_exp and out_alpha are required");
     if ((g->channels & 3) == 0 && !aligned16(out_feat)) return fail(SPLAT_ERR_INVALID_ARG, "out_feat misaligned");
+    if (los && (!los->target_range || !out_los || !(los->eps >= 0.f)))
+        return fail(SPLAT_ERR_INVALID_ARG, "%s: los.target_range and out_los are required, los.eps >= 0", name);
     RasterIn in{(const float4*)proj.rec, bins.isect_ids, (const int2*)bins.tile_ranges, g->features, g->n,
-                g->channels};
+                g->channels, los ? los->target_range : nullptr, los ? los->eps : 0.f};
     RasterOut out{out_feat, out_T, out_last, out_range_exp, out_range_med, out_alpha,
                   (unsigned long long*)evaluated};
+    out.los = los ? out_los : nullptr;
     if (!launch_raster_fwd(true, g->channels, tw, th, fr, fr.n_lid_blocks, in, out, (cudaStream_t)stream))
         return fail(SPLAT_ERR_INVALID_ARG, "unsupported lidar configuration");
-    return check_launch("splat_render_lidar");
+    return check_launch(name);
+}
+
+
+splat_status splat_render_lidar(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
+                                splat_projected proj, splat_bins bins, float* out_feat, float* out_range_exp,
+                                float* out_range_med, float* out_alpha, float* out_T, int32_t* out_last,
+                                uint64_t* evaluated, void* stream) {
+    return render_lidar_impl(g, n_sensors, sensors, proj, bins, out_feat, out_range_exp, out_range_med, out_alpha,
+                             out_T, out_last, nullptr, nullptr, evaluated, stream, "splat_render_lidar");
+}
+
+splat_status splat_render_lidar_los(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
+                                    splat_projected proj, splat_bins bins, float* out_feat, float* out_range_exp,
+                                    float* out_range_med, float* out_alpha, float* out_T, int32_t* out_last,
+                                    splat_los los, float* out_los, uint64_t* evaluated, void* stream) {
+    return render_lidar_impl(g, n_sensors, sensors, proj, bins, out_feat, out_range_exp, out_range_med, out_alpha,
+                             out_T, out_last, &los, out_los, evaluated, stream, "splat_render_lidar_los");
 }
 
 splat_status splat_render_camera_backward(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
@@ -335,11 +356,12 @@ splat_status splat_render_camera_backward(const splat_gaussians* g, int32_t n_se
     return check_launch("splat_render_camera_backward");
 }
 
-splat_status splat_render_lidar_backward(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
-                                         splat_projected proj, splat_bins bins, const float* out_T,
-                                         const int32_t* out_last, const float* dL_dfeat,
-                                         const float* dL_drange_exp, const float* dL_dalpha, float* grad_proj,
-                                         float* dL_dfeatures, void* stream) {
+static splat_status render_lidar_backward_impl(const splat_gaussians* g, int32_t n_sensors,
+                                               const splat_sensor* sensors, splat_projected proj, splat_bins bins,
+                                               const float* out_T, const int32_t* out_last, const float* dL_dfeat,
+                                               const float* dL_drange_exp, const float* dL_dalpha,
+                                               const splat_los* los, const float* dL_dlos, float* grad_proj,
+                                               float* dL_dfeatures, void* stream, const char* name) {
     Frame fr;
     int tw, th;
     splat_status st = render_common(g, n_sensors, sensors, proj, bins, fr, true, tw, th);
@@ -350,13 +372,37 @@ splat_status splat_render_lidar_backward(const splat_gaussians* g, int32_t n_sen
         return fail(SPLAT_ERR_INVALID_ARG, "out_T and out_last must both be given or both be NULL");
     if (!aligned16(grad_proj) || ((g->channels & 3) == 0 && !aligned16(dL_dfeatures)))
         return fail(SPLAT_ERR_INVALID_ARG, "gradient buffers misaligned");
+    if (los && (!los->target_range || !dL_dlos || !(los->eps >= 0.f)))
+        return fail(SPLAT_ERR_INVALID_ARG, "%s: los.target_range and dL_dlos are required, los.eps >= 0", name);
     RasterIn in{(const float4*)proj.rec, bins.isect_ids, (const int2*)bins.tile_ranges, g->features, g->n,
-                g->channels};
-    RasterGrad gr{out_T, out_last, dL_dfeat, nullptr, dL_drange_exp, dL_dalpha, (float4*)grad_proj, dL_dfeatures};
+                g->channels, los ? los->target_range : nullptr, los ? los->eps : 0.f};
+    RasterGrad gr{out_T, out_last, dL_dfeat, nullptr, dL_drange_exp, dL_dalpha, (float4*)grad_proj, dL_dfeatures,
+                  los ? dL_dlos : nullptr};
     if (!launch_raster_bwd(true, g->channels, tw, th, fr, fr.n_lid_blocks, in, gr, out_T == nullptr,
                            (cudaStream_t)stream))
         return fail(SPLAT_ERR_INVALID_ARG, "unsupported lidar configuration");
-    return check_launch("splat_render_lidar_backward");
+    return check_launch(name);
+}
+
+splat_status splat_render_lidar_backward(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
+                                         splat_projected proj, splat_bins bins, const float* out_T,
+                                         const int32_t* out_last, const float* dL_dfeat,
+                                         const float* dL_drange_exp, const float* dL_dalpha, float* grad_proj,
+                                         float* dL_dfeatures, void* stream) {
+    return render_lidar_backward_impl(g, n_sensors, sensors, proj, bins, out_T, out_last, dL_dfeat, dL_drange_exp,
+                                      dL_dalpha, nullptr, nullptr, grad_proj, dL_dfeatures, stream,
+                                      "splat_render_lidar_backward");
+}
+
+splat_status splat_render_lidar_backward_los(const splat_gaussians* g, int32_t n_sensors,
+                                             const splat_sensor* sensors, splat_projected proj, splat_bins bins,
+                                             const float* out_T, const int32_t* out_last, const float* dL_dfeat,
+                                             const float* dL_drange_exp, const float* dL_dalpha, splat_los los,
+                                             const float* dL_dlos, float* grad_proj, float* dL_dfeatures,
+                                             void* stream) {
+    return render_lidar_backward_impl(g, n_sensors, sensors, proj, bins, out_T, out_last, dL_dfeat, dL_drange_exp,
+                                      dL_dalpha, &los, dL_dlos, grad_proj, dL_dfeatures, stream,
+                                      "splat_render_lidar_backward_los");
 }
 
 splat_status splat_project_backward(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,

@@ -213,6 +213,7 @@ struct FwdState {
     float T;
     int last;
     float de, dm;
+    float los, cut;   // lidar line-of-sight term and its range cut r_p - eps
     bool med, done;
 };
 
@@ -233,6 +234,8 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
         st[q].dm = 0.f;
         st[q].med = false;
         st[q].done = !r[q].inside;
+        st[q].los = 0.f;
+        st[q].cut = (LIDAR && in.los_range && r[q].inside) ? in.los_range[r[q].o] - in.los_eps : -INFINITY;
         all_done &= st[q].done;
     }
     for (int start = range.x; start < range.y; start += B) {
@@ -272,6 +275,7 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
                                 st[q].dm = rrs;
                                 st[q].med = true;
                             }
+                            if (rrs < st[q].cut) st[q].los += a;   // line-of-sight term (App. B)
                         }
                         st[q].T = Tn;
                         st[q].last = start + k - range.x + 1;
@@ -376,6 +380,7 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, false, LIDAR, TW * 
         if (out.last) out.last[r[q].o] = st[q].last;
         if (LIDAR) {
             out.range_exp[r[q].o] = st[q].de;
+            if (out.los) out.los[r[q].o] = st[q].los;
             if (out.range_med) out.range_med[r[q].o] = st[q].dm;
             out.alpha[r[q].o] = 1.f - st[q].T;
         }
@@ -507,6 +512,7 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
         }
     }
     float gF[PX][CM], gTT[PX], gD[PX], T[PX], S[PX], SD[PX];
+    float gL[PX], cut[PX];   // lidar line-of-sight upstream gradient and range cut
     int my_last = 0;
 #pragma unroll
     for (int q = 0; q < PX; q++) {
@@ -523,6 +529,8 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
             }
         }
         gTT[q] = gT * Tfin[q];
+        gL[q] = (LIDAR && gr.dlos && r[q].inside) ? gr.dlos[r[q].o] : 0.f;
+        cut[q] = (LIDAR && in.los_range && r[q].inside) ? in.los_range[r[q].o] - in.los_eps : -INFINITY;
         T[q] = Tfin[q];
         S[q] = 0.f;    // sum_c gF_c B_c, B = normalised blend of everything behind
         SD[q] = 0.f;   // its counterpart for the range
@@ -575,6 +583,7 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
                 if (LIDAR) {
                     const float rrs = sm.g2[k].x + sm.g2[k].y * tq;
                     dalpha += Ti * gD[q] * (rrs - SD[q]);
+                    if (rrs < cut[q]) dalpha += gL[q];   // d(line-of-sight term) / d alpha
                     SD[q] += aq * (rrs - SD[q]);
                     drrs = gD[q] * wgt;
                 }

@@ -35,6 +35,8 @@ struct RasterIn {
     const float* feat;      // [n][C]
     int64_t n;
     int C;                  // channels (<= the kernel's compile-time maximum CM)
+    const float* los_range; // lidar, optional: return range per ray for the line-of-sight term
+    float los_eps;
 };
 
 struct RasterOut {
@@ -50,6 +52,7 @@ struct RasterOut {
     float* l1_grad;
     float* l1_loss;
     float l1_scale;
+    float* los;             // lidar, optional: line-of-sight term per ray
 };
 
 struct RasterGrad {
@@ -61,6 +64,7 @@ struct RasterGrad {
     const float* dalpha;   // lidar: dL/d (1 - T)
     float4* grad_proj;     // [S][3][n]
     float* dfeatures;      // [n][C]
+    const float* dlos;     // lidar, optional: dL/d line-of-sight term
 };
 
 struct BinWorkspace {

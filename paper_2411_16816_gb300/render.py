@@ -82,6 +82,7 @@ class Frame:
         self.capacity = 0
         self._alloc_capacity(capacity if capacity is not None else max(1 << 16, 8 * self.n))
         self.grad_proj = None
+        self.los = None           # line-of-sight term: (return range per lidar ray, eps) or None
         self.version = 0
 
     # -- set-up ------------------------------------------------------------------------
@@ -187,10 +188,32 @@ class Frame:
         elif self.cam_idx:
             L.call("splat_render_camera", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
                    self.c_bins(), _vp(out["cam_feat"]), _vp(out["cam_T"]), _vp(out.get("cam_last")), _vp(ev_c), st)
-        if self.lid_idx:
+        if self.lid_idx and self.los is not None:
+            if out.get("lid_los") is None:
+                out["lid_los"] = torch.empty(self.lid_rays, dtype=torch.float32, device=self.device)
+            L.call("splat_render_lidar_los", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
+                   self.c_bins(), _vp(out["lid_feat"]), _vp(out["lid_range_exp"]), _vp(out["lid_range_med"]),
+                   _vp(out["lid_alpha"]), _vp(out.get("lid_T")), _vp(out.get("lid_last")), self._c_los(),
+                   _vp(out["lid_los"]), _vp(ev_l), st)
+        elif self.lid_idx:
             L.call("splat_render_lidar", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
                    self.c_bins(), _vp(out["lid_feat"]), _vp(out["lid_range_exp"]), _vp(out["lid_range_med"]),
                    _vp(out["lid_alpha"]), _vp(out.get("lid_T")), _vp(out.get("lid_last")), _vp(ev_l), st)
+
+    def set_line_of_sight(self, target_range: torch.Tensor | None, eps: float = 0.8):
+        """Enable (or with None disable) the line-of-sight term of App. B: the lidar
+        forward then also writes out["lid_los"] (summed alpha of the Gaussians blended
+        before target_range - eps, one return range per lidar ray, <= 0: none) and the
+        backward takes its upstream gradient as grads["lid_los"]."""
+        if target_range is None:
+            self.los = None
+            return
+        if target_range.shape != (self.lid_rays,) or target_range.dtype != torch.float32:
+            raise ValueError("target_range must be float32 with one entry per lidar ray")
+        self.los = (target_range.contiguous(), float(eps))
+
+    def _c_los(self):
+        return L.splat_los(self.los[0].data_ptr(), self.los[1], 0)
 
     def forward(self, g: dict, keep_state: bool = True, check: bool = True, out: dict | None = None,
                 stream=None, cam_l1=None) -> dict:
@@ -250,11 +273,21 @@ class Frame:
             if dF is None:
                 dF = torch.zeros((self.lid_rays, self.channels), dtype=torch.float32, device=dev)
             keep = out.get("lid_last") is not None
-            L.call("splat_render_lidar_backward", ctypes.byref(cg), len(self.sensors), self.c_sensors,
-                   self.c_proj(), self.c_bins(), _vp(out.get("lid_T") if keep else None),
-                   _vp(out.get("lid_last") if keep else None), _vp(dF.contiguous()),
-                   _vp(grads.get("lid_range_exp")), _vp(grads.get("lid_alpha")), _vp(self.grad_proj),
-                   _vp(param_grads["features"]), st)
+            dlos = grads.get("lid_los")
+            if dlos is not None:
+                if self.los is None:
+                    raise ValueError("grads['lid_los'] needs set_line_of_sight() before the forward")
+                L.call("splat_render_lidar_backward_los", ctypes.byref(cg), len(self.sensors), self.c_sensors,
+                       self.c_proj(), self.c_bins(), _vp(out.get("lid_T") if keep else None),
+                       _vp(out.get("lid_last") if keep else None), _vp(dF.contiguous()),
+                       _vp(grads.get("lid_range_exp")), _vp(grads.get("lid_alpha")), self._c_los(),
+                       _vp(dlos.contiguous()), _vp(self.grad_proj), _vp(param_grads["features"]), st)
+            else:
+                L.call("splat_render_lidar_backward", ctypes.byref(cg), len(self.sensors), self.c_sensors,
+                       self.c_proj(), self.c_bins(), _vp(out.get("lid_T") if keep else None),
+                       _vp(out.get("lid_last") if keep else None), _vp(dF.contiguous()),
+                       _vp(grads.get("lid_range_exp")), _vp(grads.get("lid_alpha")), _vp(self.grad_proj),
+                       _vp(param_grads["features"]), st)
         L.call("splat_project_backward", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
                _vp(self.grad_proj), _vp(param_grads["means"]), _vp(param_grads["scales"]),
                _vp(param_grads["quats"]), _vp(param_grads["opacities"]), _vp(param_grads.get("velocities")), st)

@@ -348,3 +348,45 @@ def test_sync_status_reports_ok_on_a_clean_stream():
     from paper_2411_16816_gb300.render import _stream
     torch.zeros(16, device=U.DEV).add_(1.0)
     assert L.load().splat_sync_status(_stream()) == L.SPLAT_OK
+
+
+def _los_returns(g, s, seed):
+    """A return range per lidar ray near the rendered expected range (some rays without a
+    return), as a recorded sweep would give."""
+    rng = np.random.default_rng(seed)
+    ref = oracle.render(g, s)
+    alpha = ref["alpha"]
+    r = np.where(alpha > 1e-3, ref["range_exp"] / np.maximum(alpha, 1e-3), 0.0)
+    r = r * rng.uniform(0.8, 1.3, size=r.shape)
+    r[rng.uniform(size=r.shape) < 0.1] = 0.0
+    return r.astype(np.float32)
+
+
+def test_line_of_sight_term_and_gradient_match_oracle():
+    """App. B line-of-sight term on the lidar traversal: forward per ray and its gradient
+    against the oracle; the other lidar outputs are unchanged by it."""
+    g, sensors = _dynamic_tiny()
+    lid = sensors[1]
+    gd = gaussians_to_device(g, U.DEV)
+    rp = _los_returns(g, lid, 5)
+    fr0 = Frame([lid], len(g["opacities"]), g["features"].shape[1], U.DEV)
+    out0 = fr0.forward(gd)
+    fr = Frame([lid], len(g["opacities"]), g["features"].shape[1], U.DEV)
+    fr.set_line_of_sight(torch.as_tensor(rp, device=U.DEV), 0.8)
+    out = fr.forward(gd)
+    torch.cuda.synchronize()
+    for k in ("lid_feat", "lid_range_exp", "lid_alpha", "lid_T", "lid_last"):
+        assert torch.equal(out[k], out0[k]), k
+    ref = oracle.render(g, lid, los_range=rp)
+    ok = ~ref["marginal"]
+    assert ok.mean() > 0.95 and (ref["los"][ok] > 0.05).sum() > 50
+    np.testing.assert_allclose(out["lid_los"].cpu().numpy()[ok], ref["los"][ok], atol=U.TOL_FEAT, rtol=0)
+    # gradient: only the line-of-sight upstream, on the non-marginal rays
+    gl = np.random.default_rng(6).normal(size=lid.n_rays) * ok
+    C = g["features"].shape[1]
+    grads = {"lid_feat": torch.zeros((lid.n_rays, C), device=U.DEV),
+             "lid_los": torch.as_tensor(gl.astype(np.float32), device=U.DEV)}
+    pg = fr.backward(gd, out, grads)
+    torch.cuda.synchronize()
+    want = oracle.render_backward(g, lid, np.zeros((lid.n_rays, C)), gL=gl, los_range=rp)
+    U.check_grads(pg, want, keys=("means", "scales", "quats", "opacities", "velocities"))
