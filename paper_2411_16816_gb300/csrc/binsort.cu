@@ -265,13 +265,14 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
 // Sorts by bits [0, 8*passes) of the keys.  Buffers ping-pong: pass p reads buffer
 // p % 2 and writes buffer (p + 1) % 2; the result is in buffer passes % 2.
 void radix_sort(uint32_t* keys[2], uint32_t* vals[2], int passes, int64_t max_count, const int64_t* count_ptr,
-                int64_t capacity, uint32_t* hist, int64_t* partials, cudaStream_t st) {
+                int64_t capacity, uint32_t* hist, int64_t* partials, cudaStream_t st, bool first_hist_done = false) {
     const int64_t nblocks = (max_count + kSortTile - 1) / kSortTile;
     if (nblocks == 0) return;
     for (int p = 0; p < passes; p++) {
         const int a = p & 1, b = a ^ 1;
-        k_radix_hist<<<(unsigned)nblocks, kSortThreads, 0, st>>>(keys[a], count_ptr, max_count, capacity, 8 * p, hist,
-                                                                nblocks);
+        if (p > 0 || !first_hist_done)
+            k_radix_hist<<<(unsigned)nblocks, kSortThreads, 0, st>>>(keys[a], count_ptr, max_count, capacity, 8 * p,
+                                                                    hist, nblocks);
         device_scan(HistIn{hist}, HistOut{hist}, 256 * nblocks, nullptr, INT64_MAX, partials, nullptr, st);
         k_radix_scatter<<<(unsigned)nblocks, kSortThreads, 0, st>>>(keys[a], vals[a], keys[b], vals[b], count_ptr,
                                                                    max_count, capacity, 8 * p, hist, nblocks);
@@ -309,6 +310,8 @@ struct EmitIn {
 constexpr int kEmitThreads = 256;
 constexpr int kEmitItems = 8;
 constexpr int kEmitTile = kEmitThreads * kEmitItems;  // output slots per block
+static_assert(kEmitTile == kSortTile, "emit blocks must be the first radix pass's blocks");
+static_assert(kEmitThreads == 256, "one thread per digit of the emitted histogram");
 
 // Exclusive prefix of the tile counts, in depth order.  It also records, for every emit
 // block, the visible pair that owns the block's first slot (the pair whose slot range
@@ -331,22 +334,31 @@ struct EmitTables {
     int is_lidar[kMaxSensors];
 };
 
-// Writes intersections [b*2048, (b+1)*2048): each block binary-searches the first
-// visible pair that owns one of its slots, stages the owners' offsets in shared memory
-// and every thread then writes one (tile, Gaussian) pair per slot it owns.  Work per
-// block is fixed whatever the size of the Gaussians, and the writes are contiguous.
+// Writes intersections [b*2048, (b+1)*2048): the offsets scan recorded the visible pair
+// that owns each block's first slot; the block stages the owners' offsets in shared
+// memory and every thread then writes one (tile, Gaussian) pair per slot it owns.  Work
+// per block is fixed whatever the size of the Gaussians, and the writes are contiguous.
+// The blocks are those of the first radix pass over the keys, so each block also writes
+// that pass's low-byte digit histogram.
 __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restrict__ sorted_pairs,
                                                       const int64_t* __restrict__ offsets,
                                                       const uint32_t* __restrict__ first_owner,
                                                       const int64_t* vis_count, const int64_t* n_isect,
                                                       int64_t capacity, const short4* __restrict__ rect, int64_t n,
                                                       float inv_n, const __grid_constant__ EmitTables tab,
-                                                      uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+                                                      uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                      uint32_t* __restrict__ hist) {
     __shared__ int s_off[kEmitTile];   // owners' first slots relative to the block (the first may be < 0)
+    __shared__ uint32_t s_hist[256];   // low-byte digit counts of this block's keys (first radix pass)
     const int64_t total = *n_isect;
     if (total > capacity) return;   // over capacity: write nothing
     const int64_t o0 = (int64_t)blockIdx.x * kEmitTile;
-    if (o0 >= total) return;
+    const int64_t nblocks = gridDim.x;   // the radix passes cut the keys into the same 2048-slot blocks
+    if (o0 >= total) {
+        hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = 0;
+        return;
+    }
+    s_hist[threadIdx.x] = 0;
     const int64_t V = *vis_count;
     const int nslot = (int)min((int64_t)kEmitTile, total - o0);
     const int64_t jlo = first_owner[blockIdx.x];
@@ -379,6 +391,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
               rc.w <= tab.tiles_y[s])) {   // malformed projection: an id past every tile, never ranged
             keys[o0 + o] = 0xffffffffu;
             vals[o0 + o] = i;
+            atomicAdd(&s_hist[255], 1u);
             continue;
         }
         int dy = (int)__fdividef((float)q + 0.5f, (float)w);
@@ -394,20 +407,46 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
         int col = rc.x + dx;
         const int tx = tab.tiles_x[s];
         if (tab.is_lidar[s] && col >= tx) col -= tx;
-        keys[o0 + o] = (uint32_t)(tab.tile_base[s] + ty * tx + col);
+        const uint32_t key = (uint32_t)(tab.tile_base[s] + ty * tx + col);
+        keys[o0 + o] = key;
         vals[o0 + o] = i;
+        atomicAdd(&s_hist[key & 255u], 1u);
     }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = s_hist[threadIdx.x];
 }
 
+// Tile ranges of the sorted ids: four keys per thread (one vector load) plus the two
+// neighbours; keys past every tile (malformed projections) are never ranged.
 __global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict__ keys, const int64_t* count_ptr,
                                                       int64_t capacity, int64_t total_tiles, int2* ranges) {
     const int64_t count = eff_count(count_ptr, capacity, capacity);
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < count;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t t = keys[j];
-        if ((int64_t)t >= total_tiles) continue;   // never a tile: left out of every range
-        if (j == 0 || keys[j - 1] != t) ranges[t].x = (int)j;
-        if (j == count - 1 || keys[j + 1] != t) ranges[t].y = (int)(j + 1);
+    const int64_t groups = (count + 3) / 4;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < groups;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j0 = 4 * q;
+        uint32_t k[6];   // k[1 + i] = keys[j0 + i]; k[0], k[5]: neighbours
+        if (j0 + 4 <= count) {
+            const uint4 v = *reinterpret_cast<const uint4*>(keys + j0);
+            k[1] = v.x;
+            k[2] = v.y;
+            k[3] = v.z;
+            k[4] = v.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; i++) k[1 + i] = j0 + i < count ? keys[j0 + i] : 0u;
+        }
+        k[0] = j0 > 0 ? keys[j0 - 1] : 0u;
+        k[5] = j0 + 4 < count ? keys[j0 + 4] : 0u;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int64_t j = j0 + i;
+            if (j >= count) break;
+            const uint32_t t = k[1 + i];
+            if ((int64_t)t >= total_tiles) continue;
+            if (j == 0 || k[i] != t) ranges[t].x = (int)j;
+            if (j == count - 1 || k[2 + i] != t) ranges[t].y = (int)(j + 1);
+        }
     }
 }
 
@@ -480,9 +519,9 @@ void launch_bin_sort(const Frame& fr, int64_t n, const float4* rec, const short4
     if (emit_blocks > 0)
         k_emit<<<(unsigned)emit_blocks, kEmitThreads, 0, st>>>(sorted_pairs, w.offsets, w.first_owner, w.vis_count,
                                                                n_isect, capacity, rect, n, (float)(1.0 / (double)n),
-                                                               tab, w.ikeys[0], vals_buf[0]);
+                                                               tab, w.ikeys[0], vals_buf[0], w.hist);
     // 4. stable sort of the intersections by tile id
-    radix_sort(w.ikeys, vals_buf, passes, capacity, n_isect, capacity, w.hist, w.partials, st);
+    radix_sort(w.ikeys, vals_buf, passes, capacity, n_isect, capacity, w.hist, w.partials, st, emit_blocks > 0);
     // 5. per-tile ranges
     int64_t blocks = (capacity + 255) / 256;
     if (blocks > 152 * 8) blocks = 152 * 8;
