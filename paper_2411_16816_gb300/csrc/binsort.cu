@@ -174,8 +174,21 @@ struct HistOut {
     __device__ void operator()(int64_t i, int64_t prefix, int64_t) const { h[i] = (uint32_t)prefix; }
 };
 
-// Each warp ranks 512 consecutive keys in order (32 at a time, __match_any_sync groups
-// equal digits); warps' digit counts are then scanned in warp order, so the block's
+// Lanes of the warp holding the same 9-bit value (an 8-bit digit or 256 for no key): one
+// ballot per bit, keeping the lanes that agree with this lane on every bit.
+__device__ __forceinline__ uint32_t warp_peers(uint32_t d) {
+    uint32_t m = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 9; b++) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+        m &= bit ? bal : ~bal;
+    }
+    return m;
+}
+
+// Each warp ranks 256 consecutive keys in order (32 at a time, warp_peers groups equal
+// digits); warps' digit counts are then scanned in warp order, so the block's
 // ranking -- and with the digit-major global scan, the whole pass -- is stable.  The
 // block first writes its keys in sorted order to shared memory and then copies each
 // digit's run to its global position, so consecutive threads write consecutive
@@ -218,7 +231,7 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
         const int64_t idx = base + it * 32 + lane;
         const bool valid = idx < count;
         const uint32_t d = valid ? ((kk[it] >> shift) & 255u) : 256u;
-        const uint32_t peers = __match_any_sync(0xffffffffu, d);
+        const uint32_t peers = warp_peers(d);
         const uint32_t cnt = valid ? wh[warp][d] : 0u;
         rr[it] = cnt + __popc(peers & ((1u << lane) - 1u));
         __syncwarp();
