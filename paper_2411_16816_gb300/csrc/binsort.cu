@@ -361,7 +361,14 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
                                                       float inv_n, const __grid_constant__ EmitTables tab,
                                                       uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                       uint32_t* __restrict__ hist) {
-    __shared__ int s_off[kEmitTile];   // owners' first slots relative to the block (the first may be < 0)
+    // per owner (visible pair): first slot relative to the block (the first may be < 0),
+    // Gaussian index, rectangle x0 | width << 16 (width 0: malformed), tile id of (x = 0,
+    // y0), tiles_x | lidar << 31
+    __shared__ int s_off[kEmitTile];
+    __shared__ uint32_t s_id[kEmitTile];
+    __shared__ int s_xw[kEmitTile];
+    __shared__ int s_row0[kEmitTile];
+    __shared__ int s_tx[kEmitTile];
     __shared__ uint32_t s_hist[256];   // low-byte digit counts of this block's keys (first radix pass)
     const int64_t total = *n_isect;
     if (total > capacity) return;   // over capacity: write nothing
@@ -375,9 +382,26 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
     const int64_t V = *vis_count;
     const int nslot = (int)min((int64_t)kEmitTile, total - o0);
     const int64_t jlo = first_owner[blockIdx.x];
-    // owners of this block's slots are jlo .. jlo + nown - 1 (every visible pair owns a slot)
-    const int nown = (int)min((int64_t)kEmitTile, V - jlo);
-    for (int q = threadIdx.x; q < nown; q += kEmitThreads) s_off[q] = (int)(offsets[jlo + q] - o0);
+    // owners of this block's slots are jlo .. the owner of the next block's first slot (at
+    // most kEmitTile of them: every visible pair owns a slot)
+    const int64_t jhi = o0 + kEmitTile < total ? (int64_t)first_owner[blockIdx.x + 1] + 1 : V;
+    const int nown = (int)min((int64_t)kEmitTile, jhi - jlo);
+    for (int q = threadIdx.x; q < nown; q += kEmitThreads) {
+        s_off[q] = (int)(offsets[jlo + q] - o0);
+        const uint32_t p = sorted_pairs[jlo + q];
+        // sensor s = floor(p / n): a float estimate within one of the quotient, corrected
+        int s = (int)((float)p * inv_n);
+        if ((uint64_t)s * (uint64_t)n > p) s--;
+        else if ((uint64_t)(s + 1) * (uint64_t)n <= p) s++;
+        const short4 rc = rect[p];
+        const int tx = tab.tiles_x[s], w = rc.z - rc.x;
+        const bool ok = rc.x >= 0 && rc.x < tx && w > 0 && w <= tx && rc.y >= 0 && rc.w > rc.y &&
+                        rc.w <= tab.tiles_y[s];   // else a malformed projection: never ranged
+        s_id[q] = (uint32_t)(p - (uint64_t)s * (uint64_t)n);
+        s_xw[q] = ok ? ((int)rc.x | (w << 16)) : 0;
+        s_row0[q] = tab.tile_base[s] + (int)rc.y * tx;
+        s_tx[q] = tx | (tab.is_lidar[s] ? (int)0x80000000 : 0);
+    }
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < kEmitItems; it++) {
@@ -390,39 +414,28 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
             if (s_off[mid] <= o) lo = mid;
             else hi = mid - 1;
         }
-        const uint32_t p = sorted_pairs[jlo + lo];
-        // sensor s = floor(p / n) and row / column in the rectangle, each from a float
-        // estimate that is within one of the quotient, then corrected exactly
-        int s = (int)((float)p * inv_n);
-        if ((uint64_t)s * (uint64_t)n > p) s--;
-        else if ((uint64_t)(s + 1) * (uint64_t)n <= p) s++;
-        const uint32_t i = (uint32_t)(p - (uint64_t)s * (uint64_t)n);
-        const short4 rc = rect[p];
-        const int w = rc.z - rc.x;
-        const int q = o - s_off[lo];
-        if (!(rc.x >= 0 && rc.x < tab.tiles_x[s] && w > 0 && w <= tab.tiles_x[s] && rc.y >= 0 && rc.w > rc.y &&
-              rc.w <= tab.tiles_y[s])) {   // malformed projection: an id past every tile, never ranged
-            keys[o0 + o] = 0xffffffffu;
-            vals[o0 + o] = i;
-            atomicAdd(&s_hist[255], 1u);
-            continue;
+        const int xw = s_xw[lo], w = xw >> 16;
+        uint32_t key = 0xffffffffu;   // an id past every tile
+        if (w > 0) {
+            // row and column in the rectangle from a float estimate of the quotient that is
+            // within one of it, then corrected exactly
+            const int q = o - s_off[lo];
+            int dy = (int)__fdividef((float)q + 0.5f, (float)w);
+            int dx = q - dy * w;
+            if (dx < 0) {
+                dy--;
+                dx += w;
+            } else if (dx >= w) {
+                dy++;
+                dx -= w;
+            }
+            const int txf = s_tx[lo], tx = txf & 0x7fffffff;
+            int col = (xw & 0xffff) + dx;
+            if (txf < 0 && col >= tx) col -= tx;   // lidar azimuth wrap
+            key = (uint32_t)(s_row0[lo] + dy * tx + col);
         }
-        int dy = (int)__fdividef((float)q + 0.5f, (float)w);
-        int dx = q - dy * w;
-        if (dx < 0) {
-            dy--;
-            dx += w;
-        } else if (dx >= w) {
-            dy++;
-            dx -= w;
-        }
-        const int ty = rc.y + dy;
-        int col = rc.x + dx;
-        const int tx = tab.tiles_x[s];
-        if (tab.is_lidar[s] && col >= tx) col -= tx;
-        const uint32_t key = (uint32_t)(tab.tile_base[s] + ty * tx + col);
         keys[o0 + o] = key;
-        vals[o0 + o] = i;
+        vals[o0 + o] = s_id[lo];
         atomicAdd(&s_hist[key & 255u], 1u);
     }
     __syncthreads();
