@@ -4,13 +4,20 @@
 // lightweight two-hidden-layer MLP; loss weights lambda_intens = 1, lambda_raydrop = 0.1
 // in Eq. loss_fn).
 //
-// Weights are stored in BF16 (W1 | W2 | W3 packed) with FP32 biases and FP32 master copies
-// for the optimiser; every product is accumulated in FP32 on the FMA pipe (activations
-// stay FP32, so the decoder's error is that of FP32 accumulation, not of BF16 operands).
-// Each block converts the weights to FP32 in shared memory once; a thread owns one ray.
-// The training kernel runs the per-ray forward and backward, then forms the weight
-// gradients of a 128-ray tile as tile-wide contractions out of shared memory, keeping
-// them in registers across a persistent grid and flushing once per block.
+// Weights are stored in BF16 (W1 | W2 | W3 packed, row-major [in][out]) with FP32 biases
+// and FP32 master copies for the optimiser.  Every contraction runs on the tensor cores
+// (mma.sync m16n8k16, BF16 operands, FP32 accumulation).  Activations and gradients stay
+// FP32 values: each is split into a BF16 high part and a BF16 residual, and a product
+// with an exact BF16 weight takes two MMAs (high and residual), a product of two split
+// values three (the residual x residual term is below FP32 accumulation noise), so the
+// decoder's numerics are those of FP32 activations with BF16 weights.
+//
+// A warp owns 16 rays (one MMA row tile).  A layer's accumulator fragments (rows = rays,
+// columns = units) are exactly the next layer's A-operand fragments, so activations pass
+// from layer to layer in registers.  Training blocks take 64 rays (4 warps) at a time:
+// after each warp's forward and backward, the weight gradients dW = A^T dZ contract over
+// the block's rays from transposed BF16 copies in shared memory, and stay in registers
+// across a persistent grid until one flush per block.
 #include <cuda_bf16.h>
 
 #include "types.cuh"
@@ -20,235 +27,439 @@ namespace splat {
 constexpr int kHIn = 32, kHHid = 64, kHOut = 2;
 constexpr int kW1 = kHIn * kHHid, kW2 = kHHid * kHHid, kW3 = kHHid * kHOut;
 constexpr int kHeadParams = kW1 + kHHid + kW2 + kHHid + kW3 + kHOut;   // W1 b1 W2 b2 W3 b3
-constexpr int kHeadTile = 128;
+constexpr int kHeadWarps = 4;
+constexpr int kHeadThreads = 32 * kHeadWarps;
+constexpr int kHeadRays = 16 * kHeadWarps;   // rays per training-block iteration
+constexpr int kP32 = 40;                      // padded row lengths (BF16 elements) of the shared
+constexpr int kP64 = 72;                      // operands: conflict-free fragment loads
+constexpr int kPR = kHeadRays + 8;            // transposed activations [unit][ray]
 
+using bf16 = __nv_bfloat16;
+
+__device__ __forceinline__ uint32_t bits2(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t*>(&v); }
+__device__ __forceinline__ uint32_t ld2(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+// FP32 pair -> BF16 high parts and BF16 residuals (a = hi + lo to about 16 bits).
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    hi = bits2(h);
+    lo = bits2(__floats2bfloat162_rn(a - hf.x, b - hf.y));
+}
+
+__device__ __forceinline__ void split_one(float a, bf16& hi, bf16& lo) {
+    hi = __float2bfloat16_rn(a);
+    lo = __float2bfloat16_rn(a - __bfloat162float(hi));
+}
+
+// d += A (16 x 16, row) * B (16 x 8, col): BF16 operands, FP32 accumulators.  Fragments:
+// g = lane / 4, t = lane % 4; A regs (g, 2t..) (g+8, 2t..) (g, 2t+8..) (g+8, 2t+8..);
+// B regs (k 2t.., n g) (k 2t+8.., n g); d (g, 2t) (g, 2t+1) (g+8, 2t) (g+8, 2t+1).
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+struct SplitA {   // an A fragment of split FP32 values
+    uint32_t h[4], l[4];
+};
+
+// Weights in shared memory, in the layouts the fragments read: W^T [out][in] for the
+// forward products, W [in][out] for the backward ones.
 struct HeadSmemW {
-    float W1[kW1];
-    float W2[kW2];
-    float W3[kW3];
+    bf16 w1t[kHHid][kP32];
+    bf16 w2t[kHHid][kP64];
+    bf16 w3t[8][kP64];     // outputs 2..7 are zero (one 8-wide MMA tile)
+    bf16 w1[kHIn][kP64];
+    bf16 w2[kHHid][kP64];
+    float w3[kHHid][kHOut];
     float b1[kHHid], b2[kHHid], b3[kHOut];
 };
 
-__device__ __forceinline__ float bf16_to_f32(uint16_t u) { return __uint_as_float(((uint32_t)u) << 16); }
-
 __device__ __forceinline__ void load_head_weights(HeadSmemW& s, const HeadW& hw) {
-    for (int i = threadIdx.x; i < kW1 + kW2 + kW3; i += blockDim.x) {
-        const float v = bf16_to_f32(hw.w[i]);
-        if (i < kW1) s.W1[i] = v;
-        else if (i < kW1 + kW2) s.W2[i - kW1] = v;
-        else s.W3[i - kW1 - kW2] = v;
+    const bf16* w = reinterpret_cast<const bf16*>(hw.w);
+    for (int e = threadIdx.x; e < kW1; e += blockDim.x) {
+        const int i = e / kHHid, j = e % kHHid;
+        s.w1t[j][i] = w[e];
+        s.w1[i][j] = w[e];
     }
-    for (int i = threadIdx.x; i < 2 * kHHid + kHOut; i += blockDim.x) {
-        const float v = hw.b[i];
-        if (i < kHHid) s.b1[i] = v;
-        else if (i < 2 * kHHid) s.b2[i - kHHid] = v;
-        else s.b3[i - 2 * kHHid] = v;
+    for (int e = threadIdx.x; e < kW2; e += blockDim.x) {
+        const int i = e / kHHid, j = e % kHHid;
+        s.w2t[j][i] = w[kW1 + e];
+        s.w2[i][j] = w[kW1 + e];
     }
-}
-
-__device__ __forceinline__ void load_x(const float* x, int64_t r, float (&xr)[kHIn]) {
-    const float4* p = reinterpret_cast<const float4*>(x + r * kHIn);
-#pragma unroll
-    for (int k = 0; k < kHIn / 4; k++) {
-        const float4 v = p[k];
-        xr[4 * k] = v.x;
-        xr[4 * k + 1] = v.y;
-        xr[4 * k + 2] = v.z;
-        xr[4 * k + 3] = v.w;
+    for (int e = threadIdx.x; e < 8 * kHHid; e += blockDim.x) {
+        const int k = e / kHHid, i = e % kHHid;
+        s.w3t[k][i] = k < kHOut ? w[kW1 + kW2 + i * kHOut + k] : __float2bfloat16_rn(0.f);
+        if (k < kHOut) s.w3[i][k] = __bfloat162float(w[kW1 + kW2 + i * kHOut + k]);
+    }
+    for (int e = threadIdx.x; e < 2 * kHHid + kHOut; e += blockDim.x) {
+        const float v = hw.b[e];
+        if (e < kHHid) s.b1[e] = v;
+        else if (e < 2 * kHHid) s.b2[e - kHHid] = v;
+        else s.b3[e - 2 * kHHid] = v;
     }
 }
 
-// h1 = relu(W1^T x + b1)
-__device__ __forceinline__ void layer1(const HeadSmemW& s, const float (&xr)[kHIn], float (&h1)[kHHid]) {
-#pragma unroll
-    for (int j = 0; j < kHHid; j++) h1[j] = s.b1[j];
-#pragma unroll 4
-    for (int i = 0; i < kHIn; i++) {
-        const float xi = xr[i];
-#pragma unroll
-        for (int j = 0; j < kHHid; j++) h1[j] += xi * s.W1[i * kHHid + j];
-    }
-#pragma unroll
-    for (int j = 0; j < kHHid; j++) h1[j] = fmaxf(h1[j], 0.f);
+// One C tile (n-tile nt of a 64-wide layer) -> the A fragment of the next layer.
+__device__ __forceinline__ void c_to_a(const float (&d)[4], int nt, SplitA (&a)[4]) {
+    const int ks = nt >> 1, r = (nt & 1) * 2;
+    split_pair(d[0], d[1], a[ks].h[r], a[ks].l[r]);
+    split_pair(d[2], d[3], a[ks].h[r + 1], a[ks].l[r + 1]);
 }
 
-// o = W3^T relu(W2^T h1 + b2) + b3, one hidden unit at a time; also returns the active mask.
-__device__ __forceinline__ void layer23(const HeadSmemW& s, const float (&h1)[kHHid], float& o0, float& o1,
-                                        uint64_t& mask, float* h2_out) {
-    o0 = s.b3[0];
-    o1 = s.b3[1];
-    mask = 0;
-#pragma unroll 2
-    for (int j = 0; j < kHHid; j += 4) {
-        float z[4];
+// The forward of one 16-ray tile: x fragments in, H1 / H2 fragments, ReLU masks (bit
+// 4 nt + e for accumulator e of n-tile nt) and the two outputs of rows g and g + 8 out
+// (valid on lanes with t == 0).
+struct HeadFwd {
+    SplitA h1[4], h2[4];
+    uint32_t m1, m2;
+    float o[4];   // (o0, o1) of row g, (o0, o1) of row g + 8
+};
+
+__device__ __forceinline__ void head_forward_tile(const HeadSmemW& s, const SplitA (&xa)[2], HeadFwd& f) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    f.m1 = f.m2 = 0;
 #pragma unroll
-        for (int q = 0; q < 4; q++) z[q] = s.b2[j + q];
+    for (int nt = 0; nt < 8; nt++) {
+        const float ba = s.b1[8 * nt + 2 * t], bb = s.b1[8 * nt + 2 * t + 1];
+        float d[4] = {ba, bb, ba, bb};
 #pragma unroll
-        for (int i = 0; i < kHHid; i++) {
-            const float hi = h1[i];
-#pragma unroll
-            for (int q = 0; q < 4; q++) z[q] += hi * s.W2[i * kHHid + j + q];
+        for (int ks = 0; ks < 2; ks++) {
+            const uint32_t b0 = ld2(&s.w1t[8 * nt + g][16 * ks + 2 * t]);
+            const uint32_t b1 = ld2(&s.w1t[8 * nt + g][16 * ks + 8 + 2 * t]);
+            mma16816(d, xa[ks].h, b0, b1);
+            mma16816(d, xa[ks].l, b0, b1);
         }
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            if (d[e] > 0.f) f.m1 |= 1u << (4 * nt + e);
+            else d[e] = 0.f;
+        }
+        c_to_a(d, nt, f.h1);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 8; nt++) {
+        const float ba = s.b2[8 * nt + 2 * t], bb = s.b2[8 * nt + 2 * t + 1];
+        float d[4] = {ba, bb, ba, bb};
+#pragma unroll
+        for (int ks = 0; ks < 4; ks++) {
+            const uint32_t b0 = ld2(&s.w2t[8 * nt + g][16 * ks + 2 * t]);
+            const uint32_t b1 = ld2(&s.w2t[8 * nt + g][16 * ks + 8 + 2 * t]);
+            mma16816(d, f.h1[ks].h, b0, b1);
+            mma16816(d, f.h1[ks].l, b0, b1);
+        }
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            if (d[e] > 0.f) f.m2 |= 1u << (4 * nt + e);
+            else d[e] = 0.f;
+        }
+        c_to_a(d, nt, f.h2);
+    }
+    const float b30 = t == 0 ? s.b3[0] : 0.f, b31 = t == 0 ? s.b3[1] : 0.f;
+    float d[4] = {b30, b31, b30, b31};
+#pragma unroll
+    for (int ks = 0; ks < 4; ks++) {
+        const uint32_t b0 = ld2(&s.w3t[g][16 * ks + 2 * t]);
+        const uint32_t b1 = ld2(&s.w3t[g][16 * ks + 8 + 2 * t]);
+        mma16816(d, f.h2[ks].h, b0, b1);
+        mma16816(d, f.h2[ks].l, b0, b1);
+    }
+#pragma unroll
+    for (int e = 0; e < 4; e++) f.o[e] = d[e];
+}
+
+// x rows r0 + g and r0 + g + 8 (zero past R) as split A fragments of the two k-steps;
+// also returns the raw values (k-step ks, register q, element e) for transposed copies.
+__device__ __forceinline__ void load_x_frags(const float* __restrict__ x, int64_t r0, int64_t R, SplitA (&xa)[2],
+                                             float (&xv)[2][4][2]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int64_t ra = r0 + g, rb = r0 + g + 8;
+#pragma unroll
+    for (int ks = 0; ks < 2; ks++) {
 #pragma unroll
         for (int q = 0; q < 4; q++) {
-            const float h2 = fmaxf(z[q], 0.f);
-            if (z[q] > 0.f) mask |= (uint64_t)1 << (j + q);
-            if (h2_out) h2_out[j + q] = h2;
-            o0 += h2 * s.W3[(j + q) * kHOut];
-            o1 += h2 * s.W3[(j + q) * kHOut + 1];
+            const int64_t r = (q & 1) ? rb : ra;
+            const int col = 16 * ks + ((q & 2) ? 8 : 0) + 2 * t;
+            float2 v = make_float2(0.f, 0.f);
+            if (r < R) v = *reinterpret_cast<const float2*>(x + r * kHIn + col);
+            xv[ks][q][0] = v.x;
+            xv[ks][q][1] = v.y;
+            split_pair(v.x, v.y, xa[ks].h[q], xa[ks].l[q]);
         }
     }
 }
 
-__global__ void __launch_bounds__(256) k_head_fwd(const float* __restrict__ x, int64_t R, HeadW hw,
-                                                  float* __restrict__ out) {
+__global__ void __launch_bounds__(kHeadThreads) k_head_fwd(const float* __restrict__ x, int64_t R, HeadW hw,
+                                                           float* __restrict__ out) {
     __shared__ HeadSmemW s;
     load_head_weights(s, hw);
     __syncthreads();
-    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
-        float xr[kHIn], h1[kHHid];
-        load_x(x, r, xr);
-        layer1(s, xr, h1);
-        float o0, o1;
-        uint64_t mask;
-        layer23(s, h1, o0, o1, mask, nullptr);
-        reinterpret_cast<float2*>(out)[r] = make_float2(o0, o1);
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int64_t tiles = (R + 15) / 16;
+    for (int64_t tile = (int64_t)blockIdx.x * kHeadWarps + (threadIdx.x >> 5); tile < tiles;
+         tile += (int64_t)gridDim.x * kHeadWarps) {
+        const int64_t r0 = tile * 16;
+        SplitA xa[2];
+        float xv[2][4][2];
+        load_x_frags(x, r0, R, xa, xv);
+        HeadFwd f;
+        head_forward_tile(s, xa, f);
+        if (t == 0) {
+            if (r0 + g < R) reinterpret_cast<float2*>(out)[r0 + g] = make_float2(f.o[0], f.o[1]);
+            if (r0 + g + 8 < R) reinterpret_cast<float2*>(out)[r0 + g + 8] = make_float2(f.o[2], f.o[3]);
+        }
     }
 }
 
+// Per-iteration shared buffers of a training block (64 rays): transposed BF16 split copies
+// of X, H1, dZ1, dZ2 for the weight-gradient contractions; H2 and dO in FP32.
 struct HeadTrainSmem {
     HeadSmemW w;
-    float X[kHeadTile][kHIn];
-    float H1[kHeadTile][kHHid];
-    float A[kHeadTile][kHHid];     // h2, then dZ1 (relu'(z1) * dh1)
-    float DZ2[kHeadTile][kHHid];
-    float DO[kHeadTile][kHOut];
-    float red[kHeadTile / 32];
+    bf16 xt_h[kHIn][kPR], xt_l[kHIn][kPR];
+    bf16 h1t_h[kHHid][kPR], h1t_l[kHHid][kPR];
+    bf16 z1t_h[kHHid][kPR], z1t_l[kHHid][kPR];
+    bf16 z2t_h[kHHid][kPR], z2t_l[kHHid][kPR];
+    float h2[kHeadRays][kHHid];
+    float dO[kHeadRays][kHOut];
 };
+
+// Transposed split store of one C tile: values of rows (rays) g and g + 8, columns
+// (units) c0 and c0 + 1.
+__device__ __forceinline__ void store_t(bf16 (*th)[kPR], bf16 (*tl)[kPR], const float (&d)[4], int c0, int ray) {
+    bf16 h, l;
+    split_one(d[0], h, l);
+    th[c0][ray] = h;
+    tl[c0][ray] = l;
+    split_one(d[1], h, l);
+    th[c0 + 1][ray] = h;
+    tl[c0 + 1][ray] = l;
+    split_one(d[2], h, l);
+    th[c0][ray + 8] = h;
+    tl[c0][ray + 8] = l;
+    split_one(d[3], h, l);
+    th[c0 + 1][ray + 8] = h;
+    tl[c0 + 1][ray + 8] = l;
+}
+
+// A fragment (rows = units r0.., k = rays k0..) and B fragment (k = rays k0.., n = units
+// n0..) of the weight-gradient products, from transposed [unit][ray] copies.
+__device__ __forceinline__ void ld_at(const bf16 (*tt)[kPR], int r0, int k0, uint32_t (&a)[4]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    a[0] = ld2(&tt[r0 + g][k0 + 2 * t]);
+    a[1] = ld2(&tt[r0 + g + 8][k0 + 2 * t]);
+    a[2] = ld2(&tt[r0 + g][k0 + 8 + 2 * t]);
+    a[3] = ld2(&tt[r0 + g + 8][k0 + 8 + 2 * t]);
+}
 
 // Loss lam_i mean (sigmoid(o0) - y_int)^2 + lam_d mean BCE(o1, y_drop) over R rays; adds
 // its gradients to grad (W1 b1 W2 b2 W3 b3, FP32) and, if dx is given, writes dL/dx.
-__global__ void __launch_bounds__(kHeadTile) k_head_train(const float* __restrict__ x, int64_t R, HeadW hw,
-                                                         const float* __restrict__ y_int,
-                                                         const float* __restrict__ y_drop, float lam_i, float lam_d,
-                                                         float* __restrict__ grad, float* loss, float* __restrict__ dx) {
+__global__ void __launch_bounds__(kHeadThreads) k_head_train(const float* __restrict__ x, int64_t R, HeadW hw,
+                                                            const float* __restrict__ y_int,
+                                                            const float* __restrict__ y_drop, float lam_i,
+                                                            float lam_d, float* __restrict__ grad, float* loss,
+                                                            float* __restrict__ dx) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     HeadTrainSmem& s = *reinterpret_cast<HeadTrainSmem*>(smem_raw);
     load_head_weights(s.w, hw);
-    const int t = threadIdx.x;
-    // register accumulators of this thread's share of the weight gradients
-    float gW1[kW1 / kHeadTile], gW2[kW2 / kHeadTile], gW3 = 0.f, gb = 0.f, gb3a = 0.f, gb3b = 0.f;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t = lane & 3;
+    // persistent accumulators: dW2 row tile `warp` (8 n-tiles), dW1 row tile warp & 1 with
+    // n-tiles 4 (warp >> 1) .. + 3, and one CUDA-core output each of dW3 / biases
+    float aw2[8][4], aw1[4][4];
 #pragma unroll
-    for (int k = 0; k < kW1 / kHeadTile; k++) gW1[k] = 0.f;
+    for (int j = 0; j < 8; j++)
 #pragma unroll
-    for (int k = 0; k < kW2 / kHeadTile; k++) gW2[k] = 0.f;
-    float lsum = 0.f;
+        for (int e = 0; e < 4; e++) aw2[j][e] = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+#pragma unroll
+        for (int e = 0; e < 4; e++) aw1[j][e] = 0.f;
+    float aw3 = 0.f, ab = 0.f, ab3 = 0.f, lsum = 0.f;
     const float invR = 1.f / (float)R;
-    const int64_t ntiles = (R + kHeadTile - 1) / kHeadTile;
-    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t r = tile * kHeadTile + t;
-        const bool valid = r < R;
-        __syncthreads();   // weights loaded / previous tile's contractions done
-        float xr[kHIn], h1[kHHid];
-        if (valid) load_x(x, r, xr);
-        else {
+    const int64_t iters = (R + kHeadRays - 1) / kHeadRays;
+    const int ray = 16 * warp + g;   // this lane's rows within the block's 64 rays: ray, ray + 8
+    for (int64_t it = blockIdx.x; it < iters; it += gridDim.x) {
+        const int64_t r0 = it * kHeadRays + 16 * warp;
+        __syncthreads();   // weights loaded / previous iteration's contractions done
+        SplitA xa[2];
+        float xv[2][4][2];
+        load_x_frags(x, r0, R, xa, xv);
 #pragma unroll
-            for (int i = 0; i < kHIn; i++) xr[i] = 0.f;
-        }
+        for (int ks = 0; ks < 2; ks++) {
 #pragma unroll
-        for (int i = 0; i < kHIn; i++) s.X[t][i] = xr[i];
-        layer1(s.w, xr, h1);
-#pragma unroll
-        for (int j = 0; j < kHHid; j++) s.H1[t][j] = h1[j];
-        float o0, o1;
-        uint64_t mask;
-        layer23(s.w, h1, o0, o1, mask, s.A[t]);
-        float d0 = 0.f, d1 = 0.f;
-        if (valid) {
-            const float sg = 1.f / (1.f + __expf(-o0));
-            const float e = sg - y_int[r];
-            const float y = y_drop[r];
-            const float bce = fmaxf(o1, 0.f) - o1 * y + log1pf(__expf(-fabsf(o1)));
-            lsum += lam_i * e * e * invR + lam_d * bce * invR;
-            d0 = lam_i * 2.f * e * sg * (1.f - sg) * invR;
-            d1 = lam_d * (1.f / (1.f + __expf(-o1)) - y) * invR;
-        }
-        s.DO[t][0] = d0;
-        s.DO[t][1] = d1;
-        gb3a += d0;
-        gb3b += d1;
-        // dZ2 = relu'(z2) * (W3 dO)
-#pragma unroll
-        for (int j = 0; j < kHHid; j++) {
-            const float v = s.w.W3[j * kHOut] * d0 + s.w.W3[j * kHOut + 1] * d1;
-            s.DZ2[t][j] = ((mask >> j) & 1) ? v : 0.f;
-        }
-        __syncthreads();
-        // dW3 (64 x 2) and the biases: one entry per thread for this tile (h2 in A)
-        {
-            const int i = t >> 1, k = t & 1;   // 128 threads <-> 64 x 2 entries
-            float acc = 0.f;
-#pragma unroll 8
-            for (int rr = 0; rr < kHeadTile; rr++) acc += s.A[rr][i] * s.DO[rr][k];
-            gW3 += acc;
-        }
-        __syncthreads();
-        // dZ1 = relu'(z1) * (W2 dZ2), written over h2
-        {
-            float dz2[kHHid];
-#pragma unroll
-            for (int j = 0; j < kHHid; j++) dz2[j] = s.DZ2[t][j];
-#pragma unroll 4
-            for (int i = 0; i < kHHid; i++) {
-                float acc = 0.f;
-#pragma unroll
-                for (int j = 0; j < kHHid; j++) acc += s.w.W2[i * kHHid + j] * dz2[j];
-                s.A[t][i] = s.H1[t][i] > 0.f ? acc : 0.f;
+            for (int q = 0; q < 4; q++) {
+                const int col = 16 * ks + ((q & 2) ? 8 : 0) + 2 * t, rr = ray + ((q & 1) ? 8 : 0);
+                bf16 h, l;
+                split_one(xv[ks][q][0], h, l);
+                s.xt_h[col][rr] = h;
+                s.xt_l[col][rr] = l;
+                split_one(xv[ks][q][1], h, l);
+                s.xt_h[col + 1][rr] = h;
+                s.xt_l[col + 1][rr] = l;
             }
         }
-        __syncthreads();
-        if (dx && valid) {
-            float dz1[kHHid];
+        HeadFwd f;
+        head_forward_tile(s.w, xa, f);
+        // H1 (transposed, for dW2) and H2 (FP32, for dW3) from the fragments
 #pragma unroll
-            for (int j = 0; j < kHHid; j++) dz1[j] = s.A[t][j];
-#pragma unroll 4
-            for (int i = 0; i < kHIn; i++) {
-                float acc = 0.f;
+        for (int nt = 0; nt < 8; nt++) {
+            const int ks = nt >> 1, q = (nt & 1) * 2;
+            float d[4];
+            {
+                const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&f.h1[ks].h[q]));
+                const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&f.h1[ks].l[q]));
+                const float2 c = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&f.h1[ks].h[q + 1]));
+                const float2 e = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&f.h1[ks].l[q + 1]));
+                d[0] = a.x + b.x;
+                d[1] = a.y + b.y;
+                d[2] = c.x + e.x;
+                d[3] = c.y + e.y;
+            }
+            store_t(s.h1t_h, s.h1t_l, d, 8 * nt + 2 * t, ray);
+            const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&f.h2[ks].h[q]));
+            const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&f.h2[ks].l[q]));
+            const float2 c = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&f.h2[ks].h[q + 1]));
+            const float2 e = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&f.h2[ks].l[q + 1]));
+            s.h2[ray][8 * nt + 2 * t] = a.x + b.x;
+            s.h2[ray][8 * nt + 2 * t + 1] = a.y + b.y;
+            s.h2[ray + 8][8 * nt + 2 * t] = c.x + e.x;
+            s.h2[ray + 8][8 * nt + 2 * t + 1] = c.y + e.y;
+        }
+        // loss and dL/dO on the lanes holding the outputs (t == 0), rows g and g + 8
+        float dO[4] = {0.f, 0.f, 0.f, 0.f};
+        if (t == 0) {
 #pragma unroll
-                for (int j = 0; j < kHHid; j++) acc += s.w.W1[i * kHHid + j] * dz1[j];
-                dx[r * kHIn + i] = acc;
+            for (int h = 0; h < 2; h++) {
+                const int64_t r = r0 + g + 8 * h;
+                if (r < R) {
+                    const float o0 = f.o[2 * h], o1 = f.o[2 * h + 1];
+                    const float sg = 1.f / (1.f + __expf(-o0));
+                    const float e = sg - y_int[r];
+                    const float y = y_drop[r];
+                    const float bce = fmaxf(o1, 0.f) - o1 * y + log1pf(__expf(-fabsf(o1)));
+                    lsum += lam_i * e * e * invR + lam_d * bce * invR;
+                    dO[2 * h] = lam_i * 2.f * e * sg * (1.f - sg) * invR;
+                    dO[2 * h + 1] = lam_d * (1.f / (1.f + __expf(-o1)) - y) * invR;
+                }
+            }
+            s.dO[ray][0] = dO[0];
+            s.dO[ray][1] = dO[1];
+            s.dO[ray + 8][0] = dO[2];
+            s.dO[ray + 8][1] = dO[3];
+        }
+#pragma unroll
+        for (int e = 0; e < 4; e++) dO[e] = __shfl_sync(0xffffffffu, dO[e], lane & ~3);
+        // dZ2 = relu'(z2) (dO W3^T), as fragments and transposed
+        SplitA z2[4];
+#pragma unroll
+        for (int nt = 0; nt < 8; nt++) {
+            const int j = 8 * nt + 2 * t;
+            float d[4];
+            d[0] = dO[0] * s.w.w3[j][0] + dO[1] * s.w.w3[j][1];
+            d[1] = dO[0] * s.w.w3[j + 1][0] + dO[1] * s.w.w3[j + 1][1];
+            d[2] = dO[2] * s.w.w3[j][0] + dO[3] * s.w.w3[j][1];
+            d[3] = dO[2] * s.w.w3[j + 1][0] + dO[3] * s.w.w3[j + 1][1];
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                if (!((f.m2 >> (4 * nt + e)) & 1u)) d[e] = 0.f;
+            c_to_a(d, nt, z2);
+            store_t(s.z2t_h, s.z2t_l, d, j, ray);
+        }
+        // dZ1 = relu'(z1) (dZ2 W2^T)
+        SplitA z1[4];
+#pragma unroll
+        for (int nt = 0; nt < 8; nt++) {
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int ks = 0; ks < 4; ks++) {
+                const uint32_t b0 = ld2(&s.w.w2[8 * nt + g][16 * ks + 2 * t]);
+                const uint32_t b1 = ld2(&s.w.w2[8 * nt + g][16 * ks + 8 + 2 * t]);
+                mma16816(d, z2[ks].h, b0, b1);
+                mma16816(d, z2[ks].l, b0, b1);
+            }
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                if (!((f.m1 >> (4 * nt + e)) & 1u)) d[e] = 0.f;
+            c_to_a(d, nt, z1);
+            store_t(s.z1t_h, s.z1t_l, d, 8 * nt + 2 * t, ray);
+        }
+        if (dx) {   // dX = dZ1 W1^T
+#pragma unroll
+            for (int nt = 0; nt < 4; nt++) {
+                float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int ks = 0; ks < 4; ks++) {
+                    const uint32_t b0 = ld2(&s.w.w1[8 * nt + g][16 * ks + 2 * t]);
+                    const uint32_t b1 = ld2(&s.w.w1[8 * nt + g][16 * ks + 8 + 2 * t]);
+                    mma16816(d, z1[ks].h, b0, b1);
+                    mma16816(d, z1[ks].l, b0, b1);
+                }
+                const int col = 8 * nt + 2 * t;
+                if (r0 + g < R) *reinterpret_cast<float2*>(dx + (r0 + g) * kHIn + col) = make_float2(d[0], d[1]);
+                if (r0 + g + 8 < R)
+                    *reinterpret_cast<float2*>(dx + (r0 + g + 8) * kHIn + col) = make_float2(d[2], d[3]);
             }
         }
-        // dW1 = X^T dZ1, dW2 = H1^T dZ2 over the tile; thread t owns entries t + 128 k
+        __syncthreads();   // the block's transposed copies are complete
+        // dW2 += H1^T dZ2 (rows 16 warp .., all 64 columns), K = the block's 64 rays
 #pragma unroll
-        for (int k = 0; k < kW1 / kHeadTile; k++) {
-            const int e = t + kHeadTile * k, i = e / kHHid, j = e % kHHid;
-            float acc = 0.f;
-#pragma unroll 8
-            for (int rr = 0; rr < kHeadTile; rr++) acc += s.X[rr][i] * s.A[rr][j];
-            gW1[k] += acc;
-        }
+        for (int ks = 0; ks < kHeadRays / 16; ks++) {
+            uint32_t ah[4], al[4];
+            ld_at(s.h1t_h, 16 * warp, 16 * ks, ah);
+            ld_at(s.h1t_l, 16 * warp, 16 * ks, al);
 #pragma unroll
-        for (int k = 0; k < kW2 / kHeadTile; k++) {
-            const int e = t + kHeadTile * k, i = e / kHHid, j = e % kHHid;
-            float acc = 0.f;
-#pragma unroll 8
-            for (int rr = 0; rr < kHeadTile; rr++) acc += s.H1[rr][i] * s.DZ2[rr][j];
-            gW2[k] += acc;
+            for (int nt = 0; nt < 8; nt++) {
+                const uint32_t bh0 = ld2(&s.z2t_h[8 * nt + g][16 * ks + 2 * t]);
+                const uint32_t bh1 = ld2(&s.z2t_h[8 * nt + g][16 * ks + 8 + 2 * t]);
+                const uint32_t bl0 = ld2(&s.z2t_l[8 * nt + g][16 * ks + 2 * t]);
+                const uint32_t bl1 = ld2(&s.z2t_l[8 * nt + g][16 * ks + 8 + 2 * t]);
+                mma16816(aw2[nt], ah, bh0, bh1);
+                mma16816(aw2[nt], ah, bl0, bl1);
+                mma16816(aw2[nt], al, bh0, bh1);
+            }
         }
-        // biases: b1 (threads 0..63 sum dZ1 columns), b2 (64..127 sum dZ2), b3 below
+        // dW1 += X^T dZ1 (rows 16 (warp & 1) .., columns 32 (warp >> 1) ..)
+#pragma unroll
+        for (int ks = 0; ks < kHeadRays / 16; ks++) {
+            uint32_t ah[4], al[4];
+            ld_at(s.xt_h, 16 * (warp & 1), 16 * ks, ah);
+            ld_at(s.xt_l, 16 * (warp & 1), 16 * ks, al);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int n0 = 32 * (warp >> 1) + 8 * q;
+                const uint32_t bh0 = ld2(&s.z1t_h[n0 + g][16 * ks + 2 * t]);
+                const uint32_t bh1 = ld2(&s.z1t_h[n0 + g][16 * ks + 8 + 2 * t]);
+                const uint32_t bl0 = ld2(&s.z1t_l[n0 + g][16 * ks + 2 * t]);
+                const uint32_t bl1 = ld2(&s.z1t_l[n0 + g][16 * ks + 8 + 2 * t]);
+                mma16816(aw1[q], ah, bh0, bh1);
+                mma16816(aw1[q], ah, bl0, bl1);
+                mma16816(aw1[q], al, bh0, bh1);
+            }
+        }
+        // dW3 (64 x 2, one entry per thread), b1 / b2 (one unit per thread), b3
         {
+            const int i = tid >> 1, k = tid & 1;
             float acc = 0.f;
-            if (t < kHHid)
 #pragma unroll 8
-            for (int rr = 0; rr < kHeadTile; rr++) acc += s.A[rr][t];
-            else
+            for (int r = 0; r < kHeadRays; r++) acc += s.h2[r][i] * s.dO[r][k];
+            aw3 += acc;
+            const bf16(*th)[kPR] = tid < kHHid ? s.z1t_h : s.z2t_h;
+            const bf16(*tl)[kPR] = tid < kHHid ? s.z1t_l : s.z2t_l;
+            const int u = tid & (kHHid - 1);
+            float sb = 0.f;
 #pragma unroll 8
-            for (int rr = 0; rr < kHeadTile; rr++) acc += s.DZ2[rr][t - kHHid];
-            gb += acc;
+            for (int r = 0; r < kHeadRays; r++) sb += __bfloat162float(th[u][r]) + __bfloat162float(tl[u][r]);
+            ab += sb;
+            if (tid < kHOut) {
+                float s3 = 0.f;
+                for (int r = 0; r < kHeadRays; r++) s3 += s.dO[r][tid];
+                ab3 += s3;
+            }
         }
     }
-    __syncthreads();
     // flush: W1 | b1 | W2 | b2 | W3 | b3
     float* gW1p = grad;
     float* gb1p = grad + kW1;
@@ -256,23 +467,28 @@ __global__ void __launch_bounds__(kHeadTile) k_head_train(const float* __restric
     float* gb2p = gW2p + kW2;
     float* gW3p = gb2p + kHHid;
 #pragma unroll
-    for (int k = 0; k < kW1 / kHeadTile; k++) atomicAdd(gW1p + t + kHeadTile * k, gW1[k]);
-#pragma unroll
-    for (int k = 0; k < kW2 / kHeadTile; k++) atomicAdd(gW2p + t + kHeadTile * k, gW2[k]);
-    atomicAdd(gW3p + t, gW3);
-    if (t < kHHid) atomicAdd(gb1p + t, gb);
-    else atomicAdd(gb2p + t - kHHid, gb);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-        gb3a += __shfl_xor_sync(0xffffffffu, gb3a, o);
-        gb3b += __shfl_xor_sync(0xffffffffu, gb3b, o);
+    for (int nt = 0; nt < 8; nt++) {
+        const int i = 16 * warp + g, j = 8 * nt + 2 * t;
+        atomicAdd(gW2p + i * kHHid + j, aw2[nt][0]);
+        atomicAdd(gW2p + i * kHHid + j + 1, aw2[nt][1]);
+        atomicAdd(gW2p + (i + 8) * kHHid + j, aw2[nt][2]);
+        atomicAdd(gW2p + (i + 8) * kHHid + j + 1, aw2[nt][3]);
     }
-    if ((t & 31) == 0) {
-        atomicAdd(gW3p + kW3, gb3a);
-        atomicAdd(gW3p + kW3 + 1, gb3b);
-        if (loss) atomicAdd(loss, lsum);
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const int i = 16 * (warp & 1) + g, j = 32 * (warp >> 1) + 8 * q + 2 * t;
+        atomicAdd(gW1p + i * kHHid + j, aw1[q][0]);
+        atomicAdd(gW1p + i * kHHid + j + 1, aw1[q][1]);
+        atomicAdd(gW1p + (i + 8) * kHHid + j, aw1[q][2]);
+        atomicAdd(gW1p + (i + 8) * kHHid + j + 1, aw1[q][3]);
     }
+    atomicAdd(gW3p + tid, aw3);
+    if (tid < kHHid) atomicAdd(gb1p + tid, ab);
+    else atomicAdd(gb2p + tid - kHHid, ab);
+    if (tid < kHOut) atomicAdd(gW3p + kW3 + tid, ab3);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    if (lane == 0 && loss) atomicAdd(loss, lsum);
 }
 
 // Adam on the FP32 masters (W1 b1 W2 b2 W3 b3), then the BF16 weight copy and FP32 biases
@@ -333,9 +549,9 @@ size_t head_train_smem() { return sizeof(HeadTrainSmem); }
 
 void launch_head_fwd(const float* x, int64_t R, const HeadW& hw, float* out, cudaStream_t st) {
     if (R <= 0) return;
-    int64_t blocks = (R + 255) / 256;
-    if (blocks > 152 * 4) blocks = 152 * 4;
-    k_head_fwd<<<(unsigned)blocks, 256, 0, st>>>(x, R, hw, out);
+    int64_t blocks = ((R + 15) / 16 + kHeadWarps - 1) / kHeadWarps;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_head_fwd<<<(unsigned)blocks, kHeadThreads, 0, st>>>(x, R, hw, out);
 }
 
 void launch_head_train(const float* x, int64_t R, const HeadW& hw, const float* y_int, const float* y_drop, float lam_i,
@@ -343,9 +559,14 @@ void launch_head_train(const float* x, int64_t R, const HeadW& hw, const float* 
     if (R <= 0) return;
     const size_t sm = sizeof(HeadTrainSmem);
     cudaFuncSetAttribute(k_head_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    int64_t blocks = (R + kHeadTile - 1) / kHeadTile;
-    if (blocks > 152) blocks = 152;
-    k_head_train<<<(unsigned)blocks, kHeadTile, sm, st>>>(x, R, hw, y_int, y_drop, lam_i, lam_d, grad, loss, dx);
+    int per_sm = 1, dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_head_train, kHeadThreads, sm);
+    if (per_sm < 1) per_sm = 1;
+    int64_t blocks = (R + kHeadRays - 1) / kHeadRays;
+    if (blocks > (int64_t)sms * per_sm) blocks = (int64_t)sms * per_sm;
+    k_head_train<<<(unsigned)blocks, kHeadThreads, sm, st>>>(x, R, hw, y_int, y_drop, lam_i, lam_d, grad, loss, dx);
 }
 
 void launch_head_adam(float* p, const float* g, float* m, float* v, float lr, float beta1, float beta2, float eps,
