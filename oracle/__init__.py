@@ -72,9 +72,9 @@ def _declare(L):
                                 [ctypes.c_double, _P])
     L.oracle_render_backward.restype = ctypes.c_int
     L.oracle_render_backward.argtypes = ([_I64] + [_P] * 6 + [ctypes.c_int] + [_P] * 3 + [_I64] + [_P] * 13 +
-                                         [ctypes.c_double, _P])
+                                         [ctypes.c_double, _P, _P])
     L.oracle_projection_backward.restype = ctypes.c_int
-    L.oracle_projection_backward.argtypes = [_I64] + [_P] * 13
+    L.oracle_projection_backward.argtypes = [_I64] + [_P] * 14
     L.oracle_jacobian.restype = ctypes.c_int
     L.oracle_jacobian.argtypes = [_P, _P, _P, ctypes.c_double, _P, _P, _P, _P, _P]
     if hasattr(L, "head_forward"):
@@ -226,7 +226,8 @@ def render_backward(g: dict, s, gF, gT=None, gD=None, gA=None, sel=None, gL=None
                     los_eps: float = 0.8) -> dict:
     """Gradients of sum(gF*F) + sum(gT*T) [+ sum(gD*range_exp) + sum(gA*alpha)
     + sum(gL*los)] over the selected rays (None: all rays; the upstream arrays then hold
-    one row per selected ray)."""
+    one row per selected ray).  out["sensor"] holds the gradients with respect to the
+    sensor's linear and angular velocity and (cameras) its time offset."""
     L = lib()
     n = len(g["opacities"])
     m = _g(g)
@@ -236,13 +237,16 @@ def render_backward(g: dict, s, gF, gT=None, gD=None, gA=None, sel=None, gL=None
     out = {"d2": np.zeros((n, 10)), "features": np.zeros((n, C)), "means": np.zeros((n, 3)),
            "scales": np.zeros((n, 3)), "quats": np.zeros((n, 4)), "opacities": np.zeros(n),
            "velocities": np.zeros((n, 3))}
+    ds = np.zeros(7)   # sensor: linear velocity, angular velocity, camera time offset
     sel_arr = None if sel is None else np.ascontiguousarray(sel, dtype=np.int64)
     L.oracle_render_backward(n, *[_ptr(a) for a in m], _ptr(feat), C, _ptr(P), _ptr(_elev(s)), _ptr(_rays(s)),
                              0 if sel_arr is None else len(sel_arr), _ptr(sel_arr),
                              _ptr(_f64(gF)), _ptr(_f64(gT)), _ptr(_f64(gD)), _ptr(_f64(gA)), _ptr(out["d2"]),
                              _ptr(out["features"]), _ptr(out["means"]), _ptr(out["scales"]), _ptr(out["quats"]),
                              _ptr(out["opacities"]), _ptr(out["velocities"]),
-                             _ptr(None if los_range is None else _f64(los_range)), float(los_eps), _ptr(_f64(gL)))
+                             _ptr(None if los_range is None else _f64(los_range)), float(los_eps), _ptr(_f64(gL)),
+                             _ptr(ds))
+    out["sensor"] = {"lin_vel": ds[0:3], "ang_vel": ds[3:6], "time_offset": float(ds[6])}
     return out
 
 
@@ -256,7 +260,7 @@ def projection_backward(g: dict, s, d2) -> dict:
     L.oracle_projection_backward(n, *[_ptr(a) for a in m], _ptr(P), _ptr(_elev(s)),
                                  _ptr(np.ascontiguousarray(d2, dtype=np.float64)), _ptr(out["means"]),
                                  _ptr(out["scales"]), _ptr(out["quats"]), _ptr(out["opacities"]),
-                                 _ptr(out["velocities"]))
+                                 _ptr(out["velocities"]), None)
     return out
 
 

@@ -661,7 +661,7 @@ int oracle_render(int64_t n, const double *means, const double *scales, const do
  * ------------------------------------------------------------------------------- */
 static void ray_backward(const double *P, int C, const double *feat, const double *rec, const contrib_t *cb, int nb,
                          double Tfinal, const double *gF, double gT, double gD, double gL, double rp, double los_eps,
-                         double *d2, double *dfeat) {
+                         double *d2, double *dfeat, double *dtime) {
     double B[64];
     double BD = 0;
     for (int c = 0; c < C; c++) B[c] = 0;
@@ -697,6 +697,8 @@ static void ray_backward(const double *P, int C, const double *feat, const doubl
             double ddy = dsig * (g[R_CB] * e->dx + g[R_CC] * e->dy);
             loc[0] = -ddx; loc[1] = -ddy;
             loc[7] = -ddx * e->t; loc[8] = -ddy * e->t;
+            /* the ray time (row time + camera time offset) moves the mean by v t */
+            if (dtime) *dtime += -(ddx * g[R_VA] + ddy * g[R_VB]);
         }
         for (int q = 0; q < 10; q++) {
 #pragma omp atomic
@@ -770,7 +772,7 @@ static void dJ_dm(const double *P, const proj_state *st, double dJ[9][3]) {
 static void projection_backward(const double *P, const double *elev, int64_t i, const double *means,
                                 const double *scales, const double *quats, const double *opac, const double *vel,
                                 const double *d2, double *dmean, double *dscale, double *dquat, double *dopac,
-                                double *dvel) {
+                                double *dvel, double *dsensor) {
     proj_state st;
     double rec[REC];
     int rc[4], orc[4], irc[4], mg;
@@ -831,6 +833,17 @@ static void projection_backward(const double *P, const double *elev, int64_t i, 
     double oxdw[3];
     cross3(P + P_W, dw, oxdw);
     for (int k = 0; k < 3; k++) dm[k] += oxdw[k];
+    /* sensor velocities (the paper optimises both): dL/dv_s = -dL/dw, dL/domega = dL/dw x m */
+    if (dsensor) {
+        double dwxm[3];
+        cross3(dw, st.m, dwxm);
+        for (int k = 0; k < 3; k++) {
+#pragma omp atomic
+            dsensor[k] -= dw[k];
+#pragma omp atomic
+            dsensor[3 + k] += dwxm[k];
+        }
+    }
     const double *R = P + P_R;
     if (dvel)
         for (int k = 0; k < 3; k++) dvel[3 * i + k] += R[k] * dw[0] + R[3 + k] * dw[1] + R[6 + k] * dw[2];
@@ -870,7 +883,7 @@ int oracle_render_backward(int64_t n, const double *means, const double *scales,
                            const double *elev, const double *rays, int64_t n_sel, const int64_t *sel,
                            const double *gF, const double *gT, const double *gD, const double *gA, double *d2,
                            double *dfeat, double *dmean, double *dscale, double *dquat, double *dopac, double *dvel,
-                           const double *los_range, double los_eps, const double *gL) {
+                           const double *los_range, double los_eps, const double *gL, double *dsensor) {
     if (C > 64) return -1;
     double *rec = (double *)malloc(sizeof(double) * REC * (size_t)(n > 0 ? n : 1));
     int32_t *rect = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)(n > 0 ? n : 1));
@@ -894,8 +907,14 @@ int oracle_render_backward(int64_t n, const double *means, const double *scales,
                                 NULL, cb, (int)(n > 0 ? n : 1), 0, 0, NULL);
             double gt = gT ? gT[j] : 0;
             if (gA) gt -= gA[j]; /* alpha_acc = 1 - T */
+            double dt = 0;
             ray_backward(P, C, feat, rec, cb, nb, T, gF + (int64_t)C * j, gt, gD ? gD[j] : 0,
-                         (gL && los_range) ? gL[j] : 0, los_range ? los_range[j] : 0, los_eps, loc2, dfeat);
+                         (gL && los_range) ? gL[j] : 0, los_range ? los_range[j] : 0, los_eps, loc2, dfeat,
+                         (dsensor && (int)P[P_KIND] == 0) ? &dt : NULL);
+            if (dsensor) {
+#pragma omp atomic
+                dsensor[6] += dt;
+            }
         }
         free(cands); free(cb);
     }
@@ -904,7 +923,7 @@ int oracle_render_backward(int64_t n, const double *means, const double *scales,
     for (int64_t i = 0; i < n; i++) {
         if (!vis[i]) continue;
         projection_backward(P, elev, i, means, scales, quats, opac, vel, loc2 + 10 * i, dmean, dscale, dquat, dopac,
-                            dvel);
+                            dvel, dsensor);
     }
     free(loc2); free(rec); free(rect); free(orect); free(irect); free(vis); free(marg);
     return 0;
@@ -914,10 +933,10 @@ int oracle_render_backward(int64_t n, const double *means, const double *scales,
 int oracle_projection_backward(int64_t n, const double *means, const double *scales, const double *quats,
                                const double *opac, const double *vel, const double *P, const double *elev,
                                const double *d2, double *dmean, double *dscale, double *dquat, double *dopac,
-                               double *dvel) {
+                               double *dvel, double *dsensor) {
     for (int64_t i = 0; i < n; i++)
         projection_backward(P, elev, i, means, scales, quats, opac, vel, d2 + 10 * i, dmean, dscale, dquat, dopac,
-                            dvel);
+                            dvel, dsensor);
     return 0;
 }
 

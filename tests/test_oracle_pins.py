@@ -470,6 +470,65 @@ def test_lidar_gradients_match_finite_differences():
     assert _fd_check(g, lid, seed=2) > 40
 
 
+def _fd_sensor_check(g, s, seed, h=1e-5):
+    """Gradients with respect to the sensor's linear and angular velocity (and a camera's
+    time offset) against central differences of the rendered loss."""
+    import dataclasses
+    C = g["features"].shape[1]
+    w = _weights(s, C, seed)
+    an = oracle.render_backward(g, s, w["F"], w["T"], w["D"] if s.kind == "lidar" else None,
+                                w["A"] if s.kind == "lidar" else None)["sensor"]
+    _, c0 = _loss(g, s, w)
+    fields = [("lin_vel", k) for k in range(3)] + [("ang_vel", k) for k in range(3)]
+    if s.kind == "camera":
+        fields.append(("time_offset", None))
+    checked = 0
+    for name, k in fields:
+        base = getattr(s, name)
+        x0 = float(base if k is None else base[k])
+        step = h * max(1.0, abs(x0))
+
+        # sensor parameters reach the renderer as FP32: difference by the rounded values
+        xp, xm = float(np.float32(x0 + step)), float(np.float32(x0 - step))
+
+        def moved(xv):
+            if k is None:
+                return dataclasses.replace(s, **{name: xv})
+            v = np.array(base, dtype=np.float64).copy()
+            v[k] = xv
+            return dataclasses.replace(s, **{name: v})
+
+        Lp, cp = _loss(g, moved(xp), w)
+        Lm, cm = _loss(g, moved(xm), w)
+        assert np.array_equal(cp, c0) and np.array_equal(cm, c0), f"discontinuity at {name}{k}"
+        num = (Lp - Lm) / (xp - xm)
+        got = an[name] if k is None else an[name][k]
+        assert got == pytest.approx(num, rel=1e-4, abs=2e-5 * max(1.0, abs(num))), (name, k, got, num)
+        checked += num != 0
+    return checked
+
+
+def test_camera_sensor_velocity_and_time_offset_gradients_match_fd():
+    """The paper optimises the sensors' linear and angular velocities and the cameras'
+    time offset (App. B learning rates, ablation e): their gradients through the pixel
+    velocity (Eq. pixel velocity) and the pixel times (Eq. t_pix)."""
+    vs, ws = np.array([0.8, -0.3, 5.0]), np.array([0.03, -0.05, 0.02])
+    cam = scenes.Camera(R=scenes.camera_rotation(0.1), t=np.array([0.0, 0.1, 0.0]), width=40, height=30, fx=30,
+                        fy=28, cx=20.3, cy=14.8, lin_vel=vs, ang_vel=ws, rs_time=0.04, time_offset=0.003,
+                        tile_w=8, tile_h=8)
+    g = random_small_scene(21, 7, (3.0, -2.0, -1.5), (7.0, 2.0, 1.5), channels=3)
+    g["velocities"] = np.random.default_rng(4).normal(0, 1.0, size=(7, 3)).astype(np.float32)
+    assert _fd_sensor_check(g, cam, seed=5) == 7
+
+
+def test_lidar_sensor_velocity_gradients_match_fd():
+    vs, ws = np.array([12.0, 0.5, 0.0]), np.array([0.0, 0.02, 0.1])
+    lid = small_lidar(n_beams=8, n_az=96, lo=-12, hi=10, R=rodrigues([0, 0, 0.2]), lin_vel=vs, ang_vel=ws,
+                      sweep_time=0.1, eps2d=2e-5, tile_el=4, tile_az=16)
+    g = random_small_scene(33, 6, (-6.0, -6.0, -1.0), (6.0, 6.0, 1.0), channels=2, log_scale=(-1.2, 0.3))
+    assert _fd_sensor_check(g, lid, seed=6) == 6
+
+
 def test_line_of_sight_gradients_match_finite_differences():
     """App. B line-of-sight term: its gradient (1 on every alpha in front of the return)
     through the alpha chain, against central differences; returns are placed between the
