@@ -381,7 +381,7 @@ def run_ours(args):
     timed("raster_camera_bwd", lambda: L.call("splat_render_camera_backward", ctypes.byref(cg), S, fr.c_sensors,
                                                 fr.c_proj(), fr.c_bins(), _vp(out["cam_T"]), _vp(out["cam_last"]),
                                                 _vp(grads["cam_feat"]), None, _vp(fr.grad_proj),
-                                                _vp(pgrads["features"]), st))
+                                                _vp(pgrads["features"]), None, st))
     timed("raster_lidar_bwd", lambda: L.call("splat_render_lidar_backward", ctypes.byref(cg), S, fr.c_sensors,
                                                fr.c_proj(), fr.c_bins(), _vp(out["lid_T"]), _vp(out["lid_last"]),
                                                _vp(grads["lid_feat"]), _vp(grads["lid_range_exp"]), None,
@@ -389,7 +389,7 @@ def run_ours(args):
     timed("project_bwd", lambda: L.call("splat_project_backward", ctypes.byref(cg), S, fr.c_sensors, fr.c_proj(),
                                           _vp(fr.grad_proj), _vp(pgrads["means"]), _vp(pgrads["scales"]),
                                           _vp(pgrads["quats"]), _vp(pgrads["opacities"]),
-                                          _vp(pgrads["velocities"]), st))
+                                          _vp(pgrads["velocities"]), None, st))
 
     peaks = measured_peaks()
     clocks = clk.summary()

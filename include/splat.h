@@ -248,12 +248,16 @@ splat_status splat_render_lidar_los(const splat_gaussians *g, int32_t n_sensors,
 /* Backward of splat_render_camera.  Inputs: the forward's out_T and out_last (or both
  * NULL: the kernel then recomputes them per tile), dL_dfeat[pixels][channels] and
  * dL_dT[pixels] (may be NULL).  Accumulates into
- *   grad_proj[n_sensors][3][n][4]: gradients of proj.rec (same layout), and
- *   dL_dfeatures[n][channels]. */
+ *   grad_proj[n_sensors][3][n][4]: gradients of proj.rec (same layout),
+ *   dL_dfeatures[n][channels], and, if dL_dsensors is not NULL, entry 6 of
+ *   dL_dsensors[n_sensors][8] of every camera: the gradient with respect to its time
+ *   offset (the camera "time to centre" the paper optimises; every pixel time of Eq.
+ *   t_pix carries it). */
 splat_status splat_render_camera_backward(const splat_gaussians *g, int32_t n_sensors, const splat_sensor *sensors,
                                           splat_projected proj, splat_bins bins, const float *out_T,
                                           const int32_t *out_last, const float *dL_dfeat, const float *dL_dT,
-                                          float *grad_proj, float *dL_dfeatures, void *stream);
+                                          float *grad_proj, float *dL_dfeatures, float *dL_dsensors,
+                                          void *stream);
 
 /* Backward of splat_render_lidar for dL_dfeat[rays][channels], dL_drange_exp[rays] and
  * dL_dalpha[rays] (the latter two may be NULL).  The median range has no gradient.
@@ -279,11 +283,14 @@ splat_status splat_render_lidar_backward_los(const splat_gaussians *g, int32_t n
  * per Gaussian, no atomics).  Accumulates into dL_dmeans[n][3], dL_dscales[n][3],
  * dL_dquats[n][4], dL_dopacities[n], dL_dvelocities[n][3] (may be NULL).  Gradients
  * are with respect to the ACTIVATED scales and opacities and the unnormalised
- * quaternion. */
+ * quaternion.  If dL_dsensors is not NULL, entries 0..5 of dL_dsensors[n_sensors][8]
+ * accumulate the gradients with respect to each sensor's linear and angular velocity
+ * (sensor frame, through the relative velocity of Eq. pixel velocity / App. D; the
+ * paper optimises both), summed over the Gaussians with one atomic per warp. */
 splat_status splat_project_backward(const splat_gaussians *g, int32_t n_sensors, const splat_sensor *sensors,
                                     splat_projected proj, const float *grad_proj, float *dL_dmeans,
                                     float *dL_dscales, float *dL_dquats, float *dL_dopacities,
-                                    float *dL_dvelocities, void *stream);
+                                    float *dL_dvelocities, float *dL_dsensors, void *stream);
 
 /* L1 term of the training loss (Eq. loss_fn, lambda_r L1): adds scale * sum |pred - target|
  * over `count` floats to *loss (device float, accumulated) and, if grad is not NULL,

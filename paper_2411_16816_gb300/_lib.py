@@ -105,9 +105,9 @@ def load(build_if_missing: bool = True):
     L.splat_render_lidar_backward_los.argtypes = ([G, c_int32, SE, splat_projected, splat_bins] + [c_void_p] * 5 +
                                                   [splat_los] + [c_void_p] * 4)
     L.splat_render_lidar.argtypes = [G, c_int32, SE, splat_projected, splat_bins] + [c_void_p] * 8
-    L.splat_render_camera_backward.argtypes = [G, c_int32, SE, splat_projected, splat_bins] + [c_void_p] * 7
+    L.splat_render_camera_backward.argtypes = [G, c_int32, SE, splat_projected, splat_bins] + [c_void_p] * 8
     L.splat_render_lidar_backward.argtypes = [G, c_int32, SE, splat_projected, splat_bins] + [c_void_p] * 8
-    L.splat_project_backward.argtypes = [G, c_int32, SE, splat_projected] + [c_void_p] * 7
+    L.splat_project_backward.argtypes = [G, c_int32, SE, splat_projected] + [c_void_p] * 8
     L.splat_l1_loss.argtypes = [c_void_p, c_void_p, c_int64, c_float, c_void_p, c_void_p, c_void_p]
     L.splat_head_param_count.argtypes = []
     L.splat_head_inputs.argtypes = [SE, c_void_p, c_int32, c_void_p, c_void_p]

@@ -336,7 +336,7 @@ splat_status splat_render_lidar_los(const splat_gaussians* g, int32_t n_sensors,
 splat_status splat_render_camera_backward(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
                                           splat_projected proj, splat_bins bins, const float* out_T,
                                           const int32_t* out_last, const float* dL_dfeat, const float* dL_dT,
-                                          float* grad_proj, float* dL_dfeatures, void* stream) {
+                                          float* grad_proj, float* dL_dfeatures, float* dL_dsensors, void* stream) {
     Frame fr;
     int tw, th;
     splat_status st = render_common(g, n_sensors, sensors, proj, bins, fr, false, tw, th);
@@ -349,7 +349,8 @@ splat_status splat_render_camera_backward(const splat_gaussians* g, int32_t n_se
         return fail(SPLAT_ERR_INVALID_ARG, "gradient buffers misaligned");
     RasterIn in{(const float4*)proj.rec, bins.isect_ids, (const int2*)bins.tile_ranges, g->features, g->n,
                 g->channels};
-    RasterGrad gr{out_T, out_last, dL_dfeat, dL_dT, nullptr, nullptr, (float4*)grad_proj, dL_dfeatures};
+    RasterGrad gr{out_T, out_last, dL_dfeat, dL_dT, nullptr, nullptr, (float4*)grad_proj, dL_dfeatures, nullptr,
+                  dL_dsensors};
     if (!launch_raster_bwd(false, g->channels, tw, th, fr, fr.n_cam_blocks, in, gr, out_T == nullptr,
                            (cudaStream_t)stream))
         return fail(SPLAT_ERR_INVALID_ARG, "unsupported camera configuration");
@@ -408,7 +409,7 @@ splat_status splat_render_lidar_backward_los(const splat_gaussians* g, int32_t n
 splat_status splat_project_backward(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
                                     splat_projected proj, const float* grad_proj, float* dL_dmeans,
                                     float* dL_dscales, float* dL_dquats, float* dL_dopacities,
-                                    float* dL_dvelocities, void* stream) {
+                                    float* dL_dvelocities, float* dL_dsensors, void* stream) {
     splat_status st = check_gaussians(g, false);
     if (st != SPLAT_OK) return st;
     Frame fr;
@@ -418,7 +419,7 @@ splat_status splat_project_backward(const splat_gaussians* g, int32_t n_sensors,
         return fail(SPLAT_ERR_INVALID_ARG, "gradient pointer is NULL");
     if (!aligned16(grad_proj)) return fail(SPLAT_ERR_INVALID_ARG, "grad_proj misaligned");
     launch_project_backward(gauss_in(g), fr, proj.n_tiles, (const float4*)grad_proj,
-                            GradOut{dL_dmeans, dL_dscales, dL_dquats, dL_dopacities, dL_dvelocities},
+                            GradOut{dL_dmeans, dL_dscales, dL_dquats, dL_dopacities, dL_dvelocities, dL_dsensors},
                             (cudaStream_t)stream);
     return check_launch("splat_project_backward");
 }

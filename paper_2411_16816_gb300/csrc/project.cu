@@ -321,7 +321,7 @@ __device__ __forceinline__ void cov2d_jac_backward(const float* J0, const float*
 // Accumulate one sensor's contribution to dL/dmean (world), dL/dSigma (world, full
 // matrix), dL/dopacity and dL/dvelocity.
 __device__ void camera_backward(const SensorDev& S, const GaussLocal& G, float4 g0, float4 g1, float3& dmean,
-                                float* dSw, float& dop, float3& dvel) {
+                                float* dSw, float& dop, float3& dvel, float (&dsens)[6]) {
     const float3 m = xform(S.R, S.t, G.mean);
     const Sym3 Sc = rotate_sym(S.R, G.Sig);
     CamJ cj;
@@ -365,6 +365,14 @@ __device__ void camera_backward(const SensorDev& S, const GaussLocal& G, float4 
     dm.x += oxdw.x;
     dm.y += oxdw.y;
     dm.z += oxdw.z;
+    // sensor velocities: w = -omega x m - v_s + ..., so dL/dv_s = -dL/dw, dL/domega = dL/dw x m
+    const float3 dwxm = cross(dw, m);
+    dsens[0] = -dw.x;
+    dsens[1] = -dw.y;
+    dsens[2] = -dw.z;
+    dsens[3] = dwxm.x;
+    dsens[4] = dwxm.y;
+    dsens[5] = dwxm.z;
     const float3 dvg = rot_t(S.R, dw);
     dvel.x += dvg.x;
     dvel.y += dvg.y;
@@ -386,7 +394,7 @@ __device__ void camera_backward(const SensorDev& S, const GaussLocal& G, float4 
 }
 
 __device__ void lidar_backward(const SensorDev& S, const GaussLocal& G, float4 g0, float4 g1, float4 g2,
-                               float3& dmean, float* dSw, float& dop, float3& dvel) {
+                               float3& dmean, float* dSw, float& dop, float3& dvel, float (&dsens)[6]) {
     const float3 m = xform(S.R, S.t, G.mean);
     const Sym3 Sc = rotate_sym(S.R, G.Sig);
     LidJ lj;
@@ -441,6 +449,14 @@ __device__ void lidar_backward(const SensorDev& S, const GaussLocal& G, float4 g
     dm.x += oxdw.x;
     dm.y += oxdw.y;
     dm.z += oxdw.z;
+    // sensor velocities: w = -omega x m - v_s + ..., so dL/dv_s = -dL/dw, dL/domega = dL/dw x m
+    const float3 dwxm = cross(dw, m);
+    dsens[0] = -dw.x;
+    dsens[1] = -dw.y;
+    dsens[2] = -dw.z;
+    dsens[3] = dwxm.x;
+    dsens[4] = dwxm.y;
+    dsens[5] = dwxm.z;
     const float3 dvg = rot_t(S.R, dw);
     dvel.x += dvg.x;
     dvel.y += dvg.y;
@@ -464,27 +480,42 @@ __global__ void __launch_bounds__(256) k_project_backward(GaussIn g, const __gri
                                                           const int32_t* __restrict__ n_tiles,
                                                           const float4* __restrict__ grad, GradOut out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= g.n) return;
+    // no early exit: the optional per-sensor sums below reduce over whole warps
+    bool active = i < g.n;
     bool any = false;
-    for (int s = 0; s < fr.n_sensors; s++) any |= n_tiles[(size_t)s * g.n + i] > 0;
-    if (!any) return;
+    if (active)
+        for (int s = 0; s < fr.n_sensors; s++) any |= n_tiles[(size_t)s * g.n + i] > 0;
+    active = active && any;
+    if (!active && !out.sensor) return;
     GaussLocal G;
-    load_gaussian(g, i, G);
+    if (active) load_gaussian(g, i, G);
     float3 dmean = make_float3(0.f, 0.f, 0.f), dvel = make_float3(0.f, 0.f, 0.f);
     float dSw[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float dop = 0.f;
     for (int s = 0; s < fr.n_sensors; s++) {
-        if (n_tiles[(size_t)s * g.n + i] <= 0) continue;
-        const SensorDev& S = fr.s[s];
-        const float4 g0 = grad[rec_index(s, 0, g.n, i)];
-        const float4 g1 = grad[rec_index(s, 1, g.n, i)];
-        if (S.kind == SPLAT_SENSOR_CAMERA) {
-            camera_backward(S, G, g0, g1, dmean, dSw, dop, dvel);
-        } else {
-            const float4 g2 = grad[rec_index(s, 2, g.n, i)];
-            lidar_backward(S, G, g0, g1, g2, dmean, dSw, dop, dvel);
+        float dsens[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        if (active && n_tiles[(size_t)s * g.n + i] > 0) {
+            const SensorDev& S = fr.s[s];
+            const float4 g0 = grad[rec_index(s, 0, g.n, i)];
+            const float4 g1 = grad[rec_index(s, 1, g.n, i)];
+            if (S.kind == SPLAT_SENSOR_CAMERA) {
+                camera_backward(S, G, g0, g1, dmean, dSw, dop, dvel, dsens);
+            } else {
+                const float4 g2 = grad[rec_index(s, 2, g.n, i)];
+                lidar_backward(S, G, g0, g1, g2, dmean, dSw, dop, dvel, dsens);
+            }
+        }
+        if (out.sensor) {   // the warp's sum, one atomic per component (uniform branch)
+#pragma unroll
+            for (int k = 0; k < 6; k++) {
+                float v = dsens[k];
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if ((threadIdx.x & 31) == 0 && v != 0.f) atomicAdd(out.sensor + 8 * s + k, v);
+            }
         }
     }
+    if (!active) return;
     // Sigma = M M^T, M = Rq diag(s): dM = (dS + dS^T) M
     float M[9], dM[9];
 #pragma unroll

@@ -513,6 +513,7 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
     }
     float gF[PX][CM], gTT[PX], gD[PX], T[PX], S[PX], SD[PX];
     float gL[PX], cut[PX];   // lidar line-of-sight upstream gradient and range cut
+    float dtime = 0.f;       // camera: this thread's share of dL/d (camera time offset)
     int my_last = 0;
 #pragma unroll
     for (int q = 0; q < PX; q++) {
@@ -594,6 +595,8 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
                 const float ddy = dsig * (g1.y * dx[q] + g1.z * dy[q]);
                 const float t0[8] = {-ddx, -ddy, -ddx * tq, -ddy * tq, dsig * 0.5f * dx[q] * dx[q],
                                      dsig * dx[q] * dy[q], dsig * 0.5f * dy[q] * dy[q], dg * Gq};
+                // every pixel time carries the camera time offset; the mean moves by v t
+                if (!LIDAR && gr.dsensor) dtime += t0[0] * g0.z + t0[1] * g0.w;
                 if (q == 0) {
 #pragma unroll
                     for (int j = 0; j < 8; j++) v[j] = t0[j];
@@ -684,6 +687,18 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
             }
 #pragma unroll
             for (int q = 0; q < ROW; q += 4) *reinterpret_cast<float4*>(a_row + q) = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    }
+    if (!LIDAR && gr.dsensor) {   // one atomic per block (uniform branch)
+        __shared__ float s_dt[NT / 32 > 0 ? NT / 32 : 1];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) dtime += __shfl_xor_sync(0xffffffffu, dtime, o);
+        if (lane == 0) s_dt[threadIdx.x >> 5] = dtime;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float tot = 0.f;
+            for (int w = 0; w < NT / 32; w++) tot += s_dt[w];
+            if (tot != 0.f) atomicAdd(gr.dsensor + 8 * tc.s + 6, tot);
         }
     }
 }

@@ -244,10 +244,17 @@ class Frame:
         return views
 
     # -- backward -----------------------------------------------------------------------
-    def backward(self, g: dict, out: dict, grads: dict, param_grads: dict | None = None, stream=None) -> dict:
+    def backward(self, g: dict, out: dict, grads: dict, param_grads: dict | None = None, stream=None,
+                 sensor_grads: torch.Tensor | None = None) -> dict:
         """Gradients with respect to the Gaussian parameters (activated scales and
         opacities, unnormalised quaternions) for upstream gradients
-        grads = {cam_feat, cam_T, lid_feat, lid_range_exp, lid_alpha} (any may be absent)."""
+        grads = {cam_feat, cam_T, lid_feat, lid_range_exp, lid_alpha, lid_los} (any may be
+        absent).  sensor_grads (float32 [sensors][8], device, accumulated) receives the
+        gradients with respect to each sensor's linear velocity (0..2), angular velocity
+        (3..5) and, for cameras, time offset (6)."""
+        if sensor_grads is not None and (sensor_grads.shape != (len(self.sensors), 8) or
+                                         sensor_grads.dtype != torch.float32 or not sensor_grads.is_contiguous()):
+            raise ValueError("sensor_grads must be a contiguous float32 [sensors][8] tensor")
         cg = self.c_gaussians(g)
         st = _stream(stream)
         dev = self.device
@@ -267,7 +274,7 @@ class Frame:
             L.call("splat_render_camera_backward", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
                    self.c_bins(), _vp(out.get("cam_T") if out.get("cam_last") is not None else None),
                    _vp(out.get("cam_last")), _vp(dF.contiguous()), _vp(grads.get("cam_T")), _vp(self.grad_proj),
-                   _vp(param_grads["features"]), st)
+                   _vp(param_grads["features"]), _vp(sensor_grads), st)
         if self.lid_idx:
             dF = grads.get("lid_feat")
             if dF is None:
@@ -290,7 +297,8 @@ class Frame:
                        _vp(param_grads["features"]), st)
         L.call("splat_project_backward", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
                _vp(self.grad_proj), _vp(param_grads["means"]), _vp(param_grads["scales"]),
-               _vp(param_grads["quats"]), _vp(param_grads["opacities"]), _vp(param_grads.get("velocities")), st)
+               _vp(param_grads["quats"]), _vp(param_grads["opacities"]), _vp(param_grads.get("velocities")),
+               _vp(sensor_grads), st)
         return param_grads
 
     # -- inspection ---------------------------------------------------------------------

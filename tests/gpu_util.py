@@ -96,11 +96,14 @@ def oracle_grads(g, sensors, per):
             r = oracle.render_backward(g, s, u["gF"], u["gT"])
         else:
             r = oracle.render_backward(g, s, u["gF"], None, u["gD"], u["gA"])
+        sens = r.pop("sensor")
         if tot is None:
             tot = r
+            tot["sensor"] = [sens]
         else:
-            for k in tot:
+            for k in r:
                 tot[k] = tot[k] + r[k]
+            tot["sensor"].append(sens)
     return tot
 
 

@@ -390,3 +390,29 @@ def test_line_of_sight_term_and_gradient_match_oracle():
     torch.cuda.synchronize()
     want = oracle.render_backward(g, lid, np.zeros((lid.n_rays, C)), gL=gl, los_range=rp)
     U.check_grads(pg, want, keys=("means", "scales", "quats", "opacities", "velocities"))
+
+
+def test_sensor_velocity_and_time_offset_gradients_match_oracle():
+    """Gradients with respect to every sensor's linear and angular velocity (projection
+    backward) and the camera time offset (camera raster backward), the parameters the
+    paper optimises besides the Gaussians, against the oracle."""
+    g, sensors = _dynamic_tiny()
+    fr, gd, out = U.run(g, sensors)
+    grads, per = U.upstream(fr, sensors, g, seed=8)
+    sg = torch.zeros((len(sensors), 8), device=U.DEV)
+    pg = fr.backward(gd, out, grads, sensor_grads=sg)
+    torch.cuda.synchronize()
+    ref = U.oracle_grads(g, sensors, per)
+    U.check_grads(pg, ref)   # the parameter gradients are unchanged by the extra output
+    got = sg.cpu().numpy().astype(np.float64)
+    for k, s in enumerate(sensors):
+        r = ref["sensor"][k]
+        want = np.concatenate([r["lin_vel"], r["ang_vel"], [r["time_offset"]]])
+        n = 7 if s.kind == "camera" else 6
+        want = want[:n]
+        assert np.abs(want).max() > 0
+        rel = np.linalg.norm(got[k, :n] - want) / np.linalg.norm(want)
+        assert rel < U.TOL_GRAD, (s.kind, rel, got[k, :n], want)
+        np.testing.assert_allclose(got[k, :n], want, atol=U.TOL_GRAD * np.abs(want).max(), rtol=0)
+        if s.kind != "camera":
+            assert got[k, 6] == 0.0
