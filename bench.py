@@ -106,9 +106,12 @@ def oracle_sample_step(g, sensors, rays_per_sensor, seed):
 def cpu_baseline(g, sensors, budget_s=20.0):
     import oracle
     oracle.build()
-    n_s, dt = oracle_sample_step(g, sensors, 32, seed=0)          # calibration
-    per_ray = dt / n_s
-    rays = int(max(32, min(4096, budget_s / max(per_ray, 1e-6) / len(sensors))))
+    # calibration: a fixed per-sensor projection cost plus a per-ray cost
+    n1, t1 = oracle_sample_step(g, sensors, 16, seed=0)
+    n2, t2 = oracle_sample_step(g, sensors, 64, seed=0)
+    per_ray = max((t2 - t1) / max(n2 - n1, 1), 1e-7)
+    fixed = max(t1 - per_ray * n1, 0.0)
+    rays = int(max(32, min(65536, (budget_s - fixed) / per_ray / len(sensors))))
     n_s, dt = oracle_sample_step(g, sensors, rays, seed=1)
     return {"value": n_s / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
             "sample": f"{rays} strided rays per sensor ({n_s} total) of the same frame, FP64 fwd+bwd incl. "
@@ -410,7 +413,7 @@ def run_ours(args):
     peak = fp32_peak if bound == "alu" else peaks["hbm_gbs"]
     # DRAM bytes per launch from ncu captures of the current kernels (one camera of the
     # driving scene, scaled by the six cameras of the frame; profiles/ holds the captures)
-    traffic = {"raster_camera_bwd": 6 * 159.8e6} if args.workload == "driving" else {}
+    traffic = {"raster_camera_bwd": 6 * 159.74e6} if args.workload == "driving" else {}
     roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "traffic": traffic.get(dom),
                 "peak_source": (f"FP32 FMA 152x128x2 at {peaks['sm_max_mhz']:.0f} MHz" if bound == "alu"
