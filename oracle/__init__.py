@@ -227,7 +227,8 @@ def render_backward(g: dict, s, gF, gT=None, gD=None, gA=None, sel=None, gL=None
     """Gradients of sum(gF*F) + sum(gT*T) [+ sum(gD*range_exp) + sum(gA*alpha)
     + sum(gL*los)] over the selected rays (None: all rays; the upstream arrays then hold
     one row per selected ray).  out["sensor"] holds the gradients with respect to the
-    sensor's linear and angular velocity and (cameras) its time offset."""
+    sensor's linear and angular velocity, (cameras) its time offset, its translation t
+    and its rotation (R perturbed as (I + [theta]x) R, theta in the sensor frame)."""
     L = lib()
     n = len(g["opacities"])
     m = _g(g)
@@ -237,7 +238,7 @@ def render_backward(g: dict, s, gF, gT=None, gD=None, gA=None, sel=None, gL=None
     out = {"d2": np.zeros((n, 10)), "features": np.zeros((n, C)), "means": np.zeros((n, 3)),
            "scales": np.zeros((n, 3)), "quats": np.zeros((n, 4)), "opacities": np.zeros(n),
            "velocities": np.zeros((n, 3))}
-    ds = np.zeros(7)   # sensor: linear velocity, angular velocity, camera time offset
+    ds = np.zeros(16)  # sensor: linear velocity, angular velocity, camera time offset, -, translation, rotation
     sel_arr = None if sel is None else np.ascontiguousarray(sel, dtype=np.int64)
     L.oracle_render_backward(n, *[_ptr(a) for a in m], _ptr(feat), C, _ptr(P), _ptr(_elev(s)), _ptr(_rays(s)),
                              0 if sel_arr is None else len(sel_arr), _ptr(sel_arr),
@@ -246,7 +247,8 @@ def render_backward(g: dict, s, gF, gT=None, gD=None, gA=None, sel=None, gL=None
                              _ptr(out["opacities"]), _ptr(out["velocities"]),
                              _ptr(None if los_range is None else _f64(los_range)), float(los_eps), _ptr(_f64(gL)),
                              _ptr(ds))
-    out["sensor"] = {"lin_vel": ds[0:3], "ang_vel": ds[3:6], "time_offset": float(ds[6])}
+    out["sensor"] = {"lin_vel": ds[0:3], "ang_vel": ds[3:6], "time_offset": float(ds[6]), "t": ds[8:11],
+                     "rot": ds[11:14]}
     return out
 
 

@@ -844,6 +844,31 @@ static void projection_backward(const double *P, const double *elev, int64_t i, 
             dsensor[3 + k] += dwxm[k];
         }
     }
+    /* sensor pose: m = R mu + t, Sc = R S R^T, w contains R v_g.  Translation: dL/dt = dm.
+     * Rotation, perturbed as R <- (I + [theta]x) R: the mean moves by theta x (m - t),
+     * R v_g by theta x (R v_g), and Sc by [theta]x Sc - Sc [theta]x, whose gradient is
+     * 2 axial(Sc G - G Sc) with G = dL/dSc. */
+    if (dsensor) {
+        double a[3], rv[3], c1[3], c2[3];
+        const double *Rm = P + P_R, *tt = P + P_T;
+        for (int k = 0; k < 3; k++) {
+            a[k] = st.m[k] - tt[k];
+            rv[k] = vel ? Rm[3 * k] * vel[3 * i] + Rm[3 * k + 1] * vel[3 * i + 1] + Rm[3 * k + 2] * vel[3 * i + 2] : 0;
+        }
+        cross3(a, dm, c1);
+        cross3(rv, dw, c2);
+        double Gs[9], M[9];   /* Sc G with G the symmetric part of dL/dSc (Sc is symmetric) */
+        for (int p = 0; p < 3; p++)
+            for (int q = 0; q < 3; q++) Gs[3 * p + q] = 0.5 * (dSc[3 * p + q] + dSc[3 * q + p]);
+        mm3(st.Sc, Gs, M);
+        const double ax[3] = {2 * (M[5] - M[7]), 2 * (M[6] - M[2]), 2 * (M[1] - M[3])};
+        for (int k = 0; k < 3; k++) {
+#pragma omp atomic
+            dsensor[8 + k] += dm[k];
+#pragma omp atomic
+            dsensor[11 + k] += c1[k] + c2[k] + ax[k];
+        }
+    }
     const double *R = P + P_R;
     if (dvel)
         for (int k = 0; k < 3; k++) dvel[3 * i + k] += R[k] * dw[0] + R[3 + k] * dw[1] + R[6 + k] * dw[2];

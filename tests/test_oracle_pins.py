@@ -472,36 +472,65 @@ def test_lidar_gradients_match_finite_differences():
 
 def _fd_sensor_check(g, s, seed, h=1e-5):
     """Gradients with respect to the sensor's linear and angular velocity (and a camera's
-    time offset) against central differences of the rendered loss."""
+    time offset), translation and rotation against central differences of the rendered
+    loss.  Rays whose blended set changes under any of the perturbations (a discrete
+    alpha or tile decision within the step) get zero weight."""
     import dataclasses
     C = g["features"].shape[1]
     w = _weights(s, C, seed)
-    an = oracle.render_backward(g, s, w["F"], w["T"], w["D"] if s.kind == "lidar" else None,
-                                w["A"] if s.kind == "lidar" else None)["sensor"]
-    _, c0 = _loss(g, s, w)
-    fields = [("lin_vel", k) for k in range(3)] + [("ang_vel", k) for k in range(3)]
+    c0 = oracle.render(g, s, guard=0.0)["count"]
+    # every perturbed sensor, as (label, sensor at +, sensor at -, applied parameter change)
+    R0 = np.asarray(s.R, np.float64)
+    R0f = R0.astype(np.float32).astype(np.float64)
+
+    def applied_rot(Rm):   # rotation a rounded FP32 matrix applies to the rounded base
+        A = Rm.astype(np.float32).astype(np.float64) @ R0f.T
+        return 0.5 * np.array([A[2, 1] - A[1, 2], A[0, 2] - A[2, 0], A[1, 0] - A[0, 1]])
+
+    cases = []
+    fields = [("lin_vel", k) for k in range(3)] + [("ang_vel", k) for k in range(3)] + [("t", k) for k in range(3)]
     if s.kind == "camera":
         fields.append(("time_offset", None))
-    checked = 0
     for name, k in fields:
         base = getattr(s, name)
         x0 = float(base if k is None else base[k])
         step = h * max(1.0, abs(x0))
-
         # sensor parameters reach the renderer as FP32: difference by the rounded values
         xp, xm = float(np.float32(x0 + step)), float(np.float32(x0 - step))
 
-        def moved(xv):
+        def moved(xv, name=name, k=k, base=base):
             if k is None:
                 return dataclasses.replace(s, **{name: xv})
             v = np.array(base, dtype=np.float64).copy()
             v[k] = xv
             return dataclasses.replace(s, **{name: v})
 
-        Lp, cp = _loss(g, moved(xp), w)
-        Lm, cm = _loss(g, moved(xm), w)
-        assert np.array_equal(cp, c0) and np.array_equal(cm, c0), f"discontinuity at {name}{k}"
-        num = (Lp - Lm) / (xp - xm)
+        cases.append(((name, k), moved(xp), moved(xm), xp - xm))
+    hr = 1e-4
+    for k in range(3):
+        e = np.zeros(3)
+        e[k] = hr
+        Rp, Rm = rodrigues(e) @ R0, rodrigues(-e) @ R0
+        cases.append((("rot", k), dataclasses.replace(s, R=Rp), dataclasses.replace(s, R=Rm),
+                      applied_rot(Rp) - applied_rot(Rm)))
+    keep = np.ones(s.n_rays, bool)
+    for _, sp, sm_, _ in cases:
+        keep &= oracle.render(g, sp, guard=0.0)["count"] == c0
+        keep &= oracle.render(g, sm_, guard=0.0)["count"] == c0
+    assert keep.mean() > 0.98
+    w = {k: (v * (keep[:, None] if v.ndim == 2 else keep)) for k, v in w.items()}
+    an = oracle.render_backward(g, s, w["F"], w["T"], w["D"] if s.kind == "lidar" else None,
+                                w["A"] if s.kind == "lidar" else None)["sensor"]
+    checked = 0
+    for (name, k), sp, sm_, d in cases:
+        Lp, _ = _loss(g, sp, w)
+        Lm, _ = _loss(g, sm_, w)
+        if name == "rot":
+            pred = float(np.dot(an["rot"], d))
+            assert Lp - Lm == pytest.approx(pred, rel=1e-3, abs=1e-10), ("rot", k, Lp - Lm, pred)
+            checked += (Lp - Lm) != 0
+            continue
+        num = (Lp - Lm) / d
         got = an[name] if k is None else an[name][k]
         assert got == pytest.approx(num, rel=1e-4, abs=2e-5 * max(1.0, abs(num))), (name, k, got, num)
         checked += num != 0
@@ -518,7 +547,7 @@ def test_camera_sensor_velocity_and_time_offset_gradients_match_fd():
                         tile_w=8, tile_h=8)
     g = random_small_scene(21, 7, (3.0, -2.0, -1.5), (7.0, 2.0, 1.5), channels=3)
     g["velocities"] = np.random.default_rng(4).normal(0, 1.0, size=(7, 3)).astype(np.float32)
-    assert _fd_sensor_check(g, cam, seed=5) == 7
+    assert _fd_sensor_check(g, cam, seed=5) == 13
 
 
 def test_lidar_sensor_velocity_gradients_match_fd():
@@ -526,7 +555,7 @@ def test_lidar_sensor_velocity_gradients_match_fd():
     lid = small_lidar(n_beams=8, n_az=96, lo=-12, hi=10, R=rodrigues([0, 0, 0.2]), lin_vel=vs, ang_vel=ws,
                       sweep_time=0.1, eps2d=2e-5, tile_el=4, tile_az=16)
     g = random_small_scene(33, 6, (-6.0, -6.0, -1.0), (6.0, 6.0, 1.0), channels=2, log_scale=(-1.2, 0.3))
-    assert _fd_sensor_check(g, lid, seed=6) == 6
+    assert _fd_sensor_check(g, lid, seed=6) == 12
 
 
 def test_line_of_sight_gradients_match_finite_differences():
