@@ -250,7 +250,7 @@ splat_status splat_render_lidar_los(const splat_gaussians *g, int32_t n_sensors,
  * dL_dT[pixels] (may be NULL).  Accumulates into
  *   grad_proj[n_sensors][3][n][4]: gradients of proj.rec (same layout),
  *   dL_dfeatures[n][channels], and, if dL_dsensors is not NULL, entry 6 of
- *   dL_dsensors[n_sensors][8] of every camera: the gradient with respect to its time
+ *   dL_dsensors[n_sensors][16] of every camera: the gradient with respect to its time
  *   offset (the camera "time to centre" the paper optimises; every pixel time of Eq.
  *   t_pix carries it). */
 splat_status splat_render_camera_backward(const splat_gaussians *g, int32_t n_sensors, const splat_sensor *sensors,
@@ -283,10 +283,13 @@ splat_status splat_render_lidar_backward_los(const splat_gaussians *g, int32_t n
  * per Gaussian, no atomics).  Accumulates into dL_dmeans[n][3], dL_dscales[n][3],
  * dL_dquats[n][4], dL_dopacities[n], dL_dvelocities[n][3] (may be NULL).  Gradients
  * are with respect to the ACTIVATED scales and opacities and the unnormalised
- * quaternion.  If dL_dsensors is not NULL, entries 0..5 of dL_dsensors[n_sensors][8]
- * accumulate the gradients with respect to each sensor's linear and angular velocity
- * (sensor frame, through the relative velocity of Eq. pixel velocity / App. D; the
- * paper optimises both), summed over the Gaussians with one atomic per warp. */
+ * quaternion.  If dL_dsensors is not NULL, dL_dsensors[n_sensors][16] accumulates, per
+ * sensor and summed over the Gaussians (one atomic per warp): entries 0..2 and 3..5, the
+ * gradients with respect to its linear and angular velocity (sensor frame, through the
+ * relative velocity of Eq. pixel velocity / App. D; the paper optimises both); 8..10,
+ * its translation t (mu_sensor = R mu + t); 11..13, its rotation, perturbed as
+ * R <- (I + [theta]x) R with theta in the sensor frame.  Entry 6 is the camera time
+ * offset (splat_render_camera_backward); 7, 14, 15 are unused. */
 splat_status splat_project_backward(const splat_gaussians *g, int32_t n_sensors, const splat_sensor *sensors,
                                     splat_projected proj, const float *grad_proj, float *dL_dmeans,
                                     float *dL_dscales, float *dL_dquats, float *dL_dopacities,

@@ -320,8 +320,44 @@ __device__ __forceinline__ void cov2d_jac_backward(const float* J0, const float*
 
 // Accumulate one sensor's contribution to dL/dmean (world), dL/dSigma (world, full
 // matrix), dL/dopacity and dL/dvelocity.
+// Sensor-parameter terms of one (sensor, Gaussian) pair, from the sensor-frame mean m, its
+// total gradient dm, the covariance Sc and its gradient dSc, and dL/dw of the relative
+// velocity w = -omega x m - v_s + R v_g:
+//   [0..2] dL/dv_s = -dw, [3..5] dL/domega = dw x m, [6..8] dL/dt = dm (m = R mu + t),
+//   [9..11] rotation R <- (I + [theta]x) R: (m - t) x dm + (R v_g) x dw + 2 axial(Sc G - G Sc),
+//   G the symmetric part of dSc.
+__device__ __forceinline__ void sensor_terms(const SensorDev& S, const float3 m, const Sym3& Sc, const float (&dSc)[9],
+                                             const float3 dm, const float3 dw, const float3 vg, float (&ds)[12]) {
+    const float3 dwxm = cross(dw, m);
+    ds[0] = -dw.x;
+    ds[1] = -dw.y;
+    ds[2] = -dw.z;
+    ds[3] = dwxm.x;
+    ds[4] = dwxm.y;
+    ds[5] = dwxm.z;
+    ds[6] = dm.x;
+    ds[7] = dm.y;
+    ds[8] = dm.z;
+    const float3 a = make_float3(m.x - S.t[0], m.y - S.t[1], m.z - S.t[2]);
+    const float3 c1 = cross(a, dm), c2 = cross(rot(S.R, vg), dw);
+    const float Sm[9] = {Sc.xx, Sc.xy, Sc.xz, Sc.xy, Sc.yy, Sc.yz, Sc.xz, Sc.yz, Sc.zz};
+    float M[9];
+#pragma unroll
+    for (int p = 0; p < 3; p++)
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < 3; k++) acc += Sm[3 * p + k] * 0.5f * (dSc[3 * k + q] + dSc[3 * q + k]);
+            M[3 * p + q] = acc;
+        }
+    ds[9] = c1.x + c2.x + 2.f * (M[5] - M[7]);
+    ds[10] = c1.y + c2.y + 2.f * (M[6] - M[2]);
+    ds[11] = c1.z + c2.z + 2.f * (M[1] - M[3]);
+}
+
 __device__ void camera_backward(const SensorDev& S, const GaussLocal& G, float4 g0, float4 g1, float3& dmean,
-                                float* dSw, float& dop, float3& dvel, float (&dsens)[6]) {
+                                float* dSw, float& dop, float3& dvel, bool want_sensor, float (&dsens)[12]) {
     const float3 m = xform(S.R, S.t, G.mean);
     const Sym3 Sc = rotate_sym(S.R, G.Sig);
     CamJ cj;
@@ -365,14 +401,7 @@ __device__ void camera_backward(const SensorDev& S, const GaussLocal& G, float4 
     dm.x += oxdw.x;
     dm.y += oxdw.y;
     dm.z += oxdw.z;
-    // sensor velocities: w = -omega x m - v_s + ..., so dL/dv_s = -dL/dw, dL/domega = dL/dw x m
-    const float3 dwxm = cross(dw, m);
-    dsens[0] = -dw.x;
-    dsens[1] = -dw.y;
-    dsens[2] = -dw.z;
-    dsens[3] = dwxm.x;
-    dsens[4] = dwxm.y;
-    dsens[5] = dwxm.z;
+    if (want_sensor) sensor_terms(S, m, Sc, dSc, dm, dw, G.vel, dsens);
     const float3 dvg = rot_t(S.R, dw);
     dvel.x += dvg.x;
     dvel.y += dvg.y;
@@ -394,7 +423,8 @@ __device__ void camera_backward(const SensorDev& S, const GaussLocal& G, float4 
 }
 
 __device__ void lidar_backward(const SensorDev& S, const GaussLocal& G, float4 g0, float4 g1, float4 g2,
-                               float3& dmean, float* dSw, float& dop, float3& dvel, float (&dsens)[6]) {
+                               float3& dmean, float* dSw, float& dop, float3& dvel, bool want_sensor,
+                               float (&dsens)[12]) {
     const float3 m = xform(S.R, S.t, G.mean);
     const Sym3 Sc = rotate_sym(S.R, G.Sig);
     LidJ lj;
@@ -449,14 +479,7 @@ __device__ void lidar_backward(const SensorDev& S, const GaussLocal& G, float4 g
     dm.x += oxdw.x;
     dm.y += oxdw.y;
     dm.z += oxdw.z;
-    // sensor velocities: w = -omega x m - v_s + ..., so dL/dv_s = -dL/dw, dL/domega = dL/dw x m
-    const float3 dwxm = cross(dw, m);
-    dsens[0] = -dw.x;
-    dsens[1] = -dw.y;
-    dsens[2] = -dw.z;
-    dsens[3] = dwxm.x;
-    dsens[4] = dwxm.y;
-    dsens[5] = dwxm.z;
+    if (want_sensor) sensor_terms(S, m, Sc, dSc, dm, dw, G.vel, dsens);
     const float3 dvg = rot_t(S.R, dw);
     dvel.x += dvg.x;
     dvel.y += dvg.y;
@@ -493,25 +516,28 @@ __global__ void __launch_bounds__(256) k_project_backward(GaussIn g, const __gri
     float dSw[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float dop = 0.f;
     for (int s = 0; s < fr.n_sensors; s++) {
-        float dsens[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float dsens[12];
+#pragma unroll
+        for (int k = 0; k < 12; k++) dsens[k] = 0.f;
         if (active && n_tiles[(size_t)s * g.n + i] > 0) {
             const SensorDev& S = fr.s[s];
             const float4 g0 = grad[rec_index(s, 0, g.n, i)];
             const float4 g1 = grad[rec_index(s, 1, g.n, i)];
             if (S.kind == SPLAT_SENSOR_CAMERA) {
-                camera_backward(S, G, g0, g1, dmean, dSw, dop, dvel, dsens);
+                camera_backward(S, G, g0, g1, dmean, dSw, dop, dvel, out.sensor != nullptr, dsens);
             } else {
                 const float4 g2 = grad[rec_index(s, 2, g.n, i)];
-                lidar_backward(S, G, g0, g1, g2, dmean, dSw, dop, dvel, dsens);
+                lidar_backward(S, G, g0, g1, g2, dmean, dSw, dop, dvel, out.sensor != nullptr, dsens);
             }
         }
         if (out.sensor) {   // the warp's sum, one atomic per component (uniform branch)
 #pragma unroll
-            for (int k = 0; k < 6; k++) {
+            for (int k = 0; k < 12; k++) {
                 float v = dsens[k];
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if ((threadIdx.x & 31) == 0 && v != 0.f) atomicAdd(out.sensor + 8 * s + k, v);
+                // slots: velocities 0..5, (6: camera time offset), translation 8..10, rotation 11..13
+                if ((threadIdx.x & 31) == 0 && v != 0.f) atomicAdd(out.sensor + 16 * s + (k < 6 ? k : k + 2), v);
             }
         }
     }

@@ -698,7 +698,7 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
         if (threadIdx.x == 0) {
             float tot = 0.f;
             for (int w = 0; w < NT / 32; w++) tot += s_dt[w];
-            if (tot != 0.f) atomicAdd(gr.dsensor + 8 * tc.s + 6, tot);
+            if (tot != 0.f) atomicAdd(gr.dsensor + 16 * tc.s + 6, tot);
         }
     }
 }

@@ -26,7 +26,7 @@ struct GradOut {
     float* quats;
     float* opac;
     float* vel;
-    float* sensor;   // optional [sensors][8]: lin_vel, ang_vel, time_offset, reserved
+    float* sensor;   // optional [sensors][16]: lin_vel, ang_vel, time_offset, -, t, rotation, -
 };
 
 struct RasterIn {
@@ -66,7 +66,7 @@ struct RasterGrad {
     float4* grad_proj;     // [S][3][n]
     float* dfeatures;      // [n][C]
     const float* dlos;     // lidar, optional: dL/d line-of-sight term
-    float* dsensor;        // camera, optional: [sensors][8], entry 6 = dL/d time offset
+    float* dsensor;        // camera, optional: [sensors][16], entry 6 = dL/d time offset
 };
 
 struct BinWorkspace {

@@ -249,12 +249,13 @@ class Frame:
         """Gradients with respect to the Gaussian parameters (activated scales and
         opacities, unnormalised quaternions) for upstream gradients
         grads = {cam_feat, cam_T, lid_feat, lid_range_exp, lid_alpha, lid_los} (any may be
-        absent).  sensor_grads (float32 [sensors][8], device, accumulated) receives the
+        absent).  sensor_grads (float32 [sensors][16], device, accumulated) receives the
         gradients with respect to each sensor's linear velocity (0..2), angular velocity
-        (3..5) and, for cameras, time offset (6)."""
-        if sensor_grads is not None and (sensor_grads.shape != (len(self.sensors), 8) or
+        (3..5), for cameras time offset (6), translation (8..10) and rotation (11..13,
+        R perturbed as (I + [theta]x) R)."""
+        if sensor_grads is not None and (sensor_grads.shape != (len(self.sensors), 16) or
                                          sensor_grads.dtype != torch.float32 or not sensor_grads.is_contiguous()):
-            raise ValueError("sensor_grads must be a contiguous float32 [sensors][8] tensor")
+            raise ValueError("sensor_grads must be a contiguous float32 [sensors][16] tensor")
         cg = self.c_gaussians(g)
         st = _stream(stream)
         dev = self.device

@@ -392,14 +392,14 @@ def test_line_of_sight_term_and_gradient_match_oracle():
     U.check_grads(pg, want, keys=("means", "scales", "quats", "opacities", "velocities"))
 
 
-def test_sensor_velocity_and_time_offset_gradients_match_oracle():
+def test_sensor_velocity_time_offset_and_pose_gradients_match_oracle():
     """Gradients with respect to every sensor's linear and angular velocity (projection
     backward) and the camera time offset (camera raster backward), the parameters the
     paper optimises besides the Gaussians, against the oracle."""
     g, sensors = _dynamic_tiny()
     fr, gd, out = U.run(g, sensors)
     grads, per = U.upstream(fr, sensors, g, seed=8)
-    sg = torch.zeros((len(sensors), 8), device=U.DEV)
+    sg = torch.zeros((len(sensors), 16), device=U.DEV)
     pg = fr.backward(gd, out, grads, sensor_grads=sg)
     torch.cuda.synchronize()
     ref = U.oracle_grads(g, sensors, per)
@@ -407,12 +407,14 @@ def test_sensor_velocity_and_time_offset_gradients_match_oracle():
     got = sg.cpu().numpy().astype(np.float64)
     for k, s in enumerate(sensors):
         r = ref["sensor"][k]
-        want = np.concatenate([r["lin_vel"], r["ang_vel"], [r["time_offset"]]])
-        n = 7 if s.kind == "camera" else 6
-        want = want[:n]
-        assert np.abs(want).max() > 0
-        rel = np.linalg.norm(got[k, :n] - want) / np.linalg.norm(want)
-        assert rel < U.TOL_GRAD, (s.kind, rel, got[k, :n], want)
-        np.testing.assert_allclose(got[k, :n], want, atol=U.TOL_GRAD * np.abs(want).max(), rtol=0)
-        if s.kind != "camera":
+        blocks = [(slice(0, 3), r["lin_vel"]), (slice(3, 6), r["ang_vel"]), (slice(8, 11), r["t"]),
+                  (slice(11, 14), r["rot"])]
+        if s.kind == "camera":
+            blocks.append((slice(6, 7), np.array([r["time_offset"]])))
+        else:
             assert got[k, 6] == 0.0
+        for sl, want in blocks:
+            assert np.abs(want).max() > 0
+            rel = np.linalg.norm(got[k, sl] - want) / np.linalg.norm(want)
+            assert rel < U.TOL_GRAD, (s.kind, sl, rel, got[k, sl], want)
+            np.testing.assert_allclose(got[k, sl], want, atol=U.TOL_GRAD * np.abs(want).max(), rtol=0)
