@@ -68,10 +68,10 @@ def _declare(L):
     L.oracle_isect_list.restype = _I64
     L.oracle_isect_list.argtypes = [_I64, _P, _P, _P, _P, _I64, _P, _P]
     L.oracle_render.restype = ctypes.c_int
-    L.oracle_render.argtypes = ([_I64] + [_P] * 6 + [ctypes.c_int] + [_P] * 3 + [ctypes.c_double, _I64] + [_P] * 8 +
-                                [ctypes.c_double, _P])
+    L.oracle_render.argtypes = ([_I64] + [_P] * 6 + [ctypes.c_int] + [_P] * 3 + [_I64, ctypes.c_double, _I64] +
+                                [_P] * 8 + [ctypes.c_double, _P])
     L.oracle_render_backward.restype = ctypes.c_int
-    L.oracle_render_backward.argtypes = ([_I64] + [_P] * 6 + [ctypes.c_int] + [_P] * 3 + [_I64] + [_P] * 13 +
+    L.oracle_render_backward.argtypes = ([_I64] + [_P] * 6 + [ctypes.c_int] + [_P] * 3 + [_I64, _I64] + [_P] * 13 +
                                          [ctypes.c_double, _P, _P])
     L.oracle_projection_backward.restype = ctypes.c_int
     L.oracle_projection_backward.argtypes = [_I64] + [_P] * 14
@@ -189,14 +189,17 @@ def isect_list(g: dict, s, proj: dict | None = None):
     return tiles[:total], ids[:total]
 
 
-def render(g: dict, s, sel=None, guard: float | None = None, los_range=None, los_eps: float = 0.8) -> dict:
+def render(g: dict, s, sel=None, guard: float | None = None, los_range=None, los_eps: float = 0.8,
+           free_rays=None) -> dict:
     """Render the selected rays (indices into the sensor's ray grid; None: all).
 
     Camera ray k is pixel (row, col) = divmod(k, width); lidar ray k is
     (beam, azimuth bin) = divmod(k, n_az).  With los_range (one return range per
     selected lidar ray; <= 0: no return) the line-of-sight term of App. B is returned
     as out["los"]: the summed alpha of the blended Gaussians whose range r_rs lies
-    before los_range - los_eps.
+    before los_range - los_eps.  With free_rays ((k, 3) phi, omega, t of a lidar, e.g.
+    from points_to_rays) those rays are rendered instead of the grid, each in the tile
+    its own (phi, omega) falls in (App. A.2).
     """
     L = lib()
     n = len(g["opacities"])
@@ -206,13 +209,15 @@ def render(g: dict, s, sel=None, guard: float | None = None, los_range=None, los
     P = sensor_params(s)
     guard = guard_for(s) if guard is None else guard
     sel_arr = None if sel is None else np.ascontiguousarray(sel, dtype=np.int64)
-    nr = s.n_rays if sel is None else len(sel_arr)
+    fr = None if free_rays is None else _sensor_array(np.asarray(free_rays).reshape(-1, 3))
+    nfree = 0 if fr is None else len(fr)
+    nr = (nfree if fr is not None else s.n_rays) if sel is None else len(sel_arr)
     F = np.zeros((nr, C)); T = np.zeros(nr); De = np.zeros(nr); Dm = np.zeros(nr)
     mg = np.zeros(nr, np.uint8); cnt = np.zeros(nr, np.int32)
     lr = None if los_range is None else _f64(los_range)
     los = np.zeros(nr) if lr is not None else None
-    L.oracle_render(n, *[_ptr(a) for a in m], _ptr(feat), C, _ptr(P), _ptr(_elev(s)), _ptr(_rays(s)), guard,
-                    nr, _ptr(sel_arr), _ptr(F), _ptr(T), _ptr(De), _ptr(Dm), _ptr(mg), _ptr(cnt), _ptr(lr),
+    L.oracle_render(n, *[_ptr(a) for a in m], _ptr(feat), C, _ptr(P), _ptr(_elev(s)),
+                    _ptr(fr if fr is not None else _rays(s)), nfree, guard, nr, _ptr(sel_arr), _ptr(F), _ptr(T), _ptr(De), _ptr(Dm), _ptr(mg), _ptr(cnt), _ptr(lr),
                     float(los_eps), _ptr(los))
     out = {"F": F, "T": T, "marginal": mg.astype(bool), "marginal_bits": mg, "count": cnt}
     if los is not None:
@@ -223,7 +228,7 @@ def render(g: dict, s, sel=None, guard: float | None = None, los_range=None, los
 
 
 def render_backward(g: dict, s, gF, gT=None, gD=None, gA=None, sel=None, gL=None, los_range=None,
-                    los_eps: float = 0.8) -> dict:
+                    los_eps: float = 0.8, free_rays=None) -> dict:
     """Gradients of sum(gF*F) + sum(gT*T) [+ sum(gD*range_exp) + sum(gA*alpha)
     + sum(gL*los)] over the selected rays (None: all rays; the upstream arrays then hold
     one row per selected ray).  out["sensor"] holds the gradients with respect to the
@@ -240,7 +245,9 @@ def render_backward(g: dict, s, gF, gT=None, gD=None, gA=None, sel=None, gL=None
            "velocities": np.zeros((n, 3))}
     ds = np.zeros(16)  # sensor: linear velocity, angular velocity, camera time offset, -, translation, rotation
     sel_arr = None if sel is None else np.ascontiguousarray(sel, dtype=np.int64)
-    L.oracle_render_backward(n, *[_ptr(a) for a in m], _ptr(feat), C, _ptr(P), _ptr(_elev(s)), _ptr(_rays(s)),
+    fr = None if free_rays is None else _sensor_array(np.asarray(free_rays).reshape(-1, 3))
+    L.oracle_render_backward(n, *[_ptr(a) for a in m], _ptr(feat), C, _ptr(P), _ptr(_elev(s)),
+                             _ptr(fr if fr is not None else _rays(s)), 0 if fr is None else len(fr),
                              0 if sel_arr is None else len(sel_arr), _ptr(sel_arr),
                              _ptr(_f64(gF)), _ptr(_f64(gT)), _ptr(_f64(gD)), _ptr(_f64(gA)), _ptr(out["d2"]),
                              _ptr(out["features"]), _ptr(out["means"]), _ptr(out["scales"]), _ptr(out["quats"]),
@@ -264,6 +271,40 @@ def projection_backward(g: dict, s, d2) -> dict:
                                  _ptr(out["scales"]), _ptr(out["quats"]), _ptr(out["opacities"]),
                                  _ptr(out["velocities"]), None)
     return out
+
+
+def points_to_rays(points, times, s):
+    """App. A.2: lidar points (sensor frame at the sweep's reference time, i.e. ego-motion
+    compensated) and their capture times -> rays (phi, omega, t), ranges r and tiles.
+    The compensation is removed with the sensor's constant velocities (the motion model
+    of the rolling-shutter projection): a static point p appears at p - t (v + omega x p)
+    in the sensor frame of its capture time.  Each point then takes the tile of a
+    zero-extent Gaussian at its (phi, omega): column floor(phi / w_phi) and the row
+    whose elevation boundaries contain omega; tile -1 outside the beam fan.  FP64."""
+    p = np.asarray(points, np.float32).astype(np.float64).reshape(-1, 3)
+    t = np.asarray(times, np.float32).astype(np.float64).reshape(-1)
+    v = np.asarray(s.lin_vel, np.float32).astype(np.float64)
+    w = np.asarray(s.ang_vel, np.float32).astype(np.float64)
+    q = p - t[:, None] * (v[None, :] + np.cross(w[None, :], p))
+    r = np.linalg.norm(q, axis=1)
+    phi = np.mod(np.arctan2(q[:, 1], q[:, 0]), 2 * np.pi)
+    om = np.arcsin(np.clip(q[:, 2] / np.maximum(r, 1e-300), -1.0, 1.0))
+    elev = np.asarray(s.beam_elev, np.float32).astype(np.float64)
+    nb, tel = len(elev), s.tile_el
+    mw = nb // tel
+    bnd = [elev[0] - 0.5 * (elev[1] - elev[0])]
+    bnd += [0.5 * (elev[k * tel - 1] + elev[k * tel]) for k in range(1, mw)]
+    bnd.append(elev[-1] + 0.5 * (elev[-1] - elev[-2]))
+    bnd = np.array(bnd)
+    mphi = (s.n_az + s.tile_az - 1) // s.tile_az
+    wphi = s.tile_az * float(np.float32(s.az_res))
+    col = np.minimum(np.floor(phi / wphi).astype(np.int64), mphi - 1)
+    row = np.zeros(len(p), np.int64)
+    for k in range(1, mw):
+        row = np.where(bnd[k] <= om, k, row)
+    inside = (om > bnd[0]) & (om < bnd[mw])
+    tile = np.where(inside, row * mphi + col, -1)
+    return np.stack([phi, om, t], axis=1), r, tile
 
 
 def jacobian(mean, scale, quat, opac, s):

@@ -477,12 +477,40 @@ typedef struct {           /* one blended Gaussian of a ray, kept for the backwa
     int clamped;
 } contrib_t;
 
+/* Lidar tile of a free ray (App. A.2: a lidar point mapped like a Gaussian of zero
+ * extent): column floor(phi / w_phi), the row whose elevation boundaries contain omega;
+ * -1 outside the beam fan.  *marg is set within FP32 noise of a tile edge. */
+static void free_ray_tile(const double *P, const double *elev, double phi, double om, int *tx, int *ty, int *marg) {
+    int nb = (int)P[P_NB], naz = (int)P[P_NAZ], taz = (int)P[P_TAZ], tel = (int)P[P_TEL];
+    int mphi = (naz + taz - 1) / taz, mw = nb / tel;
+    double wphi = taz * P[P_AZRES];
+    double bnd[1025];
+    elevation_bounds(elev, nb, tel, bnd);
+    *tx = *ty = -1;
+    for (int k = 0; k <= mw; k++)
+        if (fabs(om - bnd[k]) < 2e-7) *marg = 1;
+    if (frac_dist(phi / wphi) < 2e-6 || phi < 2e-7 || fabs(phi - TWO_PI) < 2e-7) *marg = 1;
+    if (!(om > bnd[0]) || !(om < bnd[mw]) || !(phi >= 0) || !(phi < TWO_PI)) return;
+    int c = (int)floor(phi / wphi);
+    if (c > mphi - 1) c = mphi - 1;
+    int r = 0;
+    for (int k = 1; k < mw; k++)
+        if (bnd[k] <= om) r = k;
+    *tx = c;
+    *ty = r;
+}
+
 /* Ray geometry: tile, sample point and time.
  *   camera: pixel centre (col+0.5, row+0.5); t_pix = ((row+0.5)/H - 0.5) t_rs + offset (Eq. t_pix)
  *   lidar:  regular grid phi=(a+0.5) res, omega = beam elevation,
  *           t = ((a+0.5)/n_az - 0.5) t_sweep, unless explicit (phi, omega, t) are given. */
-static void ray_setup(const double *P, const double *elev, const double *rays, int64_t k, int *tx, int *ty,
-                      double *pa, double *pb, double *t) {
+static void ray_setup(const double *P, const double *elev, const double *rays, int64_t nfree, int64_t k, int *tx,
+                      int *ty, double *pa, double *pb, double *t, int *marg) {
+    if (nfree > 0) {   /* free lidar rays (App. A.2): (phi, omega, t) per ray, tile from them */
+        *pa = rays[3 * k]; *pb = rays[3 * k + 1]; *t = rays[3 * k + 2];
+        free_ray_tile(P, elev, *pa, *pb, tx, ty, marg);
+        return;
+    }
     if ((int)P[P_KIND] == 0) {
         int W = (int)P[P_WIDTH], H = (int)P[P_HEIGHT];
         int row = (int)(k / W), col = (int)(k % W);
@@ -509,17 +537,18 @@ static void ray_setup(const double *P, const double *elev, const double *rays, i
 static double wrap_pi(double d) { return d - TWO_PI * floor((d + M_PI) / TWO_PI); }
 
 /* Render one ray: returns the number of blended Gaussians (written to cb if non-null). */
-static int render_ray(const double *P, const double *elev, const double *rays, int64_t n, const double *rec,
+static int render_ray(const double *P, const double *elev, const double *rays, int64_t nfree, int64_t n,
+                      const double *rec,
                       const int32_t *rect, const int32_t *orect, const int32_t *irect, const uint8_t *vis,
                       const uint8_t *gmarg,
                       const double *feat, int C,
                       int64_t k, cand_t *cands, double *F, double *Tout, double *Dexp, double *Dmed,
                       int *marginal, contrib_t *cb, int cb_cap, double rp, double los_eps, double *los) {
     int lidar = (int)P[P_KIND] == 1;
-    int tx, ty;
+    int tx, ty, tmarg = 0;
     double pa, pb, t;
-    ray_setup(P, elev, rays, k, &tx, &ty, &pa, &pb, &t);
-    int nc = 0, mg = 0;
+    ray_setup(P, elev, rays, nfree, k, &tx, &ty, &pa, &pb, &t, &tmarg);
+    int nc = 0, mg = tmarg ? 128 : 0;
     for (int64_t i = 0; i < n; i++) {
         /* a marginal Gaussian's membership is uncertain between its inner and outer boxes;
          * it matters only where it would be blended (alpha at or above the threshold) */
@@ -617,7 +646,8 @@ static int64_t sensor_rays(const double *P) {
  * number of blended Gaussians. */
 int oracle_render(int64_t n, const double *means, const double *scales, const double *quats, const double *opac,
                   const double *vel, const double *feat, int C, const double *P, const double *elev,
-                  const double *rays, double guard, int64_t n_sel, const int64_t *sel, double *outF, double *outT,
+                  const double *rays, int64_t nfree, double guard, int64_t n_sel, const int64_t *sel, double *outF,
+                  double *outT,
                   double *outDexp, double *outDmed, uint8_t *outMarg, int32_t *outCount, const double *los_range,
                   double los_eps, double *outLos) {
     double *rec = (double *)malloc(sizeof(double) * REC * (size_t)(n > 0 ? n : 1));
@@ -627,7 +657,7 @@ int oracle_render(int64_t n, const double *means, const double *scales, const do
     uint8_t *vis = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
     uint8_t *marg = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
     project_all(n, means, scales, quats, opac, vel, P, elev, guard, rec, rect, orect, irect, vis, marg);
-    int64_t nr = sel ? n_sel : sensor_rays(P);
+    int64_t nr = sel ? n_sel : (nfree > 0 ? nfree : sensor_rays(P));
 #pragma omp parallel
     {
         cand_t *cands = (cand_t *)malloc(sizeof(cand_t) * (size_t)(n > 0 ? n : 1));
@@ -637,7 +667,7 @@ int oracle_render(int64_t n, const double *means, const double *scales, const do
             double T, de, dm;
             int mg;
             double lsum = 0;
-            int cnt = render_ray(P, elev, rays, n, rec, rect, orect, irect, vis, marg, feat, C, k, cands,
+            int cnt = render_ray(P, elev, rays, nfree, n, rec, rect, orect, irect, vis, marg, feat, C, k, cands,
                                  outF + (int64_t)C * j, &T, &de, &dm, &mg, NULL, 0, los_range ? los_range[j] : 0,
                                  los_eps, los_range ? &lsum : NULL);
             if (outLos) outLos[j] = lsum;
@@ -905,7 +935,7 @@ static void projection_backward(const double *P, const double *elev, int64_t i, 
  * parameter gradients. */
 int oracle_render_backward(int64_t n, const double *means, const double *scales, const double *quats,
                            const double *opac, const double *vel, const double *feat, int C, const double *P,
-                           const double *elev, const double *rays, int64_t n_sel, const int64_t *sel,
+                           const double *elev, const double *rays, int64_t nfree, int64_t n_sel, const int64_t *sel,
                            const double *gF, const double *gT, const double *gD, const double *gA, double *d2,
                            double *dfeat, double *dmean, double *dscale, double *dquat, double *dopac, double *dvel,
                            const double *los_range, double los_eps, const double *gL, double *dsensor) {
@@ -917,7 +947,7 @@ int oracle_render_backward(int64_t n, const double *means, const double *scales,
     uint8_t *vis = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
     uint8_t *marg = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
     project_all(n, means, scales, quats, opac, vel, P, elev, 0.0, rec, rect, orect, irect, vis, marg);
-    int64_t nr = sel ? n_sel : sensor_rays(P);
+    int64_t nr = sel ? n_sel : (nfree > 0 ? nfree : sensor_rays(P));
     double *loc2 = (double *)calloc((size_t)(n > 0 ? n : 1) * 10, sizeof(double));
 #pragma omp parallel
     {
@@ -928,7 +958,8 @@ int oracle_render_backward(int64_t n, const double *means, const double *scales,
         for (int64_t j = 0; j < nr; j++) {
             const int64_t k = sel ? sel[j] : j;   /* ray index; upstream gradients are indexed by j */
             double T, de, dm;
-            int nb = render_ray(P, elev, rays, n, rec, rect, orect, irect, vis, NULL, feat, C, k, cands, F, &T, &de, &dm,
+            int nb = render_ray(P, elev, rays, nfree, n, rec, rect, orect, irect, vis, NULL, feat, C, k, cands, F, &T, &de,
+                                &dm,
                                 NULL, cb, (int)(n > 0 ? n : 1), 0, 0, NULL);
             double gt = gT ? gT[j] : 0;
             if (gA) gt -= gA[j]; /* alpha_acc = 1 - T */

@@ -625,3 +625,86 @@ def test_ray_stops_before_transmittance_drops_below_1e4():
     assert 1 < n < 8 and out["count"][k] == n and a[-1] < 0.1
     assert out["T"][k] == pytest.approx(T, rel=1e-12) and out["T"][k] >= 1e-4
     assert out["F"][k, 0] == pytest.approx(F, rel=1e-12)
+
+
+# ----------------------------------------------------------------------------------
+# App. A.2: lidar points -> rays (ego-motion removal, spherical coordinates, tiles)
+# ----------------------------------------------------------------------------------
+
+def test_points_to_rays_static_sensor_spherical_coordinates():
+    lid = small_lidar()
+    pts = np.array([[10.0, 0.0, 0.0], [0.0, 5.0, 0.0], [1.0, 1.0, math.sqrt(2.0)], [-3.0, -4.0, 0.0]])
+    rays, r, _ = oracle.points_to_rays(pts, np.zeros(4), lid)
+    np.testing.assert_allclose(r, [10.0, 5.0, 2.0, 5.0], rtol=1e-7)
+    np.testing.assert_allclose(rays[:, 0], [0.0, math.pi / 2, math.pi / 4, math.pi + math.atan2(4.0, 3.0)],
+                               atol=1e-7)
+    np.testing.assert_allclose(rays[:, 1], [0.0, 0.0, math.pi / 4, 0.0], atol=1e-7)
+
+
+def test_points_to_rays_undoes_ego_motion_to_first_order():
+    """A static world point X of an ego-motion-compensated sweep sits, at its capture time
+    t, at exp(-t [omega]x) (X - v t) in the moving sensor's frame (exact kinematics for
+    constant sensor-frame velocities, translation taken first).  The removal must agree
+    with it to second order in t."""
+    v, w = np.array([15.0, 0.4, 0.0]), np.array([0.0, 0.02, 0.3])
+    lid = small_lidar(lin_vel=v, ang_vel=w)
+    rng = np.random.default_rng(3)
+    X = rng.uniform(-20, 20, size=(200, 3))
+    X[:, 2] = rng.uniform(-2, 2, size=200)
+    errs = []
+    for t in (0.004, 0.002, 0.001):
+        rays, r, _ = oracle.points_to_rays(X, np.full(200, t), lid)
+        q = (rodrigues(-t * w) @ (X - t * v).T).T
+        want = np.stack([np.mod(np.arctan2(q[:, 1], q[:, 0]), 2 * math.pi),
+                         np.arcsin(q[:, 2] / np.linalg.norm(q, axis=1))], 1)
+        d = np.abs(rays[:, :2] - want)
+        d[:, 0] = np.minimum(d[:, 0], 2 * math.pi - d[:, 0])
+        first = t * np.linalg.norm(v + np.cross(w, X), axis=1) / np.linalg.norm(X, axis=1)
+        errs.append(d.max())
+        assert d.max() < 0.02 * first.min()                  # far below the first-order shift
+        np.testing.assert_allclose(rays[:, 2], t)
+    assert errs[0] / errs[2] > 10                              # shrinks like t^2 (x16 for t / 4)
+
+
+def test_points_to_rays_tiles_match_brute_force():
+    lid = small_lidar(n_beams=16, n_az=1000)
+    rng = np.random.default_rng(4)
+    d = rng.normal(size=(4000, 3))
+    d[:, 2] *= 0.25
+    rays, _, tile = oracle.points_to_rays(d * 20.0, np.zeros(4000), lid)
+    el = np.asarray(lid.beam_elev, np.float32).astype(np.float64)
+    bnd = np.concatenate([[el[0] - 0.5 * (el[1] - el[0])], 0.5 * (el[7:-1:8] + el[8::8]),
+                          [el[-1] + 0.5 * (el[-1] - el[-2])]])
+    wphi = 32 * float(np.float32(lid.az_res))
+    mphi = (1000 + 31) // 32
+    hits = 0
+    for k in range(4000):
+        phi, om = rays[k, 0], rays[k, 1]
+        want = -1
+        for ty in range(len(bnd) - 1):
+            for tx in range(mphi):
+                if tx * wphi <= phi < (tx + 1) * wphi and bnd[ty] <= om < bnd[ty + 1]:
+                    want = ty * mphi + tx
+        assert tile[k] == want, (k, phi, om, tile[k], want)
+        hits += want >= 0
+    assert 1000 < hits < 4000
+
+
+def test_free_rays_at_grid_positions_render_like_the_grid():
+    """Rays given as a free list (App. A.2) at exactly the grid's (phi, omega, t) fall in
+    the grid cells' tiles and must render identically."""
+    lid = small_lidar(n_az=256, lin_vel=np.array([8.0, 0.0, 0.0]), sweep_time=0.1)
+    g = random_small_scene(5, 60, (-12.0, -12.0, -2.0), (12.0, 12.0, 2.0), channels=2, log_scale=(-1.0, 0.4))
+    grid = oracle.render(g, lid)
+    el = np.asarray(lid.beam_elev, np.float32).astype(np.float64)
+    res = float(np.float32(lid.az_res))
+    a = np.arange(256)
+    phi = np.tile((a + 0.5) * res, len(el))
+    om = np.repeat(el, 256)
+    t = np.tile(((a + 0.5) / 256 - 0.5) * float(np.float32(lid.sweep_time)), len(el))
+    free = oracle.render(g, lid, free_rays=np.stack([phi, om, t], 1))
+    assert grid["count"].sum() > 500
+    np.testing.assert_array_equal(free["count"], grid["count"])
+    # free rays reach the renderer as FP32 (phi within 2.4e-7 of the grid's FP64 value)
+    np.testing.assert_allclose(free["F"], grid["F"], atol=1e-5)
+    np.testing.assert_allclose(free["range_exp"], grid["range_exp"], atol=1e-4)
