@@ -354,7 +354,7 @@ def run_ours(args):
     visible = int((fr.n_tiles > 0).sum().item())
     parts = {}
 
-    def timed(name, fn, reps=5):
+    def timed(name, fn, reps=5, into=parts):
         ts = []
         for _ in range(reps):
             flush.fill_(1.0)
@@ -364,7 +364,7 @@ def run_ours(args):
             b.record(stream)
             torch.cuda.synchronize()
             ts.append(a.elapsed_time(b))
-        parts[name] = statistics.mean(ts)
+        into[name] = statistics.mean(ts)
 
     from paper_2411_16816_gb300 import _lib as L
     from paper_2411_16816_gb300.render import _stream, _vp
@@ -393,6 +393,8 @@ def run_ours(args):
                                           _vp(fr.grad_proj), _vp(pgrads["means"]), _vp(pgrads["scales"]),
                                           _vp(pgrads["quats"]), _vp(pgrads["opacities"]),
                                           _vp(pgrads["velocities"]), None, st))
+
+    point_cloud = point_cloud_bench(fr, cg, gd, out, timed) if fr.lid_idx else None
 
     peaks = measured_peaks()
     clocks = clk.summary()
@@ -433,7 +435,7 @@ def run_ours(args):
             "e2e": e2e, "gpu_launches": launches_per_step(fr, len(l1_terms)) * args.steps,
             "roofline": roofline, "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
-            "wall_s": wall, "overflow": overflow}
+            "wall_s": wall, "overflow": overflow, "point_cloud": point_cloud}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, sensors)
     if rank == 0 and world == 1:
@@ -448,6 +450,53 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def point_cloud_bench(fr, cg, gd, out, timed):
+    """The lidar's sweep as a point cloud (App. A.2): one return per grid cell that the
+    frame's render hits (alpha > 0.5), jittered by up to half a cell in azimuth and
+    elevation, at the rendered range; points -> rays, binning, free-ray forward and
+    backward, beside the grid-ray lidar kernels of the same frame."""
+    import torch
+    from paper_2411_16816_gb300.render import _stream
+    k = fr.lid_idx[0]
+    s = fr.sensors[k]
+    dev = fr.device
+    rng = np.random.default_rng(7)
+    lid_off = sum(fr.rays[j] for j in fr.lid_idx if j < k)
+    nr = fr.rays[k]
+    alpha = out["lid_alpha"][lid_off:lid_off + nr].cpu().numpy().astype(np.float64)
+    rexp = out["lid_range_exp"][lid_off:lid_off + nr].cpu().numpy().astype(np.float64)
+    hit = np.nonzero(alpha > 0.5)[0]
+    b, a = np.divmod(hit, s.n_az)
+    elev = np.asarray(s.beam_elev, np.float64)
+    de = np.gradient(elev)
+    phi = (a + 0.5 + rng.uniform(-0.5, 0.5, size=len(hit))) * s.az_res
+    om = elev[b] + rng.uniform(-0.45, 0.45, size=len(hit)) * de[b]
+    r = rexp[hit] / alpha[hit]
+    t = ((a + 0.5) / s.n_az - 0.5) * s.sweep_time
+    pts = np.stack([r * np.cos(om) * np.cos(phi), r * np.cos(om) * np.sin(phi), r * np.sin(om)], 1)
+    P = torch.as_tensor(pts.astype(np.float32), device=dev)
+    T = torch.as_tensor(t.astype(np.float32), device=dev)
+    ms = {}
+    pr = fr.lidar_points_to_rays(k, P, T)
+    bins = fr.bin_rays(k, pr["rays"])
+    o = fr.render_rays(cg, k, pr["rays"], bins)
+    n = len(hit)
+    C = fr.channels
+    grads = {"feat": torch.randn((n, C), device=dev), "range_exp": torch.randn(n, device=dev) * 0.05}
+    pgr = {key: torch.zeros_like(v) for key, v in gd.items() if v is not None}
+    timed("points_to_rays", lambda: fr.lidar_points_to_rays(k, P, T), into=ms)
+    timed("bin_rays", lambda: fr.bin_rays(k, pr["rays"]), into=ms)
+    timed("raster_rays_fwd", lambda: fr.render_rays(cg, k, pr["rays"], bins), into=ms)
+    timed("rays_bwd_with_projection_bwd", lambda: fr.backward_rays(gd, k, pr["rays"], bins, o, grads,
+                                                                    param_grads=pgr), into=ms)
+    torch.cuda.synchronize()
+    chunks = int(bins["chunk_base"][-1].item())
+    return {"points": n, "tiles": fr.tiles[k], "chunks": chunks,
+            "binned": int(bins["tile_ranges"][-1, 1].item()), "ms": ms,
+            "note": "ms include the output allocation of the Python wrapper; grid-ray lidar kernels under "
+                    "roofline.kernel_ms"}
 
 
 def serving_bench(args, dev):

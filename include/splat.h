@@ -279,6 +279,74 @@ splat_status splat_render_lidar_backward_los(const splat_gaussians *g, int32_t n
                                              const float *dL_dlos, float *grad_proj, float *dL_dfeatures,
                                              void *stream);
 
+/* ---- Lidar point clouds as rays (App. A.2) ------------------------------------------
+ * A lidar's measured points arrive ego-motion compensated: in its sensor frame at the
+ * sweep's reference time.  Rendering them needs the rays they were measured along:
+ * splat_lidar_points_to_rays undoes the compensation with the sensor's constant linear
+ * and angular velocity (lin_vel, ang_vel of splat_sensor, sensor frame), a static point
+ * p captured at time t appearing at q = p - t (lin_vel + ang_vel x p), and takes q's
+ * azimuth phi = atan2(q_y, q_x) in [0, 2 pi), elevation omega = asin(q_z / |q|) and t.
+ * Each ray belongs to the tile a zero-extent Gaussian at (phi, omega) would: column
+ * floor(phi / (tile_w az_res)) (the last column also takes the rest of the circle), the
+ * tile row whose elevation boundaries (those of the lidar tiling, App. A.1) hold omega;
+ * none (-1) outside the beam fan.  splat_lidar_bin_rays groups the rays by that tile
+ * and splat_render_lidar_rays renders them against the frame's projection and sorted
+ * lists, exactly as the grid rays of that tile are rendered (the rays' times should lie
+ * within the sweep, [-sweep_time/2, sweep_time/2], which the tiles' motion margins
+ * cover).  Rays outside every tile are not rendered and their outputs not written. */
+
+/* One lidar's free rays grouped by tile (device memory, caller-owned).
+ *   ray_ids[n_rays]       ray indices grouped by tile; the first tile_ranges[tiles-1][1]
+ *                         entries are used, the order inside a tile is unspecified
+ *   tile_ranges[tiles][2] (start, end) of each tile of the lidar in ray_ids
+ *   chunk_base[tiles + 1] first 256-ray work chunk of each tile; [tiles] = the number of
+ *                         chunks (sum over tiles of ceil(count / 256))
+ * tiles = ceil(n_az / tile_w) * (n_beams / tile_h) of that lidar. */
+typedef struct {
+    int32_t *ray_ids;
+    int32_t *tile_ranges;
+    int32_t *chunk_base;
+} splat_ray_bins;
+
+/* points[n_points][3] (float, sensor frame at the reference time), times[n_points]
+ * (seconds relative to it) -> rays[n_points][3] (phi, omega, t), ranges[n_points] (|q|,
+ * the measured range along the ray) and, if tiles is not NULL, tiles[n_points] (the
+ * lidar's local tile of each ray, -1 outside the fan).  `lidar` indexes a lidar sensor
+ * of the table.  FP32; n_points < 2^31. */
+splat_status splat_lidar_points_to_rays(int32_t n_sensors, const splat_sensor *sensors, int32_t lidar,
+                                        const float *points, const float *times, int64_t n_points, float *rays,
+                                        float *ranges, int32_t *tiles, void *stream);
+
+/* Counting sort of rays[n_rays][3] (phi, omega, t; e.g. from splat_lidar_points_to_rays)
+ * by their tile of lidar `lidar` into bins (written; see splat_ray_bins). */
+splat_status splat_lidar_bin_rays(int32_t n_sensors, const splat_sensor *sensors, int32_t lidar, const float *rays,
+                                  int64_t n_rays, splat_ray_bins bins, void *stream);
+
+/* Renders the binned rays of lidar `lidar` (sensor table as for the frame's projection
+ * and bins).  Outputs are indexed by ray: out_feat[n_rays][channels], out_range_exp,
+ * out_range_med, out_alpha, out_T, out_last [n_rays] with the meaning of
+ * splat_render_lidar (out_range_med, out_T, out_last may be NULL).  los may be NULL;
+ * otherwise its target_range is indexed by ray (e.g. the ranges of
+ * splat_lidar_points_to_rays) and out_los[n_rays] receives the line-of-sight term. */
+splat_status splat_render_lidar_rays(const splat_gaussians *g, int32_t n_sensors, const splat_sensor *sensors,
+                                     int32_t lidar, splat_projected proj, splat_bins bins, const float *rays,
+                                     int64_t n_rays, splat_ray_bins ray_bins, float *out_feat,
+                                     float *out_range_exp, float *out_range_med, float *out_alpha, float *out_T,
+                                     int32_t *out_last, const splat_los *los, float *out_los, void *stream);
+
+/* Backward of splat_render_lidar_rays: upstream gradients indexed by ray as its outputs
+ * (dL_drange_exp, dL_dalpha may be NULL; dL_dlos only with los, else NULL), out_T and
+ * out_last of the forward or both NULL (recomputed).  Accumulates into grad_proj and
+ * dL_dfeatures like splat_render_lidar_backward.  The rays are data: no gradient flows
+ * into the points or the sensor through them. */
+splat_status splat_render_lidar_rays_backward(const splat_gaussians *g, int32_t n_sensors,
+                                              const splat_sensor *sensors, int32_t lidar, splat_projected proj,
+                                              splat_bins bins, const float *rays, int64_t n_rays,
+                                              splat_ray_bins ray_bins, const float *out_T, const int32_t *out_last,
+                                              const float *dL_dfeat, const float *dL_drange_exp,
+                                              const float *dL_dalpha, const splat_los *los, const float *dL_dlos,
+                                              float *grad_proj, float *dL_dfeatures, void *stream);
+
 /* Chain rule from grad_proj to the Gaussian parameters, summed over sensors (one thread
  * per Gaussian, no atomics).  Accumulates into dL_dmeans[n][3], dL_dscales[n][3],
  * dL_dquats[n][4], dL_dopacities[n], dL_dvelocities[n][3] (may be NULL).  Gradients

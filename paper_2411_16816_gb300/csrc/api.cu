@@ -2,6 +2,7 @@
 // argument checks on the host, the per-frame sensor table, and kernel launches.
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -404,6 +405,134 @@ splat_status splat_render_lidar_backward_los(const splat_gaussians* g, int32_t n
     return render_lidar_backward_impl(g, n_sensors, sensors, proj, bins, out_T, out_last, dL_dfeat, dL_drange_exp,
                                       dL_dalpha, &los, dL_dlos, grad_proj, dL_dfeatures, stream,
                                       "splat_render_lidar_backward_los");
+}
+
+// ---- free lidar rays (App. A.2) ------------------------------------------------------
+
+static splat_status lidar_of(int32_t n_sensors, const splat_sensor* sensors, int32_t lidar, Frame& fr,
+                             const char* name) {
+    splat_status st = build_frame(n_sensors, sensors, fr, nullptr);
+    if (st != SPLAT_OK) return st;
+    if (lidar < 0 || lidar >= n_sensors || fr.s[lidar].kind != SPLAT_SENSOR_LIDAR)
+        return fail(SPLAT_ERR_INVALID_ARG, "%s: sensor %d is not a lidar of the table", name, lidar);
+    return SPLAT_OK;
+}
+
+static splat_status check_ray_bins(const splat_ray_bins& b, int64_t n_rays, const char* name) {
+    if (n_rays < 0 || n_rays > INT32_MAX) return fail(SPLAT_ERR_INVALID_ARG, "%s: n_rays out of range", name);
+    if ((n_rays > 0 && !b.ray_ids) || !b.tile_ranges || !b.chunk_base)
+        return fail(SPLAT_ERR_INVALID_ARG, "%s: ray bins pointer is NULL", name);
+    if (((uintptr_t)b.tile_ranges & 7u) != 0)
+        return fail(SPLAT_ERR_INVALID_ARG, "%s: tile_ranges must be 8-byte aligned", name);
+    return SPLAT_OK;
+}
+
+splat_status splat_lidar_points_to_rays(int32_t n_sensors, const splat_sensor* sensors, int32_t lidar,
+                                        const float* points, const float* times, int64_t n_points, float* rays,
+                                        float* ranges, int32_t* tiles, void* stream) {
+    Frame fr;
+    splat_status st = lidar_of(n_sensors, sensors, lidar, fr, "splat_lidar_points_to_rays");
+    if (st != SPLAT_OK) return st;
+    if (n_points < 0 || n_points > INT32_MAX) return fail(SPLAT_ERR_INVALID_ARG, "n_points out of range");
+    if (n_points == 0) return SPLAT_OK;
+    if (!points || !times || !rays || !ranges)
+        return fail(SPLAT_ERR_INVALID_ARG, "splat_lidar_points_to_rays: points, times, rays and ranges are required");
+    launch_points_to_rays(fr.s[lidar], points, times, n_points, rays, ranges, tiles, (cudaStream_t)stream);
+    return check_launch("splat_lidar_points_to_rays");
+}
+
+splat_status splat_lidar_bin_rays(int32_t n_sensors, const splat_sensor* sensors, int32_t lidar, const float* rays,
+                                  int64_t n_rays, splat_ray_bins bins, void* stream) {
+    Frame fr;
+    splat_status st = lidar_of(n_sensors, sensors, lidar, fr, "splat_lidar_bin_rays");
+    if (st != SPLAT_OK) return st;
+    if ((st = check_ray_bins(bins, n_rays, "splat_lidar_bin_rays")) != SPLAT_OK) return st;
+    if (n_rays > 0 && !rays) return fail(SPLAT_ERR_INVALID_ARG, "splat_lidar_bin_rays: rays is NULL");
+    launch_bin_rays(fr.s[lidar], rays, n_rays, bins.ray_ids, (int2*)bins.tile_ranges, bins.chunk_base,
+                    (cudaStream_t)stream);
+    return check_launch("splat_lidar_bin_rays");
+}
+
+// Free-ray raster input: the frame's lists plus the lidar's binned rays; the grid bounds
+// the number of 256-ray chunks (sum of ceil(count / 256) <= n_rays / 256 + tiles).
+static splat_status list_input(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
+                               int32_t lidar, splat_projected proj, splat_bins bins, const float* rays,
+                               int64_t n_rays, const splat_ray_bins& rb, Frame& fr, RasterIn& in, int& blocks,
+                               const char* name) {
+    int tw, th;
+    splat_status st = render_common(g, n_sensors, sensors, proj, bins, fr, true, tw, th);
+    if (st != SPLAT_OK) return st;
+    if (lidar < 0 || lidar >= n_sensors || fr.s[lidar].kind != SPLAT_SENSOR_LIDAR)
+        return fail(SPLAT_ERR_INVALID_ARG, "%s: sensor %d is not a lidar of the table", name, lidar);
+    if ((st = check_ray_bins(rb, n_rays, name)) != SPLAT_OK) return st;
+    if (n_rays > 0 && !rays) return fail(SPLAT_ERR_INVALID_ARG, "%s: rays is NULL", name);
+    const SensorDev& S = fr.s[lidar];
+    const int tiles = S.tiles_x * S.tiles_y;
+    const int64_t b = (n_rays + kListChunk - 1) / kListChunk + tiles;
+    if (b > INT32_MAX) return fail(SPLAT_ERR_INVALID_ARG, "%s: too many rays", name);
+    blocks = n_rays > 0 ? (int)b : 0;
+    in = RasterIn{(const float4*)proj.rec, bins.isect_ids, (const int2*)bins.tile_ranges, g->features, g->n,
+                  g->channels};
+    in.list = RayList{rays, rb.ray_ids, (const int2*)rb.tile_ranges, rb.chunk_base, tiles, lidar};
+    return SPLAT_OK;
+}
+
+splat_status splat_render_lidar_rays(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
+                                     int32_t lidar, splat_projected proj, splat_bins bins, const float* rays,
+                                     int64_t n_rays, splat_ray_bins ray_bins, float* out_feat,
+                                     float* out_range_exp, float* out_range_med, float* out_alpha, float* out_T,
+                                     int32_t* out_last, const splat_los* los, float* out_los, void* stream) {
+    const char* name = "splat_render_lidar_rays";
+    Frame fr;
+    RasterIn in;
+    int blocks = 0;
+    splat_status st = list_input(g, n_sensors, sensors, lidar, proj, bins, rays, n_rays, ray_bins, fr, in, blocks,
+                                 name);
+    if (st != SPLAT_OK) return st;
+    if (n_rays == 0) return SPLAT_OK;
+    if (!out_feat || !out_range_exp || !out_alpha)
+        return fail(SPLAT_ERR_INVALID_ARG, "%s: out_feat, out_range_exp and out_alpha are required", name);
+    if ((g->channels & 3) == 0 && !aligned16(out_feat)) return fail(SPLAT_ERR_INVALID_ARG, "out_feat misaligned");
+    if (los && (!los->target_range || !out_los || !(los->eps >= 0.f)))
+        return fail(SPLAT_ERR_INVALID_ARG, "%s: los.target_range and out_los are required, los.eps >= 0", name);
+    in.los_range = los ? los->target_range : nullptr;
+    in.los_eps = los ? los->eps : 0.f;
+    RasterOut out{out_feat, out_T, out_last, out_range_exp, out_range_med, out_alpha, nullptr};
+    out.los = los ? out_los : nullptr;
+    if (!launch_raster_list_fwd(g->channels, fr, blocks, in, out, (cudaStream_t)stream))
+        return fail(SPLAT_ERR_INVALID_ARG, "%s: unsupported configuration", name);
+    return check_launch(name);
+}
+
+splat_status splat_render_lidar_rays_backward(const splat_gaussians* g, int32_t n_sensors,
+                                              const splat_sensor* sensors, int32_t lidar, splat_projected proj,
+                                              splat_bins bins, const float* rays, int64_t n_rays,
+                                              splat_ray_bins ray_bins, const float* out_T, const int32_t* out_last,
+                                              const float* dL_dfeat, const float* dL_drange_exp,
+                                              const float* dL_dalpha, const splat_los* los, const float* dL_dlos,
+                                              float* grad_proj, float* dL_dfeatures, void* stream) {
+    const char* name = "splat_render_lidar_rays_backward";
+    Frame fr;
+    RasterIn in;
+    int blocks = 0;
+    splat_status st = list_input(g, n_sensors, sensors, lidar, proj, bins, rays, n_rays, ray_bins, fr, in, blocks,
+                                 name);
+    if (st != SPLAT_OK) return st;
+    if (n_rays == 0) return SPLAT_OK;
+    if (!dL_dfeat || !grad_proj || !dL_dfeatures) return fail(SPLAT_ERR_INVALID_ARG, "gradient pointer is NULL");
+    if ((out_T == nullptr) != (out_last == nullptr))
+        return fail(SPLAT_ERR_INVALID_ARG, "out_T and out_last must both be given or both be NULL");
+    if (!aligned16(grad_proj) || ((g->channels & 3) == 0 && !aligned16(dL_dfeatures)))
+        return fail(SPLAT_ERR_INVALID_ARG, "gradient buffers misaligned");
+    if ((los != nullptr) != (dL_dlos != nullptr) || (los && (!los->target_range || !(los->eps >= 0.f))))
+        return fail(SPLAT_ERR_INVALID_ARG, "%s: los and dL_dlos go together, los.eps >= 0", name);
+    in.los_range = los ? los->target_range : nullptr;
+    in.los_eps = los ? los->eps : 0.f;
+    RasterGrad gr{out_T, out_last, dL_dfeat, nullptr, dL_drange_exp, dL_dalpha, (float4*)grad_proj, dL_dfeatures,
+                  dL_dlos};
+    if (!launch_raster_list_bwd(g->channels, fr, blocks, in, gr, out_T == nullptr, (cudaStream_t)stream))
+        return fail(SPLAT_ERR_INVALID_ARG, "%s: unsupported configuration", name);
+    return check_launch(name);
 }
 
 splat_status splat_project_backward(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,

@@ -108,6 +108,17 @@ __device__ __forceinline__ float wrap_pi(float d) {
     return d - kTwoPi * floorf(d * (1.0f / kTwoPi) + 0.5f);
 }
 
+// Elevation boundary k of the lidar's tile rows (App. A.1): below the first beam by half
+// its spacing, midway between the last beam of a row and the first of the next, above
+// the last beam by half its spacing.
+__device__ __forceinline__ float elev_bound(const SensorDev& S, int k) {
+    const int Mw = S.nb / S.tile_h;
+    const float* e = S.elev;
+    if (k == 0) return e[0] - 0.5f * (e[1] - e[0]);
+    if (k >= Mw) return e[S.nb - 1] + 0.5f * (e[S.nb - 1] - e[S.nb - 2]);
+    return 0.5f * (e[k * S.tile_h - 1] + e[k * S.tile_h]);
+}
+
 __device__ __forceinline__ int sensor_of_block(const Frame& fr, int block, bool lidar) {
     const int n = lidar ? fr.n_lids : fr.n_cams;
     const int* list = lidar ? fr.lid_sensors : fr.cam_sensors;

@@ -142,14 +142,6 @@ __device__ __forceinline__ void lidar_jacobian(float3 m, LidJ& lj) {
     lj.J[8] = m.z / lj.r;
 }
 
-__device__ __forceinline__ float elev_bound(const SensorDev& S, int k) {
-    const int Mw = S.nb / S.tile_h;
-    const float* e = S.elev;
-    if (k == 0) return e[0] - 0.5f * (e[1] - e[0]);
-    if (k >= Mw) return e[S.nb - 1] + 0.5f * (e[S.nb - 1] - e[S.nb - 2]);
-    return 0.5f * (e[k * S.tile_h - 1] + e[k * S.tile_h]);
-}
-
 __device__ bool project_camera(const SensorDev& S, const GaussLocal& G, float4& r0, float4& r1, float4& r2,
                                short4& rect, int& nt) {
     const float3 m = xform(S.R, S.t, G.mean);

@@ -99,6 +99,64 @@ __device__ __forceinline__ RayCtx ray_setup(const Frame& fr, const TileCtx& tc, 
     return ray_setup_rt<LIDAR>(fr.s[tc.s], tc.tx, tc.ty, p, TW, TH);
 }
 
+// Block -> (tile, chunk) of a free-ray list: the tile is the last one whose first chunk is
+// at or before this block's (tiles without rays own no chunk), the chunk's rays are
+// [first, min(first + kListChunk, end)) of ids.  False for the blocks past the last chunk
+// (the grid is sized by an upper bound); the whole block returns together.
+__device__ __forceinline__ bool list_setup(const Frame& fr, const RayList& L, TileCtx& tc, int& first, int& end) {
+    const int chunk = blockIdx.x;
+    if (chunk >= L.chunk_base[L.tiles]) return false;
+    int lo = 0, hi = L.tiles - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (L.chunk_base[mid] <= chunk) lo = mid;
+        else hi = mid - 1;
+    }
+    const SensorDev& S = fr.s[L.sensor];
+    tc.s = L.sensor;
+    tc.gtile = S.tile_base + lo;
+    tc.tx = lo % S.tiles_x;
+    tc.ty = lo / S.tiles_x;
+    const int2 rr = L.ranges[lo];
+    first = rr.x + (chunk - L.chunk_base[lo]) * kListChunk;
+    end = rr.y;
+    return true;
+}
+
+// Slot j of the list: its ray (phi, omega, t) and output index (the ray's own index).
+__device__ __forceinline__ RayCtx list_ray(const RayList& L, int j, int end) {
+    RayCtx r;
+    r.inside = j < end;
+    r.o = 0;
+    r.pa = r.pb = r.t = 0.f;
+    if (r.inside) {
+        r.o = L.ids[j];
+        const float* p = L.rays + 3 * r.o;
+        r.pa = p[0];
+        r.pb = p[1];
+        r.t = p[2];
+    }
+    return r;
+}
+
+// The block's tile and this thread's rays: the sensor's ray grid, or a chunk of a free-ray
+// list (LIST).  False: a list block without a chunk.
+template <int TW, int TH, bool LIDAR, bool LIST, int PX, int NT>
+__device__ __forceinline__ bool block_setup(const Frame& fr, const RasterIn& in, TileCtx& tc, RayCtx (&r)[PX]) {
+    if constexpr (LIST) {
+        static_assert(LIDAR && TW * TH == kListChunk, "list kernels take one chunk of lidar rays per block");
+        int first, end;
+        if (!list_setup(fr, in.list, tc, first, end)) return false;
+#pragma unroll
+        for (int q = 0; q < PX; q++) r[q] = list_ray(in.list, first + (int)threadIdx.x + q * NT, end);
+    } else {
+        tc = tile_setup<LIDAR>(fr);
+#pragma unroll
+        for (int q = 0; q < PX; q++) r[q] = ray_setup<TW, TH, LIDAR>(fr, tc, threadIdx.x + q * NT);
+    }
+    return true;
+}
+
 template <int CM, int B, bool LIDAR>
 struct Stage {
     float4 g0[B];
@@ -289,17 +347,16 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
     return evals;
 }
 
-template <int CM, int TW, int TH, bool LIDAR, bool COUNT>
+template <int CM, int TW, int TH, bool LIDAR, bool COUNT, bool LIST = false>
 __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, false, LIDAR, TW * TH>::value)
     k_raster_fwd(const __grid_constant__ Frame fr, RasterIn in, RasterOut out) {
     constexpr int PX = RaysPerThread<CM, false, LIDAR, TW * TH>::value;
     constexpr int NT = TW * TH / PX;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Stage<CM, NT, LIDAR>& sm = *reinterpret_cast<Stage<CM, NT, LIDAR>*>(smem_raw);
-    const TileCtx tc = tile_setup<LIDAR>(fr);
+    TileCtx tc;
     RayCtx r[PX];
-#pragma unroll
-    for (int q = 0; q < PX; q++) r[q] = ray_setup<TW, TH, LIDAR>(fr, tc, threadIdx.x + q * NT);
+    if (!block_setup<TW, TH, LIDAR, LIST, PX, NT>(fr, in, tc, r)) return;
     const int2 range = in.ranges[tc.gtile];
     TileBox box{};
     if (!LIDAR) box = camera_tile_box(fr.s[tc.s], tc.tx, tc.ty, TW, TH);
@@ -470,7 +527,7 @@ struct BwdLayout {
     __host__ __device__ static constexpr int slices(int warps) { return warps <= 2 ? warps : 1; }
 };
 
-template <int CM, int TW, int TH, bool LIDAR, bool RECOMPUTE>
+template <int CM, int TW, int TH, bool LIDAR, bool RECOMPUTE, bool LIST = false>
 __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * TH>::value)
     k_raster_bwd(const __grid_constant__ Frame fr, RasterIn in, RasterGrad gr) {
     constexpr int PX = RaysPerThread<CM, true, LIDAR, TW * TH>::value;
@@ -485,10 +542,9 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
     __shared__ int s_max_last[NT / 32 > 0 ? NT / 32 : 1];
     const int Crt = in.C;
     const int V = OFF + Crt;
-    const TileCtx tc = tile_setup<LIDAR>(fr);
+    TileCtx tc;
     RayCtx r[PX];
-#pragma unroll
-    for (int q = 0; q < PX; q++) r[q] = ray_setup<TW, TH, LIDAR>(fr, tc, threadIdx.x + q * NT);
+    if (!block_setup<TW, TH, LIDAR, LIST, PX, NT>(fr, in, tc, r)) return;
     const int2 range = in.ranges[tc.gtile];
     const int len = range.y - range.x;
     TileBox box{};
@@ -739,6 +795,28 @@ static void launch_bwd_t(const Frame& fr, int blocks, const RasterIn& in, const 
     }
 }
 
+// Free-ray lists (App. A.2): one block per chunk of 256 rays whatever the lidar's tile
+// shape (the tile only selects the Gaussian list); `blocks` bounds the number of chunks.
+template <int CM>
+bool dispatch_list(const Frame& fr, int blocks, const RasterIn& in, const RasterOut* out, const RasterGrad* g,
+                   bool recompute, cudaStream_t st) {
+    if (out) {
+        constexpr int NT = 256 / RaysPerThread<CM, false, true, 256>::value;
+        const size_t sm = sizeof(Stage<CM, NT, true>);
+        auto k = k_raster_fwd<CM, 32, 8, true, false, true>;
+        set_smem(k, sm);
+        k<<<blocks, NT, sm, st>>>(fr, in, *out);
+        return true;
+    }
+    constexpr int NT = 256 / RaysPerThread<CM, true, true, 256>::value;
+    using LY = BwdLayout<CM, true>;
+    const size_t sm = sizeof(Stage<CM, NT, true>) + sizeof(float) * LY::slices(NT / 32) * NT * LY::kRow;
+    auto k = recompute ? k_raster_bwd<CM, 32, 8, true, true, true> : k_raster_bwd<CM, 32, 8, true, false, true>;
+    set_smem(k, sm);
+    k<<<blocks, NT, sm, st>>>(fr, in, *g);
+    return true;
+}
+
 template <int CM, bool LIDAR>
 bool dispatch_shape(int tw, int th, const Frame& fr, int blocks, const RasterIn& in, const RasterOut* out,
                     const RasterGrad* g, bool recompute, cudaStream_t st) {
@@ -767,6 +845,8 @@ bool dispatch_shape(int tw, int th, const Frame& fr, int blocks, const RasterIn&
     template bool dispatch_shape<CMV, false>(int, int, const Frame&, int, const RasterIn&, const RasterOut*,  \
                                              const RasterGrad*, bool, cudaStream_t);                         \
     template bool dispatch_shape<CMV, true>(int, int, const Frame&, int, const RasterIn&, const RasterOut*,   \
-                                            const RasterGrad*, bool, cudaStream_t);
+                                            const RasterGrad*, bool, cudaStream_t);                          \
+    template bool dispatch_list<CMV>(const Frame&, int, const RasterIn&, const RasterOut*, const RasterGrad*, \
+                                     bool, cudaStream_t);
 
 }  // namespace splat

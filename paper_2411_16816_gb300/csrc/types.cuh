@@ -29,6 +29,18 @@ struct GradOut {
     float* sensor;   // optional [sensors][16]: lin_vel, ang_vel, time_offset, -, t, rotation, -
 };
 
+// Free lidar rays grouped by tile (App. A.2): the list kernels render these instead of a
+// sensor's ray grid, one block per chunk of kListChunk rays of one tile.
+constexpr int kListChunk = 256;
+struct RayList {
+    const float* rays;          // [n_rays][3] phi, omega, t
+    const int32_t* ids;         // ray indices grouped by tile of the lidar
+    const int2* ranges;         // [tiles] (start, end) into ids
+    const int32_t* chunk_base;  // [tiles + 1] first chunk of each tile; [tiles] = number of chunks
+    int tiles;
+    int sensor;                 // index of the lidar in the frame
+};
+
 struct RasterIn {
     const float4* rec;      // [S][3][n]
     const uint32_t* ids;    // sorted Gaussian indices
@@ -38,6 +50,7 @@ struct RasterIn {
     int C;                  // channels (<= the kernel's compile-time maximum CM)
     const float* los_range; // lidar, optional: return range per ray for the line-of-sight term
     float los_eps;
+    RayList list;           // list kernels only
 };
 
 struct RasterOut {
@@ -93,6 +106,14 @@ bool launch_raster_fwd(bool lidar, int C, int tw, int th, const Frame& fr, int b
                        const RasterOut& out, cudaStream_t st);
 bool launch_raster_bwd(bool lidar, int C, int tw, int th, const Frame& fr, int blocks, const RasterIn& in,
                        const RasterGrad& g, bool recompute, cudaStream_t st);
+bool launch_raster_list_fwd(int C, const Frame& fr, int blocks, const RasterIn& in, const RasterOut& out,
+                            cudaStream_t st);
+bool launch_raster_list_bwd(int C, const Frame& fr, int blocks, const RasterIn& in, const RasterGrad& g,
+                            bool recompute, cudaStream_t st);
+void launch_points_to_rays(const SensorDev& S, const float* points, const float* times, int64_t n, float* rays,
+                           float* range, int32_t* tiles, cudaStream_t st);
+void launch_bin_rays(const SensorDev& S, const float* rays, int64_t n, int32_t* ids, int2* ranges,
+                     int32_t* chunk_base, cudaStream_t st);
 bool raster_shape_supported(bool lidar, int tw, int th);
 bool raster_channels_supported(int C);
 void launch_l1(const float* pred, const float* target, int64_t count, float scale, float* grad, float* loss,

@@ -215,16 +215,21 @@ class Frame:
     def _c_los(self):
         return L.splat_los(self.los[0].data_ptr(), self.los[1], 0)
 
-    def forward(self, g: dict, keep_state: bool = True, check: bool = True, out: dict | None = None,
-                stream=None, cam_l1=None) -> dict:
-        """Project, bin and rasterize every sensor.  With keep_state the per-ray final
-        transmittance and last index are kept for the backward pass; without it the
-        backward recomputes them per tile.  cam_l1 as for rasterize()."""
+    def prepare(self, g: dict, check: bool = True, stream=None):
+        """Project and bin (the per-frame lists every raster launch reads)."""
         cg = self.c_gaussians(g)
         self.project(cg, stream)
         self.bin_sort(stream)
         if check:
             self.ensure_capacity(stream)
+        return cg
+
+    def forward(self, g: dict, keep_state: bool = True, check: bool = True, out: dict | None = None,
+                stream=None, cam_l1=None) -> dict:
+        """Project, bin and rasterize every sensor.  With keep_state the per-ray final
+        transmittance and last index are kept for the backward pass; without it the
+        backward recomputes them per tile.  cam_l1 as for rasterize()."""
+        cg = self.prepare(g, check, stream)
         out = self.alloc_outputs(keep_state) if out is None else out
         self.rasterize(cg, out, stream, cam_l1=cam_l1)
         self.version += 1
@@ -296,6 +301,110 @@ class Frame:
                        _vp(out.get("lid_last") if keep else None), _vp(dF.contiguous()),
                        _vp(grads.get("lid_range_exp")), _vp(grads.get("lid_alpha")), _vp(self.grad_proj),
                        _vp(param_grads["features"]), st)
+        L.call("splat_project_backward", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
+               _vp(self.grad_proj), _vp(param_grads["means"]), _vp(param_grads["scales"]),
+               _vp(param_grads["quats"]), _vp(param_grads["opacities"]), _vp(param_grads.get("velocities")),
+               _vp(sensor_grads), st)
+        return param_grads
+
+    # -- lidar point clouds as rays (App. A.2) ------------------------------------------
+    def _check_lidar(self, lidar: int):
+        if not 0 <= lidar < len(self.sensors) or self.sensors[lidar].kind != "lidar":
+            raise ValueError(f"sensor {lidar} is not a lidar of the frame")
+
+    def lidar_points_to_rays(self, lidar: int, points: torch.Tensor, times: torch.Tensor, stream=None) -> dict:
+        """Points (n, 3; sensor frame at the sweep's reference time) and capture times (n,)
+        -> {"rays": (n, 3) phi, omega, t; "ranges": (n,); "tiles": (n,) int32, -1 outside
+        the beam fan}."""
+        self._check_lidar(lidar)
+        points = points.contiguous()
+        times = times.contiguous()
+        n = points.shape[0]
+        if points.shape != (n, 3) or times.shape != (n,):
+            raise ValueError("points must be (n, 3) and times (n,)")
+        dev = self.device
+        out = {"rays": torch.empty((n, 3), dtype=torch.float32, device=dev),
+               "ranges": torch.empty(n, dtype=torch.float32, device=dev),
+               "tiles": torch.empty(n, dtype=torch.int32, device=dev)}
+        L.call("splat_lidar_points_to_rays", len(self.sensors), self.c_sensors, lidar, _vp(points), _vp(times), n,
+               _vp(out["rays"]), _vp(out["ranges"]), _vp(out["tiles"]), _stream(stream))
+        return out
+
+    def bin_rays(self, lidar: int, rays: torch.Tensor, stream=None) -> dict:
+        """Group free rays (n, 3) of a lidar by tile: {"ray_ids", "tile_ranges", "chunk_base"}."""
+        self._check_lidar(lidar)
+        rays = rays.contiguous()
+        n, dev = rays.shape[0], self.device
+        tiles = self.tiles[lidar]
+        b = {"ray_ids": torch.empty(max(n, 1), dtype=torch.int32, device=dev),
+             "tile_ranges": torch.empty((tiles, 2), dtype=torch.int32, device=dev),
+             "chunk_base": torch.empty(tiles + 1, dtype=torch.int32, device=dev), "n": n}
+        L.call("splat_lidar_bin_rays", len(self.sensors), self.c_sensors, lidar, _vp(rays), n, self._c_ray_bins(b),
+               _stream(stream))
+        return b
+
+    @staticmethod
+    def _c_ray_bins(b: dict):
+        return L.splat_ray_bins(b["ray_ids"].data_ptr(), b["tile_ranges"].data_ptr(), b["chunk_base"].data_ptr())
+
+    def render_rays(self, cg, lidar: int, rays: torch.Tensor, ray_bins: dict, keep_state: bool = True,
+                    los: tuple | None = None, stream=None) -> dict:
+        """Render binned free rays of a lidar against this frame's lists (prepare() first).
+        Outputs are indexed by ray; rays outside the beam fan stay 0.  los = (target_range
+        per ray, eps) adds out["los"]."""
+        self._check_lidar(lidar)
+        rays = rays.contiguous()
+        n, dev, C = rays.shape[0], self.device, self.channels
+        out = {"feat": torch.zeros((n, C), dtype=torch.float32, device=dev),
+               "range_exp": torch.zeros(n, dtype=torch.float32, device=dev),
+               "range_med": torch.zeros(n, dtype=torch.float32, device=dev),
+               "alpha": torch.zeros(n, dtype=torch.float32, device=dev),
+               "T": torch.ones(n, dtype=torch.float32, device=dev) if keep_state else None,
+               "last": torch.zeros(n, dtype=torch.int32, device=dev) if keep_state else None}
+        c_los = None
+        if los is not None:
+            out["los"] = torch.zeros(n, dtype=torch.float32, device=dev)
+            c_los = ctypes.byref(L.splat_los(los[0].data_ptr(), float(los[1]), 0))
+        L.call("splat_render_lidar_rays", ctypes.byref(cg), len(self.sensors), self.c_sensors, lidar, self.c_proj(),
+               self.c_bins(), _vp(rays), n, self._c_ray_bins(ray_bins), _vp(out["feat"]),
+               _vp(out["range_exp"]), _vp(out["range_med"]), _vp(out["alpha"]), _vp(out["T"]), _vp(out["last"]),
+               c_los, _vp(out.get("los")), _stream(stream))
+        return out
+
+    def backward_rays(self, g: dict, lidar: int, rays: torch.Tensor, ray_bins: dict, out: dict, grads: dict,
+                      los: tuple | None = None, param_grads: dict | None = None, sensor_grads=None,
+                      stream=None) -> dict:
+        """Gradients of the free-ray render for grads = {feat, range_exp, alpha, los} (by
+        ray; any may be absent), through the projection to the Gaussian parameters."""
+        self._check_lidar(lidar)
+        cg = self.c_gaussians(g)
+        st = _stream(stream)
+        rays = rays.contiguous()
+        n = rays.shape[0]
+        dlos = grads.get("los")
+        dlos = dlos.contiguous() if dlos is not None else None
+        if self.grad_proj is None:
+            self.grad_proj = torch.zeros_like(self.rec)
+        else:
+            self.grad_proj.zero_()
+        if param_grads is None:
+            param_grads = {k: torch.zeros_like(g[k]) for k in _PARAMS if g.get(k) is not None}
+        else:
+            for v in param_grads.values():
+                v.zero_()
+        dF = grads.get("feat")
+        dF = torch.zeros((n, self.channels), dtype=torch.float32, device=self.device) if dF is None else dF.contiguous()
+        c_los = None
+        if dlos is not None:
+            if los is None:
+                raise ValueError("grads['los'] needs the los of the forward")
+            c_los = ctypes.byref(L.splat_los(los[0].data_ptr(), float(los[1]), 0))
+        keep = out.get("last") is not None
+        L.call("splat_render_lidar_rays_backward", ctypes.byref(cg), len(self.sensors), self.c_sensors, lidar,
+               self.c_proj(), self.c_bins(), _vp(rays), n, self._c_ray_bins(ray_bins),
+               _vp(out["T"] if keep else None), _vp(out["last"] if keep else None), _vp(dF),
+               _vp(grads.get("range_exp")), _vp(grads.get("alpha")), c_los, _vp(dlos), _vp(self.grad_proj),
+               _vp(param_grads["features"]), st)
         L.call("splat_project_backward", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
                _vp(self.grad_proj), _vp(param_grads["means"]), _vp(param_grads["scales"]),
                _vp(param_grads["quats"]), _vp(param_grads["opacities"]), _vp(param_grads.get("velocities")),

@@ -418,3 +418,144 @@ def test_sensor_velocity_time_offset_and_pose_gradients_match_oracle():
             rel = np.linalg.norm(got[k, sl] - want) / np.linalg.norm(want)
             assert rel < U.TOL_GRAD, (s.kind, sl, rel, got[k, sl], want)
             np.testing.assert_allclose(got[k, sl], want, atol=U.TOL_GRAD * np.abs(want).max(), rtol=0)
+
+
+# ----------------------------------------------------------------------------------
+# App. A.2: lidar point clouds rendered as free rays
+# ----------------------------------------------------------------------------------
+
+def _point_cloud(lid, n, seed):
+    """Points of a recorded sweep in front of the rig (where the tiny scene lies): azimuth
+    within +-0.9 rad, elevations slightly wider than the beam fan, ranges 4-30 m, capture
+    times across the sweep; a dense cluster puts several hundred rays into one tile."""
+    rng = np.random.default_rng(seed)
+    phi = rng.uniform(-0.9, 0.9, size=n)
+    om = rng.uniform(-0.3, 0.3, size=n)
+    k = n // 6
+    phi[:k] = rng.uniform(0.05, 0.2, size=k)
+    om[:k] = rng.uniform(0.02, 0.2, size=k)
+    r = rng.uniform(4.0, 30.0, size=n)
+    pts = np.stack([r * np.cos(om) * np.cos(phi), r * np.cos(om) * np.sin(phi), r * np.sin(om)], 1)
+    sweep = float(lid.sweep_time)
+    t = rng.uniform(-0.5 * sweep, 0.5 * sweep, size=n)
+    return pts.astype(np.float32), t.astype(np.float32)
+
+
+def _tile_margin(rays, lid):
+    """Rays whose tile decision lies within FP32 noise of a tile boundary."""
+    el = np.asarray(lid.beam_elev, np.float32).astype(np.float64)
+    tel = lid.tile_el
+    bnd = np.concatenate([[el[0] - 0.5 * (el[1] - el[0])], 0.5 * (el[tel - 1:-1:tel] + el[tel::tel]),
+                          [el[-1] + 0.5 * (el[-1] - el[-2])]])
+    wphi = lid.tile_az * float(np.float32(lid.az_res))
+    x = rays[:, 0] / wphi
+    near_col = np.abs(x - np.round(x)) < 1e-5
+    near_row = np.min(np.abs(rays[:, 1:2] - bnd[None, :]), axis=1) < 1e-5
+    return near_col | near_row
+
+
+def test_point_cloud_rays_bins_render_and_gradients_match_oracle():
+    """Points -> rays (ego motion removed with the lidar's velocities), their grouping by
+    tile, the free-ray forward (features, ranges, alpha, line-of-sight term against the
+    points' own ranges) and backward (stored state and recomputed) against the oracle.
+    Tiles hold up to ~1,400 rays (several 256-ray chunks) and some hold none."""
+    g, sensors = _dynamic_tiny()
+    lid = sensors[1]
+    n_pts = 6000
+    pts, times = _point_cloud(lid, n_pts, 21)
+    gd = gaussians_to_device(g, U.DEV)
+    fr = Frame(sensors, len(g["opacities"]), g["features"].shape[1], U.DEV)
+    pr = fr.lidar_points_to_rays(1, torch.as_tensor(pts, device=U.DEV), torch.as_tensor(times, device=U.DEV))
+    torch.cuda.synchronize()
+    rays = pr["rays"].cpu().numpy().astype(np.float64)
+    rng_gpu = pr["ranges"].cpu().numpy().astype(np.float64)
+    tiles = pr["tiles"].cpu().numpy()
+    want_rays, want_r, want_tile = oracle.points_to_rays(pts, times, lid)
+    dphi = np.abs(rays[:, 0] - want_rays[:, 0])
+    dphi = np.minimum(dphi, 2 * math.pi - dphi)
+    assert dphi.max() < 4e-6 and np.abs(rays[:, 1] - want_rays[:, 1]).max() < 4e-6
+    np.testing.assert_array_equal(rays[:, 2], want_rays[:, 2])
+    np.testing.assert_allclose(rng_gpu, want_r, rtol=2e-6)
+    marg = _tile_margin(want_rays, lid)
+    assert marg.mean() < 0.01
+    np.testing.assert_array_equal(tiles[~marg], want_tile[~marg])
+
+    # grouping: per-tile sets of ray ids, ranges and chunk numbers
+    b = fr.bin_rays(1, pr["rays"])
+    torch.cuda.synchronize()
+    ntiles = fr.tiles[1]
+    cnt = np.bincount(tiles[tiles >= 0], minlength=ntiles)
+    assert cnt.max() > 1000 and (cnt == 0).any()
+    tr = b["tile_ranges"].cpu().numpy()
+    starts = np.concatenate([[0], np.cumsum(cnt)[:-1]])
+    np.testing.assert_array_equal(tr[:, 0], starts)
+    np.testing.assert_array_equal(tr[:, 1], starts + cnt)
+    chunks = (cnt + 255) // 256
+    np.testing.assert_array_equal(b["chunk_base"].cpu().numpy(), np.concatenate([[0], np.cumsum(chunks)]))
+    ids = b["ray_ids"].cpu().numpy()
+    for k in range(ntiles):
+        np.testing.assert_array_equal(np.sort(ids[tr[k, 0]:tr[k, 1]]), np.nonzero(tiles == k)[0])
+
+    # forward, with the line-of-sight term against each point's own measured range
+    cg = fr.prepare(gd)
+    los = (pr["ranges"], 0.8)
+    out = fr.render_rays(cg, 1, pr["rays"], b, los=los)
+    torch.cuda.synchronize()
+    ref = oracle.render(g, lid, free_rays=rays, los_range=rng_gpu, los_eps=0.8)
+    ok = ~ref["marginal"]
+    assert ok.mean() > 0.97 and (ref["count"][ok] > 0).sum() > 2000
+    got = {k: v.cpu().numpy() for k, v in out.items() if v is not None}
+    np.testing.assert_allclose(got["feat"][ok], ref["F"][ok], atol=U.TOL_FEAT, rtol=0)
+    np.testing.assert_allclose(got["alpha"][ok], ref["alpha"][ok], atol=U.TOL_FEAT, rtol=0)
+    np.testing.assert_allclose(got["range_exp"][ok], ref["range_exp"][ok], rtol=U.TOL_RANGE, atol=U.TOL_RANGE)
+    np.testing.assert_allclose(got["range_med"][ok], ref["range_med"][ok], rtol=U.TOL_RANGE, atol=1e-5)
+    assert (ref["los"][ok] > 0.05).sum() > 50
+    np.testing.assert_allclose(got["los"][ok], ref["los"][ok], atol=U.TOL_FEAT, rtol=0)
+    outside = tiles < 0
+    assert outside.sum() > 100 and not got["feat"][outside].any() and not got["alpha"][outside].any()
+
+    # backward (stored state, then recomputed per tile) for every upstream term
+    C = g["features"].shape[1]
+    rs = np.random.default_rng(22)
+    gF = rs.normal(size=(n_pts, C)) * ok[:, None]
+    gD = rs.normal(size=n_pts) * ok * 0.05
+    gA = rs.normal(size=n_pts) * ok
+    gL = rs.normal(size=n_pts) * ok
+    f32 = lambda a: torch.as_tensor(np.asarray(a, np.float32), device=U.DEV)
+    grads = {"feat": f32(gF), "range_exp": f32(gD), "alpha": f32(gA), "los": f32(gL)}
+    want = oracle.render_backward(g, lid, gF.astype(np.float32).astype(np.float64), None,
+                                  gD.astype(np.float32).astype(np.float64), gA.astype(np.float32).astype(np.float64),
+                                  gL=gL.astype(np.float32).astype(np.float64), los_range=rng_gpu, los_eps=0.8,
+                                  free_rays=rays)
+    pg = fr.backward_rays(gd, 1, pr["rays"], b, out, grads, los=los)
+    torch.cuda.synchronize()
+    U.check_grads(pg, want)
+    out_r = fr.render_rays(cg, 1, pr["rays"], b, keep_state=False, los=los)
+    pg_r = fr.backward_rays(gd, 1, pr["rays"], b, out_r, grads, los=los)
+    torch.cuda.synchronize()
+    U.check_grads(pg_r, want)
+
+
+def test_point_cloud_edge_cases():
+    """No points, and points all outside the beam fan: no chunk, nothing rendered."""
+    g, sensors = _dynamic_tiny()
+    lid = sensors[1]
+    gd = gaussians_to_device(g, U.DEV)
+    fr = Frame(sensors, len(g["opacities"]), g["features"].shape[1], U.DEV)
+    cg = fr.prepare(gd)
+    empty = torch.empty((0, 3), device=U.DEV)
+    pr = fr.lidar_points_to_rays(1, empty, torch.empty(0, device=U.DEV))
+    b = fr.bin_rays(1, pr["rays"])
+    out = fr.render_rays(cg, 1, pr["rays"], b)
+    torch.cuda.synchronize()
+    assert out["feat"].shape == (0, g["features"].shape[1])
+    assert int(b["chunk_base"][-1]) == 0 and not b["tile_ranges"].any()
+    pts = np.array([[5.0, 0.0, 20.0], [0.0, 3.0, -9.0], [1.0, 1.0, 5.0]], np.float32)   # far above / below
+    pr = fr.lidar_points_to_rays(1, torch.as_tensor(pts, device=U.DEV), torch.zeros(3, device=U.DEV))
+    b = fr.bin_rays(1, pr["rays"])
+    out = fr.render_rays(cg, 1, pr["rays"], b)
+    torch.cuda.synchronize()
+    assert (pr["tiles"].cpu().numpy() == -1).all() and int(b["chunk_base"][-1]) == 0
+    assert not out["feat"].any() and (out["T"].cpu().numpy() == 1.0).all()
+    with pytest.raises(Exception):
+        fr.lidar_points_to_rays(0, torch.as_tensor(pts, device=U.DEV), torch.zeros(3, device=U.DEV))

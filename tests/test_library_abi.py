@@ -117,3 +117,25 @@ def test_bin_sort_rejects_small_workspace_before_launch():
     bins = L.splat_bins(0x1000, 0x1000, 0x1000)
     st = lib.splat_bin_sort(10, 1, arr, proj, 100, bins, ctypes.c_void_p(0x1000), 16, None)
     assert st == L.SPLAT_ERR_INVALID_ARG and "workspace too small" in lib.splat_last_error().decode()
+
+
+def test_point_cloud_entry_points_check_arguments_on_host():
+    """The free-ray entry points (App. A.2) reject a camera index, an out-of-range count
+    and missing buffers before any launch."""
+    lib = L.load()
+    cam, lid = scenes.tiny_frame()[1]
+    arr = (L.splat_sensor * 2)(_c_sensor(cam), _c_sensor(lid))
+    p = ctypes.c_void_p(0x1000)
+    st = lib.splat_lidar_points_to_rays(2, arr, 0, p, p, 10, p, p, None, None)
+    assert st == L.SPLAT_ERR_INVALID_ARG and "not a lidar" in lib.splat_last_error().decode()
+    st = lib.splat_lidar_points_to_rays(2, arr, 1, p, p, 1 << 31, p, p, None, None)
+    assert st == L.SPLAT_ERR_INVALID_ARG
+    st = lib.splat_lidar_points_to_rays(2, arr, 1, None, p, 10, p, p, None, None)
+    assert st == L.SPLAT_ERR_INVALID_ARG and "required" in lib.splat_last_error().decode()
+    bins = L.splat_ray_bins(0x1000, 0x1004, 0x1000)   # tile ranges not 8-byte aligned
+    st = lib.splat_lidar_bin_rays(2, arr, 1, p, 10, bins, None)
+    assert st == L.SPLAT_ERR_INVALID_ARG and "aligned" in lib.splat_last_error().decode()
+    bins = L.splat_ray_bins(None, 0x1000, 0x1000)
+    st = lib.splat_lidar_bin_rays(2, arr, 1, p, 10, bins, None)
+    assert st == L.SPLAT_ERR_INVALID_ARG and "NULL" in lib.splat_last_error().decode()
+    assert ctypes.sizeof(L.splat_ray_bins) == 24
