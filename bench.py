@@ -454,9 +454,9 @@ def run_ours(args):
 
 def point_cloud_bench(fr, cg, gd, out, timed):
     """The lidar's sweep as a point cloud (App. A.2): one return per grid cell that the
-    frame's render hits (alpha > 0.5), jittered by up to half a cell in azimuth and
-    elevation, at the rendered range; points -> rays, binning, free-ray forward and
-    backward, beside the grid-ray lidar kernels of the same frame."""
+    frame's render hits (alpha > 0.5), its direction jittered within the cell, at the
+    rendered range, stored ego-motion compensated; points -> rays, binning, free-ray
+    forward and backward, beside the grid-ray lidar kernels of the same frame."""
     import torch
     from paper_2411_16816_gb300.render import _stream
     k = fr.lid_idx[0]
@@ -475,7 +475,12 @@ def point_cloud_bench(fr, cg, gd, out, timed):
     om = elev[b] + rng.uniform(-0.45, 0.45, size=len(hit)) * de[b]
     r = rexp[hit] / alpha[hit]
     t = ((a + 0.5) / s.n_az - 0.5) * s.sweep_time
-    pts = np.stack([r * np.cos(om) * np.cos(phi), r * np.cos(om) * np.sin(phi), r * np.sin(om)], 1)
+    q = np.stack([r * np.cos(om) * np.cos(phi), r * np.cos(om) * np.sin(phi), r * np.sin(om)], 1)
+    # stored ego-motion compensated, as a recorded sweep is: q = p - t (v + w x p) solved for p
+    v, w = np.asarray(s.lin_vel, np.float64), np.asarray(s.ang_vel, np.float64)
+    W = np.array([[0.0, -w[2], w[1]], [w[2], 0.0, -w[0]], [-w[1], w[0], 0.0]])
+    A = np.eye(3)[None] - t[:, None, None] * W[None]
+    pts = np.linalg.solve(A, (q + t[:, None] * v[None])[..., None])[..., 0]
     P = torch.as_tensor(pts.astype(np.float32), device=dev)
     T = torch.as_tensor(t.astype(np.float32), device=dev)
     ms = {}

@@ -322,6 +322,18 @@ splat_status splat_lidar_points_to_rays(int32_t n_sensors, const splat_sensor *s
 splat_status splat_lidar_bin_rays(int32_t n_sensors, const splat_sensor *sensors, int32_t lidar, const float *rays,
                                   int64_t n_rays, splat_ray_bins bins, void *stream);
 
+/* Training-time grouping (App. A.2: a tile may receive more rays than its 256 threads,
+ * e.g. where the linear ego-motion model is violated; training shuffles each iteration
+ * and drops the rays beyond 256).  Groups like splat_lidar_bin_rays, then each tile
+ * keeps the `cap` rays (cap >= 1; 256 for one pass per tile) of smallest key
+ * (priority[ray] << 32 | ray), listed in key order; the others are dropped (not
+ * rendered, outputs not written).  priority[n_rays] (uint32, device) is the caller's
+ * random draw -- fresh values each iteration shuffle which rays a full tile keeps.
+ * `scratch` holds the uncapped grouping (same sizes as bins; caller-owned, overwritten). */
+splat_status splat_lidar_bin_rays_capped(int32_t n_sensors, const splat_sensor *sensors, int32_t lidar,
+                                         const float *rays, const uint32_t *priority, int64_t n_rays, int32_t cap,
+                                         splat_ray_bins scratch, splat_ray_bins bins, void *stream);
+
 /* Renders the binned rays of lidar `lidar` (sensor table as for the frame's projection
  * and bins).  Outputs are indexed by ray: out_feat[n_rays][channels], out_range_exp,
  * out_range_med, out_alpha, out_T, out_last [n_rays] with the meaning of

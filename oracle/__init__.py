@@ -307,6 +307,24 @@ def points_to_rays(points, times, s):
     return np.stack([phi, om, t], axis=1), r, tile
 
 
+def cap_rays(tile, priority, cap: int):
+    """App. A.2, training: a tile given more rays than it has threads keeps a random
+    subset -- the rays are shuffled each iteration and those beyond `cap` dropped.  The
+    shuffle is the caller's draw `priority` (one integer per ray): each tile keeps its cap
+    rays of smallest (priority, ray index).  Returns the kept mask and, per tile, the kept
+    ray indices in that order."""
+    tile = np.asarray(tile).reshape(-1)
+    pr = np.asarray(priority).astype(np.uint64).reshape(-1)
+    keep = np.zeros(len(tile), bool)
+    lists = {}
+    for t in np.unique(tile[tile >= 0]):
+        idx = np.nonzero(tile == t)[0]
+        order = sorted(idx.tolist(), key=lambda i: (int(pr[i]), i))[:cap]
+        keep[order] = True
+        lists[int(t)] = np.array(order, np.int64)
+    return keep, lists
+
+
 def jacobian(mean, scale, quat, opac, s):
     """(visible, J (3x3), sensor-frame covariance, relative velocity w) of one Gaussian."""
     L = lib()

@@ -24,7 +24,8 @@ EXPORTS = [
     "splat_frame_layout", "splat_workspace_size", "splat_project", "splat_bin_sort", "splat_bin_sort_backward",
     "splat_render_camera", "splat_render_camera_l1", "splat_render_lidar", "splat_render_lidar_los",
     "splat_render_camera_backward", "splat_render_lidar_backward", "splat_render_lidar_backward_los",
-    "splat_sync_status", "splat_lidar_points_to_rays", "splat_lidar_bin_rays", "splat_render_lidar_rays",
+    "splat_sync_status", "splat_lidar_points_to_rays", "splat_lidar_bin_rays", "splat_lidar_bin_rays_capped",
+    "splat_render_lidar_rays",
     "splat_render_lidar_rays_backward",
     "splat_project_backward", "splat_l1_loss", "splat_last_error", "splat_head_param_count", "splat_head_inputs",
     "splat_head_forward", "splat_head_train", "splat_head_adam", "splat_batch_table_bytes", "splat_batch_build",
@@ -112,6 +113,8 @@ def load(build_if_missing: bool = True):
     L.splat_render_lidar.argtypes = [G, c_int32, SE, splat_projected, splat_bins] + [c_void_p] * 8
     L.splat_lidar_points_to_rays.argtypes = [c_int32, SE, c_int32, c_void_p, c_void_p, c_int64] + [c_void_p] * 4
     L.splat_lidar_bin_rays.argtypes = [c_int32, SE, c_int32, c_void_p, c_int64, splat_ray_bins, c_void_p]
+    L.splat_lidar_bin_rays_capped.argtypes = [c_int32, SE, c_int32, c_void_p, c_void_p, c_int64, c_int32,
+                                              splat_ray_bins, splat_ray_bins, c_void_p]
     L.splat_render_lidar_rays.argtypes = ([G, c_int32, SE, c_int32, splat_projected, splat_bins, c_void_p, c_int64,
                                            splat_ray_bins] + [c_void_p] * 6 + [P(splat_los), c_void_p, c_void_p])
     L.splat_render_lidar_rays_backward.argtypes = ([G, c_int32, SE, c_int32, splat_projected, splat_bins, c_void_p,

@@ -453,6 +453,23 @@ splat_status splat_lidar_bin_rays(int32_t n_sensors, const splat_sensor* sensors
     return check_launch("splat_lidar_bin_rays");
 }
 
+splat_status splat_lidar_bin_rays_capped(int32_t n_sensors, const splat_sensor* sensors, int32_t lidar,
+                                         const float* rays, const uint32_t* priority, int64_t n_rays, int32_t cap,
+                                         splat_ray_bins scratch, splat_ray_bins bins, void* stream) {
+    const char* name = "splat_lidar_bin_rays_capped";
+    Frame fr;
+    splat_status st = lidar_of(n_sensors, sensors, lidar, fr, name);
+    if (st != SPLAT_OK) return st;
+    if ((st = check_ray_bins(bins, n_rays, name)) != SPLAT_OK) return st;
+    if ((st = check_ray_bins(scratch, n_rays, name)) != SPLAT_OK) return st;
+    if (cap < 1) return fail(SPLAT_ERR_INVALID_ARG, "%s: cap must be >= 1", name);
+    if (n_rays > 0 && (!rays || !priority)) return fail(SPLAT_ERR_INVALID_ARG, "%s: rays and priority are required", name);
+    launch_bin_rays_capped(fr.s[lidar], rays, priority, n_rays, cap, scratch.ray_ids, (int2*)scratch.tile_ranges,
+                           scratch.chunk_base, bins.ray_ids, (int2*)bins.tile_ranges, bins.chunk_base,
+                           (cudaStream_t)stream);
+    return check_launch(name);
+}
+
 // Free-ray raster input: the frame's lists plus the lidar's binned rays; the grid bounds
 // the number of 256-ray chunks (sum of ceil(count / 256) <= n_rays / 256 + tiles).
 static splat_status list_input(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,

@@ -64,60 +64,70 @@ __global__ void __launch_bounds__(kRayThreads)
     if (tile >= 0) atomicAdd(&ranges[tile].y, 1);
 }
 
-// One block: counts (in .y) -> (start, start) with the cursor in .y, and chunk numbers.
-// Each thread takes a contiguous run of tiles; a block-wide exclusive scan of the run
-// totals gives each run its base.
-__global__ void __launch_bounds__(kScanThreads) k_ray_scan(int2* __restrict__ ranges, int tiles,
-                                                           int32_t* __restrict__ chunk_base) {
-    __shared__ int s_cnt[kScanThreads / 32], s_chk[kScanThreads / 32];
-    const int per = (tiles + kScanThreads - 1) / kScanThreads;
-    const int t0 = min(tiles, (int)threadIdx.x * per), t1 = min(tiles, t0 + per);
-    int cnt = 0, chk = 0;
-    for (int t = t0; t < t1; t++) {
-        const int c = ranges[t].y;
-        cnt += c;
-        chk += (c + kListChunk - 1) / kListChunk;
-    }
-    // inclusive warp scans, then the warp totals
+// Exclusive prefix over the block of two per-thread values (threads in order); also the
+// block totals.  Every thread of the kScanThreads-thread block calls it.
+__device__ __forceinline__ void block_scan2(int& a, int& b, int& tot_a, int& tot_b) {
+    __shared__ int s_a[kScanThreads / 32], s_b[kScanThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int ic = cnt, ik = chk;
+    int ia = a, ib = b;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const int a = __shfl_up_sync(0xffffffffu, ic, o), b = __shfl_up_sync(0xffffffffu, ik, o);
+        const int x = __shfl_up_sync(0xffffffffu, ia, o), y = __shfl_up_sync(0xffffffffu, ib, o);
         if (lane >= o) {
-            ic += a;
-            ik += b;
+            ia += x;
+            ib += y;
         }
     }
     if (lane == 31) {
-        s_cnt[warp] = ic;
-        s_chk[warp] = ik;
+        s_a[warp] = ia;
+        s_b[warp] = ib;
     }
     __syncthreads();
     if (warp == 0) {
-        int a = s_cnt[lane], b = s_chk[lane];
+        int x = s_a[lane], y = s_b[lane];
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const int x = __shfl_up_sync(0xffffffffu, a, o), y = __shfl_up_sync(0xffffffffu, b, o);
+            const int u = __shfl_up_sync(0xffffffffu, x, o), v = __shfl_up_sync(0xffffffffu, y, o);
             if (lane >= o) {
-                a += x;
-                b += y;
+                x += u;
+                y += v;
             }
         }
-        s_cnt[lane] = a;   // inclusive totals of warps 0..lane
-        s_chk[lane] = b;
+        s_a[lane] = x;   // inclusive totals of warps 0..lane
+        s_b[lane] = y;
     }
     __syncthreads();
-    int base = ic - cnt + (warp > 0 ? s_cnt[warp - 1] : 0);
-    int cbase = ik - chk + (warp > 0 ? s_chk[warp - 1] : 0);
+    a = ia - a + (warp > 0 ? s_a[warp - 1] : 0);
+    b = ib - b + (warp > 0 ? s_b[warp - 1] : 0);
+    tot_a = s_a[kScanThreads / 32 - 1];
+    tot_b = s_b[kScanThreads / 32 - 1];
+}
+
+// One block over the tiles, each thread a contiguous run of them.  Counts are taken from
+// src (end - start, at most cap) or, without src, from .y of dst (the count kernel's
+// atomics).  dst[t] becomes (start, start) -- the scatter cursor -- or, with src,
+// (start, start + count); chunk_base[t] the first 256-ray chunk of the tile.
+__global__ void __launch_bounds__(kScanThreads) k_ray_scan(const int2* __restrict__ src, int2* __restrict__ dst,
+                                                           int tiles, int cap, int32_t* __restrict__ chunk_base) {
+    const int per = (tiles + kScanThreads - 1) / kScanThreads;
+    const int t0 = min(tiles, (int)threadIdx.x * per), t1 = min(tiles, t0 + per);
+    auto count = [&](int t) { return src ? min(src[t].y - src[t].x, cap) : dst[t].y; };
+    int cnt = 0, chk = 0;
     for (int t = t0; t < t1; t++) {
-        const int c = ranges[t].y;
-        ranges[t] = make_int2(base, base);
-        chunk_base[t] = cbase;
-        base += c;
-        cbase += (c + kListChunk - 1) / kListChunk;
+        const int c = count(t);
+        cnt += c;
+        chk += (c + kListChunk - 1) / kListChunk;
     }
-    if (threadIdx.x == kScanThreads - 1) chunk_base[tiles] = s_chk[kScanThreads / 32 - 1];
+    int tot_cnt, tot_chk;
+    block_scan2(cnt, chk, tot_cnt, tot_chk);
+    for (int t = t0; t < t1; t++) {
+        const int c = count(t);
+        dst[t] = make_int2(cnt, src ? cnt + c : cnt);
+        chunk_base[t] = chk;
+        cnt += c;
+        chk += (c + kListChunk - 1) / kListChunk;
+    }
+    if (threadIdx.x == kScanThreads - 1) chunk_base[tiles] = tot_chk;
 }
 
 __global__ void __launch_bounds__(kRayThreads)
@@ -142,8 +152,47 @@ void launch_bin_rays(const SensorDev& S, const float* rays, int64_t n, int32_t* 
     cudaMemsetAsync(ranges, 0, sizeof(int2) * (size_t)tiles, st);
     const int64_t blocks = (n + kRayThreads - 1) / kRayThreads;
     if (n > 0) k_ray_count<<<(unsigned)blocks, kRayThreads, 0, st>>>(S, rays, n, ranges);
-    k_ray_scan<<<1, kScanThreads, 0, st>>>(ranges, tiles, chunk_base);
+    k_ray_scan<<<1, kScanThreads, 0, st>>>(nullptr, ranges, tiles, 0, chunk_base);
     if (n > 0) k_ray_scatter<<<(unsigned)blocks, kRayThreads, 0, st>>>(S, rays, n, ranges, ids);
+}
+
+// Training-time cap (App. A.2): a tile keeps the `cap` rays of smallest (priority, ray
+// index); the caller draws fresh priorities each iteration, which shuffles the rays a full
+// tile keeps.  One block per tile: each ray's rank is the number of the tile's rays with a
+// smaller key (keys staged through shared memory); rank < cap writes the ray to slot
+// start + rank of the capped list, so the kept rays come out in key order.
+constexpr int kCapStage = 1024;
+__global__ void __launch_bounds__(kRayThreads)
+    k_ray_cap(const int2* __restrict__ src_ranges, const int32_t* __restrict__ src_ids,
+              const uint32_t* __restrict__ prio, int cap, const int2* __restrict__ dst_ranges,
+              int32_t* __restrict__ dst_ids) {
+    __shared__ unsigned long long s_key[kCapStage];
+    const int2 sr = src_ranges[blockIdx.x];
+    const int cnt = sr.y - sr.x, out0 = dst_ranges[blockIdx.x].x;
+    auto key_of = [&](int id) { return ((unsigned long long)prio[id] << 32) | (uint32_t)id; };
+    for (int j0 = 0; j0 < cnt; j0 += kRayThreads) {
+        const int j = j0 + threadIdx.x;
+        const int id = j < cnt ? src_ids[sr.x + j] : 0;
+        const unsigned long long kj = key_of(id);
+        int rank = 0;
+        for (int k0 = 0; k0 < cnt; k0 += kCapStage) {
+            const int nk = min(kCapStage, cnt - k0);
+            __syncthreads();
+            for (int k = threadIdx.x; k < nk; k += kRayThreads) s_key[k] = key_of(src_ids[sr.x + k0 + k]);
+            __syncthreads();
+            for (int k = 0; k < nk; k++) rank += s_key[k] < kj;
+        }
+        if (j < cnt && rank < cap) dst_ids[out0 + rank] = id;
+    }
+}
+
+void launch_bin_rays_capped(const SensorDev& S, const float* rays, const uint32_t* priority, int64_t n, int cap,
+                            int32_t* tmp_ids, int2* tmp_ranges, int32_t* tmp_chunks, int32_t* ids, int2* ranges,
+                            int32_t* chunk_base, cudaStream_t st) {
+    launch_bin_rays(S, rays, n, tmp_ids, tmp_ranges, tmp_chunks, st);
+    const int tiles = S.tiles_x * S.tiles_y;
+    k_ray_scan<<<1, kScanThreads, 0, st>>>(tmp_ranges, ranges, tiles, cap, chunk_base);
+    if (n > 0) k_ray_cap<<<tiles, kRayThreads, 0, st>>>(tmp_ranges, tmp_ids, priority, cap, ranges, ids);
 }
 
 }  // namespace splat

@@ -114,6 +114,9 @@ void launch_points_to_rays(const SensorDev& S, const float* points, const float*
                            float* range, int32_t* tiles, cudaStream_t st);
 void launch_bin_rays(const SensorDev& S, const float* rays, int64_t n, int32_t* ids, int2* ranges,
                      int32_t* chunk_base, cudaStream_t st);
+void launch_bin_rays_capped(const SensorDev& S, const float* rays, const uint32_t* priority, int64_t n, int cap,
+                            int32_t* tmp_ids, int2* tmp_ranges, int32_t* tmp_chunks, int32_t* ids, int2* ranges,
+                            int32_t* chunk_base, cudaStream_t st);
 bool raster_shape_supported(bool lidar, int tw, int th);
 bool raster_channels_supported(int C);
 void launch_l1(const float* pred, const float* target, int64_t count, float scale, float* grad, float* loss,

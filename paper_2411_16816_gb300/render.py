@@ -330,17 +330,32 @@ class Frame:
                _vp(out["rays"]), _vp(out["ranges"]), _vp(out["tiles"]), _stream(stream))
         return out
 
-    def bin_rays(self, lidar: int, rays: torch.Tensor, stream=None) -> dict:
-        """Group free rays (n, 3) of a lidar by tile: {"ray_ids", "tile_ranges", "chunk_base"}."""
+    def _ray_bins(self, lidar: int, n: int) -> dict:
+        dev, tiles = self.device, self.tiles[lidar]
+        return {"ray_ids": torch.empty(max(n, 1), dtype=torch.int32, device=dev),
+                "tile_ranges": torch.empty((tiles, 2), dtype=torch.int32, device=dev),
+                "chunk_base": torch.empty(tiles + 1, dtype=torch.int32, device=dev), "n": n}
+
+    def bin_rays(self, lidar: int, rays: torch.Tensor, cap: int | None = None,
+                 priority: torch.Tensor | None = None, stream=None) -> dict:
+        """Group free rays (n, 3) of a lidar by tile: {"ray_ids", "tile_ranges", "chunk_base"}.
+        With cap (training), each tile keeps the cap rays of smallest (priority, index);
+        priority (n,) int32/uint32 device values, drawn fresh per iteration."""
         self._check_lidar(lidar)
         rays = rays.contiguous()
-        n, dev = rays.shape[0], self.device
-        tiles = self.tiles[lidar]
-        b = {"ray_ids": torch.empty(max(n, 1), dtype=torch.int32, device=dev),
-             "tile_ranges": torch.empty((tiles, 2), dtype=torch.int32, device=dev),
-             "chunk_base": torch.empty(tiles + 1, dtype=torch.int32, device=dev), "n": n}
-        L.call("splat_lidar_bin_rays", len(self.sensors), self.c_sensors, lidar, _vp(rays), n, self._c_ray_bins(b),
-               _stream(stream))
+        n = rays.shape[0]
+        b = self._ray_bins(lidar, n)
+        if cap is None:
+            L.call("splat_lidar_bin_rays", len(self.sensors), self.c_sensors, lidar, _vp(rays), n,
+                   self._c_ray_bins(b), _stream(stream))
+            return b
+        if priority is None or priority.shape != (n,) or priority.element_size() != 4:
+            raise ValueError("a capped grouping needs one 32-bit priority per ray")
+        priority = priority.contiguous()
+        scratch = self._ray_bins(lidar, n)
+        L.call("splat_lidar_bin_rays_capped", len(self.sensors), self.c_sensors, lidar, _vp(rays), _vp(priority), n,
+               int(cap), self._c_ray_bins(scratch), self._c_ray_bins(b), _stream(stream))
+        b["scratch"] = scratch
         return b
 
     @staticmethod

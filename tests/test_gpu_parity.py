@@ -559,3 +559,44 @@ def test_point_cloud_edge_cases():
     assert not out["feat"].any() and (out["T"].cpu().numpy() == 1.0).all()
     with pytest.raises(Exception):
         fr.lidar_points_to_rays(0, torch.as_tensor(pts, device=U.DEV), torch.zeros(3, device=U.DEV))
+
+
+def test_point_cloud_training_cap_matches_oracle():
+    """Training-time grouping (App. A.2): every tile keeps its 256 rays of smallest
+    (priority, index), listed in that order (bit-exact against the oracle), one chunk
+    per tile; the kept rays render as in the uncapped list and the dropped ones are not
+    written."""
+    g, sensors = _dynamic_tiny()
+    lid = sensors[1]
+    n_pts = 6000
+    pts, times = _point_cloud(lid, n_pts, 23)
+    gd = gaussians_to_device(g, U.DEV)
+    fr = Frame(sensors, len(g["opacities"]), g["features"].shape[1], U.DEV)
+    pr = fr.lidar_points_to_rays(1, torch.as_tensor(pts, device=U.DEV), torch.as_tensor(times, device=U.DEV))
+    prio = np.random.default_rng(24).integers(0, 2**31, size=n_pts).astype(np.int32)
+    prio[:50] = 7                                               # ties broken by the ray index
+    b = fr.bin_rays(1, pr["rays"], cap=256, priority=torch.as_tensor(prio, device=U.DEV))
+    torch.cuda.synchronize()
+    tiles = pr["tiles"].cpu().numpy()
+    keep, lists = oracle.cap_rays(tiles, prio.astype(np.uint32), 256)
+    ntiles = fr.tiles[1]
+    cnt = np.bincount(tiles[tiles >= 0], minlength=ntiles)
+    assert cnt.max() > 1000
+    kept = np.minimum(cnt, 256)
+    tr = b["tile_ranges"].cpu().numpy()
+    starts = np.concatenate([[0], np.cumsum(kept)[:-1]])
+    np.testing.assert_array_equal(tr[:, 0], starts)
+    np.testing.assert_array_equal(tr[:, 1], starts + kept)
+    np.testing.assert_array_equal(b["chunk_base"].cpu().numpy(), np.concatenate([[0], np.cumsum(kept > 0)]))
+    ids = b["ray_ids"].cpu().numpy()
+    for t in range(ntiles):
+        want = lists.get(t, np.zeros(0, np.int64))
+        np.testing.assert_array_equal(ids[tr[t, 0]:tr[t, 1]], want)
+    cg = fr.prepare(gd)
+    full = fr.render_rays(cg, 1, pr["rays"], fr.bin_rays(1, pr["rays"]))
+    capd = fr.render_rays(cg, 1, pr["rays"], b)
+    torch.cuda.synchronize()
+    k = torch.as_tensor(keep, device=U.DEV)
+    for key in ("feat", "range_exp", "range_med", "alpha", "T", "last"):
+        assert torch.equal(capd[key][k], full[key][k]), key
+    assert not capd["feat"][~k].any() and (capd["T"][~k] == 1).all()

@@ -708,3 +708,29 @@ def test_free_rays_at_grid_positions_render_like_the_grid():
     # free rays reach the renderer as FP32 (phi within 2.4e-7 of the grid's FP64 value)
     np.testing.assert_allclose(free["F"], grid["F"], atol=1e-5)
     np.testing.assert_allclose(free["range_exp"], grid["range_exp"], atol=1e-4)
+
+
+def test_cap_rays_keeps_the_lowest_priorities_and_samples_uniformly():
+    """Training-time cap of App. A.2: tiles at or under the cap keep every ray; over-full
+    tiles keep exactly cap rays; with priorities equal to the ray index the first cap
+    rays survive; under uniform random priorities every ray of a tile survives with
+    probability cap / count (a uniform shuffle)."""
+    tile = np.array([0] * 10 + [1] * 3 + [-1] * 2 + [2] * 6)
+    keep, lists = oracle.cap_rays(tile, np.arange(len(tile)), 4)
+    assert keep[10:13].all() and not keep[13:15].any()
+    np.testing.assert_array_equal(np.nonzero(keep[:10])[0], [0, 1, 2, 3])
+    np.testing.assert_array_equal(lists[2], [15, 16, 17, 18])
+    prio = np.array([5, 5, 1, 9, 0, 7, 7, 3, 2, 8] + [0] * 11)
+    keep, lists = oracle.cap_rays(tile, prio, 4)
+    np.testing.assert_array_equal(lists[0], [4, 2, 8, 7])              # ties broken by index below
+    keep, lists = oracle.cap_rays(tile, np.r_[np.full(10, 3), np.zeros(11)], 4)
+    np.testing.assert_array_equal(lists[0], [0, 1, 2, 3])
+    rng = np.random.default_rng(9)
+    big = np.repeat([0, 1], [300, 200])
+    hits = np.zeros(500)
+    for _ in range(400):
+        k, _ = oracle.cap_rays(big, rng.integers(0, 2**32, size=500, dtype=np.uint64), 256)
+        assert k[:300].sum() == 256 and k[300:].all()
+        hits += k
+    frac = hits[:300] / 400
+    assert abs(frac.mean() - 256 / 300) < 1e-12 and frac.min() > 0.7 and frac.max() < 0.97
