@@ -395,6 +395,7 @@ def run_ours(args):
                                           _vp(pgrads["velocities"]), None, st))
 
     point_cloud = point_cloud_bench(fr, cg, gd, out, timed) if fr.lid_idx else None
+    opacity_aware = support_bench(sensors, gd, tgt, flush, args.warmup, min(args.steps, 20), rays, dev)
 
     peaks = measured_peaks()
     clocks = clk.summary()
@@ -435,7 +436,7 @@ def run_ours(args):
             "e2e": e2e, "gpu_launches": launches_per_step(fr, len(l1_terms)) * args.steps,
             "roofline": roofline, "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
-            "wall_s": wall, "overflow": overflow, "point_cloud": point_cloud}
+            "wall_s": wall, "overflow": overflow, "point_cloud": point_cloud, "opacity_aware": opacity_aware}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, sensors)
     if rank == 0 and world == 1:
@@ -450,6 +451,52 @@ def run_ours(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def support_bench(sensors, gd, tgt, flush, warmup, steps, rays, dev):
+    """The same step with the opacity-aware tile extent on every sensor (support = 1):
+    intersections and time per step (CUDA events, L2 flushed between steps)."""
+    import dataclasses
+    import torch
+    from paper_2411_16816_gb300.render import Frame, l1_loss
+    sv = [dataclasses.replace(s, support=1) for s in sensors]
+    n, C = gd["means"].shape[0], gd["features"].shape[1]
+    fr = Frame(sv, n, C, dev)
+    out = fr.forward(gd, check=True)
+    need = int(fr.n_isect.item())
+    fr._alloc_capacity(int(need * 1.1))
+    out = fr.forward(gd, check=True)
+    grads = {k: torch.empty_like(out[k]) for k in ("cam_feat", "lid_feat", "lid_range_exp") if k in out}
+    pgrads = {k: torch.zeros_like(v) for k, v in gd.items() if v is not None}
+    loss = torch.zeros(1, device=dev)
+    cam_l1 = (tgt["cam_feat"], 1.0 / out["cam_feat"].numel(), grads["cam_feat"], loss) if "cam_feat" in out else None
+    terms = [(k, 1.0 / out[k].numel()) for k in ("lid_feat", "lid_range_exp") if k in out]
+
+    def step():
+        loss.zero_()
+        fr.forward(gd, keep_state=True, check=False, out=out, cam_l1=cam_l1)
+        for key, sc in terms:
+            l1_loss(out[key], tgt[key], sc, grads[key], loss)
+        fr.backward(gd, out, grads, param_grads=pgrads)
+
+    for _ in range(warmup):
+        step()
+    stream = torch.cuda.current_stream()
+    ts = []
+    for k in range(steps):
+        flush.fill_(float(k))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    ms = statistics.mean(ts)
+    res = {"intersections": int(fr.n_isect.item()), "ms_per_step": ms, "rays_per_s": rays / (ms * 1e-3),
+           "steps": steps, "overflow": int(fr.n_isect.item()) > fr.capacity}
+    del fr, out, grads, pgrads
+    torch.cuda.empty_cache()
+    return res
 
 
 def point_cloud_bench(fr, cg, gd, out, timed):
@@ -493,15 +540,15 @@ def point_cloud_bench(fr, cg, gd, out, timed):
     pgr = {key: torch.zeros_like(v) for key, v in gd.items() if v is not None}
     timed("points_to_rays", lambda: fr.lidar_points_to_rays(k, P, T), into=ms)
     timed("bin_rays", lambda: fr.bin_rays(k, pr["rays"]), into=ms)
-    timed("raster_rays_fwd", lambda: fr.render_rays(cg, k, pr["rays"], bins), into=ms)
+    timed("raster_rays_fwd", lambda: fr.render_rays(cg, k, pr["rays"], bins, out=o), into=ms)
     timed("rays_bwd_with_projection_bwd", lambda: fr.backward_rays(gd, k, pr["rays"], bins, o, grads,
                                                                     param_grads=pgr), into=ms)
     torch.cuda.synchronize()
     chunks = int(bins["chunk_base"][-1].item())
     return {"points": n, "tiles": fr.tiles[k], "chunks": chunks,
             "binned": int(bins["tile_ranges"][-1, 1].item()), "ms": ms,
-            "note": "ms include the output allocation of the Python wrapper; grid-ray lidar kernels under "
-                    "roofline.kernel_ms"}
+            "note": "rays_bwd includes zeroing the projection gradient and the projection backward; "
+                    "grid-ray lidar kernels under roofline.kernel_ms"}
 
 
 def serving_bench(args, dev):

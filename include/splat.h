@@ -105,7 +105,11 @@ typedef struct {
     float az_res, sweep_time, r_min;
     /* tiling (both kinds) */
     int32_t tile_w, tile_h;
-    int32_t reserved1;
+    /* tile extent of a Gaussian: 0 = the paper's box of 3 standard deviations of Sigma'
+     * plus the motion margin (Sec. 3.2, Sec. 3.3); 1 = opacity-aware, sqrt(2 ln(255 o'))
+     * standard deviations -- exactly the bounding box of the ellipse where alpha can reach
+     * 1/255, so the tile lists then hold every Gaussian a ray of the tile can blend. */
+    int32_t support;
 } splat_sensor;
 
 /* Per-(sensor, Gaussian) projection results, caller-owned device buffers.

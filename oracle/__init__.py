@@ -109,7 +109,7 @@ def _r32(x) -> float:
 
 def sensor_params(s) -> np.ndarray:
     """Flat FP64 parameter vector of a sensor (values rounded through FP32)."""
-    P = np.zeros(32, dtype=np.float64)
+    P = np.zeros(40, dtype=np.float64)
     P[1:10] = np.asarray(s.R, dtype=np.float32).reshape(9)
     P[10:13] = np.asarray(s.t, dtype=np.float32)
     P[13:16] = np.asarray(s.lin_vel, dtype=np.float32)
@@ -122,6 +122,7 @@ def sensor_params(s) -> np.ndarray:
         P[0] = 1
         P[19:27] = [s.n_beams, s.n_az, _r32(s.az_res), _r32(s.sweep_time), _r32(s.eps2d), _r32(s.r_min),
                     s.tile_az, s.tile_el]
+    P[31] = getattr(s, "support", 0)   # tile extent: 0 = 3 sigma, 1 = opacity-aware
     return P
 
 
@@ -190,7 +191,7 @@ def isect_list(g: dict, s, proj: dict | None = None):
 
 
 def render(g: dict, s, sel=None, guard: float | None = None, los_range=None, los_eps: float = 0.8,
-           free_rays=None) -> dict:
+           free_rays=None, every_gaussian: bool = False) -> dict:
     """Render the selected rays (indices into the sensor's ray grid; None: all).
 
     Camera ray k is pixel (row, col) = divmod(k, width); lidar ray k is
@@ -199,7 +200,9 @@ def render(g: dict, s, sel=None, guard: float | None = None, los_range=None, los
     as out["los"]: the summed alpha of the blended Gaussians whose range r_rs lies
     before los_range - los_eps.  With free_rays ((k, 3) phi, omega, t of a lidar, e.g.
     from points_to_rays) those rays are rendered instead of the grid, each in the tile
-    its own (phi, omega) falls in (App. A.2).
+    its own (phi, omega) falls in (App. A.2).  every_gaussian drops the tile predicate:
+    each ray then blends, in depth order, every visible Gaussian that reaches alpha >=
+    1/255 at it -- the per-pixel definition without tiles.
     """
     L = lib()
     n = len(g["opacities"])
@@ -207,6 +210,7 @@ def render(g: dict, s, sel=None, guard: float | None = None, los_range=None, los
     feat = _f32(g["features"])
     C = feat.shape[1] if feat.ndim == 2 else 0
     P = sensor_params(s)
+    P[32] = 1.0 if every_gaussian else 0.0
     guard = guard_for(s) if guard is None else guard
     sel_arr = None if sel is None else np.ascontiguousarray(sel, dtype=np.int64)
     fr = None if free_rays is None else _sensor_array(np.asarray(free_rays).reshape(-1, 3))

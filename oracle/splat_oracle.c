@@ -33,7 +33,7 @@
 #define T_EPS 1e-4
 
 /* ---------------------------------------------------------------------------------
- * Sensor parameter vector (double[32]); values are the FP32 inputs promoted.
+ * Sensor parameter vector (double[40]); values are the FP32 inputs promoted.
  * ------------------------------------------------------------------------------- */
 enum {
     P_KIND = 0,          /* 0 camera, 1 lidar */
@@ -46,7 +46,10 @@ enum {
     P_RS = 25, P_DT = 26, P_EPS = 27, P_NEAR = 28, P_TW = 29, P_TH = 30,
     /* lidar */
     P_NB = 19, P_NAZ = 20, P_AZRES = 21, P_SWEEP = 22, P_LEPS = 23, P_RMIN = 24,
-    P_TAZ = 25, P_TEL = 26
+    P_TAZ = 25, P_TEL = 26,
+    /* both kinds */
+    P_SUPPORT = 31,      /* tile extent: 0 = 3 sigma (Sec. 3.2), 1 = where alpha can reach 1/255 */
+    P_ALLG = 32          /* render from every visible Gaussian, without the tile predicate */
 };
 
 /* Projected record (double[16]) */
@@ -174,6 +177,15 @@ static int cov2d(const proj_state *st, double eps, double out[6]) {
 }
 
 
+/* Half-extent of the tile box in standard deviations of Sigma'.  The paper's box is
+ * 3 sigma (Sec. 3.2, Sec. 3.3).  The opacity-aware alternative takes exactly the ellipse
+ * where alpha = o' exp(-d^T Sigma'^-1 d / 2) can reach 1/255: d^T Sigma'^-1 d <= 2 ln(255 o'),
+ * whose bounding box has half-widths sqrt(2 ln(255 o')) times the standard deviations. */
+static double support_sigmas(const double *P, double op) {
+    if (P[P_SUPPORT] < 0.5) return 3.0;
+    return op > ALPHA_MIN ? sqrt(2.0 * log(255.0 * op)) : 0.0;
+}
+
 /* Camera tile rectangle [x0,x1) x [y0,y1) from the AABB (Sec. 3.2), widened by `extra`
  * pixels on every side.  Returns 1 if an edge lies within `guard` pixels of a tile edge. */
 static int camera_rect(const double *P, const double *rec, double extra, int rect[4], double guard) {
@@ -239,10 +251,11 @@ static int project_camera(const double *P, const double *mean, const double *sca
     rec[R_VR] = 0;
     rec[R_SAA] = A; rec[R_SAB] = B; rec[R_SBB] = C;
     rec[R_COMP] = comp;
-    /* Rectangular 3-sigma AABB of Sigma' plus per-component |v| (t_rs/2 + |time offset|). */
+    /* Rectangular k-sigma AABB of Sigma' plus per-component |v| (t_rs/2 + |time offset|). */
     double tspan = 0.5 * P[P_RS] + fabs(P[P_DT]);
-    rec[R_EXA] = 3.0 * sqrt(A) + fabs(rec[R_VA]) * tspan;
-    rec[R_EXB] = 3.0 * sqrt(C) + fabs(rec[R_VB]) * tspan;
+    double k = support_sigmas(P, op);
+    rec[R_EXA] = k * sqrt(A) + fabs(rec[R_VA]) * tspan;
+    rec[R_EXB] = k * sqrt(C) + fabs(rec[R_VB]) * tspan;
     if (camera_rect(P, rec, 0.0, rect, guard_px)) *marg = 1;
     if (cull_marg) *marg = 1;
     if (*marg) {
@@ -356,10 +369,11 @@ static int project_lidar(const double *P, const double *elev, const double *mean
     for (int i = 0; i < 3; i++) rec[R_VA + i] = J[3 * i] * st->w[0] + J[3 * i + 1] * st->w[1] + J[3 * i + 2] * st->w[2];
     rec[R_SAA] = A; rec[R_SAB] = B; rec[R_SBB] = C;
     rec[R_COMP] = comp;
-    /* AABB: 3 sigma plus the first two components of v^S t_sweep / 2 */
+    /* AABB: k sigma plus the first two components of v^S t_sweep / 2 */
     double half = 0.5 * P[P_SWEEP];
-    rec[R_EXA] = 3.0 * sqrt(A) + fabs(rec[R_VA]) * half;
-    rec[R_EXB] = 3.0 * sqrt(C) + fabs(rec[R_VB]) * half;
+    double k = support_sigmas(P, op);
+    rec[R_EXA] = k * sqrt(A) + fabs(rec[R_VA]) * half;
+    rec[R_EXB] = k * sqrt(C) + fabs(rec[R_VB]) * half;
     int nt = lidar_rect(P, elev, rec, 0.0, rect, guard_rad, marg);
     if (cull_marg) *marg = 1;
     if (*marg) {
@@ -561,7 +575,7 @@ static int render_ray(const double *P, const double *elev, const double *rays, i
             if (sig >= 0 && g[R_OP] * exp(-sig) >= ALPHA_MIN * (1 - 1e-4)) mg |= 1;
         }
         if (!vis[i]) continue;
-        if (!rect_contains(P, rect + 4 * i, tx, ty)) continue;
+        if (P[P_ALLG] < 0.5 && !rect_contains(P, rect + 4 * i, tx, ty)) continue;
         cands[nc].id = (int32_t)i;
         cands[nc].depth = rec[REC * i + R_DEPTH];
         nc++;

@@ -46,7 +46,7 @@ class splat_sensor(ctypes.Structure):
                 ("time_offset", c_float), ("eps2d", c_float), ("near_plane", c_float), ("n_beams", c_int32),
                 ("n_az", c_int32), ("beam_elev", c_void_p), ("rays", c_void_p), ("az_res", c_float),
                 ("sweep_time", c_float), ("r_min", c_float), ("tile_w", c_int32), ("tile_h", c_int32),
-                ("reserved1", c_int32)]
+                ("support", c_int32)]
 
 
 class splat_projected(ctypes.Structure):

@@ -62,6 +62,9 @@ static splat_status build_frame(int32_t n_sensors, const splat_sensor* sensors, 
         d.tile_h = in.tile_h;
         d.eps = in.eps2d;
         if (!(in.eps2d >= 0.f)) return fail(SPLAT_ERR_INVALID_ARG, "sensor %d: eps2d must be >= 0", s);
+        if (in.support != 0 && in.support != 1)
+            return fail(SPLAT_ERR_INVALID_ARG, "sensor %d: support must be 0 (3 sigma) or 1 (opacity-aware)", s);
+        d.support = in.support;
         const bool lidar = in.kind == SPLAT_SENSOR_LIDAR;
         if (in.kind != SPLAT_SENSOR_CAMERA && !lidar) return fail(SPLAT_ERR_INVALID_ARG, "sensor %d: bad kind", s);
         if (!tile_shape_ok(in.tile_w, in.tile_h))

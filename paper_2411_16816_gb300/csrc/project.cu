@@ -162,8 +162,9 @@ __device__ bool project_camera(const SensorDev& S, const GaussLocal& G, float4& 
     const float vy = cj.J1[1] * w.y + cj.J1[2] * w.z;
     const float mx = S.fx * cj.ux + S.cx, my = S.fy * cj.uy + S.cy;
     const float tspan = 0.5f * S.rs + fabsf(S.dt);
-    const float ex = 3.f * sqrtf(A) + fabsf(vx) * tspan;
-    const float ey = 3.f * sqrtf(C) + fabsf(vy) * tspan;
+    const float k = support_sigmas(S, op);
+    const float ex = k * sqrtf(A) + fabsf(vx) * tspan;
+    const float ey = k * sqrtf(C) + fabsf(vy) * tspan;
     const float fx0 = fminf(fmaxf(floorf((mx - ex) / S.tile_w), 0.f), (float)S.tiles_x);
     const float fx1 = fminf(fmaxf(ceilf((mx + ex) / S.tile_w), 0.f), (float)S.tiles_x);
     const float fy0 = fminf(fmaxf(floorf((my - ey) / S.tile_h), 0.f), (float)S.tiles_y);
@@ -202,8 +203,9 @@ __device__ bool project_lidar(const SensorDev& S, const GaussLocal& G, float4& r
     const float vom = lj.J[3] * w.x + lj.J[4] * w.y + lj.J[5] * w.z;
     const float vr = lj.J[6] * w.x + lj.J[7] * w.y + lj.J[8] * w.z;
     const float half = 0.5f * S.sweep;
-    const float ep = 3.f * sqrtf(A) + fabsf(vphi) * half;
-    const float eo = 3.f * sqrtf(C) + fabsf(vom) * half;
+    const float k = support_sigmas(S, op);
+    const float ep = k * sqrtf(A) + fabsf(vphi) * half;
+    const float eo = k * sqrtf(C) + fabsf(vom) * half;
     // elevation rows (App. A.1): row containing omega_low .. one past the row of omega_high
     const int Mw = S.nb / S.tile_h;
     const float olo = om - eo, ohi = om + eo;

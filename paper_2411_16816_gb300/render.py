@@ -93,6 +93,7 @@ class Frame:
         c.ang_vel[:] = [float(x) for x in np.asarray(s.ang_vel, dtype=np.float32)]
         c.tile_w, c.tile_h = s.tile_w if s.kind == "camera" else s.tile_az, s.tile_h if s.kind == "camera" else s.tile_el
         c.eps2d = s.eps2d
+        c.support = int(getattr(s, "support", 0))
         if s.kind == "camera":
             c.kind = L.SPLAT_SENSOR_CAMERA
             c.width, c.height = s.width, s.height
@@ -363,22 +364,25 @@ class Frame:
         return L.splat_ray_bins(b["ray_ids"].data_ptr(), b["tile_ranges"].data_ptr(), b["chunk_base"].data_ptr())
 
     def render_rays(self, cg, lidar: int, rays: torch.Tensor, ray_bins: dict, keep_state: bool = True,
-                    los: tuple | None = None, stream=None) -> dict:
+                    los: tuple | None = None, stream=None, out: dict | None = None) -> dict:
         """Render binned free rays of a lidar against this frame's lists (prepare() first).
-        Outputs are indexed by ray; rays outside the beam fan stay 0.  los = (target_range
-        per ray, eps) adds out["los"]."""
+        Outputs are indexed by ray; rays outside the beam fan (or dropped by a cap) keep
+        their initial values (0, T = 1) -- or, with a reused `out`, the previous ones.
+        los = (target_range per ray, eps) adds out["los"]."""
         self._check_lidar(lidar)
         rays = rays.contiguous()
         n, dev, C = rays.shape[0], self.device, self.channels
-        out = {"feat": torch.zeros((n, C), dtype=torch.float32, device=dev),
-               "range_exp": torch.zeros(n, dtype=torch.float32, device=dev),
-               "range_med": torch.zeros(n, dtype=torch.float32, device=dev),
-               "alpha": torch.zeros(n, dtype=torch.float32, device=dev),
-               "T": torch.ones(n, dtype=torch.float32, device=dev) if keep_state else None,
-               "last": torch.zeros(n, dtype=torch.int32, device=dev) if keep_state else None}
+        if out is None:
+            out = {"feat": torch.zeros((n, C), dtype=torch.float32, device=dev),
+                   "range_exp": torch.zeros(n, dtype=torch.float32, device=dev),
+                   "range_med": torch.zeros(n, dtype=torch.float32, device=dev),
+                   "alpha": torch.zeros(n, dtype=torch.float32, device=dev),
+                   "T": torch.ones(n, dtype=torch.float32, device=dev) if keep_state else None,
+                   "last": torch.zeros(n, dtype=torch.int32, device=dev) if keep_state else None}
         c_los = None
         if los is not None:
-            out["los"] = torch.zeros(n, dtype=torch.float32, device=dev)
+            if out.get("los") is None:
+                out["los"] = torch.zeros(n, dtype=torch.float32, device=dev)
             c_los = ctypes.byref(L.splat_los(los[0].data_ptr(), float(los[1]), 0))
         L.call("splat_render_lidar_rays", ctypes.byref(cg), len(self.sensors), self.c_sensors, lidar, self.c_proj(),
                self.c_bins(), _vp(rays), n, self._c_ray_bins(ray_bins), _vp(out["feat"]),
