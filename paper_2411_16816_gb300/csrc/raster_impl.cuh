@@ -159,6 +159,7 @@ __device__ __forceinline__ bool block_setup(const Frame& fr, const RasterIn& in,
 
 template <int CM, int B, bool LIDAR>
 struct Stage {
+    static_assert(CM % 4 == 0, "features are staged and read as float4");
     float4 g0[B];
     float4 g1[B];
     float2 g2[LIDAR ? B : 1];
@@ -321,10 +322,14 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
                         }
                         const float wgt = a * st[q].T;
                         if (WANT_F) {   // packed FP32 pairs: each lane is the same fused multiply-add
-                            const float2* f2 = reinterpret_cast<const float2*>(sm.f + k * CM);
+                            const float4* f4 = reinterpret_cast<const float4*>(sm.f + k * CM);
                             const float2 w2 = make_float2(wgt, wgt);
 #pragma unroll
-                            for (int c = 0; c < CM / 2; c++) F[q][c] = __ffma2_rn(f2[c], w2, F[q][c]);
+                            for (int c = 0; c < CM / 4; c++) {
+                                const float4 v = f4[c];
+                                F[q][2 * c] = __ffma2_rn(make_float2(v.x, v.y), w2, F[q][2 * c]);
+                                F[q][2 * c + 1] = __ffma2_rn(make_float2(v.z, v.w), w2, F[q][2 * c + 1]);
+                            }
                         }
                         if (LIDAR) {
                             const float rrs = sm.g2[k].x + sm.g2[k].y * r[q].t;
@@ -516,6 +521,13 @@ __device__ __forceinline__ void warp_transpose_reduce(float (&v)[VP], int lane) 
     }
 }
 
+// Resident blocks the camera backward asks the register allocator for: 12 warps per SM
+// (the packed channel loops otherwise take registers enough to drop to 10).
+template <int CM, bool LIDAR, int NT>
+struct BwdMinBlocks {
+    static constexpr int value = (!LIDAR && CM <= 16 && NT <= 384) ? 384 / NT : 1;
+};
+
 template <int CM, bool LIDAR>
 struct BwdLayout {
     static constexpr int kOffF = LIDAR ? 12 : 8;          // first feature slot (16-byte aligned)
@@ -528,7 +540,8 @@ struct BwdLayout {
 };
 
 template <int CM, int TW, int TH, bool LIDAR, bool RECOMPUTE, bool LIST = false>
-__global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * TH>::value)
+__global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * TH>::value,
+                                  BwdMinBlocks<CM, LIDAR, TW * TH / RaysPerThread<CM, true, LIDAR, TW * TH>::value>::value)
     k_raster_bwd(const __grid_constant__ Frame fr, RasterIn in, RasterGrad gr) {
     constexpr int PX = RaysPerThread<CM, true, LIDAR, TW * TH>::value;
     constexpr int NT = TW * TH / PX;
@@ -567,14 +580,19 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
             last[q] = r[q].inside ? min(gr.last[r[q].o], len) : 0;   // never past this tile's list
         }
     }
-    float gF[PX][CM], gTT[PX], gD[PX], T[PX], S[PX], SD[PX];
+    float2 gF[PX][CM / 2];   // upstream feature gradient, as FP32 pairs for the packed FMAs
+    float gTT[PX], gD[PX], T[PX], S[PX], SD[PX];
     float gL[PX], cut[PX];   // lidar line-of-sight upstream gradient and range cut
     float dtime = 0.f;       // camera: this thread's share of dL/d (camera time offset)
     int my_last = 0;
 #pragma unroll
     for (int q = 0; q < PX; q++) {
 #pragma unroll
-        for (int c = 0; c < CM; c++) gF[q][c] = (r[q].inside && c < Crt) ? gr.dfeat[r[q].o * Crt + c] : 0.f;
+        for (int c = 0; c < CM / 2; c++) {
+            const int c0 = 2 * c, c1 = 2 * c + 1;
+            gF[q][c] = make_float2((r[q].inside && c0 < Crt) ? gr.dfeat[r[q].o * Crt + c0] : 0.f,
+                                   (r[q].inside && c1 < Crt) ? gr.dfeat[r[q].o * Crt + c1] : 0.f);
+        }
         float gT = 0.f;
         gD[q] = 0.f;
         if (r[q].inside) {
@@ -623,6 +641,7 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
             }
             if (!__any_sync(0xffffffffu, any)) continue;
             float v[VP];
+            float2 vf[CM / 2];   // feature-gradient terms, accumulated as packed pairs
 #pragma unroll
             for (int q = 0; q < PX; q++) {
                 // a ray that does not blend this Gaussian gets alpha = 0: every term vanishes
@@ -631,9 +650,16 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
                 const float inv = rcp_approx(1.f - aq);   // 1 - alpha >= 0.001: no special cases
                 const float Ti = T[q] * inv;
                 const float wgt = aq * Ti;
-                float Gf = 0.f;
+                // sum_c gF_c f_c in two interleaved partial sums (packed FP32 pairs)
+                const float4* f4 = reinterpret_cast<const float4*>(sm.f + k * CM);
+                float2 g2 = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int c = 0; c < CM; c++) Gf += gF[q][c] * sm.f[k * CM + c];
+                for (int c = 0; c < CM / 4; c++) {
+                    const float4 fv = f4[c];
+                    g2 = __ffma2_rn(gF[q][2 * c], make_float2(fv.x, fv.y), g2);
+                    g2 = __ffma2_rn(gF[q][2 * c + 1], make_float2(fv.z, fv.w), g2);
+                }
+                const float Gf = g2.x + g2.y;
                 float dalpha = Ti * (Gf - S[q]) - gTT[q] * inv;
                 S[q] += aq * (Gf - S[q]);
                 float drrs = 0.f, tq = r[q].t;
@@ -659,7 +685,7 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
 #pragma unroll
                     for (int j = 8; j < OFF; j++) v[j] = 0.f;
 #pragma unroll
-                    for (int c = 0; c < CM; c++) v[OFF + c] = wgt * gF[q][c];
+                    for (int c = 0; c < CM / 2; c++) vf[c] = __fmul2_rn(make_float2(wgt, wgt), gF[q][c]);
 #pragma unroll
                     for (int j = OFF + CM; j < VP; j++) v[j] = 0.f;
                     if (LIDAR) {
@@ -670,13 +696,18 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
 #pragma unroll
                     for (int j = 0; j < 8; j++) v[j] += t0[j];
 #pragma unroll
-                    for (int c = 0; c < CM; c++) v[OFF + c] += wgt * gF[q][c];
+                    for (int c = 0; c < CM / 2; c++) vf[c] = __ffma2_rn(make_float2(wgt, wgt), gF[q][c], vf[c]);
                     if (LIDAR) {
                         v[8] += drrs;
                         v[9] += drrs * tq;
                     }
                 }
                 T[q] = Ti;
+            }
+#pragma unroll
+            for (int c = 0; c < CM / 2; c++) {
+                v[OFF + 2 * c] = vf[c].x;
+                v[OFF + 2 * c + 1] = vf[c].y;
             }
             warp_transpose_reduce<VP>(v, lane);
             constexpr int M = reduce_left<VP>(), RG = 1 << reduce_plain<VP>();
