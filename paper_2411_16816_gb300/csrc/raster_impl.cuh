@@ -299,51 +299,62 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
     }
     for (int start = range.x; start < range.y; start += B) {
         if (__syncthreads_count(all_done) == NT) break;
-        if (start + (int)threadIdx.x < range.y)
+        if (start + (int)threadIdx.x < range.y) {
             stage_load<CM, B, LIDAR>(sm, in, tc.s, start + threadIdx.x, threadIdx.x, box);
+        } else {   // past the list: an entry no ray blends (dead, zero opacity)
+            sm.g0[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+            sm.g1[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (!LIDAR) sm.live[threadIdx.x] = 0;
+        }
         __syncthreads();
         if (!all_done) {
-            const int nb = min(B, range.y - start);
-            for (int k = 0; k < nb; k++) {
-                if (!LIDAR && !sm.live[k]) continue;   // alpha < 1/255 at every pixel of the tile
-                const float4 g0 = sm.g0[k], g1 = sm.g1[k];
-                all_done = true;
+            // entries in groups of four (the batch is padded with entries no ray blends);
+            // a thread leaves after the group in which its rays finished
+            const int nb4 = (min(B, range.y - start) + 3) & ~3;
+            for (int k0 = 0; k0 < nb4; k0 += 4) {
 #pragma unroll
-                for (int q = 0; q < PX; q++) {
-                    if (st[q].done) continue;
-                    if (COUNT) evals++;
-                    float dx, dy, G, a;
-                    bool cl;
-                    if (eval_alpha<LIDAR>(g0, g1, r[q], dx, dy, G, a, cl)) {
-                        const float Tn = st[q].T * (1.f - a);
-                        if (Tn < kTEps) {
-                            st[q].done = true;
-                            continue;
-                        }
-                        const float wgt = a * st[q].T;
-                        if (WANT_F) {   // packed FP32 pairs: each lane is the same fused multiply-add
-                            const float4* f4 = reinterpret_cast<const float4*>(sm.f + k * CM);
-                            const float2 w2 = make_float2(wgt, wgt);
+                for (int u = 0; u < 4; u++) {
+                    const int k = k0 + u;
+                    if (!LIDAR && !sm.live[k]) continue;   // alpha < 1/255 at every pixel of the tile
+                    const float4 g0 = sm.g0[k], g1 = sm.g1[k];
+                    all_done = true;
 #pragma unroll
-                            for (int c = 0; c < CM / 4; c++) {
-                                const float4 v = f4[c];
-                                F[q][2 * c] = __ffma2_rn(make_float2(v.x, v.y), w2, F[q][2 * c]);
-                                F[q][2 * c + 1] = __ffma2_rn(make_float2(v.z, v.w), w2, F[q][2 * c + 1]);
+                    for (int q = 0; q < PX; q++) {
+                        if (st[q].done) continue;
+                        if (COUNT) evals++;
+                        float dx, dy, G, a;
+                        bool cl;
+                        if (eval_alpha<LIDAR>(g0, g1, r[q], dx, dy, G, a, cl)) {
+                            const float Tn = st[q].T * (1.f - a);
+                            if (Tn < kTEps) {
+                                st[q].done = true;
+                                continue;
                             }
-                        }
-                        if (LIDAR) {
-                            const float rrs = sm.g2[k].x + sm.g2[k].y * r[q].t;
-                            st[q].de += rrs * wgt;
-                            if (!st[q].med && Tn < 0.5f) {
-                                st[q].dm = rrs;
-                                st[q].med = true;
+                            const float wgt = a * st[q].T;
+                            if (WANT_F) {   // packed FP32 pairs: each lane is the same fused multiply-add
+                                const float4* f4 = reinterpret_cast<const float4*>(sm.f + k * CM);
+                                const float2 w2 = make_float2(wgt, wgt);
+#pragma unroll
+                                for (int c = 0; c < CM / 4; c++) {
+                                    const float4 v = f4[c];
+                                    F[q][2 * c] = __ffma2_rn(make_float2(v.x, v.y), w2, F[q][2 * c]);
+                                    F[q][2 * c + 1] = __ffma2_rn(make_float2(v.z, v.w), w2, F[q][2 * c + 1]);
+                                }
                             }
-                            if (rrs < st[q].cut) st[q].los += a;   // line-of-sight term (App. B)
+                            if (LIDAR) {
+                                const float rrs = sm.g2[k].x + sm.g2[k].y * r[q].t;
+                                st[q].de += rrs * wgt;
+                                if (!st[q].med && Tn < 0.5f) {
+                                    st[q].dm = rrs;
+                                    st[q].med = true;
+                                }
+                                if (rrs < st[q].cut) st[q].los += a;   // line-of-sight term (App. B)
+                            }
+                            st[q].T = Tn;
+                            st[q].last = start + k - range.x + 1;
                         }
-                        st[q].T = Tn;
-                        st[q].last = start + k - range.x + 1;
+                        all_done = false;
                     }
-                    all_done = false;
                 }
                 if (all_done) break;
             }
