@@ -301,10 +301,14 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
         if (__syncthreads_count(all_done) == NT) break;
         if (start + (int)threadIdx.x < range.y) {
             stage_load<CM, B, LIDAR>(sm, in, tc.s, start + threadIdx.x, threadIdx.x, box);
-        } else {   // past the list: an entry no ray blends (dead, zero opacity)
+        } else {   // past the list: an entry no ray blends (dead, zero opacity, zero features)
             sm.g0[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
             sm.g1[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
             if (!LIDAR) sm.live[threadIdx.x] = 0;
+            if (LIDAR) sm.g2[threadIdx.x] = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < CM; c += 4)
+                *reinterpret_cast<float4*>(&sm.f[threadIdx.x * CM + c]) = make_float4(0.f, 0.f, 0.f, 0.f);
         }
         __syncthreads();
         if (!all_done) {
@@ -323,40 +327,40 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
                     all_done = true;
 #pragma unroll
                     for (int q = 0; q < PX; q++) {
-                        if (st[q].done) continue;
-                        if (COUNT) evals++;
+                        // Without branches: a ray that skips this Gaussian (finished, alpha
+                        // below 1/255, or stopping before T would fall under 1e-4) takes
+                        // weight 0, which leaves F, T and the ranges bit for bit unchanged.
+                        if (COUNT) evals += st[q].done ? 0 : 1;
                         float dx, dy, G, a;
                         bool cl;
-                        if (eval_alpha<LIDAR>(g0, g1, r[q], dx, dy, G, a, cl)) {
-                            const float Tn = st[q].T * (1.f - a);
-                            if (Tn < kTEps) {
-                                st[q].done = true;
-                                continue;
-                            }
-                            const float wgt = a * st[q].T;
-                            if (WANT_F) {   // packed FP32 pairs: each lane is the same fused multiply-add
-                                const float4* f4 = reinterpret_cast<const float4*>(sm.f + k * CM);
-                                const float2 w2 = make_float2(wgt, wgt);
+                        const bool hit = eval_alpha<LIDAR>(g0, g1, r[q], dx, dy, G, a, cl) && !st[q].done;
+                        const float Tn = st[q].T * (1.f - a);
+                        const bool stop = hit && Tn < kTEps;
+                        const bool blend = hit && !stop;
+                        st[q].done = st[q].done || stop;
+                        const float wgt = blend ? a * st[q].T : 0.f;
+                        if (WANT_F) {   // packed FP32 pairs: each lane is the same fused multiply-add
+                            const float4* f4 = reinterpret_cast<const float4*>(sm.f + k * CM);
+                            const float2 w2 = make_float2(wgt, wgt);
 #pragma unroll
-                                for (int c = 0; c < CM / 4; c++) {
-                                    const float4 v = f4[c];
-                                    F[q][2 * c] = __ffma2_rn(make_float2(v.x, v.y), w2, F[q][2 * c]);
-                                    F[q][2 * c + 1] = __ffma2_rn(make_float2(v.z, v.w), w2, F[q][2 * c + 1]);
-                                }
+                            for (int c = 0; c < CM / 4; c++) {
+                                const float4 v = f4[c];
+                                F[q][2 * c] = __ffma2_rn(make_float2(v.x, v.y), w2, F[q][2 * c]);
+                                F[q][2 * c + 1] = __ffma2_rn(make_float2(v.z, v.w), w2, F[q][2 * c + 1]);
                             }
-                            if (LIDAR) {
-                                const float rrs = sm.g2[k].x + sm.g2[k].y * r[q].t;
-                                st[q].de += rrs * wgt;
-                                if (!st[q].med && Tn < 0.5f) {
-                                    st[q].dm = rrs;
-                                    st[q].med = true;
-                                }
-                                if (rrs < st[q].cut) st[q].los += a;   // line-of-sight term (App. B)
-                            }
-                            st[q].T = Tn;
-                            st[q].last = start + k - range.x + 1;
                         }
-                        all_done = false;
+                        if (LIDAR) {
+                            const float rrs = sm.g2[k].x + sm.g2[k].y * r[q].t;
+                            st[q].de += rrs * wgt;
+                            if (blend && !st[q].med && Tn < 0.5f) {
+                                st[q].dm = rrs;
+                                st[q].med = true;
+                            }
+                            if (blend && rrs < st[q].cut) st[q].los += a;   // line-of-sight term (App. B)
+                        }
+                        st[q].T = blend ? Tn : st[q].T;
+                        st[q].last = blend ? start + k - range.x + 1 : st[q].last;
+                        all_done = all_done && st[q].done;
                     }
                 }
                 if (all_done) break;
