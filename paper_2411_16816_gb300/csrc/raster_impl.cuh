@@ -32,7 +32,7 @@ namespace splat {
 // always keeps at least one full warp.
 template <int CM, bool BWD, bool LIDAR, int RAYS>
 struct RaysPerThread {
-    static constexpr int want = (BWD && CM <= 16) ? (LIDAR ? 2 : 4) : 1;
+    static constexpr int want = (BWD && CM <= 16) ? (LIDAR ? 2 : 4) : ((!BWD && !LIDAR && CM <= 16) ? 2 : 1);
     static constexpr int value = want * 32 <= RAYS ? want : (2 * 32 <= RAYS ? 2 : 1);
 };
 
