@@ -370,8 +370,15 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
     return evals;
 }
 
+// Resident blocks the camera forward asks the register allocator for: 24 warps per SM.
+template <int CM, bool LIDAR, int NT>
+struct FwdMinBlocks {
+    static constexpr int value = (!LIDAR && CM <= 16 && NT <= 768) ? 768 / NT : 1;
+};
+
 template <int CM, int TW, int TH, bool LIDAR, bool COUNT, bool LIST = false>
-__global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, false, LIDAR, TW * TH>::value)
+__global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, false, LIDAR, TW * TH>::value,
+                                  FwdMinBlocks<CM, LIDAR, TW * TH / RaysPerThread<CM, false, LIDAR, TW * TH>::value>::value)
     k_raster_fwd(const __grid_constant__ Frame fr, RasterIn in, RasterOut out) {
     constexpr int PX = RaysPerThread<CM, false, LIDAR, TW * TH>::value;
     constexpr int NT = TW * TH / PX;
