@@ -529,19 +529,42 @@ __device__ __forceinline__ void warp_transpose_reduce(float (&v)[VP], int lane) 
         const bool upper = (lane & o) != 0;
         if (n >= 2 && n % 2 == 0) {
             const int h = n / 2;
+            float recv[VP / 2];
 #pragma unroll
             for (int i = 0; i < VP / 2; i++) {
                 if (i < h) {
                     const float send = upper ? v[i] : v[i + h];
-                    const float keep = upper ? v[i + h] : v[i];
-                    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+                    v[i] = upper ? v[i + h] : v[i];
+                    recv[i] = __shfl_xor_sync(0xffffffffu, send, o);
+                }
+            }
+            // the adds two at a time (packed FP32 pairs; the same IEEE additions)
+#pragma unroll
+            for (int i = 0; i + 1 < VP / 2; i += 2) {
+                if (i + 1 < h) {
+                    const float2 s2 = __fadd2_rn(make_float2(v[i], v[i + 1]), make_float2(recv[i], recv[i + 1]));
+                    v[i] = s2.x;
+                    v[i + 1] = s2.y;
+                } else if (i < h) {
+                    v[i] += recv[i];
                 }
             }
             n = h;
         } else {
+            float recv[VP];
 #pragma unroll
             for (int i = 0; i < VP; i++)
-                if (i < n) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+                if (i < n) recv[i] = __shfl_xor_sync(0xffffffffu, v[i], o);
+#pragma unroll
+            for (int i = 0; i + 1 < VP; i += 2) {
+                if (i + 1 < n) {
+                    const float2 s2 = __fadd2_rn(make_float2(v[i], v[i + 1]), make_float2(recv[i], recv[i + 1]));
+                    v[i] = s2.x;
+                    v[i + 1] = s2.y;
+                } else if (i < n) {
+                    v[i] += recv[i];
+                }
+            }
         }
     }
 }
