@@ -19,7 +19,8 @@ splat_status frame_sensor_constants(int32_t n_sensors, const splat_sensor* senso
 
 namespace splat {
 
-constexpr int kBatchThreads = 256;
+constexpr int kBatchThreads = 128;   // two rays per thread: one 256-ray tile per work item
+constexpr int kBatchPX = 2;
 constexpr int kMaxBatch = 1024;
 
 struct BatchReqDev {
@@ -49,6 +50,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 template <int CM, bool LIDAR>
 __device__ __forceinline__ void batch_tile(const BatchReqDev& B, int lt, unsigned char* smem_raw) {
+    constexpr int PX = kBatchPX;
     Stage<CM, kBatchThreads, LIDAR>& sm = *reinterpret_cast<Stage<CM, kBatchThreads, LIDAR>*>(smem_raw);
     const SensorDev& S = B.S;
     TileCtx tc;
@@ -56,43 +58,50 @@ __device__ __forceinline__ void batch_tile(const BatchReqDev& B, int lt, unsigne
     tc.tx = lt % S.tiles_x;
     tc.ty = lt / S.tiles_x;
     tc.gtile = S.tile_base + lt;
-    RayCtx r[1];
-    r[0] = ray_setup_rt<LIDAR>(S, tc.tx, tc.ty, threadIdx.x, S.tile_w, S.tile_h);
+    RayCtx r[PX];
+#pragma unroll
+    for (int q = 0; q < PX; q++)
+        r[q] = ray_setup_rt<LIDAR>(S, tc.tx, tc.ty, threadIdx.x + q * kBatchThreads, S.tile_w, S.tile_h);
     const RasterIn in{B.rec, B.ids, B.ranges, B.feat, B.n, B.C};
     const int2 range = in.ranges[tc.gtile];
     TileBox box{};
     if (!LIDAR) box = camera_tile_box(S, tc.tx, tc.ty, S.tile_w, S.tile_h);
-    float2 F[1][CM / 2];
+    float2 F[PX][CM / 2];
 #pragma unroll
-    for (int c = 0; c < CM / 2; c++) F[0][c] = make_float2(0.f, 0.f);
-    FwdState st[1];
+    for (int q = 0; q < PX; q++)
+#pragma unroll
+        for (int c = 0; c < CM / 2; c++) F[q][c] = make_float2(0.f, 0.f);
+    FwdState st[PX];
     // 16 x 16 only fixes the 256-ray batch size here; the ray layout comes from r[].
-    forward_tile<CM, 16, 16, LIDAR, 1, true>(sm, in, tc, box, r, range, st, F);
-    if (!r[0].inside) return;
-    const int64_t o = r[0].o;
+    forward_tile<CM, 16, 16, LIDAR, PX, true>(sm, in, tc, box, r, range, st, F);
     const int C = B.C;
-    float* fo = B.out_feat + o * C;
-    if ((C & 3) == 0) {
 #pragma unroll
-        for (int c = 0; c < CM; c += 4)
-            if (c < C)
-                *reinterpret_cast<float4*>(fo + c) =
-                    make_float4(F[0][c / 2].x, F[0][c / 2].y, F[0][c / 2 + 1].x, F[0][c / 2 + 1].y);
-    } else {
+    for (int q = 0; q < PX; q++) {
+        if (!r[q].inside) continue;
+        const int64_t o = r[q].o;
+        float* fo = B.out_feat + o * C;
+        if ((C & 3) == 0) {
 #pragma unroll
-        for (int c = 0; c < CM; c++)
-            if (c < C) fo[c] = (c & 1) ? F[0][c / 2].y : F[0][c / 2].x;
-    }
-    if (B.out_T) B.out_T[o] = st[0].T;
-    if (LIDAR) {
-        B.out_range_exp[o] = st[0].de;
-        if (B.out_range_med) B.out_range_med[o] = st[0].dm;
-        B.out_alpha[o] = 1.f - st[0].T;
+            for (int c = 0; c < CM; c += 4)
+                if (c < C)
+                    *reinterpret_cast<float4*>(fo + c) =
+                        make_float4(F[q][c / 2].x, F[q][c / 2].y, F[q][c / 2 + 1].x, F[q][c / 2 + 1].y);
+        } else {
+#pragma unroll
+            for (int c = 0; c < CM; c++)
+                if (c < C) fo[c] = (c & 1) ? F[q][c / 2].y : F[q][c / 2].x;
+        }
+        if (B.out_T) B.out_T[o] = st[q].T;
+        if (LIDAR) {
+            B.out_range_exp[o] = st[q].de;
+            if (B.out_range_med) B.out_range_med[o] = st[q].dm;
+            B.out_alpha[o] = 1.f - st[q].T;
+        }
     }
 }
 
 template <int CM>
-__global__ void __launch_bounds__(kBatchThreads) k_raster_batch(const BatchReqDev* __restrict__ tab, int n_req,
+__global__ void __launch_bounds__(kBatchThreads, 4) k_raster_batch(const BatchReqDev* __restrict__ tab, int n_req,
                                                                int64_t total, int* counters,
                                                                unsigned long long* stamps) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -173,7 +182,7 @@ splat_status splat_batch_build(const splat_batch_request* reqs, int32_t n_reques
         const splat_status st =
             frame_sensor_constants(in.group_n_sensors, in.group_sensors, in.group_sensor_index, &d.S);
         if (st != SPLAT_OK) return st;
-        if (d.S.tile_w * d.S.tile_h != kBatchThreads)
+        if (d.S.tile_w * d.S.tile_h != kBatchThreads * kBatchPX)
             return record_error(SPLAT_ERR_INVALID_ARG, "splat_batch_build: batched tiles must hold 256 rays");
         if (!in.proj.rec || !in.bins.isect_ids || !in.bins.tile_ranges || !in.features || !in.out_feat ||
             in.channels < 1 || in.channels > 32 || in.n < 0)
