@@ -193,6 +193,20 @@ __device__ __forceinline__ void load_x_frags(const float* __restrict__ x, int64_
     }
 }
 
+// The A-fragment elements of a 16-ray input tile, as loaded (FP32 pairs).
+__device__ __forceinline__ void load_x_raw(const float* __restrict__ x, int64_t r0, int64_t R, float2 (&v)[2][4]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int ks = 0; ks < 2; ks++) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int64_t r = r0 + g + ((q & 1) ? 8 : 0);
+            const int col = 16 * ks + ((q & 2) ? 8 : 0) + 2 * t;
+            v[ks][q] = r < R ? *reinterpret_cast<const float2*>(x + r * kHIn + col) : make_float2(0.f, 0.f);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kHeadThreads) k_head_fwd(const float* __restrict__ x, int64_t R, HeadW hw,
                                                            float* __restrict__ out) {
     __shared__ HeadSmemW s;
@@ -200,14 +214,25 @@ __global__ void __launch_bounds__(kHeadThreads) k_head_fwd(const float* __restri
     __syncthreads();
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int64_t tiles = (R + 15) / 16;
-    for (int64_t tile = (int64_t)blockIdx.x * kHeadWarps + (threadIdx.x >> 5); tile < tiles;
-         tile += (int64_t)gridDim.x * kHeadWarps) {
+    const int64_t stride = (int64_t)gridDim.x * kHeadWarps;
+    int64_t tile = (int64_t)blockIdx.x * kHeadWarps + (threadIdx.x >> 5);
+    float2 cur[2][4];
+    if (tile < tiles) load_x_raw(x, tile * 16, R, cur);
+    for (; tile < tiles; tile += stride) {
         const int64_t r0 = tile * 16;
+        float2 nxt[2][4];   // the next tile's inputs are in flight during this tile's MMAs
+        if (tile + stride < tiles) load_x_raw(x, (tile + stride) * 16, R, nxt);
         SplitA xa[2];
-        float xv[2][4][2];
-        load_x_frags(x, r0, R, xa, xv);
+#pragma unroll
+        for (int ks = 0; ks < 2; ks++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) split_pair(cur[ks][q].x, cur[ks][q].y, xa[ks].h[q], xa[ks].l[q]);
         HeadFwd f;
         head_forward_tile(s, xa, f);
+#pragma unroll
+        for (int ks = 0; ks < 2; ks++)
+#pragma unroll
+            for (int q = 0; q < 4; q++) cur[ks][q] = nxt[ks][q];
         if (t == 0) {
             if (r0 + g < R) reinterpret_cast<float2*>(out)[r0 + g] = make_float2(f.o[0], f.o[1]);
             if (r0 + g + 8 < R) reinterpret_cast<float2*>(out)[r0 + g + 8] = make_float2(f.o[2], f.o[3]);
