@@ -642,3 +642,56 @@ def test_opacity_aware_extent_lists_render_and_gradients():
     pg = fr.backward(gd, out, grads)
     torch.cuda.synchronize()
     U.check_grads(pg, U.oracle_grads(g, sensors, per))
+
+
+def _recorded_sweep(lid, seed, ranges=(5.0, 60.0)):
+    """Stand-in for a recorded sweep of the lidar: one return per grid cell, its direction
+    jittered within the cell, ranges uniform in `ranges`, capture times following the
+    spin, stored ego-motion compensated (the removal inverted exactly per point)."""
+    rng = np.random.default_rng(seed)
+    b, a = np.divmod(np.arange(lid.n_rays), lid.n_az)
+    elev = np.asarray(lid.beam_elev, np.float64)
+    de = np.gradient(elev)
+    phi = (a + 0.5 + rng.uniform(-0.5, 0.5, size=len(a))) * lid.az_res
+    om = elev[b] + rng.uniform(-0.45, 0.45, size=len(a)) * de[b]
+    r = rng.uniform(*ranges, size=len(a))
+    t = ((a + 0.5) / lid.n_az - 0.5) * lid.sweep_time
+    q = np.stack([r * np.cos(om) * np.cos(phi), r * np.cos(om) * np.sin(phi), r * np.sin(om)], 1)
+    v, w = np.asarray(lid.lin_vel, np.float64), np.asarray(lid.ang_vel, np.float64)
+    W = np.array([[0.0, -w[2], w[1]], [w[2], 0.0, -w[0]], [-w[1], w[0], 0.0]])
+    p = np.linalg.solve(np.eye(3)[None] - t[:, None, None] * W[None], (q + t[:, None] * v[None])[..., None])[..., 0]
+    return p.astype(np.float32), t.astype(np.float32)
+
+
+def test_full_driving_point_cloud_sampled_parity():
+    """App. A.2 at the benchmark's size: the driving frame's 32 x 1080 sweep as a point
+    cloud against the full frame's lists; a sample of the rays against the oracle."""
+    g, sensors = scenes.driving_frame()
+    k = next(i for i, s in enumerate(sensors) if s.kind == "lidar")
+    lid = sensors[k]
+    fr, gd, out = U.run(g, sensors)
+    pts, times = _recorded_sweep(lid, 31)
+    pr = fr.lidar_points_to_rays(k, torch.as_tensor(pts, device=U.DEV), torch.as_tensor(times, device=U.DEV))
+    b = fr.bin_rays(k, pr["rays"])
+    o = fr.render_rays(fr.c_gaussians(gd), k, pr["rays"], b)
+    torch.cuda.synchronize()
+    rays = pr["rays"].cpu().numpy().astype(np.float64)
+    sel = np.sort(np.random.default_rng(32).choice(len(rays), 160, replace=False))
+    ref = oracle.render(g, lid, sel=sel, free_rays=rays)
+    ok = ~ref["marginal"]
+    assert ok.mean() > 0.85 and (ref["count"][ok] > 0).sum() > 100
+    got = {key: v.cpu().numpy()[sel] for key, v in o.items() if v is not None}
+    np.testing.assert_allclose(got["feat"][ok], ref["F"][ok], atol=U.TOL_FEAT, rtol=0)
+    np.testing.assert_allclose(got["alpha"][ok], ref["alpha"][ok], atol=U.TOL_FEAT, rtol=0)
+    np.testing.assert_allclose(got["range_exp"][ok], ref["range_exp"][ok], rtol=U.TOL_RANGE, atol=U.TOL_RANGE)
+    np.testing.assert_allclose(got["range_med"][ok], ref["range_med"][ok], rtol=U.TOL_RANGE, atol=1e-5)
+
+
+def test_full_driving_frame_opacity_aware_sampled_parity():
+    """The opacity-aware extent on every sensor of the driving frame: sampled rays of each
+    sensor against the oracle with the same extent."""
+    g, sensors = scenes.driving_frame()
+    sensors = _opacity_aware(sensors)
+    fr, gd, out = U.run(g, sensors)
+    stats = U.check_render(fr, out, g, sensors, sel=_sample(sensors, 48, seed=3), max_marginal=0.25)
+    print("marginal fractions", stats)
