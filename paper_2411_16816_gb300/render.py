@@ -350,8 +350,9 @@ class Frame:
             L.call("splat_lidar_bin_rays", len(self.sensors), self.c_sensors, lidar, _vp(rays), n,
                    self._c_ray_bins(b), _stream(stream))
             return b
-        if priority is None or priority.shape != (n,) or priority.element_size() != 4:
-            raise ValueError("a capped grouping needs one 32-bit priority per ray")
+        int_types = (torch.int32,) + ((torch.uint32,) if hasattr(torch, "uint32") else ())
+        if priority is None or priority.shape != (n,) or priority.dtype not in int_types:
+            raise ValueError("a capped grouping needs one 32-bit integer priority per ray (read as unsigned)")
         priority = priority.contiguous()
         scratch = self._ray_bins(lidar, n)
         L.call("splat_lidar_bin_rays_capped", len(self.sensors), self.c_sensors, lidar, _vp(rays), _vp(priority), n,

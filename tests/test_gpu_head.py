@@ -152,7 +152,7 @@ def test_trained_head_beats_plain_composited_channels():
 
     head_rmse = np.sqrt(np.mean((1 / (1 + np.exp(-o[:, 0])) - yi_te) ** 2))
     head_pd = 1 / (1 + np.exp(-o[:, 1]))
-    # drop labels are Bernoulli draws: judge the predicted probability (held-out BCE) and
+    # drop labels are Bernoulli draws: score the predicted probability (held-out BCE) and
     # its decision against the noise-free one (p_drop > 0.5)
     head_bce, head_acc = bce(head_pd, yd_te), np.mean((head_pd > 0.5) == (pd_te > 0.5))
     # plain composited channels: the best linear read-out of the 29 rendered channels
