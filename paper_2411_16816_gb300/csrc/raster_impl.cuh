@@ -253,19 +253,50 @@ __device__ __forceinline__ float rcp_approx(float x) {
     return r;
 }
 
-// alpha of one staged Gaussian at the ray; returns false if it is skipped.
+// exp(x) as 2^(x log2 e) on the hardware base-2 exponential (ex2.approx, at most 2 ulp).
+__device__ __forceinline__ float exp2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+constexpr float kNegLog2e = -1.4426950408889634f;
+
+// alpha of one staged Gaussian at the ray; returns false if it is skipped.  Every step is
+// an explicitly rounded operation, in the order eval_alpha2 takes lane by lane, so the
+// single-ray and the paired evaluation give the same bits (the forward and the backward
+// then agree on every decision):
+//   d = p - (mean + v t),  sigma = d_x (a/2 d_x + b d_y) + (c/2 d_y) d_y,
+//   alpha = min(o' exp(-sigma), 0.999), blended if sigma >= 0 and alpha >= 1/255.
 template <bool LIDAR>
 __device__ __forceinline__ bool eval_alpha(const float4 g0, const float4 g1, const RayCtx& r, float& dx, float& dy,
                                            float& G, float& alpha, bool& clamped) {
-    dx = r.pa - (g0.x + g0.z * r.t);
-    dy = r.pb - (g0.y + g0.w * r.t);
+    dx = __fsub_rn(r.pa, __fmaf_rn(g0.z, r.t, g0.x));
+    dy = __fsub_rn(r.pb, __fmaf_rn(g0.w, r.t, g0.y));
     if (LIDAR) dx = wrap_pi(dx);
-    const float sig = 0.5f * (g1.x * dx * dx + g1.z * dy * dy) + g1.y * dx * dy;
-    G = __expf(-sig);
-    const float a = g1.w * G;
+    const float u = __fmaf_rn(__fmul_rn(0.5f, g1.x), dx, __fmul_rn(g1.y, dy));
+    const float sig = __fmaf_rn(dx, u, __fmul_rn(__fmul_rn(__fmul_rn(0.5f, g1.z), dy), dy));
+    G = exp2_approx(__fmul_rn(sig, kNegLog2e));
+    const float a = __fmul_rn(g1.w, G);
     clamped = a > kAlphaMax;
     alpha = clamped ? kAlphaMax : a;
     return sig >= 0.f && alpha >= kAlphaMin;
+}
+
+// Two rays of one thread against one staged Gaussian in packed FP32 pairs; lane q equals
+// eval_alpha for ray q bit for bit.  pa, pb, t hold the two rays' coordinates and times.
+template <bool LIDAR>
+__device__ __forceinline__ void eval_alpha2(const float4 g0, const float4 g1, float2 pa, float2 pb, float2 t,
+                                            float2& sig, float2& alpha) {
+    const float2 m1 = make_float2(-1.f, -1.f);
+    float2 dx = __ffma2_rn(__ffma2_rn(make_float2(g0.z, g0.z), t, make_float2(g0.x, g0.x)), m1, pa);
+    const float2 dy = __ffma2_rn(__ffma2_rn(make_float2(g0.w, g0.w), t, make_float2(g0.y, g0.y)), m1, pb);
+    if (LIDAR) dx = make_float2(wrap_pi(dx.x), wrap_pi(dx.y));
+    const float ha = __fmul_rn(0.5f, g1.x), hc = __fmul_rn(0.5f, g1.z);
+    const float2 u = __ffma2_rn(make_float2(ha, ha), dx, __fmul2_rn(make_float2(g1.y, g1.y), dy));
+    sig = __ffma2_rn(dx, u, __fmul2_rn(__fmul2_rn(make_float2(hc, hc), dy), dy));
+    const float2 e = __fmul2_rn(sig, make_float2(kNegLog2e, kNegLog2e));
+    const float2 a = __fmul2_rn(make_float2(g1.w, g1.w), make_float2(exp2_approx(e.x), exp2_approx(e.y)));
+    alpha = make_float2(fminf(a.x, kAlphaMax), fminf(a.y, kAlphaMax));
 }
 
 struct FwdState {
@@ -297,6 +328,13 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
         st[q].cut = (LIDAR && in.los_range && r[q].inside) ? in.los_range[r[q].o] - in.los_eps : -INFINITY;
         all_done &= st[q].done;
     }
+    float2 rpa[PX / 2 > 0 ? PX / 2 : 1], rpb[PX / 2 > 0 ? PX / 2 : 1], rt[PX / 2 > 0 ? PX / 2 : 1];   // ray pairs
+#pragma unroll
+    for (int qp = 0; qp < PX / 2; qp++) {
+        rpa[qp] = make_float2(r[2 * qp].pa, r[2 * qp + 1].pa);
+        rpb[qp] = make_float2(r[2 * qp].pb, r[2 * qp + 1].pb);
+        rt[qp] = make_float2(r[2 * qp].t, r[2 * qp + 1].t);
+    }
     for (int start = range.x; start < range.y; start += B) {
         if (__syncthreads_count(all_done) == NT) break;
         if (start + (int)threadIdx.x < range.y) {
@@ -325,20 +363,50 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
                     if (!LIDAR && !sm.live[k]) continue;   // alpha < 1/255 at every pixel of the tile
                     const float4 g0 = sm.g0[k], g1 = sm.g1[k];
                     all_done = true;
+                    // alpha, the transmittance after the Gaussian and the blend weight of
+                    // each ray; pairs of rays go through packed FP32 pairs
+                    float av[PX], Tnv[PX], wv[PX];
+                    bool ok[PX];
+                    if constexpr (PX % 2 == 0) {
+#pragma unroll
+                        for (int qp = 0; qp < PX / 2; qp++) {
+                            float2 sig2, a2;
+                            eval_alpha2<LIDAR>(g0, g1, rpa[qp], rpb[qp], rt[qp], sig2, a2);
+                            const float2 T2 = make_float2(st[2 * qp].T, st[2 * qp + 1].T);
+                            const float2 Tn2 =
+                                __fmul2_rn(T2, __ffma2_rn(a2, make_float2(-1.f, -1.f), make_float2(1.f, 1.f)));
+                            const float2 w2 = __fmul2_rn(a2, T2);
+                            av[2 * qp] = a2.x;
+                            av[2 * qp + 1] = a2.y;
+                            Tnv[2 * qp] = Tn2.x;
+                            Tnv[2 * qp + 1] = Tn2.y;
+                            wv[2 * qp] = w2.x;
+                            wv[2 * qp + 1] = w2.y;
+                            ok[2 * qp] = sig2.x >= 0.f && a2.x >= kAlphaMin;
+                            ok[2 * qp + 1] = sig2.y >= 0.f && a2.y >= kAlphaMin;
+                        }
+                    } else {
+#pragma unroll
+                        for (int q = 0; q < PX; q++) {
+                            float dx, dy, G;
+                            bool cl;
+                            ok[q] = eval_alpha<LIDAR>(g0, g1, r[q], dx, dy, G, av[q], cl);
+                            Tnv[q] = st[q].T * (1.f - av[q]);
+                            wv[q] = av[q] * st[q].T;
+                        }
+                    }
 #pragma unroll
                     for (int q = 0; q < PX; q++) {
                         // Without branches: a ray that skips this Gaussian (finished, alpha
                         // below 1/255, or stopping before T would fall under 1e-4) takes
                         // weight 0, which leaves F, T and the ranges bit for bit unchanged.
                         if (COUNT) evals += st[q].done ? 0 : 1;
-                        float dx, dy, G, a;
-                        bool cl;
-                        const bool hit = eval_alpha<LIDAR>(g0, g1, r[q], dx, dy, G, a, cl) && !st[q].done;
-                        const float Tn = st[q].T * (1.f - a);
+                        const float a = av[q], Tn = Tnv[q];
+                        const bool hit = ok[q] && !st[q].done;
                         const bool stop = hit && Tn < kTEps;
                         const bool blend = hit && !stop;
                         st[q].done = st[q].done || stop;
-                        const float wgt = blend ? a * st[q].T : 0.f;
+                        const float wgt = blend ? wv[q] : 0.f;
                         if (WANT_F) {   // packed FP32 pairs: each lane is the same fused multiply-add
                             const float4* f4 = reinterpret_cast<const float4*>(sm.f + k * CM);
                             const float2 w2 = make_float2(wgt, wgt);
