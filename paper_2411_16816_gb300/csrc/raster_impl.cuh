@@ -438,10 +438,10 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
     return evals;
 }
 
-// Resident blocks the camera forward asks the register allocator for: 24 warps per SM.
+// Resident blocks the camera forward asks the register allocator for: 20 warps per SM.
 template <int CM, bool LIDAR, int NT>
 struct FwdMinBlocks {
-    static constexpr int value = (!LIDAR && CM <= 16 && NT <= 768) ? 768 / NT : 1;
+    static constexpr int value = (!LIDAR && CM <= 16 && NT <= 640) ? 640 / NT : 1;
 };
 
 template <int CM, int TW, int TH, bool LIDAR, bool COUNT, bool LIST = false>
