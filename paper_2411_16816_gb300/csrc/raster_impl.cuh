@@ -286,16 +286,18 @@ __device__ __forceinline__ bool eval_alpha(const float4 g0, const float4 g1, con
 // eval_alpha for ray q bit for bit.  pa, pb, t hold the two rays' coordinates and times.
 template <bool LIDAR>
 __device__ __forceinline__ void eval_alpha2(const float4 g0, const float4 g1, float2 pa, float2 pb, float2 t,
-                                            float2& sig, float2& alpha) {
+                                            float2& sig, float2& alpha, float2& dx, float2& dy, float2& G,
+                                            float2& a) {
     const float2 m1 = make_float2(-1.f, -1.f);
-    float2 dx = __ffma2_rn(__ffma2_rn(make_float2(g0.z, g0.z), t, make_float2(g0.x, g0.x)), m1, pa);
-    const float2 dy = __ffma2_rn(__ffma2_rn(make_float2(g0.w, g0.w), t, make_float2(g0.y, g0.y)), m1, pb);
+    dx = __ffma2_rn(__ffma2_rn(make_float2(g0.z, g0.z), t, make_float2(g0.x, g0.x)), m1, pa);
+    dy = __ffma2_rn(__ffma2_rn(make_float2(g0.w, g0.w), t, make_float2(g0.y, g0.y)), m1, pb);
     if (LIDAR) dx = make_float2(wrap_pi(dx.x), wrap_pi(dx.y));
     const float ha = __fmul_rn(0.5f, g1.x), hc = __fmul_rn(0.5f, g1.z);
     const float2 u = __ffma2_rn(make_float2(ha, ha), dx, __fmul2_rn(make_float2(g1.y, g1.y), dy));
     sig = __ffma2_rn(dx, u, __fmul2_rn(__fmul2_rn(make_float2(hc, hc), dy), dy));
     const float2 e = __fmul2_rn(sig, make_float2(kNegLog2e, kNegLog2e));
-    const float2 a = __fmul2_rn(make_float2(g1.w, g1.w), make_float2(exp2_approx(e.x), exp2_approx(e.y)));
+    G = make_float2(exp2_approx(e.x), exp2_approx(e.y));
+    a = __fmul2_rn(make_float2(g1.w, g1.w), G);   // before the 0.999 clamp
     alpha = make_float2(fminf(a.x, kAlphaMax), fminf(a.y, kAlphaMax));
 }
 
@@ -370,8 +372,8 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
                     if constexpr (PX % 2 == 0) {
 #pragma unroll
                         for (int qp = 0; qp < PX / 2; qp++) {
-                            float2 sig2, a2;
-                            eval_alpha2<LIDAR>(g0, g1, rpa[qp], rpb[qp], rt[qp], sig2, a2);
+                            float2 sig2, a2, dx2, dy2, G2, au2;
+                            eval_alpha2<LIDAR>(g0, g1, rpa[qp], rpb[qp], rt[qp], sig2, a2, dx2, dy2, G2, au2);
                             const float2 T2 = make_float2(st[2 * qp].T, st[2 * qp + 1].T);
                             const float2 Tn2 =
                                 __fmul2_rn(T2, __ffma2_rn(a2, make_float2(-1.f, -1.f), make_float2(1.f, 1.f)));
@@ -674,6 +676,13 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
     TileCtx tc;
     RayCtx r[PX];
     if (!block_setup<TW, TH, LIDAR, LIST, PX, NT>(fr, in, tc, r)) return;
+    float2 rpa[PX / 2 > 0 ? PX / 2 : 1], rpb[PX / 2 > 0 ? PX / 2 : 1], rt[PX / 2 > 0 ? PX / 2 : 1];   // ray pairs
+#pragma unroll
+    for (int qp = 0; qp < PX / 2; qp++) {
+        rpa[qp] = make_float2(r[2 * qp].pa, r[2 * qp + 1].pa);
+        rpb[qp] = make_float2(r[2 * qp].pb, r[2 * qp + 1].pb);
+        rt[qp] = make_float2(r[2 * qp].t, r[2 * qp + 1].t);
+    }
     const int2 range = in.ranges[tc.gtile];
     const int len = range.y - range.x;
     TileBox box{};
@@ -747,83 +756,222 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
             if (idx >= wl) continue;   // warp-uniform: no ray of this warp blended this deep
             if (!LIDAR && !sm.live[k]) continue;   // no pixel of the tile can blend it
             const float4 g0 = sm.g0[k], g1 = sm.g1[k];
-            float dx[PX], dy[PX], G[PX], a[PX];
-            bool cl[PX], on[PX];
-            bool any = false;
-#pragma unroll
-            for (int q = 0; q < PX; q++) {
-                on[q] = eval_alpha<LIDAR>(g0, g1, r[q], dx[q], dy[q], G[q], a[q], cl[q]) && idx < last[q];
-                any |= on[q];
-            }
-            if (!__any_sync(0xffffffffu, any)) continue;
             float v[VP];
-            float2 vf[CM / 2];   // feature-gradient terms, accumulated as packed pairs
+            if constexpr (PX % 2 == 0) {
+                // pairs of rays in packed FP32 pairs: the same per-ray chain as below, two
+                // lanes at a time; the eight geometric terms are accumulated over the pairs
+                constexpr int NP = PX / 2;
+                float2 dx2[NP], dy2[NP], G2[NP], a2[NP];
+                bool on[PX], cl[PX];
+                bool any = false;
 #pragma unroll
-            for (int q = 0; q < PX; q++) {
-                // a ray that does not blend this Gaussian gets alpha = 0: every term vanishes
-                const float aq = on[q] ? a[q] : 0.f;
-                const float Gq = on[q] ? G[q] : 0.f;
-                const float inv = rcp_approx(1.f - aq);   // 1 - alpha >= 0.001: no special cases
-                const float Ti = T[q] * inv;
-                const float wgt = aq * Ti;
-                // sum_c gF_c f_c in two interleaved partial sums (packed FP32 pairs)
-                const float4* f4 = reinterpret_cast<const float4*>(sm.f + k * CM);
-                float2 g2 = make_float2(0.f, 0.f);
+                for (int qp = 0; qp < NP; qp++) {
+                    float2 sig2, au2;
+                    eval_alpha2<LIDAR>(g0, g1, rpa[qp], rpb[qp], rt[qp], sig2, a2[qp], dx2[qp], dy2[qp], G2[qp], au2);
+                    on[2 * qp] = sig2.x >= 0.f && a2[qp].x >= kAlphaMin && idx < last[2 * qp];
+                    on[2 * qp + 1] = sig2.y >= 0.f && a2[qp].y >= kAlphaMin && idx < last[2 * qp + 1];
+                    cl[2 * qp] = au2.x > kAlphaMax;
+                    cl[2 * qp + 1] = au2.y > kAlphaMax;
+                    any |= on[2 * qp] || on[2 * qp + 1];
+                }
+                if (!__any_sync(0xffffffffu, any)) continue;
+                const float2 m1 = make_float2(-1.f, -1.f);
+                float2 acc[LIDAR ? 10 : 8];
+                float2 vf[CM / 2];   // feature-gradient terms, accumulated as packed pairs
 #pragma unroll
-                for (int c = 0; c < CM / 4; c++) {
-                    const float4 fv = f4[c];
-                    g2 = __ffma2_rn(gF[q][2 * c], make_float2(fv.x, fv.y), g2);
-                    g2 = __ffma2_rn(gF[q][2 * c + 1], make_float2(fv.z, fv.w), g2);
+                for (int qp = 0; qp < NP; qp++) {
+                    const int q0 = 2 * qp, q1 = 2 * qp + 1;
+                    // a ray that does not blend this Gaussian gets alpha = 0: every term vanishes
+                    const float2 aq = make_float2(on[q0] ? a2[qp].x : 0.f, on[q1] ? a2[qp].y : 0.f);
+                    const float2 Gq = make_float2(on[q0] ? G2[qp].x : 0.f, on[q1] ? G2[qp].y : 0.f);
+                    const float2 om = __ffma2_rn(aq, m1, make_float2(1.f, 1.f));
+                    const float2 inv = make_float2(rcp_approx(om.x), rcp_approx(om.y));
+                    const float2 Ti = __fmul2_rn(make_float2(T[q0], T[q1]), inv);
+                    const float2 wgt = __fmul2_rn(aq, Ti);
+                    float Gf[2];
+#pragma unroll
+                    for (int j = 0; j < 2; j++) {   // sum_c gF_c f_c, two interleaved partial sums
+                        const float4* f4 = reinterpret_cast<const float4*>(sm.f + k * CM);
+                        float2 g2 = make_float2(0.f, 0.f);
+#pragma unroll
+                        for (int c = 0; c < CM / 4; c++) {
+                            const float4 fv = f4[c];
+                            g2 = __ffma2_rn(gF[q0 + j][2 * c], make_float2(fv.x, fv.y), g2);
+                            g2 = __ffma2_rn(gF[q0 + j][2 * c + 1], make_float2(fv.z, fv.w), g2);
+                        }
+                        Gf[j] = g2.x + g2.y;
+                    }
+                    const float2 S2 = make_float2(S[q0], S[q1]);
+                    const float2 dS = __ffma2_rn(S2, m1, make_float2(Gf[0], Gf[1]));   // Gf - S
+                    float2 dal = __ffma2_rn(Ti, dS, __fmul2_rn(make_float2(-gTT[q0], -gTT[q1]), inv));
+                    const float2 Sn = __ffma2_rn(aq, dS, S2);
+                    S[q0] = Sn.x;
+                    S[q1] = Sn.y;
+                    float2 drrs = make_float2(0.f, 0.f);
+                    if (LIDAR) {
+                        const float2 rrs = __ffma2_rn(make_float2(sm.g2[k].y, sm.g2[k].y), rt[qp],
+                                                      make_float2(sm.g2[k].x, sm.g2[k].x));
+                        const float2 SD2 = make_float2(SD[q0], SD[q1]);
+                        const float2 eD = __ffma2_rn(SD2, m1, rrs);   // r_rs - SD
+                        const float2 gD2 = make_float2(gD[q0], gD[q1]);
+                        dal = __ffma2_rn(__fmul2_rn(Ti, gD2), eD, dal);
+                        if (rrs.x < cut[q0]) dal.x += gL[q0];   // d(line-of-sight term) / d alpha
+                        if (rrs.y < cut[q1]) dal.y += gL[q1];
+                        const float2 SDn = __ffma2_rn(aq, eD, SD2);
+                        SD[q0] = SDn.x;
+                        SD[q1] = SDn.y;
+                        drrs = __fmul2_rn(gD2, wgt);
+                    }
+                    // clamped alpha (o' G > 0.999) passes no gradient to o' and the exponent
+                    const float2 dg = make_float2((on[q0] && !cl[q0]) ? dal.x : 0.f, (on[q1] && !cl[q1]) ? dal.y : 0.f);
+                    const float2 P = __fmul2_rn(dg, aq);   // -dL/dsigma
+                    const float2 Kx = __ffma2_rn(make_float2(g1.x, g1.x), dx2[qp],
+                                                 __fmul2_rn(make_float2(g1.y, g1.y), dy2[qp]));
+                    const float2 Ky = __ffma2_rn(make_float2(g1.y, g1.y), dx2[qp],
+                                                 __fmul2_rn(make_float2(g1.z, g1.z), dy2[qp]));
+                    const float2 nddx = __fmul2_rn(P, Kx), nddy = __fmul2_rn(P, Ky);   // -ddx, -ddy
+                    const float2 hx = __fmul2_rn(P, dx2[qp]), hy = __fmul2_rn(P, dy2[qp]);
+                    const float2 tq = rt[qp];
+                    if (qp == 0) {
+                        acc[0] = nddx;
+                        acc[1] = nddy;
+                        acc[2] = __fmul2_rn(nddx, tq);
+                        acc[3] = __fmul2_rn(nddy, tq);
+                        acc[4] = __fmul2_rn(hx, dx2[qp]);
+                        acc[5] = __fmul2_rn(hx, dy2[qp]);
+                        acc[6] = __fmul2_rn(hy, dy2[qp]);
+                        acc[7] = __fmul2_rn(dg, Gq);
+                        if constexpr (LIDAR) {
+                            acc[8] = drrs;
+                            acc[9] = __fmul2_rn(drrs, tq);
+                        }
+#pragma unroll
+                        for (int c = 0; c < CM / 2; c++) vf[c] = __fmul2_rn(make_float2(wgt.x, wgt.x), gF[q0][c]);
+                    } else {
+                        acc[0] = __fadd2_rn(acc[0], nddx);
+                        acc[1] = __fadd2_rn(acc[1], nddy);
+                        acc[2] = __ffma2_rn(nddx, tq, acc[2]);
+                        acc[3] = __ffma2_rn(nddy, tq, acc[3]);
+                        acc[4] = __ffma2_rn(hx, dx2[qp], acc[4]);
+                        acc[5] = __ffma2_rn(hx, dy2[qp], acc[5]);
+                        acc[6] = __ffma2_rn(hy, dy2[qp], acc[6]);
+                        acc[7] = __ffma2_rn(dg, Gq, acc[7]);
+                        if constexpr (LIDAR) {
+                            acc[8] = __fadd2_rn(acc[8], drrs);
+                            acc[9] = __ffma2_rn(drrs, tq, acc[9]);
+                        }
+#pragma unroll
+                        for (int c = 0; c < CM / 2; c++)
+                            vf[c] = __ffma2_rn(make_float2(wgt.x, wgt.x), gF[q0][c], vf[c]);
+                    }
+#pragma unroll
+                    for (int c = 0; c < CM / 2; c++) vf[c] = __ffma2_rn(make_float2(wgt.y, wgt.y), gF[q1][c], vf[c]);
+                    T[q0] = Ti.x;
+                    T[q1] = Ti.y;
                 }
-                const float Gf = g2.x + g2.y;
-                float dalpha = Ti * (Gf - S[q]) - gTT[q] * inv;
-                S[q] += aq * (Gf - S[q]);
-                float drrs = 0.f, tq = r[q].t;
-                if (LIDAR) {
-                    const float rrs = sm.g2[k].x + sm.g2[k].y * tq;
-                    dalpha += Ti * gD[q] * (rrs - SD[q]);
-                    if (rrs < cut[q]) dalpha += gL[q];   // d(line-of-sight term) / d alpha
-                    SD[q] += aq * (rrs - SD[q]);
-                    drrs = gD[q] * wgt;
+                // (-ddx, -ddy, -ddx t, -ddy t, dsig dx^2 / 2, dsig dx dy, dsig dy^2 / 2, dg G) summed
+                // over this thread's rays; dsig = -P
+                v[0] = acc[0].x + acc[0].y;
+                v[1] = acc[1].x + acc[1].y;
+                v[2] = acc[2].x + acc[2].y;
+                v[3] = acc[3].x + acc[3].y;
+                v[4] = -0.5f * (acc[4].x + acc[4].y);
+                v[5] = -(acc[5].x + acc[5].y);
+                v[6] = -0.5f * (acc[6].x + acc[6].y);
+                v[7] = acc[7].x + acc[7].y;
+#pragma unroll
+                for (int j = 8; j < OFF; j++) v[j] = 0.f;
+                if constexpr (LIDAR) {
+                    v[8] = acc[8].x + acc[8].y;
+                    v[9] = acc[9].x + acc[9].y;
                 }
-                // clamped alpha (o' G > 0.999) passes no gradient to o' and the exponent
-                const float dg = (on[q] && !cl[q]) ? dalpha : 0.f;
-                const float dsig = -dg * aq;
-                const float ddx = dsig * (g1.x * dx[q] + g1.y * dy[q]);
-                const float ddy = dsig * (g1.y * dx[q] + g1.z * dy[q]);
-                const float t0[8] = {-ddx, -ddy, -ddx * tq, -ddy * tq, dsig * 0.5f * dx[q] * dx[q],
-                                     dsig * dx[q] * dy[q], dsig * 0.5f * dy[q] * dy[q], dg * Gq};
                 // every pixel time carries the camera time offset; the mean moves by v t
-                if (!LIDAR && gr.dsensor) dtime += t0[0] * g0.z + t0[1] * g0.w;
-                if (q == 0) {
+                if (!LIDAR && gr.dsensor) dtime += v[0] * g0.z + v[1] * g0.w;
 #pragma unroll
-                    for (int j = 0; j < 8; j++) v[j] = t0[j];
-#pragma unroll
-                    for (int j = 8; j < OFF; j++) v[j] = 0.f;
-#pragma unroll
-                    for (int c = 0; c < CM / 2; c++) vf[c] = __fmul2_rn(make_float2(wgt, wgt), gF[q][c]);
-#pragma unroll
-                    for (int j = OFF + CM; j < VP; j++) v[j] = 0.f;
-                    if (LIDAR) {
-                        v[8] = drrs;
-                        v[9] = drrs * tq;
-                    }
-                } else {
-#pragma unroll
-                    for (int j = 0; j < 8; j++) v[j] += t0[j];
-#pragma unroll
-                    for (int c = 0; c < CM / 2; c++) vf[c] = __ffma2_rn(make_float2(wgt, wgt), gF[q][c], vf[c]);
-                    if (LIDAR) {
-                        v[8] += drrs;
-                        v[9] += drrs * tq;
-                    }
+                for (int c = 0; c < CM / 2; c++) {
+                    v[OFF + 2 * c] = vf[c].x;
+                    v[OFF + 2 * c + 1] = vf[c].y;
                 }
-                T[q] = Ti;
-            }
 #pragma unroll
-            for (int c = 0; c < CM / 2; c++) {
-                v[OFF + 2 * c] = vf[c].x;
-                v[OFF + 2 * c + 1] = vf[c].y;
+                for (int j = OFF + CM; j < VP; j++) v[j] = 0.f;
+            } else {
+                float dx[PX], dy[PX], G[PX], a[PX];
+                bool cl[PX], on[PX];
+                bool any = false;
+#pragma unroll
+                for (int q = 0; q < PX; q++) {
+                    on[q] = eval_alpha<LIDAR>(g0, g1, r[q], dx[q], dy[q], G[q], a[q], cl[q]) && idx < last[q];
+                    any |= on[q];
+                }
+                if (!__any_sync(0xffffffffu, any)) continue;
+                float2 vf[CM / 2];   // feature-gradient terms, accumulated as packed pairs
+#pragma unroll
+                for (int q = 0; q < PX; q++) {
+                    // a ray that does not blend this Gaussian gets alpha = 0: every term vanishes
+                    const float aq = on[q] ? a[q] : 0.f;
+                    const float Gq = on[q] ? G[q] : 0.f;
+                    const float inv = rcp_approx(1.f - aq);   // 1 - alpha >= 0.001: no special cases
+                    const float Ti = T[q] * inv;
+                    const float wgt = aq * Ti;
+                    // sum_c gF_c f_c in two interleaved partial sums (packed FP32 pairs)
+                    const float4* f4 = reinterpret_cast<const float4*>(sm.f + k * CM);
+                    float2 g2 = make_float2(0.f, 0.f);
+#pragma unroll
+                    for (int c = 0; c < CM / 4; c++) {
+                        const float4 fv = f4[c];
+                        g2 = __ffma2_rn(gF[q][2 * c], make_float2(fv.x, fv.y), g2);
+                        g2 = __ffma2_rn(gF[q][2 * c + 1], make_float2(fv.z, fv.w), g2);
+                    }
+                    const float Gf = g2.x + g2.y;
+                    float dalpha = Ti * (Gf - S[q]) - gTT[q] * inv;
+                    S[q] += aq * (Gf - S[q]);
+                    float drrs = 0.f, tq = r[q].t;
+                    if (LIDAR) {
+                        const float rrs = sm.g2[k].x + sm.g2[k].y * tq;
+                        dalpha += Ti * gD[q] * (rrs - SD[q]);
+                        if (rrs < cut[q]) dalpha += gL[q];   // d(line-of-sight term) / d alpha
+                        SD[q] += aq * (rrs - SD[q]);
+                        drrs = gD[q] * wgt;
+                    }
+                    // clamped alpha (o' G > 0.999) passes no gradient to o' and the exponent
+                    const float dg = (on[q] && !cl[q]) ? dalpha : 0.f;
+                    const float dsig = -dg * aq;
+                    const float ddx = dsig * (g1.x * dx[q] + g1.y * dy[q]);
+                    const float ddy = dsig * (g1.y * dx[q] + g1.z * dy[q]);
+                    const float t0[8] = {-ddx, -ddy, -ddx * tq, -ddy * tq, dsig * 0.5f * dx[q] * dx[q],
+                                         dsig * dx[q] * dy[q], dsig * 0.5f * dy[q] * dy[q], dg * Gq};
+                    // every pixel time carries the camera time offset; the mean moves by v t
+                    if (!LIDAR && gr.dsensor) dtime += t0[0] * g0.z + t0[1] * g0.w;
+                    if (q == 0) {
+#pragma unroll
+                        for (int j = 0; j < 8; j++) v[j] = t0[j];
+#pragma unroll
+                        for (int j = 8; j < OFF; j++) v[j] = 0.f;
+#pragma unroll
+                        for (int c = 0; c < CM / 2; c++) vf[c] = __fmul2_rn(make_float2(wgt, wgt), gF[q][c]);
+#pragma unroll
+                        for (int j = OFF + CM; j < VP; j++) v[j] = 0.f;
+                        if (LIDAR) {
+                            v[8] = drrs;
+                            v[9] = drrs * tq;
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 8; j++) v[j] += t0[j];
+#pragma unroll
+                        for (int c = 0; c < CM / 2; c++) vf[c] = __ffma2_rn(make_float2(wgt, wgt), gF[q][c], vf[c]);
+                        if (LIDAR) {
+                            v[8] += drrs;
+                            v[9] += drrs * tq;
+                        }
+                    }
+                    T[q] = Ti;
+                }
+#pragma unroll
+                for (int c = 0; c < CM / 2; c++) {
+                    v[OFF + 2 * c] = vf[c].x;
+                    v[OFF + 2 * c + 1] = vf[c].y;
+                }
             }
             warp_transpose_reduce<VP>(v, lane);
             constexpr int M = reduce_left<VP>(), RG = 1 << reduce_plain<VP>();
