@@ -84,6 +84,10 @@ class Frame:
         self.grad_proj = None
         self.los = None           # line-of-sight term: (return range per lidar ray, eps) or None
         self.version = 0
+        # the lidar raster launches (a few hundred blocks) run beside the camera launches on
+        # a second stream, filling the SMs the camera grid leaves idle
+        self.overlap_kinds = True
+        self._side = None
 
     # -- set-up ------------------------------------------------------------------------
     def _fill_sensor(self, c, s):
@@ -172,15 +176,43 @@ class Frame:
             out["lid_last"] = torch.empty(R, dtype=torch.int32, device=dev) if keep_state else None
         return out
 
+    def _fork(self, stream):
+        """(main stream handle, lidar stream handle, join) -- the lidar launches go to a
+        second stream ordered after everything before on `stream`; join() makes `stream`
+        wait for them."""
+        main = torch.cuda.current_stream(self.device) if stream is None else stream
+        if not (self.overlap_kinds and self.cam_idx and self.lid_idx):
+            h = ctypes.c_void_p(main.cuda_stream)
+            return h, h, lambda: None
+        if self._side is None:
+            self._side = torch.cuda.Stream(device=self.device)
+        side = self._side
+        side.wait_stream(main)
+
+        def join():
+            main.wait_stream(side)
+        return ctypes.c_void_p(main.cuda_stream), ctypes.c_void_p(side.cuda_stream), join
+
     def rasterize(self, cg, out: dict, stream=None, evaluated: torch.Tensor | None = None, cam_l1=None):
         """Camera and lidar raster launches.  `evaluated` (optional int64[2] device tensor)
         accumulates the examined (ray, Gaussian) pairs of the camera and lidar launch.
         `cam_l1` = (target, scale, grad, loss) fuses the camera L1 term into the camera
         launch: loss += scale * sum |F - target| and grad = scale * sign(F - target)."""
-        st = _stream(stream)
+        if self.lid_idx and self.los is not None and out.get("lid_los") is None:
+            out["lid_los"] = torch.empty(self.lid_rays, dtype=torch.float32, device=self.device)
+        st, st_l, join = self._fork(stream)
         ev_c = ev_l = None
         if evaluated is not None:
             ev_c, ev_l = evaluated[0:1], evaluated[1:2]
+        if self.lid_idx and self.los is not None:
+            L.call("splat_render_lidar_los", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
+                   self.c_bins(), _vp(out["lid_feat"]), _vp(out["lid_range_exp"]), _vp(out["lid_range_med"]),
+                   _vp(out["lid_alpha"]), _vp(out.get("lid_T")), _vp(out.get("lid_last")), self._c_los(),
+                   _vp(out["lid_los"]), _vp(ev_l), st_l)
+        elif self.lid_idx:
+            L.call("splat_render_lidar", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
+                   self.c_bins(), _vp(out["lid_feat"]), _vp(out["lid_range_exp"]), _vp(out["lid_range_med"]),
+                   _vp(out["lid_alpha"]), _vp(out.get("lid_T")), _vp(out.get("lid_last")), _vp(ev_l), st_l)
         if self.cam_idx and cam_l1 is not None:
             target, scale, grad, loss = cam_l1
             L.call("splat_render_camera_l1", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
@@ -189,17 +221,7 @@ class Frame:
         elif self.cam_idx:
             L.call("splat_render_camera", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
                    self.c_bins(), _vp(out["cam_feat"]), _vp(out["cam_T"]), _vp(out.get("cam_last")), _vp(ev_c), st)
-        if self.lid_idx and self.los is not None:
-            if out.get("lid_los") is None:
-                out["lid_los"] = torch.empty(self.lid_rays, dtype=torch.float32, device=self.device)
-            L.call("splat_render_lidar_los", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
-                   self.c_bins(), _vp(out["lid_feat"]), _vp(out["lid_range_exp"]), _vp(out["lid_range_med"]),
-                   _vp(out["lid_alpha"]), _vp(out.get("lid_T")), _vp(out.get("lid_last")), self._c_los(),
-                   _vp(out["lid_los"]), _vp(ev_l), st)
-        elif self.lid_idx:
-            L.call("splat_render_lidar", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
-                   self.c_bins(), _vp(out["lid_feat"]), _vp(out["lid_range_exp"]), _vp(out["lid_range_med"]),
-                   _vp(out["lid_alpha"]), _vp(out.get("lid_T")), _vp(out.get("lid_last")), _vp(ev_l), st)
+        join()
 
     def set_line_of_sight(self, target_range: torch.Tensor | None, eps: float = 0.8):
         """Enable (or with None disable) the line-of-sight term of App. B: the lidar
@@ -274,34 +296,44 @@ class Frame:
         else:
             for v in param_grads.values():
                 v.zero_()
+        # upstream buffers on the calling stream first; then the lidar backward beside the
+        # camera backward (disjoint sensor slices of grad_proj; the feature gradients are
+        # atomic sums), joined before the projection backward
+        dFc = dFl = dlos = None
         if self.cam_idx:
-            dF = grads.get("cam_feat")
-            if dF is None:
-                dF = torch.zeros((self.cam_rays, self.channels), dtype=torch.float32, device=dev)
-            L.call("splat_render_camera_backward", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
-                   self.c_bins(), _vp(out.get("cam_T") if out.get("cam_last") is not None else None),
-                   _vp(out.get("cam_last")), _vp(dF.contiguous()), _vp(grads.get("cam_T")), _vp(self.grad_proj),
-                   _vp(param_grads["features"]), _vp(sensor_grads), st)
+            dFc = grads.get("cam_feat")
+            dFc = torch.zeros((self.cam_rays, self.channels), dtype=torch.float32, device=dev) if dFc is None \
+                else dFc.contiguous()
         if self.lid_idx:
-            dF = grads.get("lid_feat")
-            if dF is None:
-                dF = torch.zeros((self.lid_rays, self.channels), dtype=torch.float32, device=dev)
-            keep = out.get("lid_last") is not None
+            dFl = grads.get("lid_feat")
+            dFl = torch.zeros((self.lid_rays, self.channels), dtype=torch.float32, device=dev) if dFl is None \
+                else dFl.contiguous()
             dlos = grads.get("lid_los")
             if dlos is not None:
                 if self.los is None:
                     raise ValueError("grads['lid_los'] needs set_line_of_sight() before the forward")
+                dlos = dlos.contiguous()
+        st, st_l, join = self._fork(stream)
+        if self.lid_idx:
+            keep = out.get("lid_last") is not None
+            if dlos is not None:
                 L.call("splat_render_lidar_backward_los", ctypes.byref(cg), len(self.sensors), self.c_sensors,
                        self.c_proj(), self.c_bins(), _vp(out.get("lid_T") if keep else None),
-                       _vp(out.get("lid_last") if keep else None), _vp(dF.contiguous()),
+                       _vp(out.get("lid_last") if keep else None), _vp(dFl),
                        _vp(grads.get("lid_range_exp")), _vp(grads.get("lid_alpha")), self._c_los(),
-                       _vp(dlos.contiguous()), _vp(self.grad_proj), _vp(param_grads["features"]), st)
+                       _vp(dlos), _vp(self.grad_proj), _vp(param_grads["features"]), st_l)
             else:
                 L.call("splat_render_lidar_backward", ctypes.byref(cg), len(self.sensors), self.c_sensors,
                        self.c_proj(), self.c_bins(), _vp(out.get("lid_T") if keep else None),
-                       _vp(out.get("lid_last") if keep else None), _vp(dF.contiguous()),
+                       _vp(out.get("lid_last") if keep else None), _vp(dFl),
                        _vp(grads.get("lid_range_exp")), _vp(grads.get("lid_alpha")), _vp(self.grad_proj),
-                       _vp(param_grads["features"]), st)
+                       _vp(param_grads["features"]), st_l)
+        if self.cam_idx:
+            L.call("splat_render_camera_backward", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
+                   self.c_bins(), _vp(out.get("cam_T") if out.get("cam_last") is not None else None),
+                   _vp(out.get("cam_last")), _vp(dFc), _vp(grads.get("cam_T")), _vp(self.grad_proj),
+                   _vp(param_grads["features"]), _vp(sensor_grads), st)
+        join()
         L.call("splat_project_backward", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(),
                _vp(self.grad_proj), _vp(param_grads["means"]), _vp(param_grads["scales"]),
                _vp(param_grads["quats"]), _vp(param_grads["opacities"]), _vp(param_grads.get("velocities")),
