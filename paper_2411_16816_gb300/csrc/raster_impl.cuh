@@ -164,7 +164,9 @@ struct Stage {
     float4 g1[B];
     float2 g2[LIDAR ? B : 1];
     uint32_t id[B];
-    int live[LIDAR ? 1 : B];   // camera: the Gaussian can reach alpha >= 1/255 somewhere in this tile
+    // camera: the Gaussian can reach alpha >= 1/255 somewhere in this tile (backward
+    // staging); the forward stages only such entries and keeps their list positions here
+    int live[LIDAR ? 1 : B];
     alignas(16) float f[B * CM];
 };
 
@@ -337,32 +339,85 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
         rpb[qp] = make_float2(r[2 * qp].pb, r[2 * qp + 1].pb);
         rt[qp] = make_float2(r[2 * qp].t, r[2 * qp + 1].t);
     }
+    // entries in groups of GU (each batch is padded with entries no ray blends); a thread
+    // leaves after the group in which its rays finished.  Measured best: 8 for cameras, 4
+    // for lidars.
+    constexpr int GU = LIDAR ? 4 : 8;
+    static_assert(B % GU == 0, "batches hold whole groups");
+    __shared__ int s_wlive[NT / 32 > 0 ? NT / 32 : 1];
     for (int start = range.x; start < range.y; start += B) {
         if (__syncthreads_count(all_done) == NT) break;
-        if (start + (int)threadIdx.x < range.y) {
-            stage_load<CM, B, LIDAR>(sm, in, tc.s, start + threadIdx.x, threadIdx.x, box);
-        } else {   // past the list: an entry no ray blends (dead, zero opacity, zero features)
-            sm.g0[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
-            sm.g1[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (!LIDAR) sm.live[threadIdx.x] = 0;
-            if (LIDAR) sm.g2[threadIdx.x] = make_float2(0.f, 0.f);
+        int nbg;   // staged entries of this batch, padded to whole groups
+        if constexpr (!LIDAR) {
+            // camera: only the entries that can reach alpha >= 1/255 somewhere in the tile are
+            // staged, packed to the front in list order; live[] keeps each one's list position
+            const int j = start + (int)threadIdx.x;
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            uint32_t id = 0;
+            float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
+            bool lv = false;
+            if (j < range.y) {
+                id = in.ids[j];
+                g0 = in.rec[rec_index(tc.s, 0, in.n, id)];
+                g1 = in.rec[rec_index(tc.s, 1, in.n, id)];
+                lv = tile_live(g0, g1, box);
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, lv);
+            if (lane == 0) s_wlive[warp] = __popc(bal);
+            __syncthreads();
+            int slot = __popc(bal & ((1u << lane) - 1u)), nlive = 0;
 #pragma unroll
-            for (int c = 0; c < CM; c += 4)
-                *reinterpret_cast<float4*>(&sm.f[threadIdx.x * CM + c]) = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int w = 0; w < NT / 32; w++) {
+                const int c = s_wlive[w];
+                slot += w < warp ? c : 0;
+                nlive += c;
+            }
+            if (lv) {
+                sm.g0[slot] = g0;
+                sm.g1[slot] = g1;
+                sm.id[slot] = id;
+                sm.live[slot] = j - range.x;
+                const int C = in.C;
+                const float* fp = in.feat + (int64_t)id * C;
+                if ((C & 3) == 0) {
+#pragma unroll
+                    for (int c = 0; c < CM; c += 4)
+                        if (c < C)
+                            *reinterpret_cast<float4*>(&sm.f[slot * CM + c]) = *reinterpret_cast<const float4*>(fp + c);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < CM; c++)
+                        if (c < C) sm.f[slot * CM + c] = fp[c];
+                }
+            }
+            nbg = (nlive + GU - 1) / GU * GU;
+            if ((int)threadIdx.x >= nlive && (int)threadIdx.x < nbg) {   // padding: no ray blends it
+                sm.g0[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+                sm.g1[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+                sm.live[threadIdx.x] = 0;
+#pragma unroll
+                for (int c = 0; c < CM; c += 4)
+                    *reinterpret_cast<float4*>(&sm.f[threadIdx.x * CM + c]) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        } else {
+            if (start + (int)threadIdx.x < range.y) {
+                stage_load<CM, B, LIDAR>(sm, in, tc.s, start + threadIdx.x, threadIdx.x, box);
+            } else {   // past the list: an entry no ray blends (zero opacity, zero features)
+                sm.g0[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+                sm.g1[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+                sm.g2[threadIdx.x] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int c = 0; c < CM; c += 4)
+                    *reinterpret_cast<float4*>(&sm.f[threadIdx.x * CM + c]) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            nbg = (min(B, range.y - start) + GU - 1) / GU * GU;
         }
         __syncthreads();
         if (!all_done) {
-            // entries in groups of GU (the batch is padded with entries no ray blends); a
-            // thread leaves after the group in which its rays finished.  Measured best:
-            // 8 for cameras, 4 for lidars.
-            constexpr int GU = LIDAR ? 4 : 8;
-            static_assert(B % GU == 0, "batches hold whole groups");
-            const int nbg = (min(B, range.y - start) + GU - 1) / GU * GU;
             for (int k0 = 0; k0 < nbg; k0 += GU) {
 #pragma unroll
                 for (int u = 0; u < GU; u++) {
                     const int k = k0 + u;
-                    if (!LIDAR && !sm.live[k]) continue;   // alpha < 1/255 at every pixel of the tile
                     const float4 g0 = sm.g0[k], g1 = sm.g1[k];
                     all_done = true;
                     // alpha, the transmittance after the Gaussian and the blend weight of
@@ -429,7 +484,7 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
                             if (blend && rrs < st[q].cut) st[q].los += a;   // line-of-sight term (App. B)
                         }
                         st[q].T = blend ? Tn : st[q].T;
-                        st[q].last = blend ? start + k - range.x + 1 : st[q].last;
+                        st[q].last = blend ? (LIDAR ? start + k - range.x : sm.live[k]) + 1 : st[q].last;
                         all_done = all_done && st[q].done;
                     }
                 }
