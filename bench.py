@@ -443,7 +443,7 @@ def run_ours(args):
     peak = fp32_peak if bound == "alu" else peaks["hbm_gbs"]
     # DRAM bytes per launch from ncu captures of the current kernels (one camera of the
     # driving scene, scaled by the six cameras of the frame; profiles/ holds the captures)
-    traffic = {"raster_camera_bwd": 6 * 159.65e6} if args.workload == "driving" else {}
+    traffic = {"raster_camera_bwd": 6 * 159.33e6} if args.workload == "driving" else {}
     roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "traffic": traffic.get(dom),
                 "peak_source": (f"FP32 FMA 152x128x2 at {peaks['sm_max_mhz']:.0f} MHz" if bound == "alu"
