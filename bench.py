@@ -260,14 +260,13 @@ def run_ours(args):
     if need * 1.05 > fr.capacity:
         fr._alloc_capacity(int(need * 1.1))
     out = fr.forward(gd, check=True)
-    grads = {"cam_feat": torch.empty_like(out["cam_feat"]), "lid_feat": torch.empty_like(out["lid_feat"]),
-             "lid_range_exp": torch.empty_like(out["lid_range_exp"])}
+    grads = {k: torch.empty_like(out[k]) for k in ("cam_feat", "lid_feat", "lid_range_exp") if k in out}
     pgrads = {k: torch.zeros_like(v) for k, v in gd.items() if v is not None}
     loss = torch.zeros(1, device=dev)
     # the camera L1 term is fused into the camera raster launch; the lidar terms run as
     # separate element-wise launches
     cam_l1 = (tgt["cam_feat"], 1.0 / out["cam_feat"].numel(), grads["cam_feat"], loss) if "cam_feat" in tgt else None
-    l1_terms = [("lid_feat", 1.0 / out["lid_feat"].numel()), ("lid_range_exp", 1.0 / out["lid_range_exp"].numel())]
+    l1_terms = [(k, 1.0 / out[k].numel()) for k in ("lid_feat", "lid_range_exp") if k in out]
     stream = torch.cuda.current_stream()
 
     def step(src=None, tg=None):
@@ -399,23 +398,28 @@ def run_ours(args):
     S = len(fr.sensors)
     timed("project", lambda: fr.project(cg))
     timed("bin_sort", lambda: fr.bin_sort())
-    timed("raster_camera_fwd", lambda: L.call("splat_render_camera_l1", ctypes.byref(cg), S, fr.c_sensors,
-                                                fr.c_proj(), fr.c_bins(), _vp(tgt["cam_feat"]), float(cam_l1[1]),
-                                                _vp(out["cam_feat"]), _vp(out["cam_T"]), _vp(out["cam_last"]),
-                                                _vp(grads["cam_feat"]), _vp(loss), None, st))
-    timed("raster_lidar_fwd", lambda: L.call("splat_render_lidar", ctypes.byref(cg), S, fr.c_sensors, fr.c_proj(),
-                                               fr.c_bins(), _vp(out["lid_feat"]), _vp(out["lid_range_exp"]),
-                                               _vp(out["lid_range_med"]), _vp(out["lid_alpha"]), _vp(out["lid_T"]),
-                                               _vp(out["lid_last"]), None, st))
+    if fr.cam_idx:
+        timed("raster_camera_fwd", lambda: L.call("splat_render_camera_l1", ctypes.byref(cg), S, fr.c_sensors,
+                                                    fr.c_proj(), fr.c_bins(), _vp(tgt["cam_feat"]), float(cam_l1[1]),
+                                                    _vp(out["cam_feat"]), _vp(out["cam_T"]), _vp(out["cam_last"]),
+                                                    _vp(grads["cam_feat"]), _vp(loss), None, st))
+    if fr.lid_idx:
+        timed("raster_lidar_fwd", lambda: L.call("splat_render_lidar", ctypes.byref(cg), S, fr.c_sensors,
+                                                   fr.c_proj(), fr.c_bins(), _vp(out["lid_feat"]),
+                                                   _vp(out["lid_range_exp"]), _vp(out["lid_range_med"]),
+                                                   _vp(out["lid_alpha"]), _vp(out["lid_T"]), _vp(out["lid_last"]),
+                                                   None, st))
     fr.grad_proj.zero_()
-    timed("raster_camera_bwd", lambda: L.call("splat_render_camera_backward", ctypes.byref(cg), S, fr.c_sensors,
-                                                fr.c_proj(), fr.c_bins(), _vp(out["cam_T"]), _vp(out["cam_last"]),
-                                                _vp(grads["cam_feat"]), None, _vp(fr.grad_proj),
-                                                _vp(pgrads["features"]), None, st))
-    timed("raster_lidar_bwd", lambda: L.call("splat_render_lidar_backward", ctypes.byref(cg), S, fr.c_sensors,
-                                               fr.c_proj(), fr.c_bins(), _vp(out["lid_T"]), _vp(out["lid_last"]),
-                                               _vp(grads["lid_feat"]), _vp(grads["lid_range_exp"]), None,
-                                               _vp(fr.grad_proj), _vp(pgrads["features"]), st))
+    if fr.cam_idx:
+        timed("raster_camera_bwd", lambda: L.call("splat_render_camera_backward", ctypes.byref(cg), S, fr.c_sensors,
+                                                    fr.c_proj(), fr.c_bins(), _vp(out["cam_T"]), _vp(out["cam_last"]),
+                                                    _vp(grads["cam_feat"]), None, _vp(fr.grad_proj),
+                                                    _vp(pgrads["features"]), None, st))
+    if fr.lid_idx:
+        timed("raster_lidar_bwd", lambda: L.call("splat_render_lidar_backward", ctypes.byref(cg), S, fr.c_sensors,
+                                                   fr.c_proj(), fr.c_bins(), _vp(out["lid_T"]), _vp(out["lid_last"]),
+                                                   _vp(grads["lid_feat"]), _vp(grads["lid_range_exp"]), None,
+                                                   _vp(fr.grad_proj), _vp(pgrads["features"]), st))
     timed("project_bwd", lambda: L.call("splat_project_backward", ctypes.byref(cg), S, fr.c_sensors, fr.c_proj(),
                                           _vp(fr.grad_proj), _vp(pgrads["means"]), _vp(pgrads["scales"]),
                                           _vp(pgrads["quats"]), _vp(pgrads["opacities"]),
