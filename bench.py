@@ -217,6 +217,23 @@ def fp32_peak_tflops(sm_mhz):
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The slowest rank's value (weak scaling: the job takes as long as its slowest rank);
+    x itself outside a process group of more than one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(rays_per_rank_step: float, world: int, seconds_per_step: float) -> float:
+    """Whole-job rays/s: every rank renders its own frame replica each step."""
+    return world * rays_per_rank_step / seconds_per_step
+
+
 def launches_per_step(fr, n_l1):
     """Kernels libsplat launches in one training step (counted from the call sequence)."""
     total_tiles = fr.total_tiles
@@ -321,14 +338,10 @@ def run_ours(args):
             dist.barrier()
         wall = time.perf_counter() - wall0
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = statistics.mean(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(statistics.mean(step_ms), dev)
     overflow = int(fr.n_isect.item()) > fr.capacity
     rays = desc["rays_per_step"]
-    value = world * rays / (ms * 1e-3)
+    value = job_throughput(rays, world, ms * 1e-3)
 
     # ---- end to end through the public API with host buffers ----
     # Every step copies its inputs (Gaussian parameters and target images) from pinned host
@@ -378,12 +391,8 @@ def run_ours(args):
     t0 = time.perf_counter()
     run_e2e(args.warmup, n_e2e)
     torch.cuda.synchronize()
-    e2e_wall = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_wall], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_wall = float(t.item())
-    e2e = {"value": world * rays * args.steps / e2e_wall, "unit": UNIT, "h2d_bytes_per_step": h2d,
+    e2e_wall = max_over_ranks(time.perf_counter() - t0, dev)
+    e2e = {"value": job_throughput(rays, world, e2e_wall / args.steps), "unit": UNIT, "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": 4,
            "pipelining": "inputs double-buffered, copies on a second stream, the step replayed from a CUDA graph"}
 
