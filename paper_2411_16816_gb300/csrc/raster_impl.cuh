@@ -340,9 +340,9 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
         rt[qp] = make_float2(r[2 * qp].t, r[2 * qp + 1].t);
     }
     // entries in groups of GU (each batch is padded with entries no ray blends); a thread
-    // leaves after the group in which its rays finished.  Measured best: 8 for cameras, 4
-    // for lidars.
-    constexpr int GU = LIDAR ? 4 : 8;
+    // leaves after the group in which its rays finished.  Measured best: 4 (2, 8 and 16
+    // are slower on the camera forward).
+    constexpr int GU = 4;
     static_assert(B % GU == 0, "batches hold whole groups");
     __shared__ int s_wlive[NT / 32 > 0 ? NT / 32 : 1];
     for (int start = range.x; start < range.y; start += B) {
