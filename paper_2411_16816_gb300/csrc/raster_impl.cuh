@@ -27,9 +27,9 @@ namespace splat {
 
 // Rays per thread.  The camera backward takes four rays per thread for up to 16 channels
 // (two for the lidar), so one warp reduction of a Gaussian's gradient covers 128 (64)
-// rays; the forward keeps one ray per thread (its per-Gaussian cost is small and occupancy
-// matters more); wide channel counts keep one ray per thread for register room.  A block
-// always keeps at least one full warp.
+// rays; the camera forward takes two (evaluated as a packed pair), the lidar forward one
+// (its rays terminate early and it needs the occupancy); wide channel counts keep one ray
+// per thread for register room.  A block always keeps at least one full warp.
 template <int CM, bool BWD, bool LIDAR, int RAYS>
 struct RaysPerThread {
     static constexpr int want = (BWD && CM <= 16) ? (LIDAR ? 2 : 4) : ((!BWD && !LIDAR && CM <= 16) ? 2 : 1);
@@ -495,7 +495,8 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
     return evals;
 }
 
-// Resident blocks the camera forward asks the register allocator for: 20 warps per SM.
+// Resident blocks the camera forward asks the register allocator for: 20 warps per SM
+// (24 spill).
 template <int CM, bool LIDAR, int NT>
 struct FwdMinBlocks {
     static constexpr int value = (!LIDAR && CM <= 16 && NT <= 640) ? 640 / NT : 1;
@@ -695,7 +696,7 @@ __device__ __forceinline__ void warp_transpose_reduce(float (&v)[VP], int lane) 
 }
 
 // Resident blocks the camera backward asks the register allocator for: 12 warps per SM
-// (the packed channel loops otherwise take registers enough to drop to 10).
+// (unbounded, the packed loops take registers enough to drop to 10; 14 would spill).
 template <int CM, bool LIDAR, int NT>
 struct BwdMinBlocks {
     static constexpr int value = (!LIDAR && CM <= 16 && NT <= 384) ? 384 / NT : 1;
