@@ -33,6 +33,7 @@ _lib = None
 
 GUARD_PX = 1e-4     # camera tile-edge guard band, pixels
 GUARD_RAD = 2e-6    # lidar tile-edge guard band, radians
+GUARD_RAD_SWEEP = 2e-5   # the same with the sweep-time margins
 
 
 def build(force: bool = False) -> str:
@@ -122,7 +123,7 @@ def sensor_params(s) -> np.ndarray:
         P[0] = 1
         P[19:27] = [s.n_beams, s.n_az, _r32(s.az_res), _r32(s.sweep_time), _r32(s.eps2d), _r32(s.r_min),
                     s.tile_az, s.tile_el]
-    P[31] = getattr(s, "support", 0)   # tile extent: 0 = 3 sigma, 1 = opacity-aware
+    P[31] = getattr(s, "support", 0)   # tile extent flags: 1 opacity-aware, 2 lidar sweep-time margins
     return P
 
 
@@ -144,7 +145,10 @@ def _g(g):
 
 
 def guard_for(s) -> float:
-    return GUARD_PX if s.kind == "camera" else GUARD_RAD
+    if s.kind == "camera":
+        return GUARD_PX
+    # the sweep-time margins go through a division and more FP32 steps on the GPU
+    return GUARD_RAD_SWEEP if (getattr(s, "support", 0) & 2) else GUARD_RAD
 
 
 def n_tiles_of(s):
@@ -156,8 +160,9 @@ def n_tiles_of(s):
 def project(g: dict, s, guard: float | None = None) -> dict:
     """Per-Gaussian projection of one sensor (FP64).
 
-    Returns rec (n,16): [mean_a, mean_b, conic a, b, c, o', depth, v_a, v_b, v_r,
-    Sigma'_aa, Sigma'_ab, Sigma'_bb, compensation, extent_a, extent_b], rect (n,4),
+    Returns rec (n,20): [mean_a, mean_b, conic a, b, c, o', depth, v_a, v_b, v_r,
+    Sigma'_aa, Sigma'_ab, Sigma'_bb, compensation, extent_a, extent_b, lidar box below / above the mean
+    along a and b], rect (n,4),
     outer and inner rects of marginal Gaussians (tiles whose membership FP32 rounding
     could change lie between the two), n_tiles, visible and marginal flags.
     """
@@ -166,7 +171,7 @@ def project(g: dict, s, guard: float | None = None) -> dict:
     m = _g(g)
     P = sensor_params(s)
     guard = guard_for(s) if guard is None else guard
-    rec = np.zeros((n, 16)); rect = np.zeros((n, 4), np.int32); orect = np.zeros((n, 4), np.int32)
+    rec = np.zeros((n, 20)); rect = np.zeros((n, 4), np.int32); orect = np.zeros((n, 4), np.int32)
     irect = np.zeros((n, 4), np.int32)
     nt = np.zeros(n, np.int32); vis = np.zeros(n, np.uint8); marg = np.zeros(n, np.uint8)
     el = _elev(s)

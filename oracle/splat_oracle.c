@@ -48,7 +48,8 @@ enum {
     P_NB = 19, P_NAZ = 20, P_AZRES = 21, P_SWEEP = 22, P_LEPS = 23, P_RMIN = 24,
     P_TAZ = 25, P_TEL = 26,
     /* both kinds */
-    P_SUPPORT = 31,      /* tile extent: 0 = 3 sigma (Sec. 3.2), 1 = where alpha can reach 1/255 */
+    P_SUPPORT = 31,      /* tile extent flags: 1 = where alpha can reach 1/255 instead of 3 sigma
+                          * (Sec. 3.2); 2 = lidar motion margins from the grid rays' own times */
     P_ALLG = 32          /* render from every visible Gaussian, without the tile predicate */
 };
 
@@ -60,9 +61,12 @@ enum {
     R_DEPTH = 6,                  /* z (camera) or range r (lidar) */
     R_VA = 7, R_VB = 8, R_VR = 9, /* sensor-space velocity */
     R_SAA = 10, R_SAB = 11, R_SBB = 12, /* Sigma' = Sigma_2d + eps I */
-    R_COMP = 13, R_EXA = 14, R_EXB = 15
+    R_COMP = 13, R_EXA = 14, R_EXB = 15,
+    /* lidar tile box below / above the mean along azimuth (a) and elevation (b); equal to
+     * the symmetric extents unless the sweep-time bounds tighten them */
+    R_LA = 16, R_HA = 17, R_LB = 18, R_HB = 19
 };
-#define REC 16
+#define REC 20
 
 typedef struct {
     double mean[3], S[9];       /* world mean and covariance */
@@ -182,8 +186,34 @@ static int cov2d(const proj_state *st, double eps, double out[6]) {
  * where alpha = o' exp(-d^T Sigma'^-1 d / 2) can reach 1/255: d^T Sigma'^-1 d <= 2 ln(255 o'),
  * whose bounding box has half-widths sqrt(2 ln(255 o')) times the standard deviations. */
 static double support_sigmas(const double *P, double op) {
-    if (P[P_SUPPORT] < 0.5) return 3.0;
+    if (!((int)P[P_SUPPORT] & 1)) return 3.0;
     return op > ALPHA_MIN ? sqrt(2.0 * log(255.0 * op)) : 0.0;
+}
+
+/* Lidar motion margins from the rays' own times (an option of the tile extent).  A grid
+ * ray at azimuth phi is fired at t(phi) = c phi - t_sweep / 2, c = t_sweep / (n_az az_res),
+ * so the mean it sees has moved by v_phi t(phi), not by up to |v_phi| t_sweep / 2: with
+ * u = phi - phi_mean, the azimuth test |u - v_phi t(phi)| <= e_phi holds for
+ * u in [(v_phi t_m - e_phi), (v_phi t_m + e_phi)] / (1 - c v_phi), t_m = t(phi_mean); the
+ * elevation margin then needs only the times of that azimuth range.  Both intervals are
+ * intersected with the symmetric box; Gaussians whose symmetric box crosses the sweep's
+ * seam at azimuth 0 (where t jumps by a whole sweep) keep it. */
+static void sweep_time_box(const double *P, double e_phi, double e_om, double half, double *rec) {
+    double phi = rec[R_MA], om = rec[R_MB], vphi = rec[R_VA], vom = rec[R_VB];
+    double plo = phi - rec[R_EXA], phi_hi = phi + rec[R_EXA];
+    double c = P[P_SWEEP] / (P[P_NAZ] * P[P_AZRES]), den = 1.0 - c * vphi;
+    if (!(plo >= 0 && phi_hi < TWO_PI && den > 0)) return;
+    double tm = c * phi - half;
+    double lo = fmax(plo, phi + (vphi * tm - e_phi) / den);
+    double hi = fmin(phi_hi, phi + (vphi * tm + e_phi) / den);
+    double t0 = fmax(c * lo - half, -half), t1 = fmin(c * hi - half, half);
+    double w0 = vom * t0, w1 = vom * t1;
+    double olo = fmax(om - rec[R_EXB], om - e_om + fmin(w0, w1));
+    double ohi = fmin(om + rec[R_EXB], om + e_om + fmax(w0, w1));
+    rec[R_LA] = phi - lo;
+    rec[R_HA] = hi - phi;
+    rec[R_LB] = om - olo;
+    rec[R_HB] = ohi - om;
 }
 
 /* Camera tile rectangle [x0,x1) x [y0,y1) from the AABB (Sec. 3.2), widened by `extra`
@@ -297,11 +327,11 @@ static int lidar_rect(const double *P, const double *elev, const double *rec, do
     int nb = (int)P[P_NB], naz = (int)P[P_NAZ], taz = (int)P[P_TAZ], tel = (int)P[P_TEL];
     int mphi = (naz + taz - 1) / taz, mw = nb / tel;
     double wphi = taz * P[P_AZRES], phimax = mphi * wphi;
-    double ea = rec[R_EXA] + extra, eb = rec[R_EXB] + extra;
+    double la = rec[R_LA] + extra, ha = rec[R_HA] + extra, lb = rec[R_LB] + extra, hb = rec[R_HB] + extra;
     rect[0] = rect[1] = rect[2] = rect[3] = 0;
-    if (ea < 0 || eb < 0) return 0;
-    double plo = rec[R_MA] - ea, phi_hi = rec[R_MA] + ea;
-    double olo = rec[R_MB] - eb, ohi = rec[R_MB] + eb;
+    if (la + ha < 0 || lb + hb < 0) return 0;
+    double plo = rec[R_MA] - la, phi_hi = rec[R_MA] + ha;
+    double olo = rec[R_MB] - lb, ohi = rec[R_MB] + hb;
     double bnd[1025];
     elevation_bounds(elev, nb, tel, bnd);
     rect[0] = rect[1] = rect[2] = rect[3] = 0;
@@ -374,6 +404,9 @@ static int project_lidar(const double *P, const double *elev, const double *mean
     double k = support_sigmas(P, op);
     rec[R_EXA] = k * sqrt(A) + fabs(rec[R_VA]) * half;
     rec[R_EXB] = k * sqrt(C) + fabs(rec[R_VB]) * half;
+    rec[R_LA] = rec[R_HA] = rec[R_EXA];
+    rec[R_LB] = rec[R_HB] = rec[R_EXB];
+    if ((int)P[P_SUPPORT] & 2) sweep_time_box(P, sqrt(A) * k, sqrt(C) * k, half, rec);
     int nt = lidar_rect(P, elev, rec, 0.0, rect, guard_rad, marg);
     if (cull_marg) *marg = 1;
     if (*marg) {

@@ -804,3 +804,53 @@ def test_opacity_aware_box_is_the_bounding_box_of_the_alpha_ellipse():
         np.testing.assert_array_equal(p["rect"][i], want)
         checked += 1
     assert checked > 100
+
+
+def test_sweep_time_margins_cover_every_grid_ray_that_can_blend():
+    """Lidar box option 2: a grid ray at azimuth phi fires at t(phi) = c phi - t_sweep/2, so
+    the margins only need the motion at those times.  Brute force over every azimuth bin:
+    each bin whose ray sees the moving mean within the spatial extent lies inside the
+    tightened azimuth box, and the mean's elevation at those rays' times lies inside the
+    tightened elevation box -- and the boxes are smaller than the symmetric ones."""
+    import dataclasses
+    g, cam, lid, replace = _support_scene()
+    lid = replace(lid, support=2)
+    p = oracle.project(g, lid)
+    rec = p["rec"]
+    half = 0.5 * float(np.float32(lid.sweep_time))
+    res = float(np.float32(lid.az_res))
+    a = np.arange(lid.n_az)
+    phi_a = (a + 0.5) * res
+    t_a = ((a + 0.5) / lid.n_az - 0.5) * float(np.float32(lid.sweep_time))
+    tightened = checked = 0
+    for i in np.nonzero(p["visible"])[0]:
+        r = rec[i]
+        phi, om, va, vb = r[0], r[1], r[7], r[8]
+        es, eo = r[14] - abs(va) * half, r[15] - abs(vb) * half
+        if not (phi - r[14] >= 0 and phi + r[14] < 2 * np.pi):
+            continue   # the seam keeps the symmetric box
+        hit = np.abs(phi_a - (phi + va * t_a)) <= es
+        if not hit.any():
+            continue
+        checked += 1
+        assert (phi_a[hit] >= phi - r[16] - 1e-12).all() and (phi_a[hit] <= phi + r[17] + 1e-12).all()
+        om_t = om + vb * t_a[hit]
+        assert (om_t - eo >= om - r[18] - 1e-12).all() and (om_t + eo <= om + r[19] + 1e-12).all()
+        assert r[16] <= r[14] + 1e-12 and r[17] <= r[14] + 1e-12
+        tightened += (r[16] + r[17] < 2 * r[14] - 1e-9)
+    assert checked > 50 and tightened > checked // 2
+
+
+def test_sweep_time_margins_keep_the_per_ray_definition():
+    """With both options (opacity-aware extent, sweep-time margins) the lidar's tile lists
+    still hold every Gaussian a grid ray can blend: rendering through them equals the
+    per-ray definition over every visible Gaussian exactly, with fewer intersections."""
+    g, cam, lid, replace = _support_scene()
+    both, aware = replace(lid, support=3), replace(lid, support=1)
+    tiled = oracle.render(g, both)
+    full = oracle.render(g, both, every_gaussian=True)
+    np.testing.assert_array_equal(tiled["F"], full["F"])
+    np.testing.assert_array_equal(tiled["range_exp"], full["range_exp"])
+    np.testing.assert_array_equal(tiled["count"], full["count"])
+    assert tiled["count"].sum() > 1000
+    assert len(oracle.isect_list(g, both)[0]) < len(oracle.isect_list(g, aware)[0])
