@@ -456,6 +456,8 @@ def run_ours(args):
 
     point_cloud = point_cloud_bench(fr, cg, gd, out, timed) if fr.lid_idx else None
     opacity_aware = support_bench(sensors, gd, tgt, flush, args.warmup, min(args.steps, 20), rays, dev)
+    lidar_sweep_times = (support_bench(sensors, gd, tgt, flush, args.warmup, min(args.steps, 20), rays, dev,
+                                       cam_flags=0, lid_flags=2) if fr.lid_idx else None)
 
     peaks = measured_peaks()
     clocks = clk.summary()
@@ -497,7 +499,8 @@ def run_ours(args):
             "e2e": e2e, "gpu_launches": launches_per_step(fr, len(l1_terms)) * args.steps,
             "roofline": roofline, "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "step_ms": {"min": min(step_ms), "median": statistics.median(step_ms), "max": max(step_ms)},
-            "wall_s": wall, "overflow": overflow, "point_cloud": point_cloud, "opacity_aware": opacity_aware}
+            "wall_s": wall, "overflow": overflow, "point_cloud": point_cloud, "opacity_aware": opacity_aware,
+            "lidar_sweep_times": lidar_sweep_times}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, sensors)
     if rank == 0 and world == 1:
@@ -514,13 +517,13 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def support_bench(sensors, gd, tgt, flush, warmup, steps, rays, dev):
-    """The same step with the opacity-aware tile extent on every sensor (support = 1):
-    intersections and time per step (CUDA events, L2 flushed between steps)."""
+def support_bench(sensors, gd, tgt, flush, warmup, steps, rays, dev, cam_flags=1, lid_flags=1):
+    """The same step with other tile-extent options (splat_sensor.support flags per sensor
+    kind): intersections and time per step (CUDA events, L2 flushed between steps)."""
     import dataclasses
     import torch
     from paper_2411_16816_gb300.render import Frame, l1_loss
-    sv = [dataclasses.replace(s, support=1) for s in sensors]
+    sv = [dataclasses.replace(s, support=cam_flags if s.kind == "camera" else lid_flags) for s in sensors]
     n, C = gd["means"].shape[0], gd["features"].shape[1]
     fr = Frame(sv, n, C, dev)
     out = fr.forward(gd, check=True)

@@ -105,10 +105,16 @@ typedef struct {
     float az_res, sweep_time, r_min;
     /* tiling (both kinds) */
     int32_t tile_w, tile_h;
-    /* tile extent of a Gaussian: 0 = the paper's box of 3 standard deviations of Sigma'
-     * plus the motion margin (Sec. 3.2, Sec. 3.3); 1 = opacity-aware, sqrt(2 ln(255 o'))
-     * standard deviations -- exactly the bounding box of the ellipse where alpha can reach
-     * 1/255, so the tile lists then hold every Gaussian a ray of the tile can blend. */
+    /* tile extent of a Gaussian, flags (0: the paper's box of 3 standard deviations of
+     * Sigma' plus the motion margin |v| t_rs / 2, Sec. 3.2, Sec. 3.3):
+     *   1  opacity-aware: sqrt(2 ln(255 o')) standard deviations -- exactly the bounding
+     *      box of the ellipse where alpha can reach 1/255, so the tile lists then hold
+     *      every Gaussian a ray of the tile can blend;
+     *   2  lidar only, regular ray grid only (rays == NULL): the motion margins use the
+     *      fire times of the grid rays, t(phi) = phi t_sweep / (n_az az_res) - t_sweep / 2,
+     *      instead of the whole sweep (a box crossing azimuth 0 keeps the full margins);
+     *      such a lidar's lists then serve its grid rays only, and the free-ray entry
+     *      points reject it. */
     int32_t support;
 } splat_sensor;
 

@@ -62,8 +62,10 @@ static splat_status build_frame(int32_t n_sensors, const splat_sensor* sensors, 
         d.tile_h = in.tile_h;
         d.eps = in.eps2d;
         if (!(in.eps2d >= 0.f)) return fail(SPLAT_ERR_INVALID_ARG, "sensor %d: eps2d must be >= 0", s);
-        if (in.support != 0 && in.support != 1)
-            return fail(SPLAT_ERR_INVALID_ARG, "sensor %d: support must be 0 (3 sigma) or 1 (opacity-aware)", s);
+        if (in.support & ~3)
+            return fail(SPLAT_ERR_INVALID_ARG, "sensor %d: support flags are 1 (opacity-aware) and 2 (sweep times)", s);
+        if ((in.support & 2) && (in.kind != SPLAT_SENSOR_LIDAR || in.rays))
+            return fail(SPLAT_ERR_INVALID_ARG, "sensor %d: sweep-time margins need a lidar on its regular ray grid", s);
         d.support = in.support;
         const bool lidar = in.kind == SPLAT_SENSOR_LIDAR;
         if (in.kind != SPLAT_SENSOR_CAMERA && !lidar) return fail(SPLAT_ERR_INVALID_ARG, "sensor %d: bad kind", s);
@@ -487,6 +489,8 @@ static splat_status list_input(const splat_gaussians* g, int32_t n_sensors, cons
     if ((st = check_ray_bins(rb, n_rays, name)) != SPLAT_OK) return st;
     if (n_rays > 0 && !rays) return fail(SPLAT_ERR_INVALID_ARG, "%s: rays is NULL", name);
     const SensorDev& S = fr.s[lidar];
+    if (S.support & 2)
+        return fail(SPLAT_ERR_INVALID_ARG, "%s: the lidar's lists assume its grid's ray times (support flag 2)", name);
     const int tiles = S.tiles_x * S.tiles_y;
     const int64_t b = (n_rays + kListChunk - 1) / kListChunk + tiles;
     if (b > INT32_MAX) return fail(SPLAT_ERR_INVALID_ARG, "%s: too many rays", name);

@@ -25,7 +25,7 @@ struct SensorDev {
     int tile_base;   // first global tile id of this sensor
     int block_base;  // first block of this sensor in its kind's raster launch
     int ray_base;    // first output ray (pixel) of this sensor in its kind's outputs
-    int support;     // tile extent: 0 = 3 sigma, 1 = opacity-aware
+    int support;     // tile extent flags: 1 opacity-aware, 2 lidar margins from the rays' fire times
     float R[9], t[3], v[3], w[3];
     // camera
     int width, height;
@@ -124,7 +124,7 @@ __device__ __forceinline__ float elev_bound(const SensorDev& S, int k) {
 // or (opacity-aware) the radius of the ellipse where o' exp(-d^T Sigma'^-1 d / 2) can
 // still reach 1/255, d^T Sigma'^-1 d <= 2 ln(255 o').
 __device__ __forceinline__ float support_sigmas(const SensorDev& S, float op) {
-    return S.support ? sqrtf(fmaxf(2.f * logf(255.f * op), 0.f)) : 3.f;
+    return (S.support & 1) ? sqrtf(fmaxf(2.f * logf(255.f * op), 0.f)) : 3.f;
 }
 
 __device__ __forceinline__ int sensor_of_block(const Frame& fr, int block, bool lidar) {

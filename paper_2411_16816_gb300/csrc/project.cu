@@ -204,11 +204,30 @@ __device__ bool project_lidar(const SensorDev& S, const GaussLocal& G, float4& r
     const float vr = lj.J[6] * w.x + lj.J[7] * w.y + lj.J[8] * w.z;
     const float half = 0.5f * S.sweep;
     const float k = support_sigmas(S, op);
-    const float ep = k * sqrtf(A) + fabsf(vphi) * half;
-    const float eo = k * sqrtf(C) + fabsf(vom) * half;
+    const float es = k * sqrtf(A), eos = k * sqrtf(C);
+    const float ep = es + fabsf(vphi) * half;
+    const float eo = eos + fabsf(vom) * half;
+    float plo = phi - ep, phi_hi = phi + ep;
+    float olo = om - eo, ohi = om + eo;
+    if ((S.support & 2) && plo >= 0.f && phi_hi < kTwoPi) {
+        // motion margins from the grid rays' own fire times t(phi) = c phi - t_sweep / 2:
+        // the azimuth test |phi - phi_mean - v_phi t(phi)| <= e_phi holds for phi - phi_mean in
+        // [v_phi t_m - e_phi, v_phi t_m + e_phi] / (1 - c v_phi); the elevation margin needs
+        // only the times of that azimuth range.  A box across the seam keeps its margins.
+        const float c = S.sweep / ((float)S.naz * S.az_res), den = 1.f - c * vphi;
+        if (den > 0.f) {
+            const float tm = c * phi - half;
+            plo = fmaxf(plo, phi + (vphi * tm - es) / den);
+            phi_hi = fminf(phi_hi, phi + (vphi * tm + es) / den);
+            const float t0 = fmaxf(c * plo - half, -half), t1 = fminf(c * phi_hi - half, half);
+            const float w0 = vom * t0, w1 = vom * t1;
+            olo = fmaxf(olo, om - eos + fminf(w0, w1));
+            ohi = fminf(ohi, om + eos + fmaxf(w0, w1));
+            if (!(phi_hi >= plo) || !(ohi >= olo)) return false;
+        }
+    }
     // elevation rows (App. A.1): row containing omega_low .. one past the row of omega_high
     const int Mw = S.nb / S.tile_h;
-    const float olo = om - eo, ohi = om + eo;
     if (!(ohi > elev_bound(S, 0)) || !(olo < elev_bound(S, Mw))) return false;
     int Olo = 0, Ohi = 0;
     for (int k = 1; k < Mw; k++)
@@ -217,7 +236,6 @@ __device__ bool project_lidar(const SensorDev& S, const GaussLocal& G, float4& r
         if (elev_bound(S, k) < ohi) Ohi = k + 1;
     // azimuth columns (App. A.1), wrapped into [0, M_phi) after the span is clamped
     const int Mphi = S.tiles_x;
-    const float plo = phi - ep, phi_hi = phi + ep;
     const float L = plo >= 0.f ? floorf(plo / S.wphi) : floorf((plo + kTwoPi - S.phimax) / S.wphi);
     const float H = phi_hi <= kTwoPi ? ceilf(phi_hi / S.wphi) : ceilf(fmodf(phi_hi, kTwoPi) / S.wphi) + (float)Mphi;
     const float span = fminf(H - L, (float)Mphi);

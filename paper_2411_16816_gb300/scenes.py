@@ -108,7 +108,7 @@ class Camera:
     near: float = 0.01
     tile_w: int = 16
     tile_h: int = 16
-    support: int = 0               # tile extent: 0 = 3 sigma (the paper), 1 = opacity-aware
+    support: int = 0               # tile extent flags: 1 opacity-aware, 2 lidar sweep-time margins
     kind: str = "camera"
 
     @property
@@ -131,7 +131,7 @@ class Lidar:
     tile_az: int = 32
     tile_el: int = 8
     rays: np.ndarray | None = None  # optional (n_beams, n_az, 3) of (phi, omega, t)
-    support: int = 0               # tile extent: 0 = 3 sigma (the paper), 1 = opacity-aware
+    support: int = 0               # tile extent flags: 1 opacity-aware, 2 lidar sweep-time margins
     kind: str = "lidar"
 
     @property

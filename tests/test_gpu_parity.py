@@ -695,3 +695,38 @@ def test_full_driving_frame_opacity_aware_sampled_parity():
     fr, gd, out = U.run(g, sensors)
     stats = U.check_render(fr, out, g, sensors, sel=_sample(sensors, 48, seed=3), max_marginal=0.25)
     print("marginal fractions", stats)
+
+
+def test_lidar_sweep_time_margins_lists_render_and_gradients():
+    """support flag 2 on the moving lidar: lists bit-exact against the oracle on a seed
+    without guard-band decisions; with both flags the forward matches the oracle and the
+    per-ray definition over every visible Gaussian, and the gradients match; the free-ray
+    entry points refuse such a lidar."""
+    import dataclasses
+    for k in range(20):
+        g, sensors = _dynamic_tiny(1001 + 1000 * k)
+        lid = dataclasses.replace(sensors[1], support=2)
+        if not oracle.project(g, lid)["marginal"].any():
+            break
+    else:
+        raise AssertionError("no clean seed")
+    fr, gd, out = U.run(g, [lid])
+    assert _compare_lists(fr, g, [lid]) == 0
+    fr0, _, _ = U.run(g, [sensors[1]])
+    assert len(fr.intersections()[0]) < len(fr0.intersections()[0])
+
+    g, sensors = _dynamic_tiny()
+    lid = dataclasses.replace(sensors[1], support=3)
+    fr, gd, out = U.run(g, [lid])
+    U.check_render(fr, out, g, [lid])
+    full = oracle.render(g, lid, every_gaussian=True)
+    ok = ~full["marginal"]
+    got = U.per_sensor(fr, out, "lid_feat", "lidar")[0]
+    np.testing.assert_allclose(got[ok], full["F"][ok], atol=U.TOL_FEAT, rtol=0)
+    grads, per = U.upstream(fr, [lid], g, seed=10)
+    pg = fr.backward(gd, out, grads)
+    torch.cuda.synchronize()
+    U.check_grads(pg, U.oracle_grads(g, [lid], per))
+    rays = torch.zeros((4, 3), device=U.DEV)
+    with pytest.raises(Exception):
+        fr.render_rays(fr.c_gaussians(gd), 0, rays, fr.bin_rays(0, rays))

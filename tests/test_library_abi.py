@@ -139,3 +139,24 @@ def test_point_cloud_entry_points_check_arguments_on_host():
     st = lib.splat_lidar_bin_rays(2, arr, 1, p, 10, bins, None)
     assert st == L.SPLAT_ERR_INVALID_ARG and "NULL" in lib.splat_last_error().decode()
     assert ctypes.sizeof(L.splat_ray_bins) == 24
+
+
+def test_support_flags_checked_on_host():
+    """Unknown extent flags, and the sweep-time flag on a camera or on a lidar with an
+    explicit ray table, are refused before any launch."""
+    lib = L.load()
+    cam, lid = scenes.tiny_frame()[1]
+    for s, flags in ((cam, 4), (cam, 2), (lid, 8)):
+        c = _c_sensor(s)
+        c.support = flags
+        arr = (L.splat_sensor * 1)(c)
+        assert lib.splat_frame_layout(1, arr, None, None, None) == L.SPLAT_ERR_INVALID_ARG, (s.kind, flags)
+    c = _c_sensor(lid)
+    c.support = 2
+    c.rays = 0x1000
+    arr = (L.splat_sensor * 1)(c)
+    assert lib.splat_frame_layout(1, arr, None, None, None) == L.SPLAT_ERR_INVALID_ARG
+    c.rays = None
+    c.support = 3
+    arr = (L.splat_sensor * 1)(c)
+    assert lib.splat_frame_layout(1, arr, None, None, None) == L.SPLAT_OK
