@@ -71,6 +71,10 @@ def _declare(L):
     L.oracle_render.restype = ctypes.c_int
     L.oracle_render.argtypes = ([_I64] + [_P] * 6 + [ctypes.c_int] + [_P] * 3 + [_I64, ctypes.c_double, _I64] +
                                 [_P] * 8 + [ctypes.c_double, _P])
+    L.oracle_render_variants.restype = ctypes.c_int
+    L.oracle_render_variants.argtypes = ([_I64] + [_P] * 6 + [ctypes.c_int] + [_P] * 3 +
+                                         [_I64, ctypes.c_double, _I64, _P, _P, ctypes.c_double, ctypes.c_int,
+                                          ctypes.c_int] + [_P] * 8)
     L.oracle_render_backward.restype = ctypes.c_int
     L.oracle_render_backward.argtypes = ([_I64] + [_P] * 6 + [ctypes.c_int] + [_P] * 3 + [_I64, _I64] + [_P] * 13 +
                                          [ctypes.c_double, _P, _P])
@@ -229,6 +233,58 @@ def render(g: dict, s, sel=None, guard: float | None = None, los_range=None, los
                     _ptr(fr if fr is not None else _rays(s)), nfree, guard, nr, _ptr(sel_arr), _ptr(F), _ptr(T), _ptr(De), _ptr(Dm), _ptr(mg), _ptr(cnt), _ptr(lr),
                     float(los_eps), _ptr(los))
     out = {"F": F, "T": T, "marginal": mg.astype(bool), "marginal_bits": mg, "count": cnt}
+    if los is not None:
+        out["los"] = los
+    if s.kind == "lidar":
+        out.update({"range_exp": De, "range_med": Dm, "alpha": 1.0 - T})
+    return out
+
+
+# Kinds of near decisions (bits of the marginal mask), see render_variants.
+NEAR_TILE, NEAR_ALPHA_MIN, NEAR_ALPHA_MAX, NEAR_STOP, NEAR_MEDIAN, NEAR_TIE, NEAR_LOS, NEAR_RAY_TILE = (
+    1, 2, 4, 8, 16, 32, 64, 128)
+MAX_NEAR = 4
+
+
+def render_variants(g: dict, s, sel=None, guard: float | None = None, los_range=None, los_eps: float = 0.8,
+                    free_rays=None, max_dec: int = MAX_NEAR) -> dict:
+    """Render the selected rays under every admissible resolution of their near decisions.
+
+    A ray's discrete decisions -- tile membership of a Gaussian whose box edge lies at a
+    tile edge, alpha >= 1/255, the stop before T < 1e-4, the T < 1/2 crossing of the
+    median range, the order of two blended Gaussians of equal depth, the line-of-sight
+    cut -- can go either way in FP32 when the FP64 value lies within the guard band of
+    the threshold.  Each way gives a correct render.  Variant 0 is the FP64 render (as
+    ``render``); variants 1 .. 2^d - 1 take each non-empty subset of the d near
+    decisions the other way, d <= max_dec.  Rays with more near decisions keep variant 0
+    only and are reported as unresolved.
+
+    Returns F (rays, V, C), T, range_exp, range_med, los (rays, V), n_var (rays,),
+    marginal_bits, n_near, unresolved (n_near > max_dec; rays whose ray tile itself is
+    uncertain, free rays only, are unresolved too)."""
+    L = lib()
+    n = len(g["opacities"])
+    m = _g(g)
+    feat = _f32(g["features"])
+    C = feat.shape[1] if feat.ndim == 2 else 0
+    P = sensor_params(s)
+    guard = guard_for(s) if guard is None else guard
+    sel_arr = None if sel is None else np.ascontiguousarray(sel, dtype=np.int64)
+    fr = None if free_rays is None else _sensor_array(np.asarray(free_rays).reshape(-1, 3))
+    nfree = 0 if fr is None else len(fr)
+    nr = (nfree if fr is not None else s.n_rays) if sel is None else len(sel_arr)
+    V = 1 << max_dec
+    F = np.zeros((nr, V, C)); T = np.zeros((nr, V)); De = np.zeros((nr, V)); Dm = np.zeros((nr, V))
+    los = np.zeros((nr, V)) if los_range is not None else None
+    nvar = np.zeros(nr, np.int32); mg = np.zeros(nr, np.uint8); nd = np.zeros(nr, np.int32)
+    lr = None if los_range is None else _f64(los_range)
+    rc = L.oracle_render_variants(n, *[_ptr(a) for a in m], _ptr(feat), C, _ptr(P), _ptr(_elev(s)),
+                                  _ptr(fr if fr is not None else _rays(s)), nfree, guard, nr, _ptr(sel_arr), _ptr(lr),
+                                  float(los_eps), max_dec, V, _ptr(F), _ptr(T), _ptr(De), _ptr(Dm), _ptr(los),
+                                  _ptr(nvar), _ptr(mg), _ptr(nd))
+    assert rc == 0
+    out = {"F": F, "T": T, "n_var": nvar, "marginal_bits": mg, "n_near": nd,
+           "unresolved": (nd > max_dec) | ((mg & NEAR_RAY_TILE) != 0)}
     if los is not None:
         out["los"] = los
     if s.kind == "lidar":

@@ -510,7 +510,41 @@ int64_t oracle_isect_list(int64_t n, const double *P, const double *rec, const i
 /* ---------------------------------------------------------------------------------
  * Per-ray blending.
  * ------------------------------------------------------------------------------- */
-typedef struct { int32_t id; double depth; } cand_t;
+/* A candidate of a ray: `member` is the Gaussian's tile membership as FP64 decides it;
+ * `optional` marks a Gaussian whose membership an FP32 evaluation could decide the
+ * other way (its box edge lies within the guard band of a tile edge). */
+typedef struct { int32_t id; double depth; int8_t member, optional; } cand_t;
+
+/* Discrete decisions of a ray that lie within the FP32 guard band of their threshold.
+ * Each kind is also the ray's bit in the marginal mask. */
+enum { D_TILE = 1, D_AMIN = 2, D_AMAX = 4, D_TERM = 8, D_MED = 16, D_TIE = 32, D_LOS = 64, D_RAYTILE = 128 };
+typedef struct { int32_t kind, id, id2; } decision_t;
+
+/* Flips to apply (a decision named by kind and Gaussian id is taken the other way) and a
+ * recorder of the near decisions met; either part may be empty. */
+typedef struct {
+    const decision_t *flip;
+    int nflip;
+    decision_t *near;
+    int cap, n_near;
+} dec_ctx;
+
+static int flipped(const dec_ctx *dc, int kind, int32_t id) {
+    if (!dc) return 0;
+    for (int q = 0; q < dc->nflip; q++)
+        if (dc->flip[q].kind == kind && dc->flip[q].id == id) return 1;
+    return 0;
+}
+
+static void note_decision(dec_ctx *dc, int kind, int32_t id, int32_t id2) {
+    if (!dc || !dc->near) return;
+    if (dc->n_near < dc->cap) {
+        dc->near[dc->n_near].kind = kind;
+        dc->near[dc->n_near].id = id;
+        dc->near[dc->n_near].id2 = id2;
+    }
+    dc->n_near++;
+}
 
 static int cmp_cand(const void *a, const void *b) {
     const cand_t *x = (const cand_t *)a, *y = (const cand_t *)b;
@@ -583,20 +617,16 @@ static void ray_setup(const double *P, const double *elev, const double *rays, i
 
 static double wrap_pi(double d) { return d - TWO_PI * floor((d + M_PI) / TWO_PI); }
 
-/* Render one ray: returns the number of blended Gaussians (written to cb if non-null). */
-static int render_ray(const double *P, const double *elev, const double *rays, int64_t nfree, int64_t n,
-                      const double *rec,
-                      const int32_t *rect, const int32_t *orect, const int32_t *irect, const uint8_t *vis,
-                      const uint8_t *gmarg,
-                      const double *feat, int C,
-                      int64_t k, cand_t *cands, double *F, double *Tout, double *Dexp, double *Dmed,
-                      int *marginal, contrib_t *cb, int cb_cap, double rp, double los_eps, double *los) {
-    int lidar = (int)P[P_KIND] == 1;
-    int tx, ty, tmarg = 0;
-    double pa, pb, t;
-    ray_setup(P, elev, rays, nfree, k, &tx, &ty, &pa, &pb, &t, &tmarg);
-    int nc = 0, mg = tmarg ? 128 : 0;
+/* Candidates of one ray: every visible Gaussian whose tile rectangle holds the ray's
+ * tile (every visible Gaussian with P_ALLG), plus the Gaussians whose membership is
+ * uncertain in FP32 and that would be blended here, sorted by (depth, id).  Sets bit
+ * D_TILE of *mg and records a D_TILE decision for each uncertain one that matters. */
+static int gather_candidates(const double *P, int64_t n, const double *rec, const int32_t *rect,
+                             const int32_t *orect, const int32_t *irect, const uint8_t *vis, const uint8_t *gmarg,
+                             int tx, int ty, double pa, double pb, double t, cand_t *cands, int *mg, dec_ctx *dc) {
+    int nc = 0;
     for (int64_t i = 0; i < n; i++) {
+        int optional = 0;
         /* a marginal Gaussian's membership is uncertain between its inner and outer boxes;
          * it matters only where it would be blended (alpha at or above the threshold) */
         if (gmarg && gmarg[i] && rect_contains(P, orect + 4 * i, tx, ty) &&
@@ -605,20 +635,67 @@ static int render_ray(const double *P, const double *elev, const double *rays, i
             double dx = pa - (g[R_MA] + g[R_VA] * t), dy = pb - (g[R_MB] + g[R_VB] * t);
             if ((int)P[P_KIND] == 1) dx = wrap_pi(dx);
             double sig = 0.5 * (g[R_CA] * dx * dx + g[R_CC] * dy * dy) + g[R_CB] * dx * dy;
-            if (sig >= 0 && g[R_OP] * exp(-sig) >= ALPHA_MIN * (1 - 1e-4)) mg |= 1;
+            if (sig >= 0 && g[R_OP] * exp(-sig) >= ALPHA_MIN * (1 - 1e-4)) {
+                *mg |= D_TILE;
+                optional = 1;
+                note_decision(dc, D_TILE, (int32_t)i, -1);
+            }
         }
-        if (!vis[i]) continue;
-        if (P[P_ALLG] < 0.5 && !rect_contains(P, rect + 4 * i, tx, ty)) continue;
+        int member = vis[i] && (P[P_ALLG] >= 0.5 || rect_contains(P, rect + 4 * i, tx, ty));
+        if (!member && !optional) continue;
         cands[nc].id = (int32_t)i;
         cands[nc].depth = rec[REC * i + R_DEPTH];
+        cands[nc].member = (int8_t)member;
+        cands[nc].optional = (int8_t)optional;
         nc++;
     }
     qsort(cands, (size_t)nc, sizeof(cand_t), cmp_cand);
+    return nc;
+}
+
+/* Front-to-back blend of a ray's sorted candidates (Eq. alpha blend / alpha / delta and
+ * the range blend of Sec. 3.3).  Decisions named in dc->flip are taken the other way:
+ *   D_TILE: membership of an optional candidate;   D_AMIN: the alpha >= 1/255 test;
+ *   D_TERM: the stop before T would fall below 1e-4; D_MED: the T < 1/2 crossing;
+ *   D_TIE: the order of two Gaussians blended one after the other (a depth tie);
+ *   D_LOS: the line-of-sight cut r_rs < r_p - eps.
+ * Decisions within the guard band are recorded in dc and flagged in *mg.  Returns the
+ * number of blended Gaussians (written to cb if non-null). */
+static int blend_ray(const double *P, const double *rec, const double *feat, int C, const cand_t *cands_in, int nc,
+                     double pa, double pb, double t, double *F, double *Tout, double *Dexp, double *Dmed, int *mg,
+                     contrib_t *cb, int cb_cap, double rp, double los_eps, double *los, dec_ctx *dc, cand_t *work) {
+    int lidar = (int)P[P_KIND] == 1;
+    const cand_t *cands = cands_in;
+    if (dc && work) {   /* depth ties taken the other way: swap the two Gaussians' places */
+        int any = 0;
+        for (int q = 0; q < dc->nflip; q++) any |= dc->flip[q].kind == D_TIE;
+        if (any) {
+            memcpy(work, cands_in, sizeof(cand_t) * (size_t)nc);
+            for (int q = 0; q < dc->nflip; q++) {
+                if (dc->flip[q].kind != D_TIE) continue;
+                int ja = -1, jb = -1;
+                for (int j = 0; j < nc; j++) {
+                    if (work[j].id == dc->flip[q].id) ja = j;
+                    if (work[j].id == dc->flip[q].id2) jb = j;
+                }
+                if (ja >= 0 && jb >= 0) {
+                    cand_t tmp = work[ja];
+                    work[ja] = work[jb];
+                    work[jb] = tmp;
+                }
+            }
+            cands = work;
+        }
+    }
     for (int c = 0; c < C; c++) F[c] = 0;
     double T = 1, de = 0, dm = 0, last_depth = -1e300, lsum = 0;
     int med = 0, nb = 0;
+    int32_t last_id = -1;
     for (int j = 0; j < nc; j++) {
-        const double *g = rec + REC * cands[j].id;
+        const int32_t id = cands[j].id;
+        int member = cands[j].member;
+        if (cands[j].optional && flipped(dc, D_TILE, id)) member = !member;
+        const double *g = rec + REC * id;
         /* Eq. (delta): the mean shifted by the sensor-space velocity at the ray's time */
         double dx = pa - (g[R_MA] + g[R_VA] * t);
         double dy = pb - (g[R_MB] + g[R_VB] * t);
@@ -627,32 +704,58 @@ static int render_ray(const double *P, const double *elev, const double *rays, i
         if (sig < 0) continue;
         double G = exp(-sig);
         double a = g[R_OP] * G;
-        if (fabs(a - ALPHA_MIN) <= 5e-5 * ALPHA_MIN) mg |= 2;
-        if (fabs(a - ALPHA_MAX) <= 5e-5 * ALPHA_MAX) mg |= 4;
+        int near_min = fabs(a - ALPHA_MIN) <= 5e-5 * ALPHA_MIN;
+        /* an optional candidate left out still records its alpha decision: an FP32 run that
+         * keeps it (a cull decision near o' = 1/255, then alpha near 1/255 at the centre)
+         * takes both */
+        if (near_min) { *mg |= D_AMIN; note_decision(dc, D_AMIN, id, -1); }
+        if (!member) continue;
+        if (fabs(a - ALPHA_MAX) <= 5e-5 * ALPHA_MAX) *mg |= D_AMAX;
         int clamped = 0;
         if (a > ALPHA_MAX) { a = ALPHA_MAX; clamped = 1; }
-        if (a < ALPHA_MIN) continue;
+        int skip = a < ALPHA_MIN;
+        if (near_min && flipped(dc, D_AMIN, id)) skip = !skip;
+        if (skip) continue;
         /* two blended Gaussians this close in depth may swap order in FP32 */
-        if (cands[j].depth - last_depth < 1e-6 * cands[j].depth) mg |= 32;
+        if (cands[j].depth - last_depth < 1e-6 * cands[j].depth) {
+            *mg |= D_TIE;
+            note_decision(dc, D_TIE, last_id, id);
+        }
         last_depth = cands[j].depth;
+        last_id = id;
         double Tn = T * (1 - a);
-        if (fabs(Tn - T_EPS) <= 2e-3 * T_EPS) mg |= 8;
-        if (Tn < T_EPS) break;
+        int stop = Tn < T_EPS;
+        if (fabs(Tn - T_EPS) <= 2e-3 * T_EPS) {
+            *mg |= D_TERM;
+            note_decision(dc, D_TERM, id, -1);
+            if (flipped(dc, D_TERM, id)) stop = !stop;
+        }
+        if (stop) break;
         double rrs = g[R_DEPTH] + g[R_VR] * t; /* r_rs = r + v_r t_l */
-        const double *f = feat + (int64_t)C * cands[j].id;
+        const double *f = feat + (int64_t)C * id;
         for (int c = 0; c < C; c++) F[c] += f[c] * a * T;
         de += rrs * a * T;
-        if (fabs(Tn - 0.5) <= 1e-3 * 0.5) mg |= 16;
-        if (!med && Tn < 0.5) { dm = rrs; med = 1; }
+        int cross = Tn < 0.5;
+        if (fabs(Tn - 0.5) <= 1e-3 * 0.5) {
+            *mg |= D_MED;
+            note_decision(dc, D_MED, id, -1);
+            if (flipped(dc, D_MED, id)) cross = !cross;
+        }
+        if (!med && cross) { dm = rrs; med = 1; }
         /* line-of-sight term (App. B): alpha of every blended Gaussian in front of the
          * return by more than eps; a range within the guard band of the cut is marginal */
         if (los) {
-            if (rrs < rp - los_eps) lsum += a;
-            if (fabs(rrs - (rp - los_eps)) <= 1e-5 * fabs(rp)) mg |= 64;
+            int front = rrs < rp - los_eps;
+            if (fabs(rrs - (rp - los_eps)) <= 1e-5 * fabs(rp)) {
+                *mg |= D_LOS;
+                note_decision(dc, D_LOS, id, -1);
+                if (flipped(dc, D_LOS, id)) front = !front;
+            }
+            if (front) lsum += a;
         }
         if (cb && nb < cb_cap) {
             contrib_t *e = cb + nb;
-            e->id = cands[j].id; e->alpha = a; e->T = T; e->G = G; e->dx = dx; e->dy = dy; e->t = t;
+            e->id = id; e->alpha = a; e->T = T; e->G = G; e->dx = dx; e->dy = dy; e->t = t;
             e->rrs = rrs; e->clamped = clamped;
         }
         nb++;
@@ -662,6 +765,24 @@ static int render_ray(const double *P, const double *elev, const double *rays, i
     if (los) *los = lsum;
     if (Dexp) *Dexp = de;
     if (Dmed) *Dmed = dm;
+    return nb;
+}
+
+/* Render one ray: returns the number of blended Gaussians (written to cb if non-null). */
+static int render_ray(const double *P, const double *elev, const double *rays, int64_t nfree, int64_t n,
+                      const double *rec,
+                      const int32_t *rect, const int32_t *orect, const int32_t *irect, const uint8_t *vis,
+                      const uint8_t *gmarg,
+                      const double *feat, int C,
+                      int64_t k, cand_t *cands, double *F, double *Tout, double *Dexp, double *Dmed,
+                      int *marginal, contrib_t *cb, int cb_cap, double rp, double los_eps, double *los) {
+    int tx, ty, tmarg = 0;
+    double pa, pb, t;
+    ray_setup(P, elev, rays, nfree, k, &tx, &ty, &pa, &pb, &t, &tmarg);
+    int mg = tmarg ? D_RAYTILE : 0;
+    int nc = gather_candidates(P, n, rec, rect, orect, irect, vis, gmarg, tx, ty, pa, pb, t, cands, &mg, NULL);
+    int nb = blend_ray(P, rec, feat, C, cands, nc, pa, pb, t, F, Tout, Dexp, Dmed, &mg, cb, cb_cap, rp, los_eps, los,
+                       NULL, NULL);
     if (marginal) *marginal = mg;
     return nb;
 }
@@ -725,6 +846,78 @@ int oracle_render(int64_t n, const double *means, const double *scales, const do
             if (outCount) outCount[j] = cnt;
         }
         free(cands);
+    }
+    free(rec); free(rect); free(orect); free(irect); free(vis); free(marg);
+    return 0;
+}
+
+/* Public: the selected rays rendered under every admissible resolution of their near
+ * decisions.  A ray whose FP64 evaluation meets decisions within the guard band of
+ * their thresholds (the marginal mask) has more than one result an FP32 evaluation may
+ * correctly reach: one per way of taking those decisions.  Variant 0 is the FP64
+ * render; variants 1 .. 2^d - 1 take the subsets of the d near decisions the other
+ * way (d <= max_dec, 2^max_dec <= max_var).  A ray with more than max_dec near decisions
+ * keeps variant 0 only (its outNdec exceeds max_dec: unresolved).
+ * Outputs per selected ray j: outF[(j * max_var + v) * C + c], outT / outDexp / outDmed /
+ * outLos[j * max_var + v], outNvar[j] variants, outMarg[j] the marginal mask, outNdec[j]
+ * the number of near decisions. */
+int oracle_render_variants(int64_t n, const double *means, const double *scales, const double *quats,
+                           const double *opac, const double *vel, const double *feat, int C, const double *P,
+                           const double *elev, const double *rays, int64_t nfree, double guard, int64_t n_sel,
+                           const int64_t *sel, const double *los_range, double los_eps, int max_dec, int max_var,
+                           double *outF, double *outT, double *outDexp, double *outDmed, double *outLos,
+                           int32_t *outNvar, uint8_t *outMarg, int32_t *outNdec) {
+    if (max_dec < 0 || max_dec > 16 || (1 << max_dec) > max_var) return -1;
+    double *rec = (double *)malloc(sizeof(double) * REC * (size_t)(n > 0 ? n : 1));
+    int32_t *rect = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)(n > 0 ? n : 1));
+    int32_t *orect = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)(n > 0 ? n : 1));
+    int32_t *irect = (int32_t *)malloc(sizeof(int32_t) * 4 * (size_t)(n > 0 ? n : 1));
+    uint8_t *vis = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
+    uint8_t *marg = (uint8_t *)malloc((size_t)(n > 0 ? n : 1));
+    project_all(n, means, scales, quats, opac, vel, P, elev, guard, rec, rect, orect, irect, vis, marg);
+    int64_t nr = sel ? n_sel : (nfree > 0 ? nfree : sensor_rays(P));
+#pragma omp parallel
+    {
+        cand_t *cands = (cand_t *)malloc(sizeof(cand_t) * (size_t)(n > 0 ? n : 1));
+        cand_t *work = (cand_t *)malloc(sizeof(cand_t) * (size_t)(n > 0 ? n : 1));
+        decision_t near[64], flip[16];
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t j = 0; j < nr; j++) {
+            int64_t k = sel ? sel[j] : j;
+            int tx, ty, tmarg = 0;
+            double pa, pb, t;
+            ray_setup(P, elev, rays, nfree, k, &tx, &ty, &pa, &pb, &t, &tmarg);
+            int mg = tmarg ? D_RAYTILE : 0;
+            dec_ctx dc = {NULL, 0, near, 64, 0};
+            int nc = gather_candidates(P, n, rec, rect, orect, irect, vis, marg, tx, ty, pa, pb, t, cands, &mg, &dc);
+            double rp = los_range ? los_range[j] : 0;
+            const int64_t o = j * max_var;
+            double lsum = 0;
+            blend_ray(P, rec, feat, C, cands, nc, pa, pb, t, outF + o * C, outT + o, outDexp ? outDexp + o : NULL,
+                      outDmed ? outDmed + o : NULL, &mg, NULL, 0, rp, los_eps, los_range ? &lsum : NULL, &dc, NULL);
+            if (outLos) outLos[o] = lsum;
+            int nd = dc.n_near;
+            int nv = 1;
+            if (nd <= max_dec) {
+                nv = 1 << nd;
+                for (int m = 1; m < nv; m++) {
+                    int nf = 0;
+                    for (int q = 0; q < nd; q++)
+                        if (m & (1 << q)) flip[nf++] = near[q];
+                    dec_ctx fc = {flip, nf, NULL, 0, 0};
+                    int mg2 = 0;
+                    double l2 = 0;
+                    blend_ray(P, rec, feat, C, cands, nc, pa, pb, t, outF + (o + m) * C, outT + o + m,
+                              outDexp ? outDexp + o + m : NULL, outDmed ? outDmed + o + m : NULL, &mg2, NULL, 0, rp,
+                              los_eps, los_range ? &l2 : NULL, &fc, work);
+                    if (outLos) outLos[o + m] = l2;
+                }
+            }
+            outNvar[j] = nv;
+            outMarg[j] = (uint8_t)mg;
+            outNdec[j] = nd;
+        }
+        free(cands); free(work);
     }
     free(rec); free(rect); free(orect); free(irect); free(vis); free(marg);
     return 0;
