@@ -185,9 +185,13 @@ splat_status splat_bin_sort(int64_t n, int32_t n_sensors, const splat_sensor *se
  * library until the process exits), so it allocates nothing.  Arguments and results are
  * those of splat_bin_sort without the workspace.  A frame whose scratch need
  * (splat_workspace_size) exceeds 32 MiB is rejected with SPLAT_ERR_INVALID_ARG before
- * anything is enqueued.  The first call on a device looks up the array's device address;
- * make it before any stream capture.  All calls share the array, so calls whose work
- * overlaps on the GPU race; nothing in it needs to start at zero. */
+ * anything is enqueued.  The first call on a device looks up the array's device address
+ * and keeps it for the device's current CUDA context; make that call before any stream
+ * capture.  After cudaDeviceReset the next call sees a new context and looks the address
+ * up again (again outside any capture).  A call that needs the look-up while its stream
+ * is capturing returns SPLAT_ERR_INVALID_ARG and enqueues nothing.  All calls share the
+ * array, so calls whose work overlaps on the GPU race; nothing in it needs to start at
+ * zero. */
 splat_status splat_bin_sort_noalloc(int64_t n, int32_t n_sensors, const splat_sensor *sensors, splat_projected proj,
                                     int64_t capacity, splat_bins bins, void *stream);
 

@@ -247,7 +247,7 @@ MAX_NEAR = 4
 
 
 def render_variants(g: dict, s, sel=None, guard: float | None = None, los_range=None, los_eps: float = 0.8,
-                    free_rays=None, max_dec: int = MAX_NEAR) -> dict:
+                    free_rays=None, every_gaussian: bool = False, max_dec: int = MAX_NEAR) -> dict:
     """Render the selected rays under every admissible resolution of their near decisions.
 
     A ray's discrete decisions -- tile membership of a Gaussian whose box edge lies at a
@@ -261,13 +261,14 @@ def render_variants(g: dict, s, sel=None, guard: float | None = None, los_range=
 
     Returns F (rays, V, C), T, range_exp, range_med, los (rays, V), n_var (rays,),
     marginal_bits, n_near, unresolved (n_near > max_dec; rays whose ray tile itself is
-    uncertain, free rays only, are unresolved too)."""
+    uncertain, free rays only, are unresolved too).  every_gaussian as in ``render``."""
     L = lib()
     n = len(g["opacities"])
     m = _g(g)
     feat = _f32(g["features"])
     C = feat.shape[1] if feat.ndim == 2 else 0
     P = sensor_params(s)
+    P[32] = 1.0 if every_gaussian else 0.0
     guard = guard_for(s) if guard is None else guard
     sel_arr = None if sel is None else np.ascontiguousarray(sel, dtype=np.int64)
     fr = None if free_rays is None else _sensor_array(np.asarray(free_rays).reshape(-1, 3))

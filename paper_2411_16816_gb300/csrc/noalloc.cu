@@ -12,11 +12,18 @@
 // The array is a file-scope __device__ variable: every GPU that loads the library holds
 // its kStaticScratchBytes until the process exits.  Host code cannot use the array's name
 // as a device address, so the first call on each device looks the address up with
-// cudaGetSymbolAddress (with that device current) and caches it; make that first call
-// before any stream capture.  All calls share the one array: two calls whose work
-// overlaps on the GPU (different streams, or different threads on the same device
-// without ordering) race on it.  Nothing in the scratch needs to start at zero -- every
-// word the sort reads is written earlier in the same call -- so no clearing is done.
+// cudaGetSymbolAddress (with that device current) and caches it together with the
+// identity of the device's current CUDA context.  A call made after that context was
+// torn down (cudaDeviceReset) sees a new context, in which the module and its array are
+// loaded afresh, and looks the address up again.  A look-up cannot run inside a stream
+// capture: make the first call on each device (and the first after a reset) before any
+// capture; a call that needs a look-up while its stream is capturing is refused with
+// SPLAT_ERR_INVALID_ARG.  All calls share the one array: two calls whose work overlaps on
+// the GPU (different streams, or different threads on the same device without ordering)
+// race on it.  Nothing in the scratch needs to start at zero -- every word the sort reads
+// is written earlier in the same call -- so no clearing is done.
+#include <cuda.h>
+
 #include <cstdio>
 #include <mutex>
 
@@ -33,23 +40,68 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_bin_scratch[kStaticScratchBytes];
 
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
+struct Slot {
+    unsigned long long ctx_id;   // context the address belongs to (0: unknown)
+    void* addr;
+};
 
-// Device address of the scratch array on the current device (looked up once per device).
-splat_status scratch_address(void** out) {
+std::mutex g_mu;
+Slot g_slot[kMaxDevices] = {};
+
+using GetCurrentFn = CUresult (*)(CUcontext*);
+using GetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Process-unique id of the calling thread's current context, 0 if there is none or the
+// driver does not offer the query.  The driver entry points are fetched through the
+// runtime, so the library does not link the driver library itself.  Called under g_mu.
+unsigned long long current_context_id() {
+    static bool tried = false;
+    static GetCurrentFn get_current = nullptr;
+    static GetIdFn get_id = nullptr;
+    if (!tried) {
+        tried = true;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetIdFn>(f);
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of the scratch array in the current device's current context (looked up
+// once per context).
+splat_status scratch_address(cudaStream_t stream, void** out) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
         return splat::record_error(SPLAT_ERR_CUDA, "splat_bin_sort_noalloc: no usable current device");
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_bin_scratch);
-        if (e != cudaSuccess || !p)
-            return splat::record_error(SPLAT_ERR_CUDA, "splat_bin_sort_noalloc: cudaGetSymbolAddress failed");
-        g_addr[dev] = p;
+    const unsigned long long id = current_context_id();
+    Slot& sl = g_slot[dev];
+    if (sl.addr && (id == 0 || id == sl.ctx_id)) {
+        *out = sl.addr;
+        return SPLAT_OK;
     }
-    *out = g_addr[dev];
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+        return splat::record_error(SPLAT_ERR_INVALID_ARG,
+                                   "splat_bin_sort_noalloc: the first call on a device (or after a device reset) "
+                                   "looks up the scratch address and cannot run inside a stream capture");
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_bin_scratch);
+    if (e != cudaSuccess || !p)
+        return splat::record_error(SPLAT_ERR_CUDA, "splat_bin_sort_noalloc: cudaGetSymbolAddress failed");
+    sl.addr = p;
+    sl.ctx_id = current_context_id();   // the look-up made the primary context current if it was not
+    *out = p;
     return SPLAT_OK;
 }
 
@@ -70,7 +122,7 @@ extern "C" splat_status splat_bin_sort_noalloc(int64_t n, int32_t n_sensors, con
         return splat::record_error(SPLAT_ERR_INVALID_ARG, msg);
     }
     void* scratch = nullptr;
-    const splat_status sa = scratch_address(&scratch);
+    const splat_status sa = scratch_address(static_cast<cudaStream_t>(stream), &scratch);
     if (sa != SPLAT_OK) return sa;
     return splat_bin_sort(n, n_sensors, sensors, proj, capacity, bins, scratch, kStaticScratchBytes, stream);
 }

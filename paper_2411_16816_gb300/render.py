@@ -469,11 +469,14 @@ class Frame:
         n = int(self.n_isect.item())
         if n > self.capacity:
             raise RuntimeError("intersection capacity exceeded")
-        ranges = self.ranges.cpu().numpy()
+        ranges = self.ranges.cpu().numpy().astype(np.int64)
         ids = self.isect_ids[:n].cpu().numpy().astype(np.int64)
-        tiles = np.zeros(n, np.int64)
-        for t in np.nonzero(ranges[:, 1] > ranges[:, 0])[0]:
-            tiles[ranges[t, 0]:ranges[t, 1]] = t
+        full = np.nonzero(ranges[:, 1] > ranges[:, 0])[0]
+        tiles = np.repeat(full, ranges[full, 1] - ranges[full, 0])
+        # the non-empty ranges tile [0, n) in tile order
+        if len(tiles) != n or (len(full) and (ranges[full[0], 0] != 0 or
+                                              np.any(ranges[full[1:], 0] != ranges[full[:-1], 1]))):
+            raise RuntimeError("tile ranges do not partition the intersection list")
         return tiles, ids
 
 
