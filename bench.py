@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--profile-only", action="store_true", help="a few untimed steps (for ncu captures)")
     p.add_argument("--no-serving", action="store_true", help="skip the batched-serving measurement")
     p.add_argument("--no-head", action="store_true", help="skip the learned ray-head measurement")
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the tiny, lidar-heavy and no-exclusion-radius frames of the default run")
     p.add_argument("--serving-replays", type=int, default=200)
     return p.parse_args()
 
@@ -51,9 +53,9 @@ def parse():
 def workload(name):
     if name == "driving":
         g, sensors = scenes.driving_frame()
-        desc = {"workload": "driving frame: 500k Gaussians (100x100x10 m box, 20% dynamic), 6 x 1920x1080 "
-                            "rolling-shutter cameras (30 ms) + 32-beam x 1080 lidar (100 ms sweep), 16 channels, "
-                            "L1 vs seeded target render",
+        desc = {"workload": "driving frame: 500k Gaussians (100x100x10 m box, 20% dynamic; means within 2 m "
+                            "horizontally of the ego vehicle re-drawn), 6 x 1920x1080 rolling-shutter cameras (30 ms) "
+                            "+ 32-beam x 1080 lidar (100 ms sweep), 16 channels, L1 vs seeded target render",
                 "gaussians": len(g["opacities"]), "rays_per_step": sum(s.n_rays for s in sensors),
                 "cameras": "6x1920x1080", "lidar": "32x1080"}
     elif name == "profile":
@@ -248,6 +250,204 @@ def launches_per_step(fr, n_l1):
     return 1 + bin_sort + raster + n_l1 + raster + 1
 
 
+def make_step(fr, gd, tgt):
+    """Buffers and the training step of a frame: forward with the camera L1 term fused into
+    the camera launch, the lidar L1 terms, backward.  step(src, tg) runs it on other input
+    buffers of the same shapes (the end-to-end path)."""
+    import torch
+    from paper_2411_16816_gb300.render import l1_loss
+    out = fr.forward(gd, check=True)
+    grads = {k: torch.empty_like(out[k]) for k in ("cam_feat", "lid_feat", "lid_range_exp") if k in out}
+    pgrads = {k: torch.zeros_like(v) for k, v in gd.items() if v is not None}
+    loss = torch.zeros(1, device=fr.device)
+    cam_l1 = (tgt["cam_feat"], 1.0 / out["cam_feat"].numel(), grads["cam_feat"], loss) if "cam_feat" in tgt else None
+    l1_terms = [(k, 1.0 / out[k].numel()) for k in ("lid_feat", "lid_range_exp") if k in out]
+
+    def step(src=None, tg=None):
+        tg = tgt if tg is None else tg
+        c1 = None if cam_l1 is None else (tg["cam_feat"],) + cam_l1[1:]
+        loss.zero_()
+        fr.forward(src if src is not None else gd, keep_state=True, check=False, out=out, cam_l1=c1)
+        for key, sc in l1_terms:
+            l1_loss(out[key], tg[key], sc, grads[key], loss)
+        fr.backward(src if src is not None else gd, out, grads, param_grads=pgrads)
+
+    return {"step": step, "out": out, "grads": grads, "pgrads": pgrads, "loss": loss, "cam_l1": cam_l1,
+            "l1_terms": l1_terms}
+
+
+def sized_frame(sensors, gd, td, dev):
+    """A Frame whose intersection buffers hold the frame with 10% room, and the target
+    render (an input of the loss, made once outside any timed region)."""
+    from paper_2411_16816_gb300.render import Frame
+    n, C = gd["means"].shape[0], gd["features"].shape[1]
+    fr = Frame(sensors, n, C, dev)
+    tout = fr.forward(td, keep_state=False)
+    tgt = {k: tout[k].clone() for k in ("cam_feat", "lid_feat", "lid_range_exp") if k in tout}
+    fr.forward(gd)
+    need = int(fr.n_isect.item())
+    if need * 1.05 > fr.capacity:
+        fr._alloc_capacity(int(need * 1.1))
+    return fr, tgt
+
+
+def capture(step, dev):
+    """The step captured once in a CUDA graph (after one eager run on a side stream)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    graph = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream(device=dev)
+    cap.wait_stream(stream)
+    with torch.cuda.stream(cap):
+        step()
+    stream.wait_stream(cap)
+    with torch.cuda.graph(graph):
+        step()
+    torch.cuda.synchronize()
+    return graph
+
+
+def replay_times(graph, flush, steps):
+    """CUDA-event time of each of `steps` replays, the L2 flushed before each."""
+    import torch
+    stream = torch.cuda.current_stream()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        graph.replay()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+
+def kernel_parts(fr, gd, st_, tgt, flush):
+    """Each library call of the step timed alone (CUDA events on the launching stream, L2
+    flushed before each), the evaluated (ray, Gaussian) pairs counted by the instrumented
+    forward, and the algorithmic work of each kernel (see the design notes)."""
+    import ctypes
+    import torch
+    from paper_2411_16816_gb300 import _lib as L
+    from paper_2411_16816_gb300.render import _stream, _vp
+    out, grads, pgrads, loss, cam_l1 = st_["out"], st_["grads"], st_["pgrads"], st_["loss"], st_["cam_l1"]
+    stream = torch.cuda.current_stream()
+    evaluated = torch.zeros(2, dtype=torch.int64, device=fr.device)
+    cg = fr.c_gaussians(gd)
+    fr.project(cg)
+    fr.bin_sort()
+    fr.rasterize(cg, out, evaluated=evaluated)
+    torch.cuda.synchronize()
+    ev_cam, ev_lid = (int(x) for x in evaluated.cpu())
+    n_isect = int(fr.n_isect.item())
+    visible = int((fr.n_tiles > 0).sum().item())
+    parts = {}
+
+    def timed(name, fn, reps=5, into=parts):
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        into[name] = statistics.mean(ts)
+
+    st = _stream()
+    S = len(fr.sensors)
+    timed("project", lambda: fr.project(cg))
+    timed("bin_sort", lambda: fr.bin_sort())
+    if fr.cam_idx:
+        timed("raster_camera_fwd", lambda: L.call("splat_render_camera_l1", ctypes.byref(cg), S, fr.c_sensors,
+                                                    fr.c_proj(), fr.c_bins(), _vp(tgt["cam_feat"]), float(cam_l1[1]),
+                                                    _vp(out["cam_feat"]), _vp(out["cam_T"]), _vp(out["cam_last"]),
+                                                    _vp(grads["cam_feat"]), _vp(loss), None, st))
+    if fr.lid_idx:
+        timed("raster_lidar_fwd", lambda: L.call("splat_render_lidar", ctypes.byref(cg), S, fr.c_sensors,
+                                                   fr.c_proj(), fr.c_bins(), _vp(out["lid_feat"]),
+                                                   _vp(out["lid_range_exp"]), _vp(out["lid_range_med"]),
+                                                   _vp(out["lid_alpha"]), _vp(out["lid_T"]), _vp(out["lid_last"]),
+                                                   None, st))
+    fr.grad_proj.zero_()
+    if fr.cam_idx:
+        timed("raster_camera_bwd", lambda: L.call("splat_render_camera_backward", ctypes.byref(cg), S, fr.c_sensors,
+                                                    fr.c_proj(), fr.c_bins(), _vp(out["cam_T"]), _vp(out["cam_last"]),
+                                                    _vp(grads["cam_feat"]), None, _vp(fr.grad_proj),
+                                                    _vp(pgrads["features"]), None, st))
+    if fr.lid_idx:
+        timed("raster_lidar_bwd", lambda: L.call("splat_render_lidar_backward", ctypes.byref(cg), S, fr.c_sensors,
+                                                   fr.c_proj(), fr.c_bins(), _vp(out["lid_T"]), _vp(out["lid_last"]),
+                                                   _vp(grads["lid_feat"]), _vp(grads["lid_range_exp"]), None,
+                                                   _vp(fr.grad_proj), _vp(pgrads["features"]), st))
+    timed("project_bwd", lambda: L.call("splat_project_backward", ctypes.byref(cg), S, fr.c_sensors, fr.c_proj(),
+                                          _vp(fr.grad_proj), _vp(pgrads["means"]), _vp(pgrads["scales"]),
+                                          _vp(pgrads["quats"]), _vp(pgrads["opacities"]),
+                                          _vp(pgrads["velocities"]), None, st))
+    n, C = fr.n, fr.channels
+    work = {
+        "raster_camera_fwd": ("alu", ev_cam * (22 + 2 * C) / 1e12, "TFLOP/s"),
+        "raster_camera_bwd": ("alu", ev_cam * (50 + 7 * C) / 1e12, "TFLOP/s"),
+        "raster_lidar_fwd": ("alu", ev_lid * (30 + 2 * C) / 1e12, "TFLOP/s"),
+        "raster_lidar_bwd": ("alu", ev_lid * (56 + 7 * C) / 1e12, "TFLOP/s"),
+        "project": ("hbm", (n * 56 + S * n * 8 + visible * 56) / 1e9, "GB/s"),
+        "project_bwd": ("hbm", (n * 56 + S * n * 4 + visible * 48 + n * 56) / 1e9, "GB/s"),
+        "bin_sort": ("hbm", (S * n * 4 + visible * 64 + n_isect * (8 + 2 * 20) + fr.total_tiles * 8) / 1e9, "GB/s"),
+    }
+    return {"parts": parts, "work": work, "timed": timed, "cg": cg, "evaluated": {"camera": ev_cam, "lidar": ev_lid},
+            "intersections": n_isect}
+
+
+def frame_roofline(kp, peaks, traffic=None):
+    """Roofline of the dominant kernel, every kernel's fraction and their time-weighted mean."""
+    parts, work = kp["parts"], kp["work"]
+    fp32_peak = fp32_peak_tflops(peaks["sm_max_mhz"])
+    dom = max(parts, key=parts.get)
+    bound, amount, unit = work[dom]
+    achieved = amount / (parts[dom] * 1e-3)
+    peak = fp32_peak if bound == "alu" else peaks["hbm_gbs"]
+    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": (traffic or {}).get(dom),
+                "peak_source": (f"FP32 FMA 152x128x2 at {peaks['sm_max_mhz']:.0f} MHz" if bound == "alu"
+                                else f"{peaks['source']} HBM copy"),
+                "kernel_ms": parts,
+                "per_kernel_frac": {k: (work[k][1] / (parts[k] * 1e-3)) /
+                                    (fp32_peak if work[k][0] == "alu" else peaks["hbm_gbs"]) for k in parts}}
+    roofline["time_weighted_frac"] = (sum(roofline["per_kernel_frac"][k] * parts[k] for k in parts) /
+                                      sum(parts.values()))
+    return roofline
+
+
+def frame_bench(g, sensors, target, desc, flush, warmup, steps, dev, kernels=True):
+    """One more workload measured like the headline one: the step replayed from a CUDA
+    graph (L2 flushed between steps, CUDA events per step), and -- with `kernels` -- each
+    kernel timed alone with the dominant kernel's roofline."""
+    import torch
+    from paper_2411_16816_gb300.render import gaussians_to_device
+    gd = gaussians_to_device(g, dev)
+    td = gaussians_to_device(target, dev)
+    fr, tgt = sized_frame(sensors, gd, td, dev)
+    st_ = make_step(fr, gd, tgt)
+    for _ in range(warmup):
+        st_["step"]()
+    torch.cuda.synchronize()
+    graph = capture(st_["step"], dev)
+    ts = replay_times(graph, flush, steps)
+    ms = statistics.mean(ts)
+    rays = desc["rays_per_step"]
+    res = dict(desc, ms_per_step=ms, rays_per_s=rays / (ms * 1e-3), steps=steps,
+               step_ms={"min": min(ts), "median": statistics.median(ts), "max": max(ts)},
+               intersections=int(fr.n_isect.item()), overflow=int(fr.n_isect.item()) > fr.capacity)
+    if kernels:
+        kp = kernel_parts(fr, gd, st_, tgt, flush)
+        res["evaluated_pairs"] = kp["evaluated"]
+        res["roofline"] = frame_roofline(kp, measured_peaks())
+    del graph, fr, st_, gd, td, tgt
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -261,40 +461,17 @@ def run_ours(args):
     dev = torch.device("cuda", local)
 
     from paper_2411_16816_gb300 import _lib
-    from paper_2411_16816_gb300.render import Frame, gaussians_to_device, l1_loss
+    from paper_2411_16816_gb300.render import gaussians_to_device
     _lib.load()
 
     g, sensors, target, desc = workload(args.workload)
-    n, C = len(g["opacities"]), g["features"].shape[1]
     gd = gaussians_to_device(g, dev)
     td = gaussians_to_device(target, dev)
-    fr = Frame(sensors, n, C, dev)
-    # target render (an input of the loss, made once outside the timed region)
-    tout = fr.forward(td, keep_state=False)
-    tgt = {k: tout[k].clone() for k in ("cam_feat", "lid_feat", "lid_range_exp") if k in tout}
-    out = fr.forward(gd)
-    need = int(fr.n_isect.item())
-    if need * 1.05 > fr.capacity:
-        fr._alloc_capacity(int(need * 1.1))
-    out = fr.forward(gd, check=True)
-    grads = {k: torch.empty_like(out[k]) for k in ("cam_feat", "lid_feat", "lid_range_exp") if k in out}
-    pgrads = {k: torch.zeros_like(v) for k, v in gd.items() if v is not None}
-    loss = torch.zeros(1, device=dev)
-    # the camera L1 term is fused into the camera raster launch; the lidar terms run as
-    # separate element-wise launches
-    cam_l1 = (tgt["cam_feat"], 1.0 / out["cam_feat"].numel(), grads["cam_feat"], loss) if "cam_feat" in tgt else None
-    l1_terms = [(k, 1.0 / out[k].numel()) for k in ("lid_feat", "lid_range_exp") if k in out]
+    fr, tgt = sized_frame(sensors, gd, td, dev)
+    st_ = make_step(fr, gd, tgt)
+    step, out, grads, pgrads = st_["step"], st_["out"], st_["grads"], st_["pgrads"]
+    loss, l1_terms = st_["loss"], st_["l1_terms"]
     stream = torch.cuda.current_stream()
-
-    def step(src=None, tg=None):
-        tg = tgt if tg is None else tg
-        c1 = None if cam_l1 is None else (tg["cam_feat"],) + cam_l1[1:]
-        loss.zero_()
-        fr.forward(src if src is not None else gd, keep_state=True, check=False, out=out, cam_l1=c1)
-        for key, sc in l1_terms:
-            l1_loss(out[key], tg[key], sc, grads[key], loss)
-        fr.backward(src if src is not None else gd, out, grads, param_grads=pgrads)
-
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
     if args.profile_only:
@@ -310,34 +487,18 @@ def run_ours(args):
         raise RuntimeError("intersection capacity exceeded during warm-up")
     # The step's ~45 launches are captured once in a CUDA graph and replayed: the host then
     # issues one launch per step, and a small frame is not bound by the host's launch rate.
-    graph = torch.cuda.CUDAGraph()
-    cap = torch.cuda.Stream(device=dev)
-    cap.wait_stream(stream)
-    with torch.cuda.stream(cap):
-        step()
-    stream.wait_stream(cap)
-    with torch.cuda.graph(graph):
-        step()
-    torch.cuda.synchronize()
+    graph = capture(step, dev)
 
     # ---- timed region: K steps, each bracketed by events; L2 flushed between steps ----
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     with ClockSampler(local) as clk:
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         wall0 = time.perf_counter()
-        for k in range(args.steps):
-            flush.fill_(float(k))
-            starts[k].record(stream)
-            graph.replay()
-            ends[k].record(stream)
-        torch.cuda.synchronize()
+        step_ms = replay_times(graph, flush, args.steps)
         if world > 1:
             dist.barrier()
         wall = time.perf_counter() - wall0
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms = max_over_ranks(statistics.mean(step_ms), dev)
     overflow = int(fr.n_isect.item()) > fr.capacity
     rays = desc["rays_per_step"]
@@ -397,104 +558,26 @@ def run_ours(args):
            "pipelining": "inputs double-buffered, copies on a second stream, the step replayed from a CUDA graph"}
 
     # ---- per-kernel timing (events around each library call) and work counters ----
-    import ctypes
-    evaluated = torch.zeros(2, dtype=torch.int64, device=dev)
-    cg = fr.c_gaussians(gd)
-    fr.project(cg)
-    fr.bin_sort()
-    fr.rasterize(cg, out, evaluated=evaluated)
-    torch.cuda.synchronize()
-    ev_cam, ev_lid = (int(x) for x in evaluated.cpu())
-    n_isect = int(fr.n_isect.item())
-    visible = int((fr.n_tiles > 0).sum().item())
-    parts = {}
-
-    def timed(name, fn, reps=5, into=parts):
-        ts = []
-        for _ in range(reps):
-            flush.fill_(1.0)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            fn()
-            b.record(stream)
-            torch.cuda.synchronize()
-            ts.append(a.elapsed_time(b))
-        into[name] = statistics.mean(ts)
-
-    from paper_2411_16816_gb300 import _lib as L
-    from paper_2411_16816_gb300.render import _stream, _vp
-    st = _stream()
-    S = len(fr.sensors)
-    timed("project", lambda: fr.project(cg))
-    timed("bin_sort", lambda: fr.bin_sort())
-    if fr.cam_idx:
-        timed("raster_camera_fwd", lambda: L.call("splat_render_camera_l1", ctypes.byref(cg), S, fr.c_sensors,
-                                                    fr.c_proj(), fr.c_bins(), _vp(tgt["cam_feat"]), float(cam_l1[1]),
-                                                    _vp(out["cam_feat"]), _vp(out["cam_T"]), _vp(out["cam_last"]),
-                                                    _vp(grads["cam_feat"]), _vp(loss), None, st))
-    if fr.lid_idx:
-        timed("raster_lidar_fwd", lambda: L.call("splat_render_lidar", ctypes.byref(cg), S, fr.c_sensors,
-                                                   fr.c_proj(), fr.c_bins(), _vp(out["lid_feat"]),
-                                                   _vp(out["lid_range_exp"]), _vp(out["lid_range_med"]),
-                                                   _vp(out["lid_alpha"]), _vp(out["lid_T"]), _vp(out["lid_last"]),
-                                                   None, st))
-    fr.grad_proj.zero_()
-    if fr.cam_idx:
-        timed("raster_camera_bwd", lambda: L.call("splat_render_camera_backward", ctypes.byref(cg), S, fr.c_sensors,
-                                                    fr.c_proj(), fr.c_bins(), _vp(out["cam_T"]), _vp(out["cam_last"]),
-                                                    _vp(grads["cam_feat"]), None, _vp(fr.grad_proj),
-                                                    _vp(pgrads["features"]), None, st))
-    if fr.lid_idx:
-        timed("raster_lidar_bwd", lambda: L.call("splat_render_lidar_backward", ctypes.byref(cg), S, fr.c_sensors,
-                                                   fr.c_proj(), fr.c_bins(), _vp(out["lid_T"]), _vp(out["lid_last"]),
-                                                   _vp(grads["lid_feat"]), _vp(grads["lid_range_exp"]), None,
-                                                   _vp(fr.grad_proj), _vp(pgrads["features"]), st))
-    timed("project_bwd", lambda: L.call("splat_project_backward", ctypes.byref(cg), S, fr.c_sensors, fr.c_proj(),
-                                          _vp(fr.grad_proj), _vp(pgrads["means"]), _vp(pgrads["scales"]),
-                                          _vp(pgrads["quats"]), _vp(pgrads["opacities"]),
-                                          _vp(pgrads["velocities"]), None, st))
-
-    point_cloud = point_cloud_bench(fr, cg, gd, out, timed) if fr.lid_idx else None
+    kp = kernel_parts(fr, gd, st_, tgt, flush)
+    cg = kp["cg"]
+    point_cloud = point_cloud_bench(fr, cg, gd, out, kp["timed"]) if fr.lid_idx else None
     opacity_aware = support_bench(sensors, gd, tgt, flush, args.warmup, min(args.steps, 20), rays, dev)
     lidar_sweep_times = (support_bench(sensors, gd, tgt, flush, args.warmup, min(args.steps, 20), rays, dev,
                                        cam_flags=0, lid_flags=2) if fr.lid_idx else None)
 
     peaks = measured_peaks()
     clocks = clk.summary()
-    fp32_peak = fp32_peak_tflops(peaks["sm_max_mhz"])
-    # algorithmic work per launch (see the design notes for the per-unit figures)
-    work = {
-        "raster_camera_fwd": ("alu", ev_cam * (22 + 2 * C) / 1e12, "TFLOP/s"),
-        "raster_camera_bwd": ("alu", ev_cam * (50 + 7 * C) / 1e12, "TFLOP/s"),
-        "raster_lidar_fwd": ("alu", ev_lid * (30 + 2 * C) / 1e12, "TFLOP/s"),
-        "raster_lidar_bwd": ("alu", ev_lid * (56 + 7 * C) / 1e12, "TFLOP/s"),
-        "project": ("hbm", (n * 56 + S * n * 8 + visible * 56) / 1e9, "GB/s"),
-        "project_bwd": ("hbm", (n * 56 + S * n * 4 + visible * 48 + n * 56) / 1e9, "GB/s"),
-        "bin_sort": ("hbm", (S * n * 4 + visible * 64 + n_isect * (8 + 2 * 20) + fr.total_tiles * 8) / 1e9, "GB/s"),
-    }
-    dom = max(parts, key=parts.get)
-    bound, amount, unit = work[dom]
-    achieved = amount / (parts[dom] * 1e-3)
-    peak = fp32_peak if bound == "alu" else peaks["hbm_gbs"]
     # DRAM bytes per launch from ncu captures of the current kernels (one camera of the
     # driving scene, scaled by the six cameras of the frame; profiles/ holds the captures)
     traffic = {"raster_camera_bwd": 6 * 159.33e6} if args.workload == "driving" else {}
-    roofline = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": traffic.get(dom),
-                "peak_source": (f"FP32 FMA 152x128x2 at {peaks['sm_max_mhz']:.0f} MHz" if bound == "alu"
-                                else f"{peaks['source']} HBM copy"),
-                "kernel_ms": parts,
-                "per_kernel_frac": {k: (work[k][1] / (parts[k] * 1e-3)) /
-                                    (fp32_peak if work[k][0] == "alu" else peaks["hbm_gbs"]) for k in parts}}
-    roofline["time_weighted_frac"] = (sum(roofline["per_kernel_frac"][k] * parts[k] for k in parts) /
-                                      sum(parts.values()))
+    roofline = frame_roofline(kp, peaks, traffic)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(desc, l2="explicit 258 MB flush between timed steps (per-step CUDA events)",
                            step="the step's launches captured once in a CUDA graph, one replay per step",
-                           intersections=n_isect, evaluated_pairs={"camera": ev_cam, "lidar": ev_lid},
+                           intersections=kp["intersections"], evaluated_pairs=kp["evaluated"],
                            parallelism=f"replicas x{world}"),
             "e2e": e2e, "gpu_launches": launches_per_step(fr, len(l1_terms)) * args.steps,
             "roofline": roofline, "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
@@ -504,8 +587,26 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, sensors)
     if rank == 0 and world == 1:
-        del graph, egraphs, fr, out, grads, pgrads, flush, dbuf, host_g, host_t
+        del graph, egraphs, fr, out, grads, pgrads, dbuf, host_g, host_t, st_, kp, gd, td, tgt
         torch.cuda.empty_cache()
+        if args.workload == "driving" and not args.no_configs:
+            # the other configurations of the benchmark table, measured the same way
+            k = min(args.steps, 50)
+            tg, ts_ = scenes.tiny_frame()
+            line["tiny_frame"] = frame_bench(tg, ts_, scenes.target_like(tg, seed=1002), dict(
+                workload="tiny frame: 2,000 Gaussians, 128x96 camera (f = 100) + 16x256 lidar, 3 channels",
+                gaussians=len(tg["opacities"]), rays_per_step=sum(s.n_rays for s in ts_)),
+                flush, args.warmup, k, dev)
+            lg, ls_, lt, ld = workload("lidar_heavy")
+            line["lidar_heavy"] = frame_bench(lg, ls_, lt, ld, flush, args.warmup, k, dev)
+            del lg, lt
+            # the driving scene without the 2 m ego exclusion radius
+            ng = scenes.driving_gaussians(len(g["opacities"]), 1002, min_radius=0.0)
+            nd = dict(desc, workload=desc["workload"] + " -- without the 2 m ego exclusion radius")
+            line["no_exclusion_radius"] = frame_bench(ng, sensors, scenes.target_like(ng, seed=1003), nd, flush,
+                                                      args.warmup, min(args.steps, 20), dev, kernels=False)
+            del ng
+            torch.cuda.empty_cache()
         if not args.no_serving:
             line["serving"] = serving_bench(args, dev)
             torch.cuda.empty_cache()

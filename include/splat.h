@@ -165,6 +165,15 @@ splat_status splat_workspace_size(int64_t n, int32_t n_sensors, const splat_sens
 splat_status splat_project(const splat_gaussians *g, int32_t n_sensors, const splat_sensor *sensors,
                            splat_projected proj, void *stream);
 
+/* Input health (no counterpart in the paper).  splat_project culls from every sensor a
+ * Gaussian whose mean, scale, quaternion, opacity or velocity holds a NaN or an infinity
+ * (and one whose quaternion is zero): it takes no tile, is never blended and receives no
+ * gradient.  This call adds to *count (one device int64, accumulated) the number of
+ * Gaussians with such a non-finite parameter; features are not inspected (a non-finite
+ * feature reaches the outputs of the rays that blend it).  Asynchronous; g's features
+ * may be NULL. */
+splat_status splat_count_nonfinite(const splat_gaussians *g, int64_t *count, void *stream);
+
 /* Tile duplication and sort (Sec. 3.2 tiling and depth sort; Sec. 3.3 range sort;
  * App. A.1 wrapped identifiers).  Emits every (tile, Gaussian) pair of the frame,
  * orders them by (tile, depth, Gaussian index) with an on-device stable radix sort and

@@ -21,7 +21,8 @@ SPLAT_SENSOR_LIDAR = 1
 SPLAT_MAX_SENSORS = 16
 
 EXPORTS = [
-    "splat_frame_layout", "splat_workspace_size", "splat_project", "splat_bin_sort", "splat_bin_sort_backward",
+    "splat_frame_layout", "splat_workspace_size", "splat_project", "splat_count_nonfinite", "splat_bin_sort",
+    "splat_bin_sort_backward",
     "splat_render_camera", "splat_render_camera_l1", "splat_render_lidar", "splat_render_lidar_los",
     "splat_render_camera_backward", "splat_render_lidar_backward", "splat_render_lidar_backward_los",
     "splat_sync_status", "splat_lidar_points_to_rays", "splat_lidar_bin_rays", "splat_lidar_bin_rays_capped",
@@ -100,6 +101,7 @@ def load(build_if_missing: bool = True):
     L.splat_frame_layout.argtypes = [c_int32, SE, P(c_int64), P(c_int64), P(c_int64)]
     L.splat_workspace_size.argtypes = [c_int64, c_int32, SE, c_int64, P(c_size_t)]
     L.splat_project.argtypes = [G, c_int32, SE, splat_projected, c_void_p]
+    L.splat_count_nonfinite.argtypes = [G, c_void_p, c_void_p]
     L.splat_bin_sort.argtypes = [c_int64, c_int32, SE, splat_projected, c_int64, splat_bins, c_void_p, c_size_t,
                                  c_void_p]
     L.splat_bin_sort_backward.argtypes = []

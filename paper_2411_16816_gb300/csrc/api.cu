@@ -200,6 +200,14 @@ splat_status splat_project(const splat_gaussians* g, int32_t n_sensors, const sp
     return check_launch("splat_project");
 }
 
+splat_status splat_count_nonfinite(const splat_gaussians* g, int64_t* count, void* stream) {
+    splat_status st = check_gaussians(g, false);
+    if (st != SPLAT_OK) return st;
+    if (!count || ((uintptr_t)count & 7u)) return fail(SPLAT_ERR_INVALID_ARG, "count is NULL or misaligned");
+    launch_count_nonfinite(gauss_in(g), reinterpret_cast<unsigned long long*>(count), (cudaStream_t)stream);
+    return check_launch("splat_count_nonfinite");
+}
+
 splat_status splat_bin_sort(int64_t n, int32_t n_sensors, const splat_sensor* sensors, splat_projected proj,
                             int64_t capacity, splat_bins bins, void* workspace, size_t workspace_bytes,
                             void* stream) {

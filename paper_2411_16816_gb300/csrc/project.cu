@@ -251,18 +251,36 @@ __device__ bool project_lidar(const SensorDev& S, const GaussLocal& G, float4& r
     return true;
 }
 
+// Every geometric parameter of Gaussian i (mean, scale, quaternion, opacity, velocity)
+// is a finite number.
+__device__ __forceinline__ bool finite_params(const GaussIn& g, int64_t i) {
+    bool ok = isfinite(g.opac[i]);
+#pragma unroll
+    for (int k = 0; k < 3; k++) ok &= isfinite(g.means[3 * i + k]) && isfinite(g.scales[3 * i + k]);
+    const float4 q = reinterpret_cast<const float4*>(g.quats)[i];
+    ok &= isfinite(q.x) && isfinite(q.y) && isfinite(q.z) && isfinite(q.w);
+    if (g.vel) {
+#pragma unroll
+        for (int k = 0; k < 3; k++) ok &= isfinite(g.vel[3 * i + k]);
+    }
+    return ok;
+}
+
 __global__ void __launch_bounds__(256) k_project(GaussIn g, const __grid_constant__ Frame fr, ProjOut out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.n) return;
     GaussLocal G;
     load_gaussian(g, i, G);
+    // a Gaussian with a non-finite parameter (or a zero quaternion) is culled from every
+    // sensor: no tile, no record, no gradient
+    bool finite = finite_params(g, i) && isfinite(G.q[0]);
     for (int s = 0; s < fr.n_sensors; s++) {
         const SensorDev& S = fr.s[s];
         float4 r0, r1, r2;
         short4 rc;
         int nt = 0;
-        const bool vis = S.kind == SPLAT_SENSOR_CAMERA ? project_camera(S, G, r0, r1, r2, rc, nt)
-                                                       : project_lidar(S, G, r0, r1, r2, rc, nt);
+        const bool vis = finite && (S.kind == SPLAT_SENSOR_CAMERA ? project_camera(S, G, r0, r1, r2, rc, nt)
+                                                                  : project_lidar(S, G, r0, r1, r2, rc, nt));
         if (vis) {
             out.rec[rec_index(s, 0, g.n, i)] = r0;
             out.rec[rec_index(s, 1, g.n, i)] = r1;
@@ -603,6 +621,21 @@ __global__ void __launch_bounds__(256) k_project_backward(GaussIn g, const __gri
         out.vel[3 * i + 1] += dvel.y;
         out.vel[3 * i + 2] += dvel.z;
     }
+}
+
+// Adds to *count the number of Gaussians with a non-finite geometric parameter (one warp
+// vote and at most one atomic per warp).
+__global__ void __launch_bounds__(256) k_count_nonfinite(GaussIn g, unsigned long long* count) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool bad = i < g.n && !finite_params(g, i);
+    const unsigned vote = __ballot_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0 && vote) atomicAdd(count, (unsigned long long)__popc(vote));
+}
+
+void launch_count_nonfinite(const GaussIn& g, unsigned long long* count, cudaStream_t st) {
+    if (g.n == 0) return;
+    const unsigned blocks = (unsigned)((g.n + 255) / 256);
+    k_count_nonfinite<<<blocks, 256, 0, st>>>(g, count);
 }
 
 void launch_project(const GaussIn& g, const Frame& fr, const ProjOut& out, cudaStream_t st) {

@@ -96,6 +96,7 @@ struct BinWorkspace {
 };
 
 void launch_project(const GaussIn& g, const Frame& fr, const ProjOut& out, cudaStream_t st);
+void launch_count_nonfinite(const GaussIn& g, unsigned long long* count, cudaStream_t st);
 void launch_project_backward(const GaussIn& g, const Frame& fr, const int32_t* n_tiles, const float4* grad,
                              const GradOut& out, cudaStream_t st);
 BinWorkspace carve_workspace(void* base, int64_t pairs, int64_t capacity);

@@ -145,6 +145,15 @@ class Frame:
     def project(self, cg, stream=None):
         L.call("splat_project", ctypes.byref(cg), len(self.sensors), self.c_sensors, self.c_proj(), _stream(stream))
 
+    def count_nonfinite(self, g: dict, count: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Device int64 count of the Gaussians with a NaN or infinite mean, scale,
+        quaternion, opacity or velocity (accumulated into `count` if given).  The
+        projection culls exactly those (and zero quaternions) from every sensor."""
+        if count is None:
+            count = torch.zeros(1, dtype=torch.int64, device=self.device)
+        L.call("splat_count_nonfinite", ctypes.byref(self.c_gaussians(g)), _vp(count), _stream(stream))
+        return count
+
     def bin_sort(self, stream=None):
         L.call("splat_bin_sort", self.n, len(self.sensors), self.c_sensors, self.c_proj(), self.capacity,
                self.c_bins(), _vp(self.workspace), self.workspace.numel(), _stream(stream))

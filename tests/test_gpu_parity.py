@@ -268,6 +268,43 @@ def test_ragged_tiles_and_huge_gaussian():
     U.check_grads(pg, U.oracle_grads(g, [cam, lid], per))
 
 
+def test_nonfinite_gaussians_are_culled_and_counted():
+    """Gaussians with a NaN or infinite mean, scale, quaternion, opacity or velocity take no
+    tile and change nothing: lists, renders and gradients are those of the frame with
+    the same Gaussians made invisible (opacity 0), and splat_count_nonfinite counts them."""
+    g, sensors = _dynamic_tiny()
+    bad = np.random.default_rng(3).choice(len(g["opacities"]), 8, replace=False)
+    cases = [("means", 0, np.nan), ("means", 2, np.inf), ("scales", 1, np.inf), ("scales", 0, np.nan),
+             ("quats", 3, np.nan), ("opacities", None, np.nan), ("opacities", None, np.inf),
+             ("velocities", 1, -np.inf)]
+    poisoned = {k: np.array(v, copy=True) for k, v in g.items()}
+    for i, (k, c, v) in zip(bad, cases):
+        if c is None:
+            poisoned[k][i] = v
+        else:
+            poisoned[k][i, c] = v
+    hidden = {k: np.array(v, copy=True) for k, v in g.items()}
+    hidden["opacities"][bad] = 0.0
+    fr_p, gd_p, out_p = U.run(poisoned, sensors)
+    fr_h, gd_h, out_h = U.run(hidden, sensors)
+    assert int(fr_p.count_nonfinite(gd_p).item()) == 8
+    assert int(fr_h.count_nonfinite(gd_h).item()) == 0
+    assert (fr_p.n_tiles.cpu().numpy()[:, bad] == 0).all()
+    tp, ip = fr_p.intersections()
+    th, ih = fr_h.intersections()
+    assert np.array_equal(tp, th) and np.array_equal(ip, ih)
+    for k, v in out_p.items():
+        if v is not None:
+            assert torch.equal(v, out_h[k]), k
+    grads, _ = U.upstream(fr_h, sensors, hidden, seed=12)
+    pg_p = {k: v.clone() for k, v in fr_p.backward(gd_p, out_p, grads).items()}
+    pg_h = fr_h.backward(gd_h, out_h, grads)
+    torch.cuda.synchronize()
+    for k, v in pg_p.items():
+        assert torch.isfinite(v).all() and not v[torch.as_tensor(bad, device=U.DEV)].any(), k
+        torch.testing.assert_close(v, pg_h[k], rtol=1e-5, atol=1e-6 * float(pg_h[k].abs().max()) + 1e-12)
+
+
 def test_capacity_overflow_is_reported_and_recovered():
     g, sensors = scenes.tiny_frame()
     gd = gaussians_to_device(g, U.DEV)

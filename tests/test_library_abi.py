@@ -160,3 +160,13 @@ def test_support_flags_checked_on_host():
     c.support = 3
     arr = (L.splat_sensor * 1)(c)
     assert lib.splat_frame_layout(1, arr, None, None, None) == L.SPLAT_OK
+
+
+def test_count_nonfinite_checks_arguments_on_host():
+    lib = L.load()
+    g = L.splat_gaussians(0x1000, 0x1000, 0x1000, 0x1000, 0x1000, None, 10, 3, 0)
+    assert lib.splat_count_nonfinite(ctypes.byref(g), None, None) == L.SPLAT_ERR_INVALID_ARG
+    assert "count" in lib.splat_last_error().decode()
+    assert lib.splat_count_nonfinite(ctypes.byref(g), ctypes.c_void_p(0x1004), None) == L.SPLAT_ERR_INVALID_ARG
+    bad = L.splat_gaussians(None, 0x1000, 0x1000, 0x1000, 0x1000, None, 10, 3, 0)
+    assert lib.splat_count_nonfinite(ctypes.byref(bad), ctypes.c_void_p(0x1000), None) == L.SPLAT_ERR_INVALID_ARG
