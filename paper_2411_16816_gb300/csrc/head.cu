@@ -20,6 +20,7 @@
 // across a persistent grid until one flush per block.
 #include <cuda_bf16.h>
 
+#include "mma.cuh"
 #include "types.cuh"
 
 namespace splat {
@@ -33,35 +34,6 @@ constexpr int kHeadRays = 16 * kHeadWarps;   // rays per training-block iteratio
 constexpr int kP32 = 40;                      // padded row lengths (BF16 elements) of the shared
 constexpr int kP64 = 72;                      // operands: conflict-free fragment loads
 constexpr int kPR = kHeadRays + 8;            // transposed activations [unit][ray]
-
-using bf16 = __nv_bfloat16;
-
-__device__ __forceinline__ uint32_t bits2(__nv_bfloat162 v) { return *reinterpret_cast<uint32_t*>(&v); }
-__device__ __forceinline__ uint32_t ld2(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
-
-// FP32 pair -> BF16 high parts and BF16 residuals (a = hi + lo to about 16 bits).
-__device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
-    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-    const float2 hf = __bfloat1622float2(h);
-    hi = bits2(h);
-    lo = bits2(__floats2bfloat162_rn(a - hf.x, b - hf.y));
-}
-
-__device__ __forceinline__ void split_one(float a, bf16& hi, bf16& lo) {
-    hi = __float2bfloat16_rn(a);
-    lo = __float2bfloat16_rn(a - __bfloat162float(hi));
-}
-
-// d += A (16 x 16, row) * B (16 x 8, col): BF16 operands, FP32 accumulators.  Fragments:
-// g = lane / 4, t = lane % 4; A regs (g, 2t..) (g+8, 2t..) (g, 2t+8..) (g+8, 2t+8..);
-// B regs (k 2t.., n g) (k 2t+8.., n g); d (g, 2t) (g, 2t+1) (g+8, 2t) (g+8, 2t+1).
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
 
 struct SplitA {   // an A fragment of split FP32 values
     uint32_t h[4], l[4];

@@ -346,6 +346,31 @@ def test_channel_counts(channels):
     U.check_grads(pg, U.oracle_grads(g, sensors, per))
 
 
+@pytest.mark.parametrize("tile, channels", [((16, 16), 16), ((32, 8), 16), ((16, 16), 13), ((32, 8), 10)])
+def test_camera_backward_16_channel_bucket_on_256_ray_tiles(tile, channels):
+    """The camera backward of the 9-16 channel kernels on both 256-ray tile shapes (four
+    rays per thread): gradients of a moving two-camera frame against the oracle, with
+    channel counts that are not multiples of four, stored state and recomputed."""
+    g, sensors = _small_driving(n=8000, w=200, h=120)
+    g = dict(g)
+    g["features"] = np.random.default_rng(channels).normal(size=(len(g["opacities"]), channels)).astype(np.float32)
+    for s in sensors:
+        if s.kind == "camera":
+            s.tile_w, s.tile_h = tile
+    fr, gd, out = U.run(g, sensors)
+    U.check_render(fr, out, g, sensors)
+    grads, per = U.upstream(fr, sensors, g, seed=14)
+    a = {k: v.clone() for k, v in fr.backward(gd, out, grads).items()}
+    torch.cuda.synchronize()
+    U.check_grads(a, U.oracle_grads(g, sensors, per))
+    out2 = fr.forward(gd, keep_state=False)
+    b = fr.backward(gd, out2, grads)
+    torch.cuda.synchronize()
+    # equal up to the order of the atomic sums (shared and global)
+    for k in a:
+        torch.testing.assert_close(b[k], a[k], rtol=1e-4, atol=1e-5 * float(a[k].abs().max()) + 1e-9)
+
+
 def test_explicit_lidar_rays_and_nonuniform_beams():
     elev = scenes.nonuniform_elevations(32)
     lid = scenes.Lidar(R=np.eye(3), t=np.zeros(3), beam_elev=elev, n_az=512, az_res=2 * math.pi / 512,
