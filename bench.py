@@ -750,35 +750,49 @@ def serving_bench(args, dev):
 
 def head_bench(args, dev):
     """Learned ray head: one training epoch over 10M lidar rays rendered from a
-    500k-Gaussian scene (29 channels) at 38 poses along a 15 m/s trajectory, and inference."""
+    500k-Gaussian scene (29 channels) at 38 poses along a 15 m/s trajectory, and inference;
+    held-out scores on four more sweeps (~1M rays) against the decoder-free baseline
+    (per-Gaussian intensity and drop channels fitted through the rasterizer's backward
+    with Adam for the same number of steps)."""
     import torch
-    from paper_2411_16816_gb300.head import RayHead, head_inputs
+    from paper_2411_16816_gb300.head import PlainChannels, RayHead, head_inputs
     from paper_2411_16816_gb300.render import Frame, gaussians_to_device
     g = scenes.driving_gaussians(500_000, 1004, channels=29)
     gd = gaussians_to_device(g, dev)
+    n_g = len(g["opacities"])
     elev = scenes.nonuniform_elevations(128)
     res = 2 * math.pi / 2048
     tp = scenes.teacher_params(77)
-    xs, yi, yd = [], [], []
+
+    def sweep(k):
+        v, w = scenes.ego_motion(np.eye(3), 15.0, 0.0)
+        return scenes.Lidar(R=np.eye(3), t=np.array([-1.5 * k, 0.0, 0.0]), beam_elev=elev, n_az=2048, az_res=res,
+                            sweep_time=0.1, eps2d=scenes.lidar_blur(elev, res), lin_vel=v, ang_vel=w)
+
+    def rendered(k):
+        lid = sweep(k)
+        fr = Frame([lid], n_g, 29, dev)
+        out = fr.forward(gd, keep_state=False)
+        x = head_inputs(fr, 0, out["lid_feat"])
+        hit = out["lid_alpha"] > 0.5
+        xn = x.cpu().numpy()
+        a, b, p = scenes.teacher_labels(xn[:, :29], xn[:, 29:], tp, seed=200 + k)
+        del fr, out
+        return lid, x, hit, a, b, p
+
+    xs, yi, yd, train_sweeps = [], [], [], []
     total = 0
     k = 0
     while total < 10_000_000:
-        v, w = scenes.ego_motion(np.eye(3), 15.0, 0.0)
-        lid = scenes.Lidar(R=np.eye(3), t=np.array([-1.5 * k, 0.0, 0.0]), beam_elev=elev, n_az=2048, az_res=res,
-                           sweep_time=0.1, eps2d=scenes.lidar_blur(elev, res), lin_vel=v, ang_vel=w)
-        fr = Frame([lid], len(g["opacities"]), 29, dev)
-        out = fr.forward(gd, keep_state=False)
-        x = head_inputs(fr, 0, out["lid_feat"])
+        lid, x, hit, a, b, _ = rendered(k)
         take = min(x.shape[0], 10_000_000 - total)
-        x = x[:take]
-        xn = x.cpu().numpy()
-        a, b, _ = scenes.teacher_labels(xn[:, :29], xn[:, 29:], tp, seed=200 + k)
-        xs.append(x)
-        yi.append(torch.as_tensor(a, device=dev))
-        yd.append(torch.as_tensor(b, device=dev))
+        xs.append(x[:take])
+        yi.append(torch.as_tensor(a[:take], device=dev))
+        yd.append(torch.as_tensor(b[:take], device=dev))
+        if take == x.shape[0]:
+            train_sweeps.append((lid, hit, yi[-1][hit], yd[-1][hit]))
         total += take
         k += 1
-        del fr, out
     X, YI, YD = torch.cat(xs), torch.cat(yi), torch.cat(yd)
     del xs, yi, yd
     head = RayHead(scenes.head_init_params(21), dev, lr=3e-3)
@@ -805,16 +819,105 @@ def head_bench(args, dev):
     b.record(stream)
     torch.cuda.synchronize()
     infer_ms = a.elapsed_time(b) / 5
+    n_train = X.shape[0]
+    del X, YI, YD, out
+    torch.cuda.empty_cache()
+
+    # the decoder-free baseline, the same number of Adam steps as the head's epoch
+    base = PlainChannels(gd, n_g, dev, lr=0.05)
+    frames = {}
+    for step in range(3 + len(starts)):
+        j = step % len(train_sweeps)
+        lid, hit, ti, td = train_sweeps[j]
+        if j not in frames:
+            frames[j] = Frame([lid], n_g, 2, dev)
+        base.step(frames[j], hit, ti, td)
+    del frames
+    torch.cuda.empty_cache()
+
+    # held-out sweeps: hit rays only, intensity RMSE, drop BCE, drop decision vs p_drop > 0.5
+    def bce(p, y):
+        p = np.clip(p, 1e-4, 1 - 1e-4)
+        return float(-np.mean(y * np.log(p) + (1 - y) * np.log(1 - p)))
+
+    hi_, hd_, bi_, bd_, yi_, yd_, pd_, hit_ = [], [], [], [], [], [], [], []
+    for kk in range(k, k + 4):
+        lid, x, hit, ti, td, pdrop = rendered(kk)
+        o = head.forward(x).cpu().numpy().astype(np.float64)
+        hi_.append(1 / (1 + np.exp(-o[:, 0])))
+        hd_.append(1 / (1 + np.exp(-o[:, 1])))
+        fr = Frame([lid], n_g, 2, dev)
+        s_i, s_d = PlainChannels.predict(base.render(fr)["lid_feat"])
+        bi_.append(s_i.cpu().numpy().astype(np.float64))
+        bd_.append(s_d.cpu().numpy().astype(np.float64))
+        yi_.append(ti)
+        yd_.append(td)
+        pd_.append(pdrop)
+        hit_.append(hit.cpu().numpy())
+        del fr
+    cat = np.concatenate
+    hi_, hd_, bi_, bd_, yi_, yd_, pd_, hit_ = (cat(v) for v in (hi_, hd_, bi_, bd_, yi_, yd_, pd_, hit_))
+
+    def score(pi, pdd, m):
+        return {"intensity_rmse": float(np.sqrt(np.mean((pi[m] - yi_[m]) ** 2))), "drop_bce": bce(pdd[m], yd_[m]),
+                "drop_decision_acc": float(np.mean((pdd[m] > 0.5) == (pd_[m] > 0.5)))}
+
+    def compare(m):
+        s_head, s_base = score(hi_, hd_, m), score(bi_, bd_, m)
+        return {"rays": int(m.sum()), "head": s_head, "plain_channels": s_base,
+                "gain": {"intensity_rmse": s_base["intensity_rmse"] - s_head["intensity_rmse"],
+                         "drop_bce": s_base["drop_bce"] - s_head["drop_bce"],
+                         "drop_decision_acc": s_head["drop_decision_acc"] - s_base["drop_decision_acc"]}}
+
+    held = {"sweeps": 4, "all_rays": compare(np.ones(len(yi_), bool)), "hit_rays": compare(hit_),
+            "baseline": "per-Gaussian intensity and drop logit channels composited by the rasterizer, fitted "
+                        f"through its backward with Adam for {3 + len(starts)} steps (one sweep each, hit rays), "
+                        "the same App. B loss"}
+
+    # inference on one more sweep: the decoder fused into the lidar forward's epilogue
+    # against the lidar forward, the input packing and the decoder as separate launches
+    from paper_2411_16816_gb300.head import render_lidar_decoded
+    fr = Frame([sweep(k + 4)], n_g, 29, dev)
+    cg = fr.prepare(gd)
+    o_unf = fr.alloc_outputs(False)
+    hout = torch.empty((fr.lid_rays, 2), dtype=torch.float32, device=dev)
+    fo = render_lidar_decoded(fr, gd, head, features=False, prepared=cg)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed_ms(fn, reps=20):
+        ts = []
+        for _ in range(3):
+            fn()
+        for i in range(reps):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.mean(ts)
+
+    ms_fused = timed_ms(lambda: render_lidar_decoded(fr, gd, head, prepared=cg, out=fo))
+    ms_render = timed_ms(lambda: fr.rasterize(cg, o_unf))
+    ms_decode = timed_ms(lambda: head.forward(head_inputs(fr, 0, o_unf["lid_feat"]), hout))
+    fused = {"rays": fr.lid_rays, "ms_fused": ms_fused, "ms_unfused": ms_render + ms_decode,
+             "ms_unfused_parts": {"lidar_forward": ms_render, "input_packing_and_decoder": ms_decode},
+             "note": "one 128x2048 sweep of the 500k-Gaussian scene; fused = splat_render_lidar_head (features "
+                     "not written), unfused = splat_render_lidar + splat_head_inputs + splat_head_forward"}
+    del fr, o_unf, hout, fo, flush
+    torch.cuda.empty_cache()
+
     flop_train = 2 * (32 * 64 + 64 * 64 + 64 * 2) * 3
     peaks = measured_peaks()
-    train_tf = X.shape[0] * flop_train / (epoch_ms * 1e-3) / 1e12
-    infer_gbs = X.shape[0] * (32 + 2) * 4 / (infer_ms * 1e-3) / 1e9
-    return {"workload": f"{X.shape[0]} lidar rays (128x2048 sweeps at {k} poses) of a 500k-Gaussian scene, "
+    train_tf = n_train * flop_train / (epoch_ms * 1e-3) / 1e12
+    infer_gbs = n_train * (32 + 2) * 4 / (infer_ms * 1e-3) / 1e9
+    return {"workload": f"{n_train} lidar rays (128x2048 sweeps at {k} poses) of a 500k-Gaussian scene, "
                         "29 rendered channels + ray direction -> 64 -> 64 -> 2, BF16 weights, FP32 accumulate",
-            "train_epoch_ms": epoch_ms, "train_rays_per_s": X.shape[0] / (epoch_ms * 1e-3),
+            "train_epoch_ms": epoch_ms, "train_rays_per_s": n_train / (epoch_ms * 1e-3),
             "minibatch": B, "steps": len(starts), "last_loss": loss,
-            "infer_ms": infer_ms, "infer_rays_per_s": X.shape[0] / (infer_ms * 1e-3),
-            "train_tflops": train_tf,
+            "infer_ms": infer_ms, "infer_rays_per_s": n_train / (infer_ms * 1e-3),
+            "train_tflops": train_tf, "held_out": held, "fused_decode": fused,
             "roofline": {"bound": "tensor", "kernel": "k_head_train", "achieved": train_tf,
                          "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": train_tf / peaks["bf16_tflops"],
                          "note": "algorithmic flops (37,632 per ray) against the measured BF16 GEMM peak; the split "

@@ -268,6 +268,22 @@ splat_status splat_render_lidar_los(const splat_gaussians *g, int32_t n_sensors,
                                     float *out_range_med, float *out_alpha, float *out_T, int32_t *out_last,
                                     splat_los los, float *out_los, uint64_t *evaluated, void *stream);
 
+/* Lidar rendering with the per-ray decoder fused into the raster epilogue (Sec. 3.3:
+ * the rendered features and the ray direction are decoded per ray into intensity and
+ * ray-drop; App. B: the two-hidden-layer decoder).  Renders every lidar sensor of the
+ * frame exactly as splat_render_lidar does (out_feat may be NULL: the features are then
+ * not written) and decodes each ray's 29 rendered channels and unit direction
+ * (cos w cos phi, cos w sin phi, sin w) with the decoder's BF16 weights head_w (W1 | W2 |
+ * W3, row-major [in][out], as splat_head_train keeps them) and FP32 biases head_b into
+ * out_head[rays][2] = (intensity logit, ray-drop logit).  The result equals
+ * splat_head_inputs followed by splat_head_forward bit for bit, without the rendered
+ * features passing through device memory.  Requires channels == 29 and the lidar tile
+ * 32 x 8 (else SPLAT_ERR_INVALID_ARG); out_head 8-byte aligned.  Asynchronous. */
+splat_status splat_render_lidar_head(const splat_gaussians *g, int32_t n_sensors, const splat_sensor *sensors,
+                                     splat_projected proj, splat_bins bins, float *out_feat, float *out_range_exp,
+                                     float *out_range_med, float *out_alpha, float *out_T, int32_t *out_last,
+                                     const uint16_t *head_w, const float *head_b, float *out_head, void *stream);
+
 /* Backward of splat_render_camera.  Inputs: the forward's out_T and out_last (or both
  * NULL: the kernel then recomputes them per tile), dL_dfeat[pixels][channels] and
  * dL_dT[pixels] (may be NULL).  Accumulates into

@@ -24,6 +24,7 @@ EXPORTS = [
     "splat_frame_layout", "splat_workspace_size", "splat_project", "splat_count_nonfinite", "splat_bin_sort",
     "splat_bin_sort_backward",
     "splat_render_camera", "splat_render_camera_l1", "splat_render_lidar", "splat_render_lidar_los",
+    "splat_render_lidar_head",
     "splat_render_camera_backward", "splat_render_lidar_backward", "splat_render_lidar_backward_los",
     "splat_sync_status", "splat_lidar_points_to_rays", "splat_lidar_bin_rays", "splat_lidar_bin_rays_capped",
     "splat_render_lidar_rays",
@@ -113,6 +114,7 @@ def load(build_if_missing: bool = True):
     L.splat_render_lidar_backward_los.argtypes = ([G, c_int32, SE, splat_projected, splat_bins] + [c_void_p] * 5 +
                                                   [splat_los] + [c_void_p] * 4)
     L.splat_render_lidar.argtypes = [G, c_int32, SE, splat_projected, splat_bins] + [c_void_p] * 8
+    L.splat_render_lidar_head.argtypes = [G, c_int32, SE, splat_projected, splat_bins] + [c_void_p] * 10
     L.splat_lidar_points_to_rays.argtypes = [c_int32, SE, c_int32, c_void_p, c_void_p, c_int64] + [c_void_p] * 4
     L.splat_lidar_bin_rays.argtypes = [c_int32, SE, c_int32, c_void_p, c_int64, splat_ray_bins, c_void_p]
     L.splat_lidar_bin_rays_capped.argtypes = [c_int32, SE, c_int32, c_void_p, c_void_p, c_int64, c_int32,

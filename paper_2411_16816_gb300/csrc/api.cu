@@ -347,6 +347,30 @@ splat_status splat_render_lidar_los(const splat_gaussians* g, int32_t n_sensors,
                              out_T, out_last, &los, out_los, evaluated, stream, "splat_render_lidar_los");
 }
 
+splat_status splat_render_lidar_head(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
+                                     splat_projected proj, splat_bins bins, float* out_feat, float* out_range_exp,
+                                     float* out_range_med, float* out_alpha, float* out_T, int32_t* out_last,
+                                     const uint16_t* head_w, const float* head_b, float* out_head, void* stream) {
+    Frame fr;
+    int tw, th;
+    splat_status st = render_common(g, n_sensors, sensors, proj, bins, fr, true, tw, th);
+    if (st != SPLAT_OK) return st;
+    if (fr.n_lids == 0) return SPLAT_OK;
+    if (g->channels != 29) return fail(SPLAT_ERR_INVALID_ARG, "splat_render_lidar_head: channels must be 29");
+    if (tw != 32 || th != 8) return fail(SPLAT_ERR_INVALID_ARG, "splat_render_lidar_head: the lidar tile must be 32 x 8");
+    if (!out_range_exp || !out_alpha || !head_w || !head_b || !out_head)
+        return fail(SPLAT_ERR_INVALID_ARG, "out_range_exp, out_alpha, head_w, head_b and out_head are required");
+    if (((uintptr_t)out_head & 7u) || ((uintptr_t)head_w & 3u))
+        return fail(SPLAT_ERR_INVALID_ARG, "out_head or head_w misaligned");
+    RasterIn in{(const float4*)proj.rec, bins.isect_ids, (const int2*)bins.tile_ranges, g->features, g->n,
+                g->channels};
+    RasterOut out{out_feat, out_T, out_last, out_range_exp, out_range_med, out_alpha, nullptr};
+    if (!launch_lidar_fwd_head(tw, th, fr, fr.n_lid_blocks, in, out, HeadW{head_w, head_b}, out_head,
+                               (cudaStream_t)stream))
+        return fail(SPLAT_ERR_INVALID_ARG, "unsupported lidar configuration");
+    return check_launch("splat_render_lidar_head");
+}
+
 splat_status splat_render_camera_backward(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
                                           splat_projected proj, splat_bins bins, const float* out_T,
                                           const int32_t* out_last, const float* dL_dfeat, const float* dL_dT,

@@ -20,165 +20,10 @@
 // across a persistent grid until one flush per block.
 #include <cuda_bf16.h>
 
-#include "mma.cuh"
-#include "types.cuh"
+#include "head_impl.cuh"
+#include "raster_impl.cuh"
 
 namespace splat {
-
-constexpr int kHIn = 32, kHHid = 64, kHOut = 2;
-constexpr int kW1 = kHIn * kHHid, kW2 = kHHid * kHHid, kW3 = kHHid * kHOut;
-constexpr int kHeadParams = kW1 + kHHid + kW2 + kHHid + kW3 + kHOut;   // W1 b1 W2 b2 W3 b3
-constexpr int kHeadWarps = 4;
-constexpr int kHeadThreads = 32 * kHeadWarps;
-constexpr int kHeadRays = 16 * kHeadWarps;   // rays per training-block iteration
-constexpr int kP32 = 40;                      // padded row lengths (BF16 elements) of the shared
-constexpr int kP64 = 72;                      // operands: conflict-free fragment loads
-constexpr int kPR = kHeadRays + 8;            // transposed activations [unit][ray]
-
-struct SplitA {   // an A fragment of split FP32 values
-    uint32_t h[4], l[4];
-};
-
-// Weights in shared memory, in the layouts the fragments read: W^T [out][in] for the
-// forward products, W [in][out] for the backward ones.
-struct HeadSmemW {
-    bf16 w1t[kHHid][kP32];
-    bf16 w2t[kHHid][kP64];
-    bf16 w3t[8][kP64];     // outputs 2..7 are zero (one 8-wide MMA tile)
-    bf16 w1[kHIn][kP64];
-    bf16 w2[kHHid][kP64];
-    float w3[kHHid][kHOut];
-    float b1[kHHid], b2[kHHid], b3[kHOut];
-};
-
-__device__ __forceinline__ void load_head_weights(HeadSmemW& s, const HeadW& hw) {
-    const bf16* w = reinterpret_cast<const bf16*>(hw.w);
-    for (int e = threadIdx.x; e < kW1; e += blockDim.x) {
-        const int i = e / kHHid, j = e % kHHid;
-        s.w1t[j][i] = w[e];
-        s.w1[i][j] = w[e];
-    }
-    for (int e = threadIdx.x; e < kW2; e += blockDim.x) {
-        const int i = e / kHHid, j = e % kHHid;
-        s.w2t[j][i] = w[kW1 + e];
-        s.w2[i][j] = w[kW1 + e];
-    }
-    for (int e = threadIdx.x; e < 8 * kHHid; e += blockDim.x) {
-        const int k = e / kHHid, i = e % kHHid;
-        s.w3t[k][i] = k < kHOut ? w[kW1 + kW2 + i * kHOut + k] : __float2bfloat16_rn(0.f);
-        if (k < kHOut) s.w3[i][k] = __bfloat162float(w[kW1 + kW2 + i * kHOut + k]);
-    }
-    for (int e = threadIdx.x; e < 2 * kHHid + kHOut; e += blockDim.x) {
-        const float v = hw.b[e];
-        if (e < kHHid) s.b1[e] = v;
-        else if (e < 2 * kHHid) s.b2[e - kHHid] = v;
-        else s.b3[e - 2 * kHHid] = v;
-    }
-}
-
-// One C tile (n-tile nt of a 64-wide layer) -> the A fragment of the next layer.
-__device__ __forceinline__ void c_to_a(const float (&d)[4], int nt, SplitA (&a)[4]) {
-    const int ks = nt >> 1, r = (nt & 1) * 2;
-    split_pair(d[0], d[1], a[ks].h[r], a[ks].l[r]);
-    split_pair(d[2], d[3], a[ks].h[r + 1], a[ks].l[r + 1]);
-}
-
-// The forward of one 16-ray tile: x fragments in, H1 / H2 fragments, ReLU masks (bit
-// 4 nt + e for accumulator e of n-tile nt) and the two outputs of rows g and g + 8 out
-// (valid on lanes with t == 0).
-struct HeadFwd {
-    SplitA h1[4], h2[4];
-    uint32_t m1, m2;
-    float o[4];   // (o0, o1) of row g, (o0, o1) of row g + 8
-};
-
-__device__ __forceinline__ void head_forward_tile(const HeadSmemW& s, const SplitA (&xa)[2], HeadFwd& f) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    f.m1 = f.m2 = 0;
-#pragma unroll
-    for (int nt = 0; nt < 8; nt++) {
-        const float ba = s.b1[8 * nt + 2 * t], bb = s.b1[8 * nt + 2 * t + 1];
-        float d[4] = {ba, bb, ba, bb};
-#pragma unroll
-        for (int ks = 0; ks < 2; ks++) {
-            const uint32_t b0 = ld2(&s.w1t[8 * nt + g][16 * ks + 2 * t]);
-            const uint32_t b1 = ld2(&s.w1t[8 * nt + g][16 * ks + 8 + 2 * t]);
-            mma16816(d, xa[ks].h, b0, b1);
-            mma16816(d, xa[ks].l, b0, b1);
-        }
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-            if (d[e] > 0.f) f.m1 |= 1u << (4 * nt + e);
-            else d[e] = 0.f;
-        }
-        c_to_a(d, nt, f.h1);
-    }
-#pragma unroll
-    for (int nt = 0; nt < 8; nt++) {
-        const float ba = s.b2[8 * nt + 2 * t], bb = s.b2[8 * nt + 2 * t + 1];
-        float d[4] = {ba, bb, ba, bb};
-#pragma unroll
-        for (int ks = 0; ks < 4; ks++) {
-            const uint32_t b0 = ld2(&s.w2t[8 * nt + g][16 * ks + 2 * t]);
-            const uint32_t b1 = ld2(&s.w2t[8 * nt + g][16 * ks + 8 + 2 * t]);
-            mma16816(d, f.h1[ks].h, b0, b1);
-            mma16816(d, f.h1[ks].l, b0, b1);
-        }
-#pragma unroll
-        for (int e = 0; e < 4; e++) {
-            if (d[e] > 0.f) f.m2 |= 1u << (4 * nt + e);
-            else d[e] = 0.f;
-        }
-        c_to_a(d, nt, f.h2);
-    }
-    const float b30 = t == 0 ? s.b3[0] : 0.f, b31 = t == 0 ? s.b3[1] : 0.f;
-    float d[4] = {b30, b31, b30, b31};
-#pragma unroll
-    for (int ks = 0; ks < 4; ks++) {
-        const uint32_t b0 = ld2(&s.w3t[g][16 * ks + 2 * t]);
-        const uint32_t b1 = ld2(&s.w3t[g][16 * ks + 8 + 2 * t]);
-        mma16816(d, f.h2[ks].h, b0, b1);
-        mma16816(d, f.h2[ks].l, b0, b1);
-    }
-#pragma unroll
-    for (int e = 0; e < 4; e++) f.o[e] = d[e];
-}
-
-// x rows r0 + g and r0 + g + 8 (zero past R) as split A fragments of the two k-steps;
-// also returns the raw values (k-step ks, register q, element e) for transposed copies.
-__device__ __forceinline__ void load_x_frags(const float* __restrict__ x, int64_t r0, int64_t R, SplitA (&xa)[2],
-                                             float (&xv)[2][4][2]) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const int64_t ra = r0 + g, rb = r0 + g + 8;
-#pragma unroll
-    for (int ks = 0; ks < 2; ks++) {
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int64_t r = (q & 1) ? rb : ra;
-            const int col = 16 * ks + ((q & 2) ? 8 : 0) + 2 * t;
-            float2 v = make_float2(0.f, 0.f);
-            if (r < R) v = *reinterpret_cast<const float2*>(x + r * kHIn + col);
-            xv[ks][q][0] = v.x;
-            xv[ks][q][1] = v.y;
-            split_pair(v.x, v.y, xa[ks].h[q], xa[ks].l[q]);
-        }
-    }
-}
-
-// The A-fragment elements of a 16-ray input tile, as loaded (FP32 pairs).
-__device__ __forceinline__ void load_x_raw(const float* __restrict__ x, int64_t r0, int64_t R, float2 (&v)[2][4]) {
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-#pragma unroll
-    for (int ks = 0; ks < 2; ks++) {
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int64_t r = r0 + g + ((q & 1) ? 8 : 0);
-            const int col = 16 * ks + ((q & 2) ? 8 : 0) + 2 * t;
-            v[ks][q] = r < R ? *reinterpret_cast<const float2*>(x + r * kHIn + col) : make_float2(0.f, 0.f);
-        }
-    }
-}
-
 __global__ void __launch_bounds__(kHeadThreads) k_head_fwd(const float* __restrict__ x, int64_t R, HeadW hw,
                                                            float* __restrict__ out) {
     __shared__ HeadSmemW s;
@@ -540,6 +385,116 @@ __global__ void k_head_inputs(const __grid_constant__ SensorDev S, const float* 
         xr[C + 1] = cw * sp;
         xr[C + 2] = sw;
     }
+}
+
+// ---------------------------------------------------------------------------------
+// Lidar forward with the decoder in its epilogue (Sec. 3.3: each ray's rendered features
+// and its direction decoded into intensity and ray-drop logits).  The block renders its
+// lidar tile exactly as k_raster_fwd does (same traversal, same outputs), then reuses
+// its staging memory for the decoder's forward weights and the tile's 256 input rows
+// [29 features, unit direction]; each warp decodes its 32 rays as two 16-ray tensor-core
+// tiles (head_forward_tile, the unfused decoder's arithmetic).  The features never
+// travel through HBM to reach the decoder.
+// ---------------------------------------------------------------------------------
+constexpr int kXRow = 40;   // floats per input row in shared memory (conflict-free fragment loads)
+
+template <int TW, int TH>
+struct FusedHeadSmem {
+    static constexpr int NT = TW * TH;
+    static constexpr size_t head = (sizeof(HeadSmemFwd) + 15) & ~size_t(15);
+    static constexpr size_t bytes_head = head + sizeof(float) * NT * kXRow;
+    static constexpr size_t bytes_stage = sizeof(Stage<32, NT, true>);
+    static constexpr size_t bytes = bytes_head > bytes_stage ? bytes_head : bytes_stage;
+};
+
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW* TH) k_lidar_fwd_head(const __grid_constant__ Frame fr, RasterIn in,
+                                                           RasterOut out, HeadW hw, float* __restrict__ head_out) {
+    constexpr int CM = 32, NT = TW * TH;
+    static_assert(RaysPerThread<CM, false, true, NT>::value == 1 && NT % 32 == 0, "one ray per thread");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Stage<CM, NT, true>& sm = *reinterpret_cast<Stage<CM, NT, true>*>(smem_raw);
+    TileCtx tc;
+    RayCtx r[1];
+    block_setup<TW, TH, true, false, 1, NT>(fr, in, tc, r);
+    const int2 range = in.ranges[tc.gtile];
+    const TileBox box{};
+    float2 F[1][CM / 2];
+#pragma unroll
+    for (int c = 0; c < CM / 2; c++) F[0][c] = make_float2(0.f, 0.f);
+    FwdState st[1];
+    forward_tile<CM, TW, TH, true, 1, true, false>(sm, in, tc, box, r, range, st, F);
+    const int C = in.C;   // kHIn - 3
+    if (r[0].inside) {
+        const int64_t o = r[0].o;
+        if (out.feat) {
+            float* fo = out.feat + o * C;
+#pragma unroll
+            for (int c = 0; c < CM; c++)
+                if (c < C) fo[c] = (c & 1) ? F[0][c / 2].y : F[0][c / 2].x;
+        }
+        if (out.T) out.T[o] = st[0].T;
+        if (out.last) out.last[o] = st[0].last;
+        out.range_exp[o] = st[0].de;
+        if (out.range_med) out.range_med[o] = st[0].dm;
+        out.alpha[o] = 1.f - st[0].T;
+    }
+    __syncthreads();   // the staging memory is free: decoder weights and input rows
+    HeadSmemFwd& hs = *reinterpret_cast<HeadSmemFwd*>(smem_raw);
+    float* xs = reinterpret_cast<float*>(smem_raw + FusedHeadSmem<TW, TH>::head);
+    load_head_fwd_weights(hs, hw);
+    {
+        float* xr = xs + threadIdx.x * kXRow;
+#pragma unroll
+        for (int c = 0; c < CM; c++)
+            if (c < C) xr[c] = (c & 1) ? F[0][c / 2].y : F[0][c / 2].x;
+        // the unit ray direction, as splat_head_inputs forms it
+        float sp, cp, sw, cw;
+        sincosf(r[0].pa, &sp, &cp);
+        sincosf(r[0].pb, &sw, &cw);
+        xr[C] = cw * cp;
+        xr[C + 1] = cw * sp;
+        xr[C + 2] = sw;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int half = 0; half < 2; half++) {
+        const int row0 = 32 * warp + 16 * half;   // the tile's rays are threads row0 .. row0 + 15
+        SplitA xa[2];
+#pragma unroll
+        for (int ks = 0; ks < 2; ks++) {
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int row = row0 + g + ((q & 1) ? 8 : 0);
+                const int col = 16 * ks + ((q & 2) ? 8 : 0) + 2 * t;
+                const float2 v = *reinterpret_cast<const float2*>(xs + row * kXRow + col);
+                split_pair(v.x, v.y, xa[ks].h[q], xa[ks].l[q]);
+            }
+        }
+        HeadFwd f;
+        head_forward_tile(hs, xa, f);
+        // rows g and g + 8 of the tile belong to lanes 16 half + g (+ 8) of this warp
+        const int64_t oa = __shfl_sync(0xffffffffu, r[0].o, 16 * half + g);
+        const int64_t ob = __shfl_sync(0xffffffffu, r[0].o, 16 * half + g + 8);
+        const bool ia = __shfl_sync(0xffffffffu, (int)r[0].inside, 16 * half + g);
+        const bool ib = __shfl_sync(0xffffffffu, (int)r[0].inside, 16 * half + g + 8);
+        if (t == 0) {
+            if (ia) reinterpret_cast<float2*>(head_out)[oa] = make_float2(f.o[0], f.o[1]);
+            if (ib) reinterpret_cast<float2*>(head_out)[ob] = make_float2(f.o[2], f.o[3]);
+        }
+    }
+}
+
+bool launch_lidar_fwd_head(int tw, int th, const Frame& fr, int blocks, const RasterIn& in, const RasterOut& out,
+                           const HeadW& hw, float* head_out, cudaStream_t st) {
+    if (tw != 32 || th != 8 || in.C != kHIn - 3) return false;
+    constexpr size_t sm = FusedHeadSmem<32, 8>::bytes;
+    auto k = k_lidar_fwd_head<32, 8>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (blocks > 0) k<<<blocks, 256, sm, st>>>(fr, in, out, hw, head_out);
+    return true;
 }
 
 size_t head_train_smem() { return sizeof(HeadTrainSmem); }

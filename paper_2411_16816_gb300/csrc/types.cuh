@@ -128,6 +128,8 @@ struct HeadW {
     const float* b;      // FP32 b1 | b2 | b3
 };
 void launch_head_fwd(const float* x, int64_t R, const HeadW& hw, float* out, cudaStream_t st);
+bool launch_lidar_fwd_head(int tw, int th, const Frame& fr, int blocks, const RasterIn& in, const RasterOut& out,
+                           const HeadW& hw, float* head_out, cudaStream_t st);
 void launch_head_train(const float* x, int64_t R, const HeadW& hw, const float* y_int, const float* y_drop, float lam_i,
                        float lam_d, float* grad, float* loss, float* dx, cudaStream_t st);
 void launch_head_adam(float* p, const float* g, float* m, float* v, float lr, float beta1, float beta2, float eps,

@@ -9,7 +9,7 @@ import torch
 
 from oracle import head as H
 from paper_2411_16816_gb300 import scenes
-from paper_2411_16816_gb300.head import RayHead, flatten, head_inputs, unflatten
+from paper_2411_16816_gb300.head import PlainChannels, RayHead, flatten, head_inputs, render_lidar_decoded, unflatten
 from paper_2411_16816_gb300.render import Frame, gaussians_to_device
 
 pytestmark = pytest.mark.gpu
@@ -99,18 +99,51 @@ def test_head_inputs_pack_features_and_ray_directions():
     np.testing.assert_allclose(x[:, 29:], d, atol=2e-6)
 
 
+def test_decoder_fused_into_the_lidar_forward_equals_the_unfused_path():
+    """splat_render_lidar_head renders the sweep exactly as the lidar forward does and
+    decodes every ray inside the raster epilogue: outputs equal render -> head_inputs ->
+    head forward bit for bit, with and without the features written; moving sensor,
+    non-uniform beams, ragged last azimuth tile."""
+    g = scenes.driving_gaussians(60_000, 1007, channels=29)
+    gd = gaussians_to_device(g, DEV)
+    elev = scenes.nonuniform_elevations(64)
+    res = 2 * math.pi / 1000
+    v, w = scenes.ego_motion(np.eye(3), 15.0, 0.05)
+    lid = scenes.Lidar(R=np.eye(3), t=np.zeros(3), beam_elev=elev, n_az=1000, az_res=res, sweep_time=0.1,
+                       eps2d=scenes.lidar_blur(elev, res), lin_vel=v, ang_vel=w)
+    head = RayHead(scenes.head_init_params(5), DEV)
+    fr = Frame([lid], len(g["opacities"]), 29, DEV)
+    ref = fr.forward(gd)
+    want = head.forward(head_inputs(fr, 0, ref["lid_feat"]))
+    fused = render_lidar_decoded(fr, gd, head)
+    torch.cuda.synchronize()
+    assert (ref["lid_alpha"] > 0.5).float().mean() > 0.3
+    for k in ("lid_feat", "lid_range_exp", "lid_range_med", "lid_alpha"):
+        assert torch.equal(fused[k], ref[k]), k
+    assert torch.equal(fused["head"], want)
+    bare = render_lidar_decoded(fr, gd, head, features=False)
+    torch.cuda.synchronize()
+    assert bare["lid_feat"] is None and torch.equal(bare["head"], want)
+    # against the FP64 decoder oracle on a sample of rays
+    x = head_inputs(fr, 0, ref["lid_feat"]).cpu().numpy().astype(np.float64)
+    sel = np.random.default_rng(3).choice(x.shape[0], 500, replace=False)
+    o = H.forward(x[sel], _bf16_params(head))
+    np.testing.assert_allclose(fused["head"].cpu().numpy()[sel], o, rtol=1e-4, atol=1e-4)
+
+
 # ----------------------------------------------------------------------------------
 # Gain: decoder trained by these kernels on rendered rays vs plain composited channels
 # ----------------------------------------------------------------------------------
 
 def _sweeps(n_gauss=200_000, n_poses=5, seed=1004):
     """Lidar sweeps (64 beams x 1024, non-uniform, 100 ms) from poses 0.5 m apart along +x,
-    rendering 29 feature channels; returns (x, rendered features) per sweep."""
+    rendering 29 feature channels.  Returns the scene on the device, the lidars, and per
+    sweep the decoder inputs of its hit rays (alpha > 0.5) and the hit mask."""
     g = scenes.driving_gaussians(n_gauss, seed, channels=29)
     gd = gaussians_to_device(g, DEV)
     elev = scenes.nonuniform_elevations(64)
     res = 2 * math.pi / 1024
-    xs, fs = [], []
+    lids, xs, masks = [], [], []
     for k in range(n_poses):
         v, w = scenes.ego_motion(np.eye(3), 15.0, 0.0)
         lid = scenes.Lidar(R=np.eye(3), t=np.array([-0.5 * k, 0.0, 0.0]), beam_elev=elev, n_az=1024, az_res=res,
@@ -119,13 +152,24 @@ def _sweeps(n_gauss=200_000, n_poses=5, seed=1004):
         out = fr.forward(gd, keep_state=False)
         x = head_inputs(fr, 0, out["lid_feat"])
         keep = out["lid_alpha"] > 0.5          # rays that hit something
+        lids.append(lid)
         xs.append(x[keep])
-        fs.append(out["lid_feat"][keep])
-    return xs, fs
+        masks.append(keep)
+    return gd, lids, xs, masks
+
+
+def _bce(p, y):
+    p = np.clip(p, 1e-4, 1 - 1e-4)
+    return -np.mean(y * np.log(p) + (1 - y) * np.log(1 - p))
 
 
 def test_trained_head_beats_plain_composited_channels():
-    xs, fs = _sweeps()
+    """App. B's decoder against the method without it (the hot-path table's baseline):
+    per-Gaussian intensity and ray-drop logit channels composited by the rasterizer and
+    fitted through its own backward with Adam, for the same 1,500 steps and loss.  Scored
+    on a held-out sweep: intensity RMSE, drop BCE and the drop decision against the
+    noise-free probability."""
+    gd, lids, xs, masks = _sweeps()
     tp = scenes.teacher_params(77)
     data = []
     for k, x in enumerate(xs):
@@ -133,6 +177,7 @@ def test_trained_head_beats_plain_composited_channels():
         yi, yd, pd = scenes.teacher_labels(xn[:, :29], xn[:, 29:], tp, seed=100 + k)
         data.append((x, torch.as_tensor(yi, device=DEV), torch.as_tensor(yd, device=DEV), xn, yi, yd, pd))
     train, test = data[:-1], data[-1]
+    steps = 1500
     xtr = torch.cat([d[0] for d in train])
     yitr = torch.cat([d[1] for d in train])
     ydtr = torch.cat([d[2] for d in train])
@@ -140,34 +185,32 @@ def test_trained_head_beats_plain_composited_channels():
     perm_rng = torch.Generator(device=DEV).manual_seed(0)
     n = xtr.shape[0]
     B = 16384
-    for step in range(1500):
+    for step in range(steps):
         idx = torch.randint(0, n, (B,), device=DEV, generator=perm_rng)
         head.train_step(xtr[idx].contiguous(), yitr[idx].contiguous(), ydtr[idx].contiguous())
     o = head.forward(test[0]).cpu().numpy().astype(np.float64)
     yi_te, yd_te, pd_te = test[4], test[5], test[6]
-
-    def bce(p, y):
-        p = np.clip(p, 1e-4, 1 - 1e-4)
-        return -np.mean(y * np.log(p) + (1 - y) * np.log(1 - p))
-
     head_rmse = np.sqrt(np.mean((1 / (1 + np.exp(-o[:, 0])) - yi_te) ** 2))
     head_pd = 1 / (1 + np.exp(-o[:, 1]))
     # drop labels are Bernoulli draws: score the predicted probability (held-out BCE) and
     # its decision against the noise-free one (p_drop > 0.5)
-    head_bce, head_acc = bce(head_pd, yd_te), np.mean((head_pd > 0.5) == (pd_te > 0.5))
-    # plain composited channels: the best linear read-out of the 29 rendered channels
-    Ftr = np.concatenate([d[3][:, :29] for d in train]).astype(np.float64)
-    A = np.concatenate([Ftr, np.ones((len(Ftr), 1))], 1)
-    yi_tr = np.concatenate([d[4] for d in train])
-    yd_tr = np.concatenate([d[5] for d in train])
-    ci = np.linalg.lstsq(A, yi_tr, rcond=None)[0]
-    cd = np.linalg.lstsq(A, yd_tr, rcond=None)[0]
-    Ate = np.concatenate([test[3][:, :29].astype(np.float64), np.ones((len(test[3]), 1))], 1)
-    base_rmse = np.sqrt(np.mean((np.clip(Ate @ ci, 0, 1) - yi_te) ** 2))
-    base_pd = Ate @ cd
-    base_bce, base_acc = bce(base_pd, yd_te), np.mean((base_pd > 0.5) == (pd_te > 0.5))
+    head_bce, head_acc = _bce(head_pd, yd_te), np.mean((head_pd > 0.5) == (pd_te > 0.5))
+
+    # the method without the decoder: two per-Gaussian channels fitted through the rasterizer
+    n_g = gd["means"].shape[0]
+    base = PlainChannels(gd, n_g, DEV, lr=0.05)
+    frames = [Frame([lid], n_g, 2, DEV) for lid in lids]
+    for step in range(steps):
+        k = step % len(train)
+        base.step(frames[k], masks[k], train[k][1], train[k][2])
+    out = base.render(frames[-1])
+    s_i, s_d = PlainChannels.predict(out["lid_feat"][masks[-1]])
+    s_i = s_i.cpu().numpy().astype(np.float64)
+    s_d = s_d.cpu().numpy().astype(np.float64)
+    base_rmse = np.sqrt(np.mean((s_i - yi_te) ** 2))
+    base_bce, base_acc = _bce(s_d, yd_te), np.mean((s_d > 0.5) == (pd_te > 0.5))
     print(f"held-out rays {len(yi_te)}: head RMSE {head_rmse:.4f} drop BCE {head_bce:.4f} decision {head_acc:.4f}; "
-          f"plain channels RMSE {base_rmse:.4f} drop BCE {base_bce:.4f} decision {base_acc:.4f}")
-    assert head_rmse < 0.5 * base_rmse
+          f"per-Gaussian channels RMSE {base_rmse:.4f} drop BCE {base_bce:.4f} decision {base_acc:.4f}")
+    assert head_rmse < 0.7 * base_rmse
     assert head_bce < base_bce
-    assert head_acc > base_acc + 0.02
+    assert head_acc > base_acc
