@@ -737,6 +737,19 @@ def serving_bench(args, dev):
     ms, lat = time_replays(br, args.serving_replays)
     overflow = br.overflowed()
     best = min(table, key=table.get)
+    from paper_2411_16816_gb300.batch import stage_times
+    stages = stage_times(br)
+    C = br.C
+    ev = stages["evaluated_pairs"]
+    flop = ev["camera"] * (22 + 2 * C) + ev["lidar"] * (30 + 2 * C)
+    peak = fp32_peak_tflops(measured_peaks()["sm_max_mhz"])
+    achieved = flop / (stages["persistent_raster"] * 1e-3) / 1e12
+    raster_roofline = {"bound": "alu", "kernel": "k_raster_batch", "achieved": achieved, "peak": peak,
+                       "unit": "TFLOP/s", "frac": achieved / peak,
+                       "work": "(22 + 2C) flop per evaluated camera pair, (30 + 2C) per lidar pair, C = 16",
+                       "per_frame_kernels_same_lists_frac": (None if stages["per_frame_raster_same_lists"] is None
+                                                             else (flop / (stages["per_frame_raster_same_lists"] *
+                                                                           1e-3) / 1e12) / peak)}
     return {"workload": "64 requests (12x640x480, 12x1280x720, 12x1920x1080 RS cameras, 14x 32x1080 and "
                         "14x 128x2048 lidar sweeps) over 200k/800k/2M-Gaussian scenes, forward, 16 channels",
             "rays_per_batch": br.rays, "replays": args.serving_replays,
@@ -745,7 +758,11 @@ def serving_bench(args, dev):
             "rays_per_s": br.rays / (float(np.median(ms)) * 1e-3),
             "tiles": {"camera": list(best[0]), "lidar": list(best[1])},
             "autotune_ms_per_batch": {f"cam{c[0]}x{c[1]}_lid{l[0]}x{l[1]}": v for (c, l), v in table.items()},
-            "autotune_s": tune_s, "gpu_launches_per_batch": br.launches(), "overflow": overflow}
+            "autotune_s": tune_s, "gpu_launches_per_batch": br.launches(), "overflow": overflow,
+            "stage_ms": {k: stages[k] for k in ("project", "bin_sort", "persistent_raster",
+                                                "per_frame_raster_same_lists")},
+            "intersections": stages["intersections"], "evaluated_pairs": ev, "raster_roofline": raster_roofline,
+            "raster_rays_per_s": br.rays / (stages["persistent_raster"] * 1e-3)}
 
 
 def head_bench(args, dev):

@@ -462,10 +462,12 @@ splat_status splat_batch_build(const splat_batch_request *reqs, int32_t n_reques
  * counters: device int32[n_requests + 1] (reset by this call); stamps, if not NULL:
  * device uint64[n_requests + 1] receiving the global-timer nanoseconds at which each
  * request's last tile finished, and in stamps[n_requests] the time the batch started.
- * max_channels is the largest channel count of the requests (<= 32).  Safe to capture
- * in a CUDA graph (it enqueues a memset and two kernels). */
+ * max_channels is the largest channel count of the requests (<= 32).  evaluated, if not
+ * NULL: device uint64[2] to which the (ray, Gaussian) pairs the launch examines are
+ * added (cameras, lidars) -- a counting variant of the kernel, for work accounting.
+ * Safe to capture in a CUDA graph (it enqueues a memset and two kernels). */
 splat_status splat_render_batch(const void *table, int32_t n_requests, int64_t total_items, int32_t max_channels,
-                                int32_t *counters, uint64_t *stamps, void *stream);
+                                int32_t *counters, uint64_t *stamps, uint64_t *evaluated, void *stream);
 
 /* Writes the device global timer (nanoseconds) to the device uint64 *at when the stream
  * reaches this point (latency bookkeeping for batches). */

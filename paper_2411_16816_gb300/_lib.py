@@ -138,7 +138,7 @@ def load(build_if_missing: bool = True):
     L.splat_batch_table_bytes.argtypes = [c_int32]
     L.splat_batch_table_bytes.restype = c_size_t
     L.splat_batch_build.argtypes = [P(splat_batch_request), c_int32, c_void_p, c_size_t, P(c_int64)]
-    L.splat_render_batch.argtypes = [c_void_p, c_int32, c_int64, c_int32, c_void_p, c_void_p, c_void_p]
+    L.splat_render_batch.argtypes = [c_void_p, c_int32, c_int64, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]
     L.splat_stamp.argtypes = [c_void_p, c_void_p]
     L.splat_last_error.argtypes = []
     L.splat_last_error.restype = ctypes.c_char_p

@@ -124,7 +124,7 @@ class BatchRenderer:
             fr.project(cg)
             fr.bin_sort()
         L.call("splat_render_batch", _vp(self.table), self.n, self.total_items, self.C, _vp(self.counters),
-               _vp(self.stamps), st)
+               _vp(self.stamps), None, st)
 
     def capture(self):
         torch.cuda.synchronize()
@@ -156,6 +156,60 @@ class BatchRenderer:
         """Outputs of the caller's request number `request_index`."""
         pos = self.order.index(request_index)
         return self.outputs[pos]
+
+
+def stage_times(br: BatchRenderer, reps: int = 5) -> dict:
+    """Where a batch's time goes: each stage launched on its own (eager, CUDA events,
+    mean of `reps`) -- every group's projection, every group's binning, the persistent
+    raster launch -- and the (ray, Gaussian) pairs the persistent launch examines
+    (camera, lidar; its counting variant), the work behind its roofline.  When the
+    batch's tile shapes are ones the per-frame kernels take, the same lists rasterized
+    by the per-frame kernels (one camera and one lidar launch per group) are timed too."""
+    stream = torch.cuda.current_stream()
+    cgs = [fr.c_gaussians(br.scenes[sc]) for fr, sc, _ in br.groups]
+
+    def timed(fn):
+        ts = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(b))
+        return float(np.mean(ts))
+
+    def project():
+        for (fr, _, _), cg in zip(br.groups, cgs):
+            fr.project(cg)
+
+    def binning():
+        for fr, _, _ in br.groups:
+            fr.bin_sort()
+
+    def raster(ev=None):
+        L.call("splat_render_batch", _vp(br.table), br.n, br.total_items, br.C, _vp(br.counters), _vp(br.stamps),
+               _vp(ev), _stream())
+
+    res = {"project": timed(project), "bin_sort": timed(binning), "persistent_raster": timed(raster)}
+    ev = torch.zeros(2, dtype=torch.int64, device=br.device)
+    raster(ev)
+    torch.cuda.synchronize()
+    res["evaluated_pairs"] = {"camera": int(ev[0].item()), "lidar": int(ev[1].item())}
+    res["intersections"] = int(sum(int(fr.n_isect.item()) for fr, _, _ in br.groups))
+    per_frame_ok = all(((s.tile_w, s.tile_h) in ((16, 16), (8, 8), (32, 8), (16, 32))) if s.kind == "camera" else
+                       ((s.tile_az, s.tile_el) in ((32, 8), (16, 8), (32, 16), (64, 8)))
+                       for fr, _, _ in br.groups for s in fr.sensors)
+    res["per_frame_raster_same_lists"] = None
+    if per_frame_ok:
+        outs = [fr.alloc_outputs(False) for fr, _, _ in br.groups]
+
+        def per_frame():
+            for (fr, _, _), cg, o in zip(br.groups, cgs, outs):
+                fr.rasterize(cg, o)
+        res["per_frame_raster_same_lists"] = timed(per_frame)
+        del outs
+    return res
 
 
 def time_replays(br: BatchRenderer, reps: int = 10):

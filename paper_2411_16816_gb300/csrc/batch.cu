@@ -48,8 +48,9 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-template <int CM, bool LIDAR>
-__device__ __forceinline__ void batch_tile(const BatchReqDev& B, int lt, unsigned char* smem_raw) {
+template <int CM, bool LIDAR, bool COUNT>
+__device__ __forceinline__ void batch_tile(const BatchReqDev& B, int lt, unsigned char* smem_raw,
+                                           unsigned long long* evaluated) {
     constexpr int PX = kBatchPX;
     Stage<CM, kBatchThreads, LIDAR>& sm = *reinterpret_cast<Stage<CM, kBatchThreads, LIDAR>*>(smem_raw);
     const SensorDev& S = B.S;
@@ -73,7 +74,13 @@ __device__ __forceinline__ void batch_tile(const BatchReqDev& B, int lt, unsigne
         for (int c = 0; c < CM / 2; c++) F[q][c] = make_float2(0.f, 0.f);
     FwdState st[PX];
     // 16 x 16 only fixes the 256-ray batch size here; the ray layout comes from r[].
-    forward_tile<CM, 16, 16, LIDAR, PX, true>(sm, in, tc, box, r, range, st, F);
+    const int evals = forward_tile<CM, 16, 16, LIDAR, PX, true, COUNT>(sm, in, tc, box, r, range, st, F);
+    if (COUNT) {
+        unsigned long long e = (unsigned long long)evals;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) e += __shfl_xor_sync(0xffffffffu, e, o);
+        if ((threadIdx.x & 31) == 0 && e) atomicAdd(evaluated + (LIDAR ? 1 : 0), e);
+    }
     const int C = B.C;
 #pragma unroll
     for (int q = 0; q < PX; q++) {
@@ -100,10 +107,11 @@ __device__ __forceinline__ void batch_tile(const BatchReqDev& B, int lt, unsigne
     }
 }
 
-template <int CM>
+template <int CM, bool COUNT>
 __global__ void __launch_bounds__(kBatchThreads, 4) k_raster_batch(const BatchReqDev* __restrict__ tab, int n_req,
                                                                int64_t total, int* counters,
-                                                               unsigned long long* stamps) {
+                                                               unsigned long long* stamps,
+                                                               unsigned long long* evaluated) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int64_t s_base[kMaxBatch + 1];
     __shared__ int64_t s_item;
@@ -123,8 +131,8 @@ __global__ void __launch_bounds__(kBatchThreads, 4) k_raster_batch(const BatchRe
         }
         const BatchReqDev& B = tab[lo];
         const int lt = (int)(item - s_base[lo]);
-        if (B.S.kind == SPLAT_SENSOR_CAMERA) batch_tile<CM, false>(B, lt, smem_raw);
-        else batch_tile<CM, true>(B, lt, smem_raw);
+        if (B.S.kind == SPLAT_SENSOR_CAMERA) batch_tile<CM, false, COUNT>(B, lt, smem_raw, evaluated);
+        else batch_tile<CM, true, COUNT>(B, lt, smem_raw, evaluated);
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
@@ -138,9 +146,10 @@ __global__ void k_stamp(unsigned long long* at) { *at = global_ns(); }
 
 template <int CM>
 static splat_status launch_batch_t(const BatchReqDev* tab, int n_req, int64_t total, int* counters,
-                                   unsigned long long* stamps, cudaStream_t st) {
+                                   unsigned long long* stamps, unsigned long long* evaluated, cudaStream_t st) {
     const size_t sm = sizeof(Stage<CM, kBatchThreads, true>);
-    auto k = k_raster_batch<CM>;
+    // the evaluated-pair counter is compiled in only when it is asked for
+    auto k = evaluated ? k_raster_batch<CM, true> : k_raster_batch<CM, false>;
     if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     int per_sm = 0, dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -152,7 +161,7 @@ static splat_status launch_batch_t(const BatchReqDev* tab, int n_req, int64_t to
     if (grid < 1) grid = 1;
     cudaMemsetAsync(counters, 0, sizeof(int) * (size_t)(n_req + 1), st);
     if (stamps) k_stamp<<<1, 1, 0, st>>>(stamps + n_req);
-    k<<<(unsigned)grid, kBatchThreads, sm, st>>>(tab, n_req, total, counters, stamps);
+    k<<<(unsigned)grid, kBatchThreads, sm, st>>>(tab, n_req, total, counters, stamps, evaluated);
     return SPLAT_OK;
 }
 
@@ -221,17 +230,18 @@ splat_status splat_stamp(uint64_t* at, void* stream) {
 }
 
 splat_status splat_render_batch(const void* table, int32_t n_requests, int64_t total_items, int32_t max_channels,
-                                int32_t* counters, uint64_t* stamps, void* stream) {
+                                int32_t* counters, uint64_t* stamps, uint64_t* evaluated, void* stream) {
     if (!table || n_requests < 1 || n_requests > kMaxBatch || total_items < 0 || !counters)
         return record_error(SPLAT_ERR_INVALID_ARG, "splat_render_batch: bad arguments");
     if (total_items == 0) return SPLAT_OK;
     const BatchReqDev* tab = reinterpret_cast<const BatchReqDev*>(table);
     cudaStream_t st = (cudaStream_t)stream;
     unsigned long long* sp = (unsigned long long*)stamps;
+    unsigned long long* ev = (unsigned long long*)evaluated;
     splat_status rc;
-    if (max_channels <= 4) rc = launch_batch_t<4>(tab, n_requests, total_items, counters, sp, st);
-    else if (max_channels <= 16) rc = launch_batch_t<16>(tab, n_requests, total_items, counters, sp, st);
-    else if (max_channels <= 32) rc = launch_batch_t<32>(tab, n_requests, total_items, counters, sp, st);
+    if (max_channels <= 4) rc = launch_batch_t<4>(tab, n_requests, total_items, counters, sp, ev, st);
+    else if (max_channels <= 16) rc = launch_batch_t<16>(tab, n_requests, total_items, counters, sp, ev, st);
+    else if (max_channels <= 32) rc = launch_batch_t<32>(tab, n_requests, total_items, counters, sp, ev, st);
     else return record_error(SPLAT_ERR_INVALID_ARG, "splat_render_batch: at most 32 channels");
     if (rc != SPLAT_OK) return rc;
     const cudaError_t e = cudaGetLastError();

@@ -111,3 +111,23 @@ def test_autotuner_picks_a_tiling():
     best.replay()
     torch.cuda.synchronize()
     assert not best.overflowed()
+
+
+def test_batch_work_counter_equals_the_per_frame_counts():
+    """The persistent launch's counting variant examines exactly the (ray, Gaussian) pairs
+    the per-frame kernels examine on the same lists (camera and lidar separately), and the
+    stage breakdown covers every stage."""
+    from paper_2411_16816_gb300.batch import stage_times
+    sc, reqs = _small_batch(seed=17)
+    gd = [gaussians_to_device(g, DEV) for g in sc]
+    br = BatchRenderer(gd, reqs, (16, 16), (32, 8), DEV).capture()
+    br.replay()
+    want = torch.zeros(2, dtype=torch.int64, device=DEV)
+    for fr, si, _ in br.groups:
+        fr.rasterize(fr.c_gaussians(gd[si]), fr.alloc_outputs(False), evaluated=want)
+    st = stage_times(br, reps=2)
+    torch.cuda.synchronize()
+    assert st["evaluated_pairs"]["camera"] == int(want[0]) > 0
+    assert st["evaluated_pairs"]["lidar"] == int(want[1]) > 0
+    for k in ("project", "bin_sort", "persistent_raster", "per_frame_raster_same_lists"):
+        assert st[k] > 0, k
