@@ -23,8 +23,17 @@ CAMERA_SHAPES = [(16, 16), (32, 8), (8, 32), (64, 4)]
 LIDAR_SHAPES = [(32, 8), (16, 16), (64, 4)]
 
 
+MAX_GROUP_TILES = 65535
+
+
 def _rays(s):
     return s.n_rays
+
+
+def _tiles(s):
+    if s.kind == "camera":
+        return (-(-s.width // s.tile_w)) * (-(-s.height // s.tile_h))
+    return (-(-s.n_az // s.tile_az)) * (s.n_beams // s.tile_el)
 
 
 class BatchRenderer:
@@ -51,8 +60,19 @@ class BatchRenderer:
         self.groups = []          # (frame, scene index, [(request position, sensor index)])
         for sc in range(len(scenes)):
             mine = [(pos, r) for pos, r in enumerate(reqs) if r[1] == sc]
-            for k in range(0, len(mine), L.SPLAT_MAX_SENSORS):
-                chunk = mine[k:k + L.SPLAT_MAX_SENSORS]
+            # a group holds at most 16 sensors and 65,535 tiles: its tile ids then fit 16 bits
+            # and its tile sort takes two 8-bit passes
+            chunks, cur, cur_tiles = [], [], 0
+            for item in mine:
+                t = _tiles(item[1][2])
+                if cur and (len(cur) == L.SPLAT_MAX_SENSORS or cur_tiles + t > MAX_GROUP_TILES):
+                    chunks.append(cur)
+                    cur, cur_tiles = [], 0
+                cur.append(item)
+                cur_tiles += t
+            if cur:
+                chunks.append(cur)
+            for chunk in chunks:
                 fr = Frame([r[2] for _, r in chunk], scenes[sc]["means"].shape[0], self.C, self.device)
                 self.groups.append((fr, sc, [(pos, j) for j, (pos, _) in enumerate(chunk)]))
         # size every group's intersection buffers once (one host read per group)

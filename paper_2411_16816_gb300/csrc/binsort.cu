@@ -174,12 +174,14 @@ struct HistOut {
     __device__ void operator()(int64_t i, int64_t prefix, int64_t) const { h[i] = (uint32_t)prefix; }
 };
 
-// Lanes of the warp holding the same 9-bit value (an 8-bit digit or 256 for no key): one
-// ballot per bit, keeping the lanes that agree with this lane on every bit.
+// Lanes of the warp holding the same BITS-bit value (an 8-bit digit, or with 9 bits also
+// 256 for no key): one ballot per bit, keeping the lanes that agree with this lane on
+// every bit.
+template <int BITS>
 __device__ __forceinline__ uint32_t warp_peers(uint32_t d) {
     uint32_t m = 0xffffffffu;
 #pragma unroll
-    for (int b = 0; b < 9; b++) {
+    for (int b = 0; b < BITS; b++) {
         const bool bit = (d >> b) & 1u;
         const uint32_t bal = __ballot_sync(0xffffffffu, bit);
         m &= bit ? bal : ~bal;
@@ -192,48 +194,36 @@ __device__ __forceinline__ uint32_t warp_peers(uint32_t d) {
 // ranking -- and with the digit-major global scan, the whole pass -- is stable.  The
 // block first writes its keys in sorted order to shared memory and then copies each
 // digit's run to its global position, so consecutive threads write consecutive
-// addresses.
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* __restrict__ kin,
-                                                                const uint32_t* __restrict__ vin,
-                                                                uint32_t* __restrict__ kout,
-                                                                uint32_t* __restrict__ vout,
-                                                                const int64_t* count_ptr, int64_t max_count,
-                                                                int64_t capacity, int shift,
-                                                                const uint32_t* __restrict__ hist_scan,
-                                                                int64_t nblocks) {
+// addresses.  Indices inside the block are 32-bit; a full block ranks 8-bit digits
+// (eight ballots), the last, partial block also marks the slots without a key.
+template <bool FULL>
+__device__ __forceinline__ void radix_rank_block(const uint32_t* __restrict__ kb, const uint32_t* __restrict__ vb,
+                                                 uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+                                                 int nvalid, int shift, const uint32_t* __restrict__ hist_scan,
+                                                 int64_t nblocks, uint32_t (*wh)[256], uint32_t* bd, uint32_t* sk,
+                                                 uint32_t* sv, int64_t* scan_sm) {
     constexpr int kWarps = kSortThreads / 32;
-    __shared__ uint32_t wh[kWarps][256];
-    __shared__ uint32_t bd[256];      // global start of each digit's run for this block
-    __shared__ uint32_t dstart[256];  // start of each digit's run within the block
-    __shared__ uint32_t sk[kSortTile];
-    __shared__ uint32_t sv[kSortTile];
-    __shared__ int64_t scan_sm[9];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int k = threadIdx.x; k < kWarps * 256; k += kSortThreads) (&wh[0][0])[k] = 0;
-    const int64_t count = eff_count(count_ptr, max_count, capacity);
-    const int64_t block0 = (int64_t)blockIdx.x * kSortTile;
-    if (block0 >= count) return;  // whole block empty (uniform)
-    const int nvalid = (int)min((int64_t)kSortTile, count - block0);
-    const int64_t base = block0 + (int64_t)warp * (kSortItems * 32);
-    __syncthreads();
+    const int wbase = warp * (kSortItems * 32);
+    const uint32_t lt = (1u << lane) - 1u;
     uint32_t kk[kSortItems], vv[kSortItems], rr[kSortItems];
     // all loads first, so that they are in flight together (the ranking below orders
     // shared-memory accesses with warp barriers, which loads cannot be moved across)
 #pragma unroll
     for (int it = 0; it < kSortItems; it++) {
-        const int64_t idx = base + it * 32 + lane;
-        const bool valid = idx < count;
-        kk[it] = valid ? kin[idx] : 0u;
-        vv[it] = valid ? vin[idx] : 0u;
+        const int l = wbase + it * 32 + lane;
+        const bool valid = FULL || l < nvalid;
+        kk[it] = valid ? kb[l] : 0u;
+        vv[it] = valid ? vb[l] : 0u;
     }
 #pragma unroll
     for (int it = 0; it < kSortItems; it++) {
-        const int64_t idx = base + it * 32 + lane;
-        const bool valid = idx < count;
+        const int l = wbase + it * 32 + lane;
+        const bool valid = FULL || l < nvalid;
         const uint32_t d = valid ? ((kk[it] >> shift) & 255u) : 256u;
-        const uint32_t peers = warp_peers(d);
+        const uint32_t peers = FULL ? warp_peers<8>(d) : warp_peers<9>(d);
         const uint32_t cnt = valid ? wh[warp][d] : 0u;
-        rr[it] = cnt + __popc(peers & ((1u << lane) - 1u));
+        rr[it] = cnt + __popc(peers & lt);
         __syncwarp();
         if (valid && lane == 31 - __clz(peers)) wh[warp][d] = cnt + __popc(peers);
         __syncwarp();
@@ -252,27 +242,60 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
         total = run;
         bd[d] = hist_scan[(int64_t)d * nblocks + blockIdx.x];
     }
-    const int64_t ds = block_exclusive_scan((int64_t)total, nullptr, scan_sm);
-    dstart[threadIdx.x] = (uint32_t)ds;
+    // ds: start of this digit's run within the block
+    const uint32_t ds = (uint32_t)block_exclusive_scan((int64_t)total, nullptr, scan_sm);
+    bd[threadIdx.x] -= ds;   // global position of a block-local sorted index i of this digit: bd[d] + i
+#pragma unroll
+    for (int w = 0; w < kWarps; w++) wh[w][threadIdx.x] += ds;
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < kSortItems; it++) {
-        const int64_t idx = base + it * 32 + lane;
-        if (idx < count) {
-            const uint32_t d = (kk[it] >> shift) & 255u;
-            const uint32_t lp = dstart[d] + wh[warp][d] + rr[it];
+        const int l = wbase + it * 32 + lane;
+        if (FULL || l < nvalid) {
+            const uint32_t lp = wh[warp][(kk[it] >> shift) & 255u] + rr[it];
             sk[lp] = kk[it];
             sv[lp] = vv[it];
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nvalid; i += kSortThreads) {
-        const uint32_t key = sk[i];
-        const uint32_t d = (key >> shift) & 255u;
-        const uint32_t pos = bd[d] + (uint32_t)i - dstart[d];
-        kout[pos] = key;
-        vout[pos] = sv[i];
+#pragma unroll
+    for (int it = 0; it < kSortItems; it++) {
+        const int i = it * kSortThreads + threadIdx.x;
+        if (FULL || i < nvalid) {
+            const uint32_t key = sk[i];
+            const uint32_t pos = bd[(key >> shift) & 255u] + (uint32_t)i;
+            kout[pos] = key;
+            vout[pos] = sv[i];
+        }
     }
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* __restrict__ kin,
+                                                                const uint32_t* __restrict__ vin,
+                                                                uint32_t* __restrict__ kout,
+                                                                uint32_t* __restrict__ vout,
+                                                                const int64_t* count_ptr, int64_t max_count,
+                                                                int64_t capacity, int shift,
+                                                                const uint32_t* __restrict__ hist_scan,
+                                                                int64_t nblocks) {
+    constexpr int kWarps = kSortThreads / 32;
+    __shared__ uint32_t wh[kWarps][256];
+    __shared__ uint32_t bd[256];      // global start of each digit's run for this block, less its block start
+    __shared__ uint32_t sk[kSortTile];
+    __shared__ uint32_t sv[kSortTile];
+    __shared__ int64_t scan_sm[9];
+    for (int k = threadIdx.x; k < kWarps * 256; k += kSortThreads) (&wh[0][0])[k] = 0;
+    const int64_t count = eff_count(count_ptr, max_count, capacity);
+    const int64_t block0 = (int64_t)blockIdx.x * kSortTile;
+    if (block0 >= count) return;  // whole block empty (uniform)
+    const int nvalid = (int)min((int64_t)kSortTile, count - block0);
+    __syncthreads();
+    if (nvalid == kSortTile)
+        radix_rank_block<true>(kin + block0, vin + block0, kout, vout, nvalid, shift, hist_scan, nblocks, wh, bd,
+                               sk, sv, scan_sm);
+    else
+        radix_rank_block<false>(kin + block0, vin + block0, kout, vout, nvalid, shift, hist_scan, nblocks, wh, bd,
+                                sk, sv, scan_sm);
 }
 
 // Sorts by bits [0, 8*passes) of the keys.  Buffers ping-pong: pass p reads buffer
@@ -403,25 +426,23 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
         s_tx[q] = tx | (tab.is_lidar[s] ? (int)0x80000000 : 0);
     }
     __syncthreads();
-#pragma unroll
-    for (int it = 0; it < kEmitItems; it++) {
-        const int o = it * kEmitThreads + threadIdx.x;
-        if (o >= nslot) break;
-        // last local owner with s_off <= o
-        int lo = 0, hi = nown - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (s_off[mid] <= o) lo = mid;
+    // thread t writes the consecutive slots [8 t, 8 t + 8): one search for the owner of
+    // the first, then a walk through the owners' tile rectangles (row-major) slot by slot
+    const int ofirst = kEmitItems * threadIdx.x;
+    if (ofirst < nslot) {
+        int cur = 0, hi = nown - 1;   // last local owner with s_off <= ofirst
+        while (cur < hi) {
+            const int mid = (cur + hi + 1) >> 1;
+            if (s_off[mid] <= ofirst) cur = mid;
             else hi = mid - 1;
         }
-        const int xw = s_xw[lo], w = xw >> 16;
-        uint32_t key = 0xffffffffu;   // an id past every tile
+        int xw = s_xw[cur], w = xw >> 16, dx = 0, dy = 0;
         if (w > 0) {
             // row and column in the rectangle from a float estimate of the quotient that is
             // within one of it, then corrected exactly
-            const int q = o - s_off[lo];
-            int dy = (int)__fdividef((float)q + 0.5f, (float)w);
-            int dx = q - dy * w;
+            const int q = ofirst - s_off[cur];
+            dy = (int)__fdividef((float)q + 0.5f, (float)w);
+            dx = q - dy * w;
             if (dx < 0) {
                 dy--;
                 dx += w;
@@ -429,14 +450,53 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
                 dy++;
                 dx -= w;
             }
-            const int txf = s_tx[lo], tx = txf & 0x7fffffff;
-            int col = (xw & 0xffff) + dx;
-            if (txf < 0 && col >= tx) col -= tx;   // lidar azimuth wrap
-            key = (uint32_t)(s_row0[lo] + dy * tx + col);
         }
-        keys[o0 + o] = key;
-        vals[o0 + o] = s_id[lo];
-        atomicAdd(&s_hist[key & 255u], 1u);
+        int next = cur + 1 < nown ? s_off[cur + 1] : kEmitTile;
+        uint32_t kk[kEmitItems], vv[kEmitItems];
+#pragma unroll
+        for (int i = 0; i < kEmitItems; i++) {
+            const int o = ofirst + i;
+            if (o >= next) {   // every owner holds at least one slot: the walk enters the next at its start
+                cur++;
+                next = cur + 1 < nown ? s_off[cur + 1] : kEmitTile;
+                xw = s_xw[cur];
+                w = xw >> 16;
+                dx = dy = 0;
+            }
+            uint32_t key = 0xffffffffu;   // an id past every tile (malformed rectangle)
+            if (w > 0) {
+                const int txf = s_tx[cur], tx = txf & 0x7fffffff;
+                int col = (xw & 0xffff) + dx;
+                if (txf < 0 && col >= tx) col -= tx;   // lidar azimuth wrap
+                key = (uint32_t)(s_row0[cur] + dy * tx + col);
+                if (++dx == w) {
+                    dx = 0;
+                    dy++;
+                }
+            }
+            kk[i] = key;
+            vv[i] = s_id[cur];
+            if (o < nslot) atomicAdd(&s_hist[key & 255u], 1u);
+        }
+        // vector stores when both arrays are 16-byte aligned (the workspace always is; the
+        // caller's list may be the value array)
+        const bool vec = ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(vals)) & 15u) == 0;
+        if (vec && ofirst + kEmitItems <= nslot) {
+            uint4* kp = reinterpret_cast<uint4*>(keys + o0 + ofirst);
+            uint4* vp = reinterpret_cast<uint4*>(vals + o0 + ofirst);
+            kp[0] = make_uint4(kk[0], kk[1], kk[2], kk[3]);
+            kp[1] = make_uint4(kk[4], kk[5], kk[6], kk[7]);
+            vp[0] = make_uint4(vv[0], vv[1], vv[2], vv[3]);
+            vp[1] = make_uint4(vv[4], vv[5], vv[6], vv[7]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < kEmitItems; i++) {
+                if (ofirst + i < nslot) {
+                    keys[o0 + ofirst + i] = kk[i];
+                    vals[o0 + ofirst + i] = vv[i];
+                }
+            }
+        }
     }
     __syncthreads();
     hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = s_hist[threadIdx.x];
