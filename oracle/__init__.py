@@ -71,6 +71,8 @@ def _declare(L):
     L.oracle_render.restype = ctypes.c_int
     L.oracle_render.argtypes = ([_I64] + [_P] * 6 + [ctypes.c_int] + [_P] * 3 + [_I64, ctypes.c_double, _I64] +
                                 [_P] * 8 + [ctypes.c_double, _P])
+    L.oracle_tile_margin.restype = ctypes.c_int
+    L.oracle_tile_margin.argtypes = [_P, _P, _I64, _P, _P, _P]
     L.oracle_render_variants.restype = ctypes.c_int
     L.oracle_render_variants.argtypes = ([_I64] + [_P] * 6 + [ctypes.c_int] + [_P] * 3 +
                                          [_I64, ctypes.c_double, _I64, _P, _P, ctypes.c_double, ctypes.c_int,
@@ -195,8 +197,21 @@ def isect_list(g: dict, s, proj: dict | None = None):
     tiles = np.zeros(max(total, 1), np.int32); ids = np.zeros(max(total, 1), np.int32)
     got = L.oracle_isect_list(n, _ptr(P), _ptr(proj["rec"]), _ptr(proj["rect"]), _ptr(proj["n_tiles"]), total,
                               _ptr(tiles), _ptr(ids))
-    assert got == total
-    return tiles[:total], ids[:total]
+    assert got <= total   # fewer with the camera tile cull (support flag 4)
+    return tiles[:got], ids[:got]
+
+
+def tile_margin(g: dict, s, tiles, ids, proj: dict | None = None) -> np.ndarray:
+    """Camera tile-cull margins (support flag 4) of (sensor-local tile, Gaussian index)
+    pairs: positive where the Gaussian cannot reach alpha >= 1/255 at any pixel of the
+    tile (the pair is not listed), by how much of the Mahalanobis form."""
+    L = lib()
+    proj = project(g, s) if proj is None else proj
+    t = np.ascontiguousarray(tiles, dtype=np.int32)
+    i = np.ascontiguousarray(ids, dtype=np.int32)
+    out = np.zeros(len(t))
+    L.oracle_tile_margin(_ptr(sensor_params(s)), _ptr(proj["rec"]), len(t), _ptr(t), _ptr(i), _ptr(out))
+    return out
 
 
 def render(g: dict, s, sel=None, guard: float | None = None, los_range=None, los_eps: float = 0.8,

@@ -49,7 +49,9 @@ enum {
     P_TAZ = 25, P_TEL = 26,
     /* both kinds */
     P_SUPPORT = 31,      /* tile extent flags: 1 = where alpha can reach 1/255 instead of 3 sigma
-                          * (Sec. 3.2); 2 = lidar motion margins from the grid rays' own times */
+                          * (Sec. 3.2); 2 = lidar motion margins from the grid rays' own times;
+                          * 4 = camera tile cull (a box tile where alpha cannot reach 1/255 is
+                          * not listed) */
     P_ALLG = 32          /* render from every visible Gaussian, without the tile predicate */
 };
 
@@ -236,6 +238,53 @@ static int camera_rect(const double *P, const double *rec, double extra, int rec
     rect[1] = (int)clampd(floor(yl), 0, nty); rect[3] = (int)clampd(ceil(yh), 0, nty);
     return m;
 }
+
+/* Camera tile cull (tile-extent option 4): the margin by which a projected Gaussian misses
+ * alpha >= 1/255 everywhere in tile (tx, ty).  Every pixel of the tile, at its row time
+ * t (Eq. t_pix), sees the mean moved to mean + v t (Eq. delta), i.e. the pixel acts as a
+ * point displaced by at most |v| (t1 - t0) / 2 per axis from the mean at the tile's
+ * mid-time; so alpha = o' exp(-m / 2) (Eq. alpha, m = d^T Sigma'^-1 d) can reach 1/255 in
+ * the tile only if the minimum of m over the rectangle of the tile's pixel centres grown
+ * by that sweep is at most 2 ln(255 o').  The margin is that minimum, over the rectangle
+ * grown by CULL_GROW more pixels, minus 2 ln(255 o') (1 + CULL_REL) - CULL_ABS: positive
+ * means the pair is not listed.  The small growth and threshold margins keep every pair
+ * that an FP32 evaluation of alpha could blend, so the cull never changes a render. */
+#define CULL_GROW 2e-3
+#define CULL_REL 2e-3
+#define CULL_ABS 2e-3
+static double camera_tile_margin(const double *P, const double *rec, int tx, int ty) {
+    double W = P[P_WIDTH], H = P[P_HEIGHT];
+    int tw = (int)P[P_TW], th = (int)P[P_TH];
+    double x0 = tx * tw + 0.5, x1 = fmin((double)(tx * tw + tw), W) - 0.5;
+    double y0 = ty * th + 0.5, y1 = fmin((double)(ty * th + th), H) - 0.5;
+    double t0 = (y0 / H - 0.5) * P[P_RS] + P[P_DT], t1 = (y1 / H - 0.5) * P[P_RS] + P[P_DT];
+    double tm = 0.5 * (t0 + t1), ht = 0.5 * fabs(t1 - t0);
+    double cx = rec[R_MA] + rec[R_VA] * tm, cy = rec[R_MB] + rec[R_VB] * tm;
+    double gx = fabs(rec[R_VA]) * ht + CULL_GROW, gy = fabs(rec[R_VB]) * ht + CULL_GROW;
+    /* the rectangle relative to the moved mean */
+    double ua = x0 - gx - cx, ub = x1 + gx - cx, va = y0 - gy - cy, vb = y1 + gy - cy;
+    double a = rec[R_CA], b = rec[R_CB], c = rec[R_CC];
+#define M_FORM(u, v) (a * (u) * (u) + 2 * b * (u) * (v) + c * (v) * (v))
+    double mmin;
+    if (ua <= 0 && ub >= 0 && va <= 0 && vb >= 0) {
+        mmin = 0;   /* the mean lies in the rectangle */
+    } else {
+        /* a convex quadratic's minimum over a rectangle without its vertex lies on an edge;
+         * on each edge it is the 1-D vertex clamped to the edge */
+        double e1 = M_FORM(ua, clampd(-b * ua / c, va, vb));
+        double e2 = M_FORM(ub, clampd(-b * ub / c, va, vb));
+        double e3 = M_FORM(clampd(-b * va / a, ua, ub), va);
+        double e4 = M_FORM(clampd(-b * vb / a, ua, ub), vb);
+        mmin = fmin(fmin(e1, e2), fmin(e3, e4));
+    }
+#undef M_FORM
+    double op = rec[R_OP];
+    if (!(op > 0)) return 1e300;
+    double thr = 2.0 * log(255.0 * op) * (1.0 + CULL_REL) + CULL_ABS;
+    return mmin - thr;
+}
+
+static int camera_cull(const double *P) { return (int)P[P_KIND] == 0 && ((int)P[P_SUPPORT] & 4); }
 
 /* ---------------------------------------------------------------------------------
  * Camera projection (Sec. 3.2).  Returns 1 if visible.  *marg is set when an FP32
@@ -495,16 +544,29 @@ int64_t oracle_isect_list(int64_t n, const double *P, const double *rec, const i
         for (int ty = rc[1]; ty < rc[3]; ty++)
             for (int tx = rc[0]; tx < rc[2]; tx++) {
                 int col = ((tx % tiles_x) + tiles_x) % tiles_x;
+                if (camera_cull(P) && camera_tile_margin(P, rec + REC * i, col, ty) > 0) continue;
                 lst[k].tile = ty * tiles_x + col;
                 lst[k].depth = rec[REC * i + R_DEPTH];
                 lst[k].id = (int32_t)i;
                 k++;
             }
     }
+    total = k;
     qsort(lst, (size_t)total, sizeof(isect_t), cmp_isect);
     for (int64_t j = 0; j < total; j++) { out_tile[j] = lst[j].tile; out_id[j] = lst[j].id; }
     free(lst);
     return total;
+}
+
+/* Public: the camera tile-cull margins of (tile, Gaussian) query pairs (tile = ty * tiles_x
+ * + tx of the sensor), from projected records rec (the option-4 definition above). */
+int oracle_tile_margin(const double *P, const double *rec, int64_t nq, const int32_t *tiles, const int32_t *ids,
+                       double *out) {
+    int tiles_x, tiles_y;
+    sensor_tiles(P, &tiles_x, &tiles_y);
+    for (int64_t q = 0; q < nq; q++)
+        out[q] = camera_tile_margin(P, rec + REC * (int64_t)ids[q], tiles[q] % tiles_x, tiles[q] / tiles_x);
+    return 0;
 }
 
 /* ---------------------------------------------------------------------------------
@@ -642,6 +704,9 @@ static int gather_candidates(const double *P, int64_t n, const double *rec, cons
             }
         }
         int member = vis[i] && (P[P_ALLG] >= 0.5 || rect_contains(P, rect + 4 * i, tx, ty));
+        /* the camera tile cull drops pairs that cannot blend anywhere in the tile */
+        if (member && P[P_ALLG] < 0.5 && camera_cull(P) && camera_tile_margin(P, rec + REC * i, tx, ty) > 0)
+            member = 0;
         if (!member && !optional) continue;
         cands[nc].id = (int32_t)i;
         cands[nc].depth = rec[REC * i + R_DEPTH];
