@@ -75,14 +75,16 @@ class BatchRenderer:
             for chunk in chunks:
                 fr = Frame([r[2] for _, r in chunk], scenes[sc]["means"].shape[0], self.C, self.device)
                 self.groups.append((fr, sc, [(pos, j) for j, (pos, _) in enumerate(chunk)]))
-        # size every group's intersection buffers once (one host read per group)
+        # size every group's intersection buffers once (a host read per group and round)
         for fr, sc, _ in self.groups:
             cg = fr.c_gaussians(scenes[sc])
             fr.project(cg)
             fr.bin_sort()
             need = int(fr.n_isect.item())
-            if need > fr.capacity:
+            while need > fr.capacity:
                 fr._alloc_capacity(int(need * headroom) + 4096)
+                fr.bin_sort()
+                need = int(fr.n_isect.item())
         self.n = len(reqs)
         self.outputs = [None] * self.n
         self.requests = [None] * self.n

@@ -62,11 +62,12 @@ static splat_status build_frame(int32_t n_sensors, const splat_sensor* sensors, 
         d.tile_h = in.tile_h;
         d.eps = in.eps2d;
         if (!(in.eps2d >= 0.f)) return fail(SPLAT_ERR_INVALID_ARG, "sensor %d: eps2d must be >= 0", s);
-        if (in.support & ~3)
-            return fail(SPLAT_ERR_INVALID_ARG, "sensor %d: support flags are 1 (opacity-aware) and 2 (sweep times)", s);
+        if (in.support & ~7)
+            return fail(SPLAT_ERR_INVALID_ARG,
+                        "sensor %d: support flags are 1 (opacity-aware), 2 (sweep times) and 4 (camera tile cull)", s);
         if ((in.support & 2) && (in.kind != SPLAT_SENSOR_LIDAR || in.rays))
             return fail(SPLAT_ERR_INVALID_ARG, "sensor %d: sweep-time margins need a lidar on its regular ray grid", s);
-        d.support = in.support;
+        d.support = in.kind == SPLAT_SENSOR_CAMERA ? in.support : (in.support & 3);   // the cull is for cameras
         const bool lidar = in.kind == SPLAT_SENSOR_LIDAR;
         if (in.kind != SPLAT_SENSOR_CAMERA && !lidar) return fail(SPLAT_ERR_INVALID_ARG, "sensor %d: bad kind", s);
         if (!tile_shape_ok(in.tile_w, in.tile_h))

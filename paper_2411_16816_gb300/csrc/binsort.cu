@@ -337,21 +337,32 @@ struct VisOut {  // compact visible pairs with their depth bits as keys
     }
 };
 
-struct EmitIn {
-    const uint32_t* sorted_pairs;
-    const int32_t* n_tiles;
-    __device__ int64_t operator()(int64_t j) const { return n_tiles[sorted_pairs[j]]; }
-};
-
+// ---------------------------------------------------------------------------------
+// Emission through row items.  Every visible pair's tile box is cut into its tile rows, in
+// depth order; a row item holds the pair's Gaussian, the row's first listed tile and its
+// tile count -- the box's columns, or for a camera with the tile cull (support flag 4) the
+// kept ones (cull_row_cols).  One scan gives every row item with tiles its first output
+// slot and a compacted index; the emission maps each slot to its row item with one search.
+// Work per row item and per slot is fixed whatever the size and shape of the Gaussians.
+// ---------------------------------------------------------------------------------
 constexpr int kEmitThreads = 256;
 constexpr int kEmitItems = 8;
-constexpr int kEmitTile = kEmitThreads * kEmitItems;  // output slots per block
+constexpr int kEmitTile = kEmitThreads * kEmitItems;  // output slots (or row items) per block
 static_assert(kEmitTile == kSortTile, "emit blocks must be the first radix pass's blocks");
 static_assert(kEmitThreads == 256, "one thread per digit of the emitted histogram");
 
-// Exclusive prefix of the tile counts, in depth order.  It also records, for every emit
-// block, the visible pair that owns the block's first slot (the pair whose slot range
-// [prefix, prefix + count) holds b * kEmitTile), so that no block has to search for it.
+struct RowsIn {   // tile rows of the j-th visible pair's box (depth order)
+    const uint32_t* sorted_pairs;
+    const short4* rect;
+    __device__ int64_t operator()(int64_t j) const {
+        const short4 rc = rect[sorted_pairs[j]];
+        return rc.w > rc.y ? (int64_t)(rc.w - rc.y) : 0;
+    }
+};
+
+// Exclusive prefix of the counts.  It also records, for every 2048-item block, the owner
+// whose range [prefix, prefix + count) holds the block's first item, so that no block has
+// to search for it.
 struct OffsetOut {
     int64_t* offsets;
     uint32_t* first_owner;
@@ -363,34 +374,128 @@ struct OffsetOut {
     }
 };
 
-struct EmitTables {
-    int tile_base[kMaxSensors];
-    int tiles_x[kMaxSensors];
-    int tiles_y[kMaxSensors];
-    int is_lidar[kMaxSensors];
+// Sensor s = floor(p / n) of a (sensor, Gaussian) pair index: a float estimate within one
+// of the quotient, corrected.
+__device__ __forceinline__ int pair_sensor(uint32_t p, int64_t n, float inv_n) {
+    int s = (int)((float)p * inv_n);
+    if ((uint64_t)s * (uint64_t)n > p) s--;
+    else if ((uint64_t)(s + 1) * (uint64_t)n <= p) s++;
+    return s;
+}
+
+// Row items [b * 2048, (b + 1) * 2048): the block stages its owners (visible pairs) and
+// every thread fills the items of its slots, strided for coalesced writes.
+__global__ void __launch_bounds__(kEmitThreads) k_rows(const uint32_t* __restrict__ sorted_pairs,
+                                                      const int64_t* __restrict__ row_off,
+                                                      const uint32_t* __restrict__ row_owner,
+                                                      const int64_t* vis_count, const int64_t* n_rows,
+                                                      int64_t capacity, const short4* __restrict__ rect,
+                                                      const float4* __restrict__ rec, int64_t n, float inv_n,
+                                                      const __grid_constant__ Frame fr, BinWorkspace w) {
+    __shared__ int s_off[kEmitTile];
+    __shared__ uint32_t s_p[kEmitTile];
+    const int64_t total = *n_rows;
+    if (total > capacity) return;   // over capacity: write nothing
+    const int64_t r0 = (int64_t)blockIdx.x * kEmitTile;
+    if (r0 >= total) return;
+    const int64_t V = *vis_count;
+    const int nr = (int)min((int64_t)kEmitTile, total - r0);
+    const int64_t jlo = row_owner[blockIdx.x];
+    const int64_t jhi = r0 + kEmitTile < total ? (int64_t)row_owner[blockIdx.x + 1] + 1 : V;
+    const int nown = (int)min((int64_t)kEmitTile, jhi - jlo);
+    for (int q = threadIdx.x; q < nown; q += kEmitThreads) {
+        s_off[q] = (int)(row_off[jlo + q] - r0);
+        s_p[q] = sorted_pairs[jlo + q];
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int it = 0; it < kEmitItems; it++) {
+        const int r = it * kEmitThreads + threadIdx.x;
+        if (r >= nr) break;
+        int lo = 0, hi = nown - 1;   // last owner with s_off <= r
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (s_off[mid] <= r) lo = mid;
+            else hi = mid - 1;
+        }
+        const uint32_t p = s_p[lo];
+        const int s = pair_sensor(p, n, inv_n);
+        const uint32_t id = (uint32_t)(p - (uint64_t)s * (uint64_t)n);
+        const short4 rc = rect[p];
+        const SensorDev& S = fr.s[s];
+        const int tx = S.tiles_x, wd = rc.z - rc.x, row = rc.y + (r - s_off[lo]);
+        const bool ok = rc.x >= 0 && rc.x < tx && wd > 0 && wd <= tx && rc.y >= 0 && rc.w > rc.y &&
+                        rc.w <= S.tiles_y;   // else a malformed projection: listed nowhere
+        int ca = rc.x, cnt = ok ? wd : 0;
+        if (ok && S.kind == SPLAT_SENSOR_CAMERA && (S.support & 4)) {
+            const float4 g0 = rec[rec_index(s, 0, n, id)], g1 = rec[rec_index(s, 1, n, id)];
+            const CullGauss cg = cull_setup(g0.x, g0.y, g0.z, g0.w, g1.x, g1.y, g1.z, g1.w);
+            int cb;
+            cull_row_cols(S, cg, row, rc.x, rc.z, &ca, &cb);
+            cnt = cb - ca;
+        }
+        const int64_t j = r0 + r;
+        w.r_key0[j] = (uint32_t)(S.tile_base + row * tx + ca);
+        w.r_id[j] = id;
+        w.r_wrap[j] = S.kind == SPLAT_SENSOR_LIDAR ? tx - ca : 0x7fffffff;   // lidar azimuth wrap
+        w.r_tx[j] = tx;
+        w.r_cnt[j] = cnt;
+    }
+}
+
+// Slots and compaction in one scan: the low 32 bits count a row item's tiles, the high 32
+// bits whether it has any (the sums stay below 2^31 each, so no carry crosses).
+struct SlotIn {
+    const int32_t* cnt;
+    __device__ int64_t operator()(int64_t j) const {
+        const int64_t c = cnt[j];
+        return c | ((int64_t)(c > 0) << 32);
+    }
+};
+struct SlotOut {
+    int32_t* c_off;
+    int32_t* c_row;
+    uint32_t* first_owner;
+    int64_t nblocks;
+    __device__ void operator()(int64_t j, int64_t prefix, int64_t v) const {
+        const int64_t c = v & 0xffffffff;
+        if (c <= 0) return;
+        const int64_t slot = prefix & 0xffffffff, k = prefix >> 32;
+        c_off[k] = (int32_t)slot;
+        c_row[k] = (int32_t)j;
+        for (int64_t b = (slot + kEmitTile - 1) / kEmitTile; b < nblocks && b * kEmitTile < slot + c; b++)
+            first_owner[b] = (uint32_t)k;
+    }
 };
 
-// Writes intersections [b*2048, (b+1)*2048): the offsets scan recorded the visible pair
-// that owns each block's first slot; the block stages the owners' offsets in shared
-// memory and every thread then writes one (tile, Gaussian) pair per slot it owns.  Work
-// per block is fixed whatever the size of the Gaussians, and the writes are contiguous.
+// The totals: intersections (or, when the row items overflowed the capacity, the capacity
+// needed) and the row items with tiles.
+__global__ void k_slot_totals(const int64_t* n_rows, int64_t capacity, const int64_t* slot_total, int64_t* n_isect,
+                              int64_t* n_owners) {
+    const int64_t r = *n_rows;
+    if (r > capacity) {
+        *n_isect = r;
+        *n_owners = 0;
+    } else {
+        *n_isect = *slot_total & 0xffffffff;
+        *n_owners = *slot_total >> 32;
+    }
+}
+
+// Writes intersections [b*2048, (b+1)*2048): the slot scan recorded the row item that owns
+// each block's first slot; the block stages its owners (first slot, first tile, Gaussian,
+// wrap) in shared memory and every thread writes the consecutive slots [8 t, 8 t + 8): one
+// search for the owner of the first, then each slot's tile is the owner's first tile plus
+// its offset (less a lidar row's column count past its wrap).  The writes are contiguous.
 // The blocks are those of the first radix pass over the keys, so each block also writes
 // that pass's low-byte digit histogram.
-__global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restrict__ sorted_pairs,
-                                                      const int64_t* __restrict__ offsets,
-                                                      const uint32_t* __restrict__ first_owner,
-                                                      const int64_t* vis_count, const int64_t* n_isect,
-                                                      int64_t capacity, const short4* __restrict__ rect, int64_t n,
-                                                      float inv_n, const __grid_constant__ EmitTables tab,
-                                                      uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                                                      uint32_t* __restrict__ hist) {
-    // per owner (visible pair): first slot relative to the block (the first may be < 0),
-    // Gaussian index, rectangle x0 | width << 16 (width 0: malformed), tile id of (x = 0,
-    // y0), tiles_x | lidar << 31
+__global__ void __launch_bounds__(kEmitThreads) k_emit(const BinWorkspace w, const int64_t* n_isect,
+                                                      int64_t capacity, uint32_t* __restrict__ keys,
+                                                      uint32_t* __restrict__ vals, uint32_t* __restrict__ hist) {
     __shared__ int s_off[kEmitTile];
+    __shared__ uint32_t s_key0[kEmitTile];
     __shared__ uint32_t s_id[kEmitTile];
-    __shared__ int s_xw[kEmitTile];
-    __shared__ int s_row0[kEmitTile];
+    __shared__ int s_wrap[kEmitTile];
     __shared__ int s_tx[kEmitTile];
     __shared__ uint32_t s_hist[256];   // low-byte digit counts of this block's keys (first radix pass)
     const int64_t total = *n_isect;
@@ -402,54 +507,30 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
         return;
     }
     s_hist[threadIdx.x] = 0;
-    const int64_t V = *vis_count;
+    const int64_t K = *w.n_owners;
     const int nslot = (int)min((int64_t)kEmitTile, total - o0);
-    const int64_t jlo = first_owner[blockIdx.x];
+    const int64_t jlo = w.first_owner[blockIdx.x];
     // owners of this block's slots are jlo .. the owner of the next block's first slot (at
-    // most kEmitTile of them: every visible pair owns a slot)
-    const int64_t jhi = o0 + kEmitTile < total ? (int64_t)first_owner[blockIdx.x + 1] + 1 : V;
+    // most kEmitTile of them with a slot here: every compacted row item owns a slot)
+    const int64_t jhi = o0 + kEmitTile < total ? (int64_t)w.first_owner[blockIdx.x + 1] + 1 : K;
     const int nown = (int)min((int64_t)kEmitTile, jhi - jlo);
     for (int q = threadIdx.x; q < nown; q += kEmitThreads) {
-        s_off[q] = (int)(offsets[jlo + q] - o0);
-        const uint32_t p = sorted_pairs[jlo + q];
-        // sensor s = floor(p / n): a float estimate within one of the quotient, corrected
-        int s = (int)((float)p * inv_n);
-        if ((uint64_t)s * (uint64_t)n > p) s--;
-        else if ((uint64_t)(s + 1) * (uint64_t)n <= p) s++;
-        const short4 rc = rect[p];
-        const int tx = tab.tiles_x[s], w = rc.z - rc.x;
-        const bool ok = rc.x >= 0 && rc.x < tx && w > 0 && w <= tx && rc.y >= 0 && rc.w > rc.y &&
-                        rc.w <= tab.tiles_y[s];   // else a malformed projection: never ranged
-        s_id[q] = (uint32_t)(p - (uint64_t)s * (uint64_t)n);
-        s_xw[q] = ok ? ((int)rc.x | (w << 16)) : 0;
-        s_row0[q] = tab.tile_base[s] + (int)rc.y * tx;
-        s_tx[q] = tx | (tab.is_lidar[s] ? (int)0x80000000 : 0);
+        const int64_t k = jlo + q;
+        const int r = w.c_row[k];
+        s_off[q] = (int)(w.c_off[k] - o0);
+        s_key0[q] = w.r_key0[r];
+        s_id[q] = w.r_id[r];
+        s_wrap[q] = w.r_wrap[r];
+        s_tx[q] = w.r_tx[r];
     }
     __syncthreads();
-    // thread t writes the consecutive slots [8 t, 8 t + 8): one search for the owner of
-    // the first, then a walk through the owners' tile rectangles (row-major) slot by slot
     const int ofirst = kEmitItems * threadIdx.x;
     if (ofirst < nslot) {
-        int cur = 0, hi = nown - 1;   // last local owner with s_off <= ofirst
+        int cur = 0, hi = nown - 1;   // last owner with s_off <= ofirst
         while (cur < hi) {
             const int mid = (cur + hi + 1) >> 1;
             if (s_off[mid] <= ofirst) cur = mid;
             else hi = mid - 1;
-        }
-        int xw = s_xw[cur], w = xw >> 16, dx = 0, dy = 0;
-        if (w > 0) {
-            // row and column in the rectangle from a float estimate of the quotient that is
-            // within one of it, then corrected exactly
-            const int q = ofirst - s_off[cur];
-            dy = (int)__fdividef((float)q + 0.5f, (float)w);
-            dx = q - dy * w;
-            if (dx < 0) {
-                dy--;
-                dx += w;
-            } else if (dx >= w) {
-                dy++;
-                dx -= w;
-            }
         }
         int next = cur + 1 < nown ? s_off[cur + 1] : kEmitTile;
         uint32_t kk[kEmitItems], vv[kEmitItems];
@@ -459,21 +540,9 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const uint32_t* __restric
             if (o >= next) {   // every owner holds at least one slot: the walk enters the next at its start
                 cur++;
                 next = cur + 1 < nown ? s_off[cur + 1] : kEmitTile;
-                xw = s_xw[cur];
-                w = xw >> 16;
-                dx = dy = 0;
             }
-            uint32_t key = 0xffffffffu;   // an id past every tile (malformed rectangle)
-            if (w > 0) {
-                const int txf = s_tx[cur], tx = txf & 0x7fffffff;
-                int col = (xw & 0xffff) + dx;
-                if (txf < 0 && col >= tx) col -= tx;   // lidar azimuth wrap
-                key = (uint32_t)(s_row0[cur] + dy * tx + col);
-                if (++dx == w) {
-                    dx = 0;
-                    dy++;
-                }
-            }
+            const int dx = o - s_off[cur];
+            const uint32_t key = s_key0[cur] + (uint32_t)dx - (dx >= s_wrap[cur] ? (uint32_t)s_tx[cur] : 0u);
             kk[i] = key;
             vv[i] = s_id[cur];
             if (o < nslot) atomicAdd(&s_hist[key & 255u], 1u);
@@ -555,6 +624,17 @@ BinWorkspace carve_workspace(void* base, int64_t pairs, int64_t capacity) {
     w.vvals[1] = (uint32_t*)take(4 * vp);
     w.vis_count = (int64_t*)take(8);
     w.offsets = (int64_t*)take(8 * vp);
+    w.row_owner = (uint32_t*)take(4 * ((cp + kEmitTile - 1) / kEmitTile + 1));
+    w.n_rows = (int64_t*)take(8);
+    w.r_key0 = (uint32_t*)take(4 * cp);
+    w.r_id = (uint32_t*)take(4 * cp);
+    w.r_wrap = (int32_t*)take(4 * cp);
+    w.r_tx = (int32_t*)take(4 * cp);
+    w.r_cnt = (int32_t*)take(4 * cp);
+    w.c_off = (int32_t*)take(4 * cp);
+    w.c_row = (int32_t*)take(4 * cp);
+    w.slot_total = (int64_t*)take(8);
+    w.n_owners = (int64_t*)take(8);
     w.ikeys[0] = (uint32_t*)take(4 * cp);
     w.ikeys[1] = (uint32_t*)take(4 * cp);
     w.ivals_tmp = (uint32_t*)take(4 * cp);
@@ -593,19 +673,19 @@ void launch_bin_sort(const Frame& fr, int64_t n, const float4* rec, const short4
     vals_buf[passes & 1] = isect_ids;
     vals_buf[(passes & 1) ^ 1] = w.ivals_tmp;
     const int64_t emit_blocks = (capacity + kEmitTile - 1) / kEmitTile;
-    device_scan(EmitIn{sorted_pairs, n_tiles}, OffsetOut{w.offsets, w.first_owner, emit_blocks}, pairs, w.vis_count,
-                INT64_MAX, w.partials, n_isect, st);
-    EmitTables tab{};
-    for (int s = 0; s < fr.n_sensors; s++) {
-        tab.tile_base[s] = fr.s[s].tile_base;
-        tab.tiles_x[s] = fr.s[s].tiles_x;
-        tab.tiles_y[s] = fr.s[s].tiles_y;
-        tab.is_lidar[s] = fr.s[s].kind == SPLAT_SENSOR_LIDAR;
-    }
+    // 3a. row items: the tile rows of the visible pairs' boxes, in depth order
+    device_scan(RowsIn{sorted_pairs, rect}, OffsetOut{w.offsets, w.row_owner, emit_blocks}, pairs, w.vis_count,
+                INT64_MAX, w.partials, w.n_rows, st);
     if (emit_blocks > 0)
-        k_emit<<<(unsigned)emit_blocks, kEmitThreads, 0, st>>>(sorted_pairs, w.offsets, w.first_owner, w.vis_count,
-                                                               n_isect, capacity, rect, n, (float)(1.0 / (double)n),
-                                                               tab, w.ikeys[0], vals_buf[0], w.hist);
+        k_rows<<<(unsigned)emit_blocks, kEmitThreads, 0, st>>>(sorted_pairs, w.offsets, w.row_owner, w.vis_count,
+                                                               w.n_rows, capacity, rect, rec, n,
+                                                               (float)(1.0 / (double)n), fr, w);
+    // 3b. each row item's first slot, the row items with tiles compacted; n_isect = total
+    device_scan(SlotIn{w.r_cnt}, SlotOut{w.c_off, w.c_row, w.first_owner, emit_blocks}, capacity, w.n_rows, capacity,
+                w.partials, w.slot_total, st);
+    k_slot_totals<<<1, 1, 0, st>>>(w.n_rows, capacity, w.slot_total, n_isect, w.n_owners);
+    if (emit_blocks > 0)
+        k_emit<<<(unsigned)emit_blocks, kEmitThreads, 0, st>>>(w, n_isect, capacity, w.ikeys[0], vals_buf[0], w.hist);
     // 4. stable sort of the intersections by tile id
     radix_sort(w.ikeys, vals_buf, passes, capacity, n_isect, capacity, w.hist, w.partials, st, emit_blocks > 0);
     // 5. per-tile ranges

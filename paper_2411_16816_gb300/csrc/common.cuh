@@ -25,7 +25,8 @@ struct SensorDev {
     int tile_base;   // first global tile id of this sensor
     int block_base;  // first block of this sensor in its kind's raster launch
     int ray_base;    // first output ray (pixel) of this sensor in its kind's outputs
-    int support;     // tile extent flags: 1 opacity-aware, 2 lidar margins from the rays' fire times
+    int support;     // tile extent flags: 1 opacity-aware, 2 lidar margins from the rays' fire times,
+                     // 4 camera tile cull
     float R[9], t[3], v[3], w[3];
     // camera
     int width, height;
@@ -125,6 +126,81 @@ __device__ __forceinline__ float elev_bound(const SensorDev& S, int k) {
 // still reach 1/255, d^T Sigma'^-1 d <= 2 ln(255 o').
 __device__ __forceinline__ float support_sigmas(const SensorDev& S, float op) {
     return (S.support & 1) ? sqrtf(fmaxf(2.f * logf(255.f * op), 0.f)) : 3.f;
+}
+
+// Camera tile cull (support flag 4).  A pixel of a tile row at its time t (Eq. t_pix) sees
+// the mean at mean + v t (Eq. delta), i.e. acts as a point within |v| (t1 - t0) / 2 per
+// axis of the pixel-centre rectangle around the mean at the row's mid-time.  A tile is
+// kept when its rectangle, grown by that sweep and by 2e-3 px, meets the ellipse
+// d^T K d <= 2 ln(255 o') (1 + 2e-3) + 2e-3 where alpha (Eq. alpha) could reach 1/255
+// (the margins keep every pair an FP32 alpha could blend): the tile columns whose grown
+// x-range meets the ellipse's x-extent inside the row's grown y-strip.  The per-Gaussian
+// constants are formed once (CullGauss); every step is an explicitly rounded operation,
+// so the projection (which counts the tiles) and the emission (which lists them) agree
+// exactly.  Tile sides are powers of two, so their reciprocals are exact.
+struct CullGauss {
+    float mx, my, vx, vy;   // mean and image velocity
+    float k01, det;         // conic cross term, conic determinant
+    float ik00, kt;         // 1 / k00, k00 thr
+    float vmax, vr;         // the ellipse's half-height, the v of its right-most point
+    bool ok;                // false: the Gaussian can reach 1/255 nowhere
+};
+
+__device__ __forceinline__ CullGauss cull_setup(float mx, float my, float vx, float vy, float k00, float k01,
+                                                float k11, float op) {
+    CullGauss G;
+    G.mx = mx;
+    G.my = my;
+    G.vx = vx;
+    G.vy = vy;
+    G.k01 = k01;
+    const float thr = __fmaf_rn(__fmul_rn(2.f, logf(__fmul_rn(255.f, op))), 1.002f, 2e-3f);
+    G.det = __fsub_rn(__fmul_rn(k00, k11), __fmul_rn(k01, k01));
+    G.ok = thr > 0.f && G.det > 0.f && k00 > 0.f && k11 > 0.f;
+    const float idet = __frcp_rn(G.det);
+    G.ik00 = __frcp_rn(k00);
+    G.kt = __fmul_rn(k00, thr);
+    G.vmax = sqrtf(fmaxf(__fmul_rn(G.kt, idet), 0.f));
+    const float uext = sqrtf(fmaxf(__fmul_rn(__fmul_rn(thr, k11), idet), 0.f));
+    G.vr = __fmul_rn(__fmul_rn(-k01, uext), __frcp_rn(k11));
+    return G;
+}
+
+// The kept columns [*ca, *cb) of tile row ty within the box columns [x0, x1).
+__device__ __forceinline__ void cull_row_cols(const SensorDev& S, const CullGauss& G, int ty, int x0, int x1,
+                                              int* ca, int* cb) {
+    *ca = *cb = x0;
+    if (!G.ok) return;
+    const float iH = __frcp_rn((float)S.height);
+    const float y0 = __fadd_rn((float)(ty * S.tile_h), 0.5f);
+    const float y1 = __fadd_rn((float)min(ty * S.tile_h + S.tile_h, S.height), -0.5f);
+    const float t0 = __fmaf_rn(__fmaf_rn(y0, iH, -0.5f), S.rs, S.dt);
+    const float t1 = __fmaf_rn(__fmaf_rn(y1, iH, -0.5f), S.rs, S.dt);
+    const float tm = __fmul_rn(0.5f, __fadd_rn(t0, t1)), ht = __fmul_rn(0.5f, fabsf(__fsub_rn(t1, t0)));
+    const float cx = __fmaf_rn(G.vx, tm, G.mx), cy = __fmaf_rn(G.vy, tm, G.my);
+    const float gx = __fmaf_rn(fabsf(G.vx), ht, 2e-3f), gy = __fmaf_rn(fabsf(G.vy), ht, 2e-3f);
+    // the row's strip within the ellipse's v-range, relative to the moved mean
+    const float va = fmaxf(__fsub_rn(__fsub_rn(y0, gy), cy), -G.vmax);
+    const float vb = fminf(__fsub_rn(__fadd_rn(y1, gy), cy), G.vmax);
+    if (!(va <= vb)) return;
+    // x-extent over the strip: the boundary u(v) = (-k01 v +- sqrt(k00 thr - det v^2)) / k00
+    // is concave (right) / convex (left) with its extreme at v = -+k01 u_ext / k11
+    const float vR = fminf(fmaxf(G.vr, va), vb), vL = fminf(fmaxf(-G.vr, va), vb);
+    const float rR = sqrtf(fmaxf(__fsub_rn(G.kt, __fmul_rn(G.det, __fmul_rn(vR, vR))), 0.f));
+    const float rL = sqrtf(fmaxf(__fsub_rn(G.kt, __fmul_rn(G.det, __fmul_rn(vL, vL))), 0.f));
+    const float uhi = __fmul_rn(__fmaf_rn(-G.k01, vR, rR), G.ik00);
+    const float ulo = __fmul_rn(__fsub_rn(__fmul_rn(-G.k01, vL), rL), G.ik00);
+    // tile tx is kept iff tx tw + 0.5 - gx <= cx + uhi and (its last pixel centre) + gx >= cx + ulo
+    const float xh = __fadd_rn(__fadd_rn(cx, uhi), gx), xl = __fsub_rn(__fadd_rn(cx, ulo), gx);
+    if (!(xl <= __fadd_rn((float)S.width, -0.5f)) || !(xh >= 0.5f)) return;
+    const float itw = __frcp_rn((float)S.tile_w);
+    const float fb = floorf(__fmul_rn(__fadd_rn(xh, -0.5f), itw)) + 1.f;
+    const float fa = ceilf(__fmaf_rn(__fadd_rn(xl, 0.5f), itw, -1.f));
+    const int a = (int)fminf(fmaxf(fa, (float)x0), (float)x1), b = (int)fminf(fmaxf(fb, (float)x0), (float)x1);
+    if (a < b) {
+        *ca = a;
+        *cb = b;
+    }
 }
 
 __device__ __forceinline__ int sensor_of_block(const Frame& fr, int block, bool lidar) {

@@ -171,11 +171,13 @@ __device__ bool project_camera(const SensorDev& S, const GaussLocal& G, float4& 
     const float fy1 = fminf(fmaxf(ceilf((my + ey) / S.tile_h), 0.f), (float)S.tiles_y);
     const int x0 = (int)fx0, x1 = (int)fx1, y0 = (int)fy0, y1 = (int)fy1;
     if (x1 <= x0 || y1 <= y0) return false;
+    // (with the camera tile cull, support flag 4, the binning drops the box tiles where
+    // alpha cannot reach 1/255; n_tiles stays the box's tile count)
+    nt = (x1 - x0) * (y1 - y0);
     r0 = make_float4(mx, my, vx, vy);
     r1 = make_float4(C / det1, -b / det1, A / det1, op);
     r2 = make_float4(m.z, 0.f, 0.f, 0.f);
     rect = make_short4((short)x0, (short)y0, (short)x1, (short)y1);
-    nt = (x1 - x0) * (y1 - y0);
     return true;
 }
 

@@ -86,10 +86,21 @@ struct BinWorkspace {
     uint32_t* vkeys[2];
     uint32_t* vvals[2];
     int64_t* vis_count;
-    int64_t* offsets;
+    int64_t* offsets;        // first row item of each visible pair (depth order)
+    uint32_t* row_owner;     // visible pair owning each row block's first row item
+    int64_t* n_rows;         // row items (tile rows of the visible pairs' boxes)
+    uint32_t* r_key0;        // per row item: tile id of its first listed column
+    uint32_t* r_id;          //   Gaussian index
+    int32_t* r_wrap;         //   columns before the lidar azimuth wrap (cameras: no wrap)
+    int32_t* r_tx;           //   tile columns of its sensor
+    int32_t* r_cnt;          //   listed tiles of the row
+    int32_t* c_off;          // per row item with tiles (compacted): first output slot
+    int32_t* c_row;          //   its row item
+    int64_t* slot_total;     // packed (slots, row items with tiles) totals
+    int64_t* n_owners;       // row items with tiles
     uint32_t* ikeys[2];
     uint32_t* ivals_tmp;
-    uint32_t* first_owner;   // visible pair owning each emit block's first slot
+    uint32_t* first_owner;   // compacted row item owning each emit block's first slot
     uint32_t* hist;
     int64_t* partials;
     size_t bytes;

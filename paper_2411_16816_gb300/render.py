@@ -159,14 +159,17 @@ class Frame:
                self.c_bins(), _vp(self.workspace), self.workspace.numel(), _stream(stream))
 
     def ensure_capacity(self, stream=None) -> bool:
-        """Reads the intersection count (one sync); grows and re-bins if it overflowed.
+        """Reads the intersection count (one sync); grows and re-bins while it overflows
+        (the first report may be the sort's row items rather than the intersections).
         Returns True if the lists had to be rebuilt."""
+        grown = False
         need = int(self.n_isect.item())
-        if need <= self.capacity:
-            return False
-        self._alloc_capacity(int(need * 1.25) + 1024)
-        self.bin_sort(stream)
-        return True
+        while need > self.capacity:
+            self._alloc_capacity(int(need * 1.25) + 1024)
+            self.bin_sort(stream)
+            grown = True
+            need = int(self.n_isect.item())
+        return grown
 
     def alloc_outputs(self, keep_state: bool = True) -> dict:
         dev, C = self.device, self.channels

@@ -20,6 +20,7 @@ TOL_FEAT = 1e-4     # absolute, rendered features / colour / transmittance / acc
 TOL_RANGE = 1e-4    # relative (plus 1e-4 m absolute), expected range
 TOL_MED = 1e-5      # absolute part of the median-range tolerance (relative part TOL_RANGE)
 TOL_GRAD = 1e-3     # relative
+CULL_BAND = 5e-3    # camera tile cull: |margin| (units of the Mahalanobis form) of a decision FP32 may flip
 
 # Near decisions that change a ray's gradient by more than FP32 noise when taken the other
 # way: membership, alpha >= 1/255, the 0.999 clamp (no gradient through a clamped alpha),
@@ -278,6 +279,9 @@ def compare_lists(fr, g, sensors, which=None):
         dt, di = diff // n, diff % n
         ok = proj["marginal"][di] & _rect_has(s.kind, proj["orect"][di], tiles_x, dt % tiles_x, dt // tiles_x) & \
             ~_rect_has(s.kind, proj["irect"][di], tiles_x, dt % tiles_x, dt // tiles_x)
+        if s.kind == "camera" and (getattr(s, "support", 0) & 4) and len(diff):
+            # the camera tile cull's decision within FP32 noise of its threshold
+            ok |= np.abs(oracle.tile_margin(g, s, dt, di, proj)) <= CULL_BAND
         assert ok.all(), (f"sensor {k}: {int((~ok).sum())} pairs differ outside the guard band, e.g. "
                           f"(tile, id, extra) {[(int(a), int(b), bool(j < len(extra))) for j, (a, b) in enumerate(zip(dt, di)) if not ok[j]][:5]}")
         # order: tile-major, then depth; within a tile consecutive entries may only invert

@@ -183,6 +183,39 @@ def test_medium_driving_frame_lists_render_and_gradients():
     U.check_grads(pg, U.oracle_grads(g, sensors, per))
 
 
+def _cull_cameras(sensors):
+    import dataclasses
+    return [dataclasses.replace(s, support=s.support | 4) if s.kind == "camera" else s for s in sensors]
+
+
+def test_camera_tile_cull_lists_render_and_gradients():
+    """Support flag 4 (camera tile cull) on the medium driving frame: lists against the
+    oracle's culled lists (pairs may differ only within FP32 noise of the cull threshold),
+    about a third fewer pairs, renders bit-identical to the uncut lists' and gradients
+    equal up to the order of the atomic sums."""
+    g, sensors = _small_driving(n=60000, w=640, h=360, box=40)
+    cut = _cull_cameras(sensors)
+    fr0, gd, out0 = U.run(g, sensors)
+    fr, _, out = U.run(g, cut)
+    pairs, optional, ties = U.compare_lists(fr, g, cut)
+    n0, n1 = int(fr0.n_isect.item()), int(fr.n_isect.item())
+    print("intersections", n0, "->", n1)
+    assert n1 < 0.85 * n0 and optional < 1e-4 * pairs
+    for k in ("cam_feat", "cam_T", "lid_feat", "lid_range_exp", "lid_alpha", "lid_range_med"):
+        assert torch.equal(out[k], out0[k]), k
+    sel = _sample(cut, 2000, seed=12)
+    U.check_render(fr, out, g, cut, sel=sel)
+    grads, per = U.sampled_upstream(fr, cut, g, sel, seed=13)
+    a = fr0.backward(gd, out0, grads)
+    a = {k: v.clone() for k, v in a.items()}
+    b = fr.backward(gd, out, grads)
+    torch.cuda.synchronize()
+    # equal up to the order of the atomic sums (the staged batches differ)
+    for k in a:
+        torch.testing.assert_close(b[k], a[k], rtol=1e-3, atol=1e-4 * float(a[k].abs().max()) + 1e-9)
+    U.check_grads(b, U.oracle_grads(g, cut, per))
+
+
 # ----------------------------------------------------------------------------------
 # Full-size frames, sampled against the oracle ray by ray
 # ----------------------------------------------------------------------------------
@@ -194,6 +227,7 @@ def test_full_driving_frame_sampled_parity():
     full-size backward (about 800 entries per camera tile, rays ending after about 80)
     against the oracle's backward of the same rays."""
     g, sensors = scenes.driving_frame()
+    sensors = _cull_cameras(sensors)   # the benchmark's lists
     fr, gd, out = U.run(g, sensors)
     stats = U.check_render(fr, out, g, sensors, sel=_sample(sensors, 2000, seed=1))
     assert max(st["near"] for st in stats) < 0.1
@@ -204,14 +238,17 @@ def test_full_driving_frame_sampled_parity():
     U.check_grads(pg, U.oracle_grads(g, sensors, per))
 
 
-def test_full_driving_frame_lists():
-    """Full-size lists of one camera (the first, ~7.5M pairs) and of the lidar against the
-    oracle's."""
+@pytest.mark.parametrize("cull", [False, True])
+def test_full_driving_frame_lists(cull):
+    """Full-size lists of one camera (the first, ~6.6M pairs of its 3-sigma boxes, ~4.2M
+    with the camera tile cull) and of the lidar against the oracle's."""
     g, sensors = scenes.driving_frame()
+    if cull:
+        sensors = _cull_cameras(sensors)
     fr, gd, out = U.run(g, sensors)
     lid = next(i for i, s in enumerate(sensors) if s.kind == "lidar")
     pairs, optional, ties = U.compare_lists(fr, g, sensors, which=[0, lid])
-    assert pairs > 5_000_000 and optional < 1e-4 * pairs
+    assert pairs > (4_000_000 if cull else 5_000_000) and optional < 1e-4 * pairs
 
 
 def test_full_lidar_heavy_sampled_parity():

@@ -143,14 +143,20 @@ def test_point_cloud_entry_points_check_arguments_on_host():
 
 def test_support_flags_checked_on_host():
     """Unknown extent flags, and the sweep-time flag on a camera or on a lidar with an
-    explicit ray table, are refused before any launch."""
+    explicit ray table, are refused before any launch; the camera tile cull (4) is
+    accepted on cameras and on lidars, where it has no effect."""
     lib = L.load()
     cam, lid = scenes.tiny_frame()[1]
-    for s, flags in ((cam, 4), (cam, 2), (lid, 8)):
+    for s, flags in ((cam, 8), (cam, 2), (lid, 8)):
         c = _c_sensor(s)
         c.support = flags
         arr = (L.splat_sensor * 1)(c)
         assert lib.splat_frame_layout(1, arr, None, None, None) == L.SPLAT_ERR_INVALID_ARG, (s.kind, flags)
+    for s, flags in ((cam, 5), (lid, 4), (lid, 6)):
+        c = _c_sensor(s)
+        c.support = flags
+        arr = (L.splat_sensor * 1)(c)
+        assert lib.splat_frame_layout(1, arr, None, None, None) == L.SPLAT_OK, (s.kind, flags)
     c = _c_sensor(lid)
     c.support = 2
     c.rays = 0x1000
