@@ -13,11 +13,15 @@
  *    inconsistent tiling) return SPLAT_ERR_INVALID_ARG before anything is enqueued;
  *    splat_last_error() then returns a message (thread-local).
  *  - Errors found on the device (intersection capacity exceeded) are reported through
- *    device-side counters described per function; nothing writes out of bounds.
+ *    device-side counters described per function; nothing writes out of bounds.  In the
+ *    checked build (libsplat_checked.so) every kernel also checks its indices against
+ *    their buffers; a failing check skips the access and raises a device status word
+ *    that splat_sync_status reports (SPLAT_ERR_BOUNDS).
  *  - Gradient outputs are ACCUMULATED (+=) so that several sensors or frames can share
  *    them; the caller zeroes them first.
  *  - The library launches no kernel that waits on another block: there are no
- *    inter-block spin waits anywhere, so no call can hang on a lost signal.
+ *    inter-block spin waits anywhere, so no call can hang on a lost signal
+ *    (SPLAT_ERR_TIMEOUT is reserved and never returned).
  *
  * Sensor model (paper Sec. 3.2, 3.3, App. A, App. D)
  * --------------------------------------------------
@@ -43,6 +47,7 @@ typedef int32_t splat_status;
 #define SPLAT_ERR_CAPACITY 2
 #define SPLAT_ERR_CUDA 3
 #define SPLAT_ERR_TIMEOUT 4
+#define SPLAT_ERR_BOUNDS 5
 
 #define SPLAT_SENSOR_CAMERA 0
 #define SPLAT_SENSOR_LIDAR 1
@@ -525,9 +530,15 @@ splat_status splat_head_adam(float *params, const float *grad, float *m, float *
 const char *splat_last_error(void);
 
 /* Waits for the stream and reports a CUDA error raised by anything enqueued on it as
- * SPLAT_ERR_CUDA (message in splat_last_error).  The library keeps no device status word:
- * capacity overflow is reported through bins.n_isect, and no kernel waits on a flag. */
+ * SPLAT_ERR_CUDA (message in splat_last_error).  It then reads and clears the device
+ * status words of the current device: SPLAT_ERR_BOUNDS if the checked build skipped an
+ * out-of-bounds index since the last call (the message names the first site).  Capacity
+ * overflow is not a status: it is reported through bins.n_isect.  Synchronous. */
 splat_status splat_sync_status(void *stream);
+
+/* 1 if this library is the checked build (every kernel index checked against its
+ * buffer; a failing check skips the access and raises SPLAT_ERR_BOUNDS), else 0. */
+int32_t splat_build_flags(void);
 
 #ifdef __cplusplus
 }

@@ -4,6 +4,7 @@ kernels; if the library cannot be loaded this module raises instead of falling b
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 
@@ -16,6 +17,7 @@ SPLAT_ERR_INVALID_ARG = 1
 SPLAT_ERR_CAPACITY = 2
 SPLAT_ERR_CUDA = 3
 SPLAT_ERR_TIMEOUT = 4
+SPLAT_ERR_BOUNDS = 5
 SPLAT_SENSOR_CAMERA = 0
 SPLAT_SENSOR_LIDAR = 1
 SPLAT_MAX_SENSORS = 16
@@ -31,7 +33,7 @@ EXPORTS = [
     "splat_render_lidar_rays_backward",
     "splat_project_backward", "splat_l1_loss", "splat_last_error", "splat_head_param_count", "splat_head_inputs",
     "splat_head_forward", "splat_head_train", "splat_head_adam", "splat_batch_table_bytes", "splat_batch_build",
-    "splat_render_batch", "splat_stamp",
+    "splat_render_batch", "splat_stamp", "splat_build_flags",
 ]
 
 
@@ -75,27 +77,28 @@ class splat_batch_request(ctypes.Structure):
                 ("out_range_med", c_void_p), ("out_alpha", c_void_p)]
 
 
-_lib = None
+_libs = {}
 
 
 class SplatError(RuntimeError):
     pass
 
 
-def library_path() -> str:
-    return _build.LIB
+def library_path(checked: bool = False) -> str:
+    return _build.lib_path(checked)
 
 
-def load(build_if_missing: bool = True):
-    """Load libsplat.so (building it in-tree if it is missing or stale)."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    path = _build.LIB
+def load(build_if_missing: bool = True, checked: bool = False):
+    """Load libsplat.so (building it in-tree if it is missing or stale); with checked=True
+    the checked build libsplat_checked.so, whose kernels check every index against its
+    buffer and report a failing check through splat_sync_status (SPLAT_ERR_BOUNDS)."""
+    if checked in _libs:
+        return _libs[checked]
+    path = _build.lib_path(checked)
     if build_if_missing:
-        path = _build.build()
+        path = _build.build(checked=checked)
     if not os.path.exists(path):
-        raise SplatError(f"libsplat.so not found at {path}; run paper_2411_16816_gb300.build.build()")
+        raise SplatError(f"{os.path.basename(path)} not found at {path}; run paper_2411_16816_gb300.build.build()")
     L = ctypes.CDLL(path)
     P, S = ctypes.POINTER, c_int32
     G, SE = P(splat_gaussians), P(splat_sensor)
@@ -140,22 +143,42 @@ def load(build_if_missing: bool = True):
     L.splat_batch_build.argtypes = [P(splat_batch_request), c_int32, c_void_p, c_size_t, P(c_int64)]
     L.splat_render_batch.argtypes = [c_void_p, c_int32, c_int64, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]
     L.splat_stamp.argtypes = [c_void_p, c_void_p]
+    L.splat_build_flags.argtypes = []
     L.splat_last_error.argtypes = []
     L.splat_last_error.restype = ctypes.c_char_p
     for name in EXPORTS:
         if name not in ("splat_last_error", "splat_batch_table_bytes", "splat_head_param_count"):
             getattr(L, name).restype = S
     L.splat_head_param_count.restype = c_int32
-    _lib = L
+    _libs[checked] = L
     return L
+
+
+_active_checked = [False]
+
+
+@contextlib.contextmanager
+def checked_build():
+    """Within the block, call() and check() go to the checked build (load(checked=True))."""
+    prev = _active_checked[0]
+    _active_checked[0] = True
+    try:
+        yield load(checked=True)
+    finally:
+        _active_checked[0] = prev
+
+
+def active():
+    """The library call() uses: the checked build inside checked_build(), else libsplat.so."""
+    return load(checked=_active_checked[0])
 
 
 def check(status: int, what: str = "") -> None:
     if status != SPLAT_OK:
-        msg = load().splat_last_error().decode()
+        msg = load(checked=_active_checked[0]).splat_last_error().decode()
         raise SplatError(f"{what} failed with status {status}: {msg}")
 
 
 def call(name: str, *args) -> None:
     """Call a libsplat entry point and raise on a non-OK status."""
-    check(getattr(load(), name)(*args), name)
+    check(getattr(load(checked=_active_checked[0]), name)(*args), name)

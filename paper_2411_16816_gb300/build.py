@@ -1,4 +1,5 @@
-"""In-tree build of libsplat.so for sm_103a (nvcc, one object per .cu, compiled in parallel)."""
+"""In-tree build of libsplat.so for sm_103a (nvcc, one object per .cu, compiled in parallel),
+and of its checked variant libsplat_checked.so (SPLAT_CHECKED: every kernel index checked)."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -10,6 +11,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsplat.so")
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libsplat_checked.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
@@ -30,15 +33,22 @@ def _stale(target: str, inputs) -> bool:
     return any(os.path.getmtime(p) > t for p in inputs)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every kernel source and link libsplat.so; returns the library path."""
-    os.makedirs(BUILD, exist_ok=True)
+def lib_path(checked: bool = False) -> str:
+    return LIB_CHECKED if checked else LIB
+
+
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile every kernel source and link libsplat.so (with checked=True the checked
+    build, libsplat_checked.so); returns the library path."""
+    bdir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    flags = FLAGS + (["-DSPLAT_CHECKED"] if checked else [])
+    os.makedirs(bdir, exist_ok=True)
     srcs = _sources()
     deps = _deps()
     objs = []
     jobs = []
     for s in srcs:
-        o = os.path.join(BUILD, os.path.basename(s) + ".o")
+        o = os.path.join(bdir, os.path.basename(s) + ".o")
         objs.append(o)
         if force or _stale(o, [s] + deps):
             jobs.append((s, o))
@@ -46,7 +56,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     def compile_one(job):
         s, o = job
         tmp = o + f".tmp{os.getpid()}"
-        cmd = [NVCC] + ARCH + FLAGS + ["-c", s, "-o", tmp]
+        cmd = [NVCC] + ARCH + flags + ["-c", s, "-o", tmp]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed on {s}:\n{r.stdout}\n{r.stderr}")
@@ -57,15 +67,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             list(ex.map(compile_one, jobs))
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":
     print(build(verbose=True))
+    print(build(verbose=True, checked=True))

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <string>
 
+#include "status.cuh"
 #include "types.cuh"
 
 using namespace splat;
@@ -270,6 +271,7 @@ splat_status splat_render_camera(const splat_gaussians* g, int32_t n_sensors, co
     if ((g->channels & 3) == 0 && !aligned16(out_feat)) return fail(SPLAT_ERR_INVALID_ARG, "out_feat misaligned");
     RasterIn in{(const float4*)proj.rec, bins.isect_ids, (const int2*)bins.tile_ranges, g->features, g->n,
                 g->channels};
+    in.n_isect = bins.n_isect;
     RasterOut out{out_feat, out_T, out_last, nullptr, nullptr, nullptr, (unsigned long long*)evaluated};
     if (!launch_raster_fwd(false, g->channels, tw, th, fr, fr.n_cam_blocks, in, out, (cudaStream_t)stream))
         return fail(SPLAT_ERR_INVALID_ARG, "unsupported camera configuration");
@@ -291,6 +293,7 @@ splat_status splat_render_camera_l1(const splat_gaussians* g, int32_t n_sensors,
         return fail(SPLAT_ERR_INVALID_ARG, "target, grad_feat or out_feat misaligned");
     RasterIn in{(const float4*)proj.rec, bins.isect_ids, (const int2*)bins.tile_ranges, g->features, g->n,
                 g->channels};
+    in.n_isect = bins.n_isect;
     RasterOut out{out_feat, out_T, out_last, nullptr, nullptr, nullptr, (unsigned long long*)evaluated,
                   target, grad_feat, loss, scale};
     if (!launch_raster_fwd(false, g->channels, tw, th, fr, fr.n_cam_blocks, in, out, (cudaStream_t)stream))
@@ -303,7 +306,19 @@ splat_status splat_sync_status(void* stream) {
     if (e != cudaSuccess) return fail(SPLAT_ERR_CUDA, "%s", cudaGetErrorString(e));
     const cudaError_t e2 = cudaGetLastError();
     if (e2 != cudaSuccess) return fail(SPLAT_ERR_CUDA, "%s", cudaGetErrorString(e2));
+    uint32_t bits = 0, site = 0;
+    take_all_status(&bits, &site);
+    if (bits & kStatusBounds)
+        return fail(SPLAT_ERR_BOUNDS, "checked build: an out-of-bounds index was skipped (site %u)", site);
     return SPLAT_OK;
+}
+
+int32_t splat_build_flags(void) {
+#ifdef SPLAT_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 static splat_status render_lidar_impl(const splat_gaussians* g, int32_t n_sensors, const splat_sensor* sensors,
@@ -323,6 +338,7 @@ static splat_status render_lidar_impl(const splat_gaussians* g, int32_t n_sensor
         return fail(SPLAT_ERR_INVALID_ARG, "%s: los.target_range and out_los are required, los.eps >= 0", name);
     RasterIn in{(const float4*)proj.rec, bins.isect_ids, (const int2*)bins.tile_ranges, g->features, g->n,
                 g->channels, los ? los->target_range : nullptr, los ? los->eps : 0.f};
+    in.n_isect = bins.n_isect;
     RasterOut out{out_feat, out_T, out_last, out_range_exp, out_range_med, out_alpha,
                   (unsigned long long*)evaluated};
     out.los = los ? out_los : nullptr;
@@ -365,6 +381,7 @@ splat_status splat_render_lidar_head(const splat_gaussians* g, int32_t n_sensors
         return fail(SPLAT_ERR_INVALID_ARG, "out_head or head_w misaligned");
     RasterIn in{(const float4*)proj.rec, bins.isect_ids, (const int2*)bins.tile_ranges, g->features, g->n,
                 g->channels};
+    in.n_isect = bins.n_isect;
     RasterOut out{out_feat, out_T, out_last, out_range_exp, out_range_med, out_alpha, nullptr};
     if (!launch_lidar_fwd_head(tw, th, fr, fr.n_lid_blocks, in, out, HeadW{head_w, head_b}, out_head,
                                (cudaStream_t)stream))
@@ -388,6 +405,7 @@ splat_status splat_render_camera_backward(const splat_gaussians* g, int32_t n_se
         return fail(SPLAT_ERR_INVALID_ARG, "gradient buffers misaligned");
     RasterIn in{(const float4*)proj.rec, bins.isect_ids, (const int2*)bins.tile_ranges, g->features, g->n,
                 g->channels};
+    in.n_isect = bins.n_isect;
     RasterGrad gr{out_T, out_last, dL_dfeat, dL_dT, nullptr, nullptr, (float4*)grad_proj, dL_dfeatures, nullptr,
                   dL_dsensors};
     if (!launch_raster_bwd(false, g->channels, tw, th, fr, fr.n_cam_blocks, in, gr, out_T == nullptr,
@@ -416,6 +434,7 @@ static splat_status render_lidar_backward_impl(const splat_gaussians* g, int32_t
         return fail(SPLAT_ERR_INVALID_ARG, "%s: los.target_range and dL_dlos are required, los.eps >= 0", name);
     RasterIn in{(const float4*)proj.rec, bins.isect_ids, (const int2*)bins.tile_ranges, g->features, g->n,
                 g->channels, los ? los->target_range : nullptr, los ? los->eps : 0.f};
+    in.n_isect = bins.n_isect;
     RasterGrad gr{out_T, out_last, dL_dfeat, nullptr, dL_drange_exp, dL_dalpha, (float4*)grad_proj, dL_dfeatures,
                   los ? dL_dlos : nullptr};
     if (!launch_raster_bwd(true, g->channels, tw, th, fr, fr.n_lid_blocks, in, gr, out_T == nullptr,
@@ -530,7 +549,8 @@ static splat_status list_input(const splat_gaussians* g, int32_t n_sensors, cons
     blocks = n_rays > 0 ? (int)b : 0;
     in = RasterIn{(const float4*)proj.rec, bins.isect_ids, (const int2*)bins.tile_ranges, g->features, g->n,
                   g->channels};
-    in.list = RayList{rays, rb.ray_ids, (const int2*)rb.tile_ranges, rb.chunk_base, tiles, lidar};
+    in.n_isect = bins.n_isect;
+    in.list = RayList{rays, rb.ray_ids, (const int2*)rb.tile_ranges, rb.chunk_base, tiles, lidar, n_rays};
     return SPLAT_OK;
 }
 
@@ -678,6 +698,19 @@ splat_status frame_sensor_constants(int32_t n_sensors, const splat_sensor* senso
     if (which < 0 || which >= n_sensors) return fail(SPLAT_ERR_INVALID_ARG, "sensor index out of range");
     *out = fr.s[which];
     return SPLAT_OK;
+}
+
+// Status words of the translation units that raise them (status.cuh).
+static StatusReader*& status_head() {
+    static StatusReader* head = nullptr;
+    return head;
+}
+void register_status_reader(StatusReader* r) {
+    r->next = status_head();
+    status_head() = r;
+}
+void take_all_status(uint32_t* bits, uint32_t* site) {
+    for (StatusReader* r = status_head(); r; r = r->next) r->take(bits, site);
 }
 
 // Lets other translation units of the library report an error through splat_last_error().

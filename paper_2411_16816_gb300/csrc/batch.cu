@@ -34,6 +34,7 @@ struct BatchReqDev {
     int sensor_index;         // index of the sensor in its group
     int tiles;
     int pad;
+    const int64_t* n_isect;   // its group's intersection count
     int64_t item_base;        // first work item of this request
     float* out_feat;
     float* out_T;
@@ -63,8 +64,9 @@ __device__ __forceinline__ void batch_tile(const BatchReqDev& B, int lt, unsigne
 #pragma unroll
     for (int q = 0; q < PX; q++)
         r[q] = ray_setup_rt<LIDAR>(S, tc.tx, tc.ty, threadIdx.x + q * kBatchThreads, S.tile_w, S.tile_h);
-    const RasterIn in{B.rec, B.ids, B.ranges, B.feat, B.n, B.C};
-    const int2 range = in.ranges[tc.gtile];
+    RasterIn in{B.rec, B.ids, B.ranges, B.feat, B.n, B.C};
+    in.n_isect = B.n_isect;
+    const int2 range = load_range(in, tc.gtile);
     TileBox box{};
     if (!LIDAR) box = camera_tile_box(S, tc.tx, tc.ty, S.tile_w, S.tile_h);
     float2 F[PX][CM / 2];
@@ -202,6 +204,7 @@ splat_status splat_batch_build(const splat_batch_request* reqs, int32_t n_reques
         d.rec = (const float4*)in.proj.rec;
         d.ids = in.bins.isect_ids;
         d.ranges = (const int2*)in.bins.tile_ranges;
+        d.n_isect = in.bins.n_isect;
         d.feat = in.features;
         d.n = in.n;
         d.C = in.channels;

@@ -15,6 +15,7 @@
 // nothing in this file can spin.  Counts that only the device knows (visible pairs,
 // intersections) are read by the kernels from device memory; grids are sized from host
 // upper bounds and surplus blocks do no work.
+#include "status.cuh"
 #include "types.cuh"
 
 namespace splat {
@@ -199,7 +200,8 @@ __device__ __forceinline__ uint32_t warp_peers(uint32_t d) {
 template <bool FULL>
 __device__ __forceinline__ void radix_rank_block(const uint32_t* __restrict__ kb, const uint32_t* __restrict__ vb,
                                                  uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
-                                                 int nvalid, int shift, const uint32_t* __restrict__ hist_scan,
+                                                 int nvalid, int64_t count, int shift,
+                                                 const uint32_t* __restrict__ hist_scan,
                                                  int64_t nblocks, uint32_t (*wh)[256], uint32_t* bd, uint32_t* sk,
                                                  uint32_t* sv, int64_t* scan_sm) {
     constexpr int kWarps = kSortThreads / 32;
@@ -264,6 +266,7 @@ __device__ __forceinline__ void radix_rank_block(const uint32_t* __restrict__ kb
         if (FULL || i < nvalid) {
             const uint32_t key = sk[i];
             const uint32_t pos = bd[(key >> shift) & 255u] + (uint32_t)i;
+            if (SPLAT_OUT_OF_BOUNDS((int64_t)pos < count, kSiteScatter)) continue;
             kout[pos] = key;
             vout[pos] = sv[i];
         }
@@ -291,11 +294,11 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
     const int nvalid = (int)min((int64_t)kSortTile, count - block0);
     __syncthreads();
     if (nvalid == kSortTile)
-        radix_rank_block<true>(kin + block0, vin + block0, kout, vout, nvalid, shift, hist_scan, nblocks, wh, bd,
+        radix_rank_block<true>(kin + block0, vin + block0, kout, vout, nvalid, count, shift, hist_scan, nblocks, wh, bd,
                                sk, sv, scan_sm);
     else
-        radix_rank_block<false>(kin + block0, vin + block0, kout, vout, nvalid, shift, hist_scan, nblocks, wh, bd,
-                                sk, sv, scan_sm);
+        radix_rank_block<false>(kin + block0, vin + block0, kout, vout, nvalid, count, shift, hist_scan, nblocks, wh,
+                                bd, sk, sv, scan_sm);
 }
 
 // Sorts by bits [0, 8*passes) of the keys.  Buffers ping-pong: pass p reads buffer
@@ -509,6 +512,7 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const BinWorkspace w, con
     s_hist[threadIdx.x] = 0;
     const int64_t K = *w.n_owners;
     const int nslot = (int)min((int64_t)kEmitTile, total - o0);
+    if (SPLAT_OUT_OF_BOUNDS(o0 + nslot <= capacity, kSiteEmit)) return;
     const int64_t jlo = w.first_owner[blockIdx.x];
     // owners of this block's slots are jlo .. the owner of the next block's first slot (at
     // most kEmitTile of them with a slot here: every compacted row item owns a slot)

@@ -417,7 +417,7 @@ __global__ void __launch_bounds__(TW* TH) k_lidar_fwd_head(const __grid_constant
     TileCtx tc;
     RayCtx r[1];
     block_setup<TW, TH, true, false, 1, NT>(fr, in, tc, r);
-    const int2 range = in.ranges[tc.gtile];
+    const int2 range = load_range(in, tc.gtile);
     const TileBox box{};
     float2 F[1][CM / 2];
 #pragma unroll

@@ -21,6 +21,7 @@
 // one set of vector atomics per (tile, Gaussian).  With `out_T`/`out_last` absent it first
 // recomputes them for its tile (no per-ray forward state kept).
 #pragma once
+#include "status.cuh"
 #include "types.cuh"
 
 namespace splat {
@@ -47,6 +48,34 @@ struct TileCtx {
     int gtile;      // global tile id
     int tx, ty;     // tile coordinates
 };
+
+// Checked-build sites (the status word records the first failing one).
+enum : uint32_t {
+    kSiteRange = 1,        // a tile range outside [0, *n_isect] (or a non-empty one with n = 0)
+    kSiteGaussId = 2,      // a listed Gaussian index >= n
+    kSiteRayRange = 3,     // a free-ray list range outside [0, n_rays]
+    kSiteRayId = 4,        // a listed ray index >= n_rays
+};
+
+// The tile's entry range.  Checked build: a range that does not fit the list is skipped
+// (read as empty).
+__device__ __forceinline__ int2 load_range(const RasterIn& in, int64_t gtile) {
+    int2 r = in.ranges[gtile];
+#ifdef SPLAT_CHECKED
+    const int64_t len = in.n_isect ? *in.n_isect : 0;
+    if (SPLAT_OUT_OF_BOUNDS(r.x == r.y || (in.n > 0 && r.x >= 0 && r.x <= r.y && (int64_t)r.y <= len), kSiteRange))
+        r = make_int2(0, 0);
+#endif
+    return r;
+}
+
+// A listed Gaussian index.  Checked build: one past the Gaussians is replaced by 0 (the
+// ranges that reach here are non-empty, so n > 0).
+__device__ __forceinline__ uint32_t load_id(const RasterIn& in, int64_t j) {
+    uint32_t id = in.ids[j];
+    if (SPLAT_OUT_OF_BOUNDS((int64_t)id < in.n, kSiteGaussId)) id = 0;
+    return id;
+}
 
 template <bool LIDAR>
 __device__ __forceinline__ TileCtx tile_setup(const Frame& fr) {
@@ -117,7 +146,9 @@ __device__ __forceinline__ bool list_setup(const Frame& fr, const RayList& L, Ti
     tc.gtile = S.tile_base + lo;
     tc.tx = lo % S.tiles_x;
     tc.ty = lo / S.tiles_x;
-    const int2 rr = L.ranges[lo];
+    int2 rr = L.ranges[lo];
+    if (SPLAT_OUT_OF_BOUNDS(rr.x >= 0 && rr.x <= rr.y && (int64_t)rr.y <= L.n_rays, kSiteRayRange))
+        rr = make_int2(0, 0);
     first = rr.x + (chunk - L.chunk_base[lo]) * kListChunk;
     end = rr.y;
     return true;
@@ -131,6 +162,11 @@ __device__ __forceinline__ RayCtx list_ray(const RayList& L, int j, int end) {
     r.pa = r.pb = r.t = 0.f;
     if (r.inside) {
         r.o = L.ids[j];
+        if (SPLAT_OUT_OF_BOUNDS(r.o >= 0 && r.o < L.n_rays, kSiteRayId)) {
+            r.inside = false;
+            r.o = 0;
+            return r;
+        }
         const float* p = L.rays + 3 * r.o;
         r.pa = p[0];
         r.pb = p[1];
@@ -220,7 +256,7 @@ __device__ __forceinline__ bool tile_live(const float4 g0, const float4 g1, cons
 template <int CM, int B, bool LIDAR>
 __device__ __forceinline__ void stage_load(Stage<CM, B, LIDAR>& sm, const RasterIn& in, int s, int64_t j, int slot,
                                            const TileBox& box) {
-    const uint32_t id = in.ids[j];
+    const uint32_t id = load_id(in, j);
     sm.id[slot] = id;
     const float4 g0 = in.rec[rec_index(s, 0, in.n, id)];
     const float4 g1 = in.rec[rec_index(s, 1, in.n, id)];
@@ -357,7 +393,7 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
             float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
             bool lv = false;
             if (j < range.y) {
-                id = in.ids[j];
+                id = load_id(in, j);
                 g0 = in.rec[rec_index(tc.s, 0, in.n, id)];
                 g1 = in.rec[rec_index(tc.s, 1, in.n, id)];
                 lv = tile_live(g0, g1, box);
@@ -513,7 +549,7 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, false, LIDAR, TW * 
     TileCtx tc;
     RayCtx r[PX];
     if (!block_setup<TW, TH, LIDAR, LIST, PX, NT>(fr, in, tc, r)) return;
-    const int2 range = in.ranges[tc.gtile];
+    const int2 range = load_range(in, tc.gtile);
     TileBox box{};
     if (!LIDAR) box = camera_tile_box(fr.s[tc.s], tc.tx, tc.ty, TW, TH);
     float2 F[PX][CM / 2];
@@ -739,7 +775,7 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
         rpb[qp] = make_float2(r[2 * qp].pb, r[2 * qp + 1].pb);
         rt[qp] = make_float2(r[2 * qp].t, r[2 * qp + 1].t);
     }
-    const int2 range = in.ranges[tc.gtile];
+    const int2 range = load_range(in, tc.gtile);
     const int len = range.y - range.x;
     TileBox box{};
     if (!LIDAR) box = camera_tile_box(fr.s[tc.s], tc.tx, tc.ty, TW, TH);

@@ -12,6 +12,7 @@
 // block scans the counts into tile starts and 256-ray chunk numbers, scatter (atomic
 // cursors).  The order of the rays inside a tile is unspecified; every ray is rendered on
 // its own, so the outputs do not depend on it.
+#include "status.cuh"
 #include "types.cuh"
 
 namespace splat {
@@ -61,6 +62,7 @@ __global__ void __launch_bounds__(kRayThreads)
     const int64_t i = (int64_t)blockIdx.x * kRayThreads + threadIdx.x;
     if (i >= n) return;
     const int tile = free_ray_tile(S, rays[3 * i], rays[3 * i + 1]);
+    if (SPLAT_OUT_OF_BOUNDS(tile < S.tiles_x * S.tiles_y, kSiteRayTile)) return;
     if (tile >= 0) atomicAdd(&ranges[tile].y, 1);
 }
 
@@ -136,7 +138,12 @@ __global__ void __launch_bounds__(kRayThreads)
     const int64_t i = (int64_t)blockIdx.x * kRayThreads + threadIdx.x;
     if (i >= n) return;
     const int tile = free_ray_tile(S, rays[3 * i], rays[3 * i + 1]);
-    if (tile >= 0) ids[atomicAdd(&ranges[tile].y, 1)] = (int32_t)i;
+    if (SPLAT_OUT_OF_BOUNDS(tile < S.tiles_x * S.tiles_y, kSiteRayTile)) return;
+    if (tile >= 0) {
+        const int slot = atomicAdd(&ranges[tile].y, 1);
+        if (SPLAT_OUT_OF_BOUNDS(slot >= 0 && slot < n, kSiteRaySlot)) return;
+        ids[slot] = (int32_t)i;
+    }
 }
 
 void launch_points_to_rays(const SensorDev& S, const float* points, const float* times, int64_t n, float* rays,

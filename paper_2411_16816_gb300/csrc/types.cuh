@@ -39,6 +39,7 @@ struct RayList {
     const int32_t* chunk_base;  // [tiles + 1] first chunk of each tile; [tiles] = number of chunks
     int tiles;
     int sensor;                 // index of the lidar in the frame
+    int64_t n_rays = 0;         // rays (and ids) of the list (checked build)
 };
 
 struct RasterIn {
@@ -51,6 +52,7 @@ struct RasterIn {
     const float* los_range; // lidar, optional: return range per ray for the line-of-sight term
     float los_eps;
     RayList list;           // list kernels only
+    const int64_t* n_isect = nullptr;   // device count of ids (the checked build bounds ranges by it)
 };
 
 struct RasterOut {

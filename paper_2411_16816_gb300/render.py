@@ -51,7 +51,7 @@ class Frame:
     def __init__(self, sensors, n: int, channels: int, device="cuda", capacity: int | None = None):
         if not 1 <= len(sensors) <= L.SPLAT_MAX_SENSORS:
             raise ValueError(f"a frame holds 1..{L.SPLAT_MAX_SENSORS} sensors")
-        self.lib = L.load()
+        self.lib = L.active()
         self.device = torch.device(device)
         if self.device.type == "cuda" and self.device.index is None:
             self.device = torch.device("cuda", torch.cuda.current_device())

@@ -176,3 +176,14 @@ def test_count_nonfinite_checks_arguments_on_host():
     assert lib.splat_count_nonfinite(ctypes.byref(g), ctypes.c_void_p(0x1004), None) == L.SPLAT_ERR_INVALID_ARG
     bad = L.splat_gaussians(None, 0x1000, 0x1000, 0x1000, 0x1000, None, 10, 3, 0)
     assert lib.splat_count_nonfinite(ctypes.byref(bad), ctypes.c_void_p(0x1000), None) == L.SPLAT_ERR_INVALID_ARG
+
+
+def test_checked_build_exports_the_same_symbols_and_says_so():
+    plain = L.load()
+    checked = L.load(checked=True)
+    assert os.path.basename(L.library_path(checked=True)) == "libsplat_checked.so"
+    for name in _declared_symbols():
+        assert hasattr(checked, name), name
+    assert plain.splat_build_flags() == 0
+    assert checked.splat_build_flags() == 1
+
