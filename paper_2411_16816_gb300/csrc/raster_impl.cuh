@@ -731,6 +731,87 @@ __device__ __forceinline__ void warp_transpose_reduce(float (&v)[VP], int lane) 
     }
 }
 
+// One halving butterfly step on v[0, 2H): the lane with lane bit `o` set keeps the high
+// half, the other the low half; each receives the partner's copy of the half it keeps.
+template <int H, int VP>
+__device__ __forceinline__ void halve_step(float (&v)[VP], int lane, int o) {
+    const bool up = (lane & o) != 0;
+    float sd[H], kp[H];
+#pragma unroll
+    for (int i = 0; i < H; i++) {
+        sd[i] = up ? v[i] : v[i + H];
+        kp[i] = up ? v[i + H] : v[i];
+    }
+#pragma unroll
+    for (int i = 0; i < H; i++) sd[i] = __shfl_xor_sync(0xffffffffu, sd[i], o);
+#pragma unroll
+    for (int i = 0; i < H; i += 2) {
+        if (i + 1 < H) {
+            const float2 s2 = __fadd2_rn(make_float2(kp[i], kp[i + 1]), make_float2(sd[i], sd[i + 1]));
+            v[i] = s2.x;
+            v[i + 1] = s2.y;
+        } else {
+            v[i] = kp[i] + sd[i];
+        }
+    }
+}
+
+template <int NSL>
+__device__ __forceinline__ void acc_put(float* row, int j, float val) {
+    if (NSL > 1) row[j] = val;                       // this warp's own slice
+    else if (val != 0.f) atomicAdd(&row[j], val);    // one slice shared by the warps
+}
+
+// Camera backward: the warp sums of an entry's 8 geometric values v[0, 8) and its CM
+// feature values v[8, 8 + CM), the features in the lane's chunk order (register chunk c =
+// channel chunk c ^ m2).  The features' chunk steps need no selects: at lane bit 4 (and 3
+// for 16 channels) each lane keeps its low chunks and sends its high ones.  Two halving
+// steps then split the last chunk, whole sums finish the remaining lane bits.  The
+// geometric values take three halving steps (lane bits 4, 3, 2) and two whole sums.  Each
+// total is reported once: geometric value (lane >> 2) & 7 by the lanes with low bits 00,
+// the feature channel of the lane by the lanes with no whole-sum bit set.
+template <int CM, int VP, int NSL>
+__device__ __forceinline__ void reduce_report_camera(float (&v)[VP], int lane, float* row, int nfeat) {
+    constexpr int OFF = 8;
+    constexpr int SC = CM >= 16 ? 2 : (CM >= 8 ? 1 : 0);
+    constexpr int O1 = 16 >> SC, O2 = O1 >> 1;   // lane bits of the two in-chunk steps
+    static_assert(OFF + CM <= VP, "camera values");
+#pragma unroll
+    for (int st = 0; st < SC; st++) {
+        const int o = 16 >> st, h = CM >> (st + 1);
+        float rc[CM / 2];
+#pragma unroll
+        for (int p = 0; p < CM / 2; p++)
+            if (p < h) rc[p] = __shfl_xor_sync(0xffffffffu, v[OFF + p + h], o);
+#pragma unroll
+        for (int p = 0; p < CM / 2; p += 2) {
+            if (p < h) {
+                const float2 s2 = __fadd2_rn(make_float2(v[OFF + p], v[OFF + p + 1]), make_float2(rc[p], rc[p + 1]));
+                v[OFF + p] = s2.x;
+                v[OFF + p + 1] = s2.y;
+            }
+        }
+    }
+    {   // the chunk's four values: keep a pair, then one of it
+        float c4[4] = {v[OFF], v[OFF + 1], v[OFF + 2], v[OFF + 3]};
+        halve_step<2>(c4, lane, O1);
+        halve_step<1>(c4, lane, O2);
+        float f = c4[0];
+#pragma unroll
+        for (int o = O2 >> 1; o > 0; o >>= 1) f += __shfl_xor_sync(0xffffffffu, f, o);
+        v[OFF] = f;
+    }
+    halve_step<4>(v, lane, 16);
+    halve_step<2>(v, lane, 8);
+    halve_step<1>(v, lane, 4);
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
+    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
+    const int m2 = (lane >> (5 - SC)) & ((1 << SC) - 1);
+    const int ch = 4 * m2 + ((lane & O1) ? 2 : 0) + ((lane & O2) ? 1 : 0);
+    if ((lane & 3) == 0) acc_put<NSL>(row, (lane >> 2) & 7, v[0]);
+    if ((lane & (O2 - 1)) == 0 && ch < nfeat) acc_put<NSL>(row, OFF + ch, v[OFF]);
+}
+
 // Resident blocks the camera backward asks the register allocator for: 12 warps per SM
 // (unbounded, the packed loops take registers enough to drop to 10; 14 would spill).
 template <int CM, bool LIDAR, int NT>
@@ -798,6 +879,16 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
         }
     }
     float2 gF[PX][CM / 2];   // upstream feature gradient, as FP32 pairs for the packed FMAs
+    // Camera (rays in pairs): the feature sums of an entry are reduced over the warp with
+    // select-free butterfly steps.  Lane l holds its channels in a lane-dependent chunk
+    // order -- register chunk c is channel chunk c ^ m2, m2 = the lane bits of the chunk
+    // steps -- and reads each Gaussian's features in the same order, so at each chunk step
+    // every lane keeps its low registers and sends its high ones, the partner's high
+    // registers being the channels of its own low ones.
+    constexpr bool kSplitRed = !LIDAR && PX % 2 == 0;
+    constexpr int kChunkSteps = CM >= 16 ? 2 : (CM >= 8 ? 1 : 0);
+    static_assert(!kSplitRed || (CM >= 4 && CM <= 16 && (CM & (CM - 1)) == 0), "chunked feature reduction");
+    const int m2 = kSplitRed ? (((int)threadIdx.x & 31) >> (5 - kChunkSteps)) & ((1 << kChunkSteps) - 1) : 0;
     float gTT[PX], gD[PX], T[PX], S[PX], SD[PX];
     float gL[PX], cut[PX];   // lidar line-of-sight upstream gradient and range cut
     float dtime = 0.f;       // camera: this thread's share of dL/d (camera time offset)
@@ -806,7 +897,7 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
     for (int q = 0; q < PX; q++) {
 #pragma unroll
         for (int c = 0; c < CM / 2; c++) {
-            const int c0 = 2 * c, c1 = 2 * c + 1;
+            const int c0 = kSplitRed ? 4 * ((c >> 1) ^ m2) + 2 * (c & 1) : 2 * c, c1 = c0 + 1;
             gF[q][c] = make_float2((r[q].inside && c0 < Crt) ? gr.dfeat[r[q].o * Crt + c0] : 0.f,
                                    (r[q].inside && c1 < Crt) ? gr.dfeat[r[q].o * Crt + c1] : 0.f);
         }
@@ -887,7 +978,7 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
                         float2 g2 = make_float2(0.f, 0.f);
 #pragma unroll
                         for (int c = 0; c < CM / 4; c++) {
-                            const float4 fv = f4[c];
+                            const float4 fv = f4[c ^ m2];   // the lane's chunk order
                             g2 = __ffma2_rn(gF[q0 + j][2 * c], make_float2(fv.x, fv.y), g2);
                             g2 = __ffma2_rn(gF[q0 + j][2 * c + 1], make_float2(fv.z, fv.w), g2);
                         }
@@ -1064,6 +1155,11 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
                     v[OFF + 2 * c] = vf[c].x;
                     v[OFF + 2 * c + 1] = vf[c].y;
                 }
+            }
+            if constexpr (kSplitRed) {
+                reduce_report_camera<CM, VP, NSL>(v, lane, acc + ((NSL > 1 ? (threadIdx.x >> 5) * B : 0) + k) * ROW,
+                                                  Crt);
+                continue;
             }
             warp_transpose_reduce<VP>(v, lane);
             constexpr int M = reduce_left<VP>(), RG = 1 << reduce_plain<VP>();
