@@ -61,25 +61,57 @@ __device__ __forceinline__ int64_t block_exclusive_scan(int64_t v, int64_t* tota
     return res;
 }
 
+// Contiguous 32-bit inputs and outputs take two 16-byte accesses per thread.
+__device__ __forceinline__ void ld8_u32(const void* p, int64_t i, uint32_t (&u)[8]) {
+    const uint4* q = reinterpret_cast<const uint4*>(reinterpret_cast<const uint32_t*>(p) + i);
+    const uint4 a = q[0], b = q[1];
+    u[0] = a.x; u[1] = a.y; u[2] = a.z; u[3] = a.w;
+    u[4] = b.x; u[5] = b.y; u[6] = b.z; u[7] = b.w;
+}
+__host__ __device__ __forceinline__ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+// A thread's kScanItems consecutive items: two 16-byte loads when the input is a
+// contiguous 32-bit array aligned for them (In::kVec and in.vec) and all are in range.
+template <typename In>
+__device__ __forceinline__ void load_items(const In& in, int64_t base, int64_t count, int64_t (&v)[kScanItems]) {
+    if constexpr (In::kVec) {
+        if (in.vec && base + kScanItems <= count) {
+            in.load8(base, v);
+            return;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) v[k] = base + k < count ? in(base + k) : 0;
+}
+
 template <typename In>
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(In in, int64_t max_count, const int64_t* count_ptr,
                                                               int64_t capacity, int64_t* partials) {
     __shared__ int64_t sm[9];
     const int64_t count = eff_count(count_ptr, max_count, capacity);
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    if ((int64_t)blockIdx.x * kScanTile >= count) {   // an empty block (the grid is an upper bound)
+        if (threadIdx.x == 0) partials[blockIdx.x] = 0;
+        return;
+    }
+    int64_t v[kScanItems];
+    load_items(in, base, count, v);
     int64_t s = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; k++)
-        if (base + k < count) s += in(base + k);
+    for (int k = 0; k < kScanItems; k++) s += v[k];
     int64_t total;
     block_exclusive_scan(s, &total, sm);
     if (threadIdx.x == 0) partials[blockIdx.x] = total;
 }
 
-// Single block: exclusive scan of the block partials in place; writes the grand total.
-__global__ void __launch_bounds__(1024) k_scan_top(int64_t* partials, int64_t nparts, int64_t* total) {
+// Single block: exclusive scan of the partials of the blocks that hold items, in place;
+// writes the grand total.
+__global__ void __launch_bounds__(1024) k_scan_top(int64_t* partials, int64_t nparts, int64_t* total,
+                                                   int64_t max_count, const int64_t* count_ptr, int64_t capacity) {
     __shared__ int64_t sm[33];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t active = (eff_count(count_ptr, max_count, capacity) + kScanTile - 1) / kScanTile;
+    if (active < nparts) nparts = active;
     int64_t carry = 0;
     for (int64_t base = 0; base < nparts; base += 1024) {
         const int64_t idx = base + threadIdx.x;
@@ -115,15 +147,26 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(In in, Out out, int
                                                              const int64_t* partials) {
     __shared__ int64_t sm[9];
     const int64_t count = eff_count(count_ptr, max_count, capacity);
+    if ((int64_t)blockIdx.x * kScanTile >= count) return;   // an empty block (uniform)
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     int64_t v[kScanItems];
+    load_items(in, base, count, v);
     int64_t s = 0;
 #pragma unroll
-    for (int k = 0; k < kScanItems; k++) {
-        v[k] = base + k < count ? in(base + k) : 0;
-        s += v[k];
-    }
+    for (int k = 0; k < kScanItems; k++) s += v[k];
     int64_t run = block_exclusive_scan(s, nullptr, sm) + partials[blockIdx.x];
+    if constexpr (Out::kVec) {
+        if (out.vec && base + kScanItems <= count) {
+            int64_t pre[kScanItems];
+#pragma unroll
+            for (int k = 0; k < kScanItems; k++) {
+                pre[k] = run;
+                run += v[k];
+            }
+            out.store8(base, pre);
+            return;
+        }
+    }
 #pragma unroll
     for (int k = 0; k < kScanItems; k++) {
         if (base + k < count) out(base + k, run, v[k]);
@@ -140,7 +183,7 @@ void device_scan(In in, Out out, int64_t max_count, const int64_t* count_ptr, in
         return;
     }
     k_scan_reduce<<<(unsigned)nblocks, kScanThreads, 0, st>>>(in, max_count, count_ptr, capacity, partials);
-    k_scan_top<<<1, 1024, 0, st>>>(partials, nblocks, total);
+    k_scan_top<<<1, 1024, 0, st>>>(partials, nblocks, total, max_count, count_ptr, capacity);
     k_scan_apply<<<(unsigned)nblocks, kScanThreads, 0, st>>>(in, out, max_count, count_ptr, capacity, partials);
 }
 
@@ -157,22 +200,43 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
     __syncthreads();
     const int64_t count = eff_count(count_ptr, max_count, capacity);
     const int64_t base = (int64_t)blockIdx.x * kSortTile;
-#pragma unroll 4
-    for (int k = 0; k < kSortItems; k++) {
-        const int64_t idx = base + k * kSortThreads + threadIdx.x;
-        if (idx < count) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+    const int64_t mine = base + (int64_t)threadIdx.x * kSortItems;   // this thread's 8 consecutive keys
+    if (mine + kSortItems <= count && aligned16(keys)) {
+        uint32_t u[8];
+        ld8_u32(keys, mine, u);
+#pragma unroll
+        for (int k = 0; k < kSortItems; k++) atomicAdd(&h[(u[k] >> shift) & 255u], 1u);
+    } else {
+#pragma unroll
+        for (int k = 0; k < kSortItems; k++)
+            if (mine + k < count) atomicAdd(&h[(keys[mine + k] >> shift) & 255u], 1u);
     }
     __syncthreads();
     hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
 }
 
 struct HistIn {
+    static constexpr bool kVec = true;
     const uint32_t* h;
+    bool vec;
     __device__ int64_t operator()(int64_t i) const { return h[i]; }
+    __device__ void load8(int64_t i, int64_t (&v)[8]) const {
+        uint32_t u[8];
+        ld8_u32(h, i, u);
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = u[k];
+    }
 };
 struct HistOut {
+    static constexpr bool kVec = true;
     uint32_t* h;
+    bool vec;
     __device__ void operator()(int64_t i, int64_t prefix, int64_t) const { h[i] = (uint32_t)prefix; }
+    __device__ void store8(int64_t i, const int64_t (&pre)[8]) const {
+        uint4* q = reinterpret_cast<uint4*>(h + i);
+        q[0] = make_uint4((uint32_t)pre[0], (uint32_t)pre[1], (uint32_t)pre[2], (uint32_t)pre[3]);
+        q[1] = make_uint4((uint32_t)pre[4], (uint32_t)pre[5], (uint32_t)pre[6], (uint32_t)pre[7]);
+    }
 };
 
 // Lanes of the warp holding the same BITS-bit value (an 8-bit digit, or with 9 bits also
@@ -312,7 +376,8 @@ void radix_sort(uint32_t* keys[2], uint32_t* vals[2], int passes, int64_t max_co
         if (p > 0 || !first_hist_done)
             k_radix_hist<<<(unsigned)nblocks, kSortThreads, 0, st>>>(keys[a], count_ptr, max_count, capacity, 8 * p,
                                                                     hist, nblocks);
-        device_scan(HistIn{hist}, HistOut{hist}, 256 * nblocks, nullptr, INT64_MAX, partials, nullptr, st);
+        device_scan(HistIn{hist, aligned16(hist)}, HistOut{hist, aligned16(hist)}, 256 * nblocks, nullptr, INT64_MAX,
+                    partials, nullptr, st);
         k_radix_scatter<<<(unsigned)nblocks, kSortThreads, 0, st>>>(keys[a], vals[a], keys[b], vals[b], count_ptr,
                                                                    max_count, capacity, 8 * p, hist, nblocks);
     }
@@ -323,10 +388,19 @@ void radix_sort(uint32_t* keys[2], uint32_t* vals[2], int passes, int64_t max_co
 // ---------------------------------------------------------------------------------
 
 struct VisIn {
+    static constexpr bool kVec = true;
     const int32_t* n_tiles;
+    bool vec;
     __device__ int64_t operator()(int64_t p) const { return n_tiles[p] > 0 ? 1 : 0; }
+    __device__ void load8(int64_t i, int64_t (&v)[8]) const {
+        uint32_t u[8];
+        ld8_u32(n_tiles, i, u);
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = (int32_t)u[k] > 0 ? 1 : 0;
+    }
 };
 struct VisOut {  // compact visible pairs with their depth bits as keys
+    static constexpr bool kVec = false;
     const float4* rec;
     int64_t n;
     uint32_t* keys;
@@ -355,6 +429,7 @@ static_assert(kEmitTile == kSortTile, "emit blocks must be the first radix pass'
 static_assert(kEmitThreads == 256, "one thread per digit of the emitted histogram");
 
 struct RowsIn {   // tile rows of the j-th visible pair's box (depth order)
+    static constexpr bool kVec = false;
     const uint32_t* sorted_pairs;
     const short4* rect;
     __device__ int64_t operator()(int64_t j) const {
@@ -367,6 +442,7 @@ struct RowsIn {   // tile rows of the j-th visible pair's box (depth order)
 // whose range [prefix, prefix + count) holds the block's first item, so that no block has
 // to search for it.
 struct OffsetOut {
+    static constexpr bool kVec = false;
     int64_t* offsets;
     uint32_t* first_owner;
     int64_t nblocks;
@@ -449,13 +525,25 @@ __global__ void __launch_bounds__(kEmitThreads) k_rows(const uint32_t* __restric
 // Slots and compaction in one scan: the low 32 bits count a row item's tiles, the high 32
 // bits whether it has any (the sums stay below 2^31 each, so no carry crosses).
 struct SlotIn {
+    static constexpr bool kVec = true;
     const int32_t* cnt;
+    bool vec;
     __device__ int64_t operator()(int64_t j) const {
         const int64_t c = cnt[j];
         return c | ((int64_t)(c > 0) << 32);
     }
+    __device__ void load8(int64_t i, int64_t (&v)[8]) const {
+        uint32_t u[8];
+        ld8_u32(cnt, i, u);
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            const int64_t c = (int32_t)u[k];
+            v[k] = c | ((int64_t)(c > 0) << 32);
+        }
+    }
 };
 struct SlotOut {
+    static constexpr bool kVec = false;
     int32_t* c_off;
     int32_t* c_row;
     uint32_t* first_owner;
@@ -665,7 +753,7 @@ void launch_bin_sort(const Frame& fr, int64_t n, const float4* rec, const short4
     const int64_t pairs = (int64_t)fr.n_sensors * n;
     cudaMemsetAsync(tile_ranges, 0, sizeof(int2) * (size_t)total_tiles, st);
     // 1. compact visible pairs (stable), keyed by depth bits
-    device_scan(VisIn{n_tiles}, VisOut{rec, n, w.vkeys[0], w.vvals[0]}, pairs, nullptr, INT64_MAX, w.partials,
+    device_scan(VisIn{n_tiles, aligned16(n_tiles)}, VisOut{rec, n, w.vkeys[0], w.vvals[0]}, pairs, nullptr, INT64_MAX, w.partials,
                 w.vis_count, st);
     // 2. stable depth sort of the visible pairs (32-bit keys)
     radix_sort(w.vkeys, w.vvals, 4, pairs, w.vis_count, INT64_MAX, w.hist, w.partials, st);
@@ -685,7 +773,7 @@ void launch_bin_sort(const Frame& fr, int64_t n, const float4* rec, const short4
                                                                w.n_rows, capacity, rect, rec, n,
                                                                (float)(1.0 / (double)n), fr, w);
     // 3b. each row item's first slot, the row items with tiles compacted; n_isect = total
-    device_scan(SlotIn{w.r_cnt}, SlotOut{w.c_off, w.c_row, w.first_owner, emit_blocks}, capacity, w.n_rows, capacity,
+    device_scan(SlotIn{w.r_cnt, aligned16(w.r_cnt)}, SlotOut{w.c_off, w.c_row, w.first_owner, emit_blocks}, capacity, w.n_rows, capacity,
                 w.partials, w.slot_total, st);
     k_slot_totals<<<1, 1, 0, st>>>(w.n_rows, capacity, w.slot_total, n_isect, w.n_owners);
     if (emit_blocks > 0)
