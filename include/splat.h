@@ -20,8 +20,10 @@
  *  - Gradient outputs are ACCUMULATED (+=) so that several sensors or frames can share
  *    them; the caller zeroes them first.
  *  - The library launches no kernel that waits on another block: there are no
- *    inter-block spin waits anywhere, so no call can hang on a lost signal
- *    (SPLAT_ERR_TIMEOUT is reserved and never returned).
+ *    inter-block spin waits anywhere, so no call can hang on a lost signal.  The one
+ *    kernel that waits at all, the decoder's training pass on the tensor cores, waits only
+ *    for its own block's matrix products, with a bound: if it runs out the block stops,
+ *    and splat_sync_status returns SPLAT_ERR_TIMEOUT.
  *
  * Sensor model (paper Sec. 3.2, 3.3, App. A, App. D)
  * --------------------------------------------------
@@ -531,8 +533,9 @@ const char *splat_last_error(void);
 
 /* Waits for the stream and reports a CUDA error raised by anything enqueued on it as
  * SPLAT_ERR_CUDA (message in splat_last_error).  It then reads and clears the device
- * status words of the current device: SPLAT_ERR_BOUNDS if the checked build skipped an
- * out-of-bounds index since the last call (the message names the first site).  Capacity
+ * status words of the current device: SPLAT_ERR_TIMEOUT if a bounded wait for tensor-core
+ * work ran out, SPLAT_ERR_BOUNDS if the checked build skipped an out-of-bounds index, since
+ * the last call (the message names the first site).  Capacity
  * overflow is not a status: it is reported through bins.n_isect.  Synchronous. */
 splat_status splat_sync_status(void *stream);
 

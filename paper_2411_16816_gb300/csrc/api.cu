@@ -308,6 +308,8 @@ splat_status splat_sync_status(void* stream) {
     if (e2 != cudaSuccess) return fail(SPLAT_ERR_CUDA, "%s", cudaGetErrorString(e2));
     uint32_t bits = 0, site = 0;
     take_all_status(&bits, &site);
+    if (bits & kStatusTimeout)
+        return fail(SPLAT_ERR_TIMEOUT, "a bounded wait for tensor-core work ran out (site %u)", site);
     if (bits & kStatusBounds)
         return fail(SPLAT_ERR_BOUNDS, "checked build: an out-of-bounds index was skipped (site %u)", site);
     return SPLAT_OK;

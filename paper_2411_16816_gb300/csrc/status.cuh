@@ -1,7 +1,8 @@
 // status.cuh -- the device status word of a translation unit.
 //
 // In the checked build (SPLAT_CHECKED) a kernel that finds an index out of its buffer's
-// bounds skips the access, raises a bit of its unit's word and records the first site.
+// bounds skips the access, raises a bit of its unit's word and records the first site; a
+// kernel whose bounded wait for its own tensor-core work runs out does the same.
 // splat_sync_status reads and clears the words of every unit that includes this header.
 #pragma once
 #include <cuda_runtime.h>
@@ -10,6 +11,7 @@
 
 namespace splat {
 
+constexpr uint32_t kStatusTimeout = 1u;   // a bounded wait for the tensor core ran out
 constexpr uint32_t kStatusBounds = 2u;    // checked build: an out-of-bounds index was skipped
 
 // Checked-build sites of the units outside the rasterizer (which numbers its own from 1).

@@ -55,6 +55,45 @@ def test_training_gradients_and_input_gradient_match_oracle():
     np.testing.assert_allclose(dx.cpu().numpy(), gx, atol=1e-3 * np.abs(gx).max(), rtol=0)
 
 
+def _near_relu_decision(x, p, rel=3e-5):
+    """Rays with a pre-activation within `rel` of the sum of its terms' magnitudes of 0:
+    there the FP32 split products and the FP64 oracle may take different ReLU branches,
+    and the input gradient of that ray may differ by a whole unit's term."""
+    x = x.astype(np.float64)
+    W1, b1, W2, b2 = (p[k].astype(np.float64) for k in ("W1", "b1", "W2", "b2"))
+    z1 = x @ W1 + b1
+    s1 = np.abs(x) @ np.abs(W1) + np.abs(b1)
+    h1 = np.maximum(z1, 0.0)
+    z2 = h1 @ W2 + b2
+    s2 = h1 @ np.abs(W2) + np.abs(b2)
+    return (np.abs(z1) < rel * s1).any(axis=1) | (np.abs(z2) < rel * s2).any(axis=1)
+
+
+def test_training_gradients_over_many_tiles_per_block_match_oracle():
+    """60,001 rays: about three 128-ray tiles per block of the persistent grid (the weight
+    gradients accumulate across a block's tiles), the last tile ragged.  The input gradient
+    is compared on the rays whose ReLU decisions are all clear of FP32 noise."""
+    head = RayHead(scenes.head_init_params(14), DEV)
+    x, yi, yd = _data(60_001, 4)
+    tx = torch.as_tensor(x, device=DEV)
+    dx = torch.empty_like(tx)
+    head.grad.zero_()
+    head.loss.zero_()
+    head.accumulate(tx, torch.as_tensor(yi, device=DEV), torch.as_tensor(yd, device=DEV), dx)
+    torch.cuda.synchronize()
+    p = _bf16_params(head)
+    loss, g, gx = H.loss_backward(x.astype(np.float64), p, yi, yd, want_dx=True)
+    assert head.loss.item() == pytest.approx(loss, rel=1e-4)
+    got = unflatten(head.grad.cpu().numpy())
+    for k in H.ORDER:
+        rel = np.linalg.norm(got[k] - g[k]) / np.linalg.norm(g[k])
+        assert rel < 1e-3, (k, rel)
+        np.testing.assert_allclose(got[k], g[k], atol=1e-3 * np.abs(g[k]).max() + 1e-7, rtol=0, err_msg=k)
+    near = _near_relu_decision(x, p)
+    assert near.mean() < 0.02, near.mean()
+    np.testing.assert_allclose(dx.cpu().numpy()[~near], gx[~near], atol=1e-3 * np.abs(gx).max(), rtol=0)
+
+
 def test_adam_step_and_bf16_copy_match_oracle():
     head = RayHead(scenes.head_init_params(13), DEV, lr=1e-2)
     x, yi, yd = _data(512, 3)
