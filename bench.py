@@ -581,9 +581,10 @@ def run_ours(args):
 
     peaks = measured_peaks()
     clocks = clk.summary()
-    # DRAM bytes per launch from ncu captures of the current kernels (one camera of the
-    # driving scene, scaled by the six cameras of the frame; profiles/ holds the captures)
-    traffic = {"raster_camera_bwd": 6 * 159.33e6} if args.workload == "driving" else {}
+    # DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum + write.sum of the
+    # six-camera launch, from the ncu launch list of this benchmark's training step; the
+    # summary and its command are in profiles/driving_frame_launches.md)
+    traffic = {"raster_camera_bwd": 923.13e6 + 0.97e6} if args.workload == "driving" else {}
     roofline = frame_roofline(kp, peaks, traffic)
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
