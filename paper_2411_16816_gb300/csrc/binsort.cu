@@ -191,7 +191,20 @@ void device_scan(In in, Out out, int64_t max_count, const int64_t* count_ptr, in
 // Stable LSD radix sort pass (8-bit digit) of (key, value) pairs.
 // ---------------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __restrict__ keys,
+// Keys [i, i + 8) as 32-bit values: two 16-byte loads of 32-bit keys or one of 16-bit keys.
+__device__ __forceinline__ void ld8_keys(const uint32_t* p, int64_t i, uint32_t (&u)[8]) { ld8_u32(p, i, u); }
+__device__ __forceinline__ void ld8_keys(const uint16_t* p, int64_t i, uint32_t (&u)[8]) {
+    const uint4 a = *reinterpret_cast<const uint4*>(p + i);
+    const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+    for (int e = 0; e < 4; e++) {
+        u[2 * e] = w[e] & 0xffffu;
+        u[2 * e + 1] = w[e] >> 16;
+    }
+}
+
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const K* __restrict__ keys,
                                                              const int64_t* count_ptr, int64_t max_count,
                                                              int64_t capacity, int shift, uint32_t* hist,
                                                              int64_t nblocks) {
@@ -203,13 +216,13 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_hist(const uint32_t* __r
     const int64_t mine = base + (int64_t)threadIdx.x * kSortItems;   // this thread's 8 consecutive keys
     if (mine + kSortItems <= count && aligned16(keys)) {
         uint32_t u[8];
-        ld8_u32(keys, mine, u);
+        ld8_keys(keys, mine, u);
 #pragma unroll
         for (int k = 0; k < kSortItems; k++) atomicAdd(&h[(u[k] >> shift) & 255u], 1u);
     } else {
 #pragma unroll
         for (int k = 0; k < kSortItems; k++)
-            if (mine + k < count) atomicAdd(&h[(keys[mine + k] >> shift) & 255u], 1u);
+            if (mine + k < count) atomicAdd(&h[((uint32_t)keys[mine + k] >> shift) & 255u], 1u);
     }
     __syncthreads();
     hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
@@ -261,9 +274,9 @@ __device__ __forceinline__ uint32_t warp_peers(uint32_t d) {
 // digit's run to its global position, so consecutive threads write consecutive
 // addresses.  Indices inside the block are 32-bit; a full block ranks 8-bit digits
 // (eight ballots), the last, partial block also marks the slots without a key.
-template <bool FULL>
-__device__ __forceinline__ void radix_rank_block(const uint32_t* __restrict__ kb, const uint32_t* __restrict__ vb,
-                                                 uint32_t* __restrict__ kout, uint32_t* __restrict__ vout,
+template <bool FULL, typename K>
+__device__ __forceinline__ void radix_rank_block(const K* __restrict__ kb, const uint32_t* __restrict__ vb,
+                                                 K* __restrict__ kout, uint32_t* __restrict__ vout,
                                                  int nvalid, int64_t count, int shift,
                                                  const uint32_t* __restrict__ hist_scan,
                                                  int64_t nblocks, uint32_t (*wh)[256], uint32_t* bd, uint32_t* sk,
@@ -279,7 +292,7 @@ __device__ __forceinline__ void radix_rank_block(const uint32_t* __restrict__ kb
     for (int it = 0; it < kSortItems; it++) {
         const int l = wbase + it * 32 + lane;
         const bool valid = FULL || l < nvalid;
-        kk[it] = valid ? kb[l] : 0u;
+        kk[it] = valid ? (uint32_t)kb[l] : 0u;
         vv[it] = valid ? vb[l] : 0u;
     }
 #pragma unroll
@@ -331,15 +344,16 @@ __device__ __forceinline__ void radix_rank_block(const uint32_t* __restrict__ kb
             const uint32_t key = sk[i];
             const uint32_t pos = bd[(key >> shift) & 255u] + (uint32_t)i;
             if (SPLAT_OUT_OF_BOUNDS((int64_t)pos < count, kSiteScatter)) continue;
-            kout[pos] = key;
+            kout[pos] = (K)key;
             vout[pos] = sv[i];
         }
     }
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* __restrict__ kin,
+template <typename K>
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const K* __restrict__ kin,
                                                                 const uint32_t* __restrict__ vin,
-                                                                uint32_t* __restrict__ kout,
+                                                                K* __restrict__ kout,
                                                                 uint32_t* __restrict__ vout,
                                                                 const int64_t* count_ptr, int64_t max_count,
                                                                 int64_t capacity, int shift,
@@ -358,27 +372,29 @@ __global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const uint32_t* 
     const int nvalid = (int)min((int64_t)kSortTile, count - block0);
     __syncthreads();
     if (nvalid == kSortTile)
-        radix_rank_block<true>(kin + block0, vin + block0, kout, vout, nvalid, count, shift, hist_scan, nblocks, wh, bd,
+        radix_rank_block<true, K>(kin + block0, vin + block0, kout, vout, nvalid, count, shift, hist_scan, nblocks, wh, bd,
                                sk, sv, scan_sm);
     else
-        radix_rank_block<false>(kin + block0, vin + block0, kout, vout, nvalid, count, shift, hist_scan, nblocks, wh,
+        radix_rank_block<false, K>(kin + block0, vin + block0, kout, vout, nvalid, count, shift, hist_scan, nblocks, wh,
                                 bd, sk, sv, scan_sm);
 }
 
-// Sorts by bits [0, 8*passes) of the keys.  Buffers ping-pong: pass p reads buffer
-// p % 2 and writes buffer (p + 1) % 2; the result is in buffer passes % 2.
-void radix_sort(uint32_t* keys[2], uint32_t* vals[2], int passes, int64_t max_count, const int64_t* count_ptr,
+// Sorts by bits [0, 8*passes) of the keys (32-bit, or 16-bit for at most two passes).
+// Buffers ping-pong: pass p reads buffer p % 2 and writes buffer (p + 1) % 2; the result is
+// in buffer passes % 2.
+template <typename K>
+void radix_sort(K* keys[2], uint32_t* vals[2], int passes, int64_t max_count, const int64_t* count_ptr,
                 int64_t capacity, uint32_t* hist, int64_t* partials, cudaStream_t st, bool first_hist_done = false) {
     const int64_t nblocks = (max_count + kSortTile - 1) / kSortTile;
     if (nblocks == 0) return;
     for (int p = 0; p < passes; p++) {
         const int a = p & 1, b = a ^ 1;
         if (p > 0 || !first_hist_done)
-            k_radix_hist<<<(unsigned)nblocks, kSortThreads, 0, st>>>(keys[a], count_ptr, max_count, capacity, 8 * p,
+            k_radix_hist<K><<<(unsigned)nblocks, kSortThreads, 0, st>>>(keys[a], count_ptr, max_count, capacity, 8 * p,
                                                                     hist, nblocks);
         device_scan(HistIn{hist, aligned16(hist)}, HistOut{hist, aligned16(hist)}, 256 * nblocks, nullptr, INT64_MAX,
                     partials, nullptr, st);
-        k_radix_scatter<<<(unsigned)nblocks, kSortThreads, 0, st>>>(keys[a], vals[a], keys[b], vals[b], count_ptr,
+        k_radix_scatter<K><<<(unsigned)nblocks, kSortThreads, 0, st>>>(keys[a], vals[a], keys[b], vals[b], count_ptr,
                                                                    max_count, capacity, 8 * p, hist, nblocks);
     }
 }
@@ -579,9 +595,10 @@ __global__ void k_slot_totals(const int64_t* n_rows, int64_t capacity, const int
 // search for the owner of the first, then each slot's tile is the owner's first tile plus
 // its offset (less a lidar row's column count past its wrap).  The writes are contiguous.
 // The blocks are those of the first radix pass over the keys, so each block also writes
-// that pass's low-byte digit histogram.
+// that pass's low-byte digit histogram.  Keys are 16-bit when every tile id fits.
+template <typename Key>
 __global__ void __launch_bounds__(kEmitThreads) k_emit(const BinWorkspace w, const int64_t* n_isect,
-                                                      int64_t capacity, uint32_t* __restrict__ keys,
+                                                      int64_t capacity, Key* __restrict__ keys,
                                                       uint32_t* __restrict__ vals, uint32_t* __restrict__ hist) {
     __shared__ int s_off[kEmitTile];
     __shared__ uint32_t s_key0[kEmitTile];
@@ -645,15 +662,20 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const BinWorkspace w, con
         if (vec && ofirst + kEmitItems <= nslot) {
             uint4* kp = reinterpret_cast<uint4*>(keys + o0 + ofirst);
             uint4* vp = reinterpret_cast<uint4*>(vals + o0 + ofirst);
-            kp[0] = make_uint4(kk[0], kk[1], kk[2], kk[3]);
-            kp[1] = make_uint4(kk[4], kk[5], kk[6], kk[7]);
+            if constexpr (sizeof(Key) == 2) {
+                kp[0] = make_uint4(kk[0] | (kk[1] << 16), kk[2] | (kk[3] << 16), kk[4] | (kk[5] << 16),
+                                   kk[6] | (kk[7] << 16));
+            } else {
+                kp[0] = make_uint4(kk[0], kk[1], kk[2], kk[3]);
+                kp[1] = make_uint4(kk[4], kk[5], kk[6], kk[7]);
+            }
             vp[0] = make_uint4(vv[0], vv[1], vv[2], vv[3]);
             vp[1] = make_uint4(vv[4], vv[5], vv[6], vv[7]);
         } else {
 #pragma unroll
             for (int i = 0; i < kEmitItems; i++) {
                 if (ofirst + i < nslot) {
-                    keys[o0 + ofirst + i] = kk[i];
+                    keys[o0 + ofirst + i] = (Key)kk[i];
                     vals[o0 + ofirst + i] = vv[i];
                 }
             }
@@ -665,7 +687,23 @@ __global__ void __launch_bounds__(kEmitThreads) k_emit(const BinWorkspace w, con
 
 // Tile ranges of the sorted ids: four keys per thread (one vector load) plus the two
 // neighbours; keys past every tile (malformed projections) are never ranged.
-__global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict__ keys, const int64_t* count_ptr,
+__device__ __forceinline__ void ld4_keys(const uint32_t* p, int64_t j, uint32_t* k) {
+    const uint4 v = *reinterpret_cast<const uint4*>(p + j);
+    k[0] = v.x;
+    k[1] = v.y;
+    k[2] = v.z;
+    k[3] = v.w;
+}
+__device__ __forceinline__ void ld4_keys(const uint16_t* p, int64_t j, uint32_t* k) {
+    const uint2 v = *reinterpret_cast<const uint2*>(p + j);
+    k[0] = v.x & 0xffffu;
+    k[1] = v.x >> 16;
+    k[2] = v.y & 0xffffu;
+    k[3] = v.y >> 16;
+}
+
+template <typename K>
+__global__ void __launch_bounds__(256) k_tile_ranges(const K* __restrict__ keys, const int64_t* count_ptr,
                                                       int64_t capacity, int64_t total_tiles, int2* ranges) {
     const int64_t count = eff_count(count_ptr, capacity, capacity);
     const int64_t groups = (count + 3) / 4;
@@ -674,17 +712,13 @@ __global__ void __launch_bounds__(256) k_tile_ranges(const uint32_t* __restrict_
         const int64_t j0 = 4 * q;
         uint32_t k[6];   // k[1 + i] = keys[j0 + i]; k[0], k[5]: neighbours
         if (j0 + 4 <= count) {
-            const uint4 v = *reinterpret_cast<const uint4*>(keys + j0);
-            k[1] = v.x;
-            k[2] = v.y;
-            k[3] = v.z;
-            k[4] = v.w;
+            ld4_keys(keys, j0, k + 1);
         } else {
 #pragma unroll
-            for (int i = 0; i < 4; i++) k[1 + i] = j0 + i < count ? keys[j0 + i] : 0u;
+            for (int i = 0; i < 4; i++) k[1 + i] = j0 + i < count ? (uint32_t)keys[j0 + i] : 0u;
         }
-        k[0] = j0 > 0 ? keys[j0 - 1] : 0u;
-        k[5] = j0 + 4 < count ? keys[j0 + 4] : 0u;
+        k[0] = j0 > 0 ? (uint32_t)keys[j0 - 1] : 0u;
+        k[5] = j0 + 4 < count ? (uint32_t)keys[j0 + 4] : 0u;
 #pragma unroll
         for (int i = 0; i < 4; i++) {
             const int64_t j = j0 + i;
@@ -746,6 +780,20 @@ static int bits_for(int64_t v) {
     return b;
 }
 
+template <typename K>
+static void tile_stage(const BinWorkspace& w, K* keys[2], uint32_t* vals_buf[2], int passes, int64_t capacity,
+                       int64_t emit_blocks, int64_t* n_isect, int64_t total_tiles, int2* tile_ranges,
+                       cudaStream_t st) {
+    if (emit_blocks > 0)
+        k_emit<K><<<(unsigned)emit_blocks, kEmitThreads, 0, st>>>(w, n_isect, capacity, keys[0], vals_buf[0], w.hist);
+    radix_sort<K>(keys, vals_buf, passes, capacity, n_isect, capacity, w.hist, w.partials, st, emit_blocks > 0);
+    int64_t blocks = (capacity + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > 0)
+        k_tile_ranges<K><<<(unsigned)blocks, 256, 0, st>>>(keys[passes & 1], n_isect, capacity, total_tiles,
+                                                           tile_ranges);
+}
+
 void launch_bin_sort(const Frame& fr, int64_t n, const float4* rec, const short4* rect, const int32_t* n_tiles,
                      int64_t capacity, uint32_t* isect_ids, int2* tile_ranges, int64_t total_tiles,
                      int64_t* n_isect, void* workspace, cudaStream_t st) {
@@ -756,7 +804,7 @@ void launch_bin_sort(const Frame& fr, int64_t n, const float4* rec, const short4
     device_scan(VisIn{n_tiles, aligned16(n_tiles)}, VisOut{rec, n, w.vkeys[0], w.vvals[0]}, pairs, nullptr, INT64_MAX, w.partials,
                 w.vis_count, st);
     // 2. stable depth sort of the visible pairs (32-bit keys)
-    radix_sort(w.vkeys, w.vvals, 4, pairs, w.vis_count, INT64_MAX, w.hist, w.partials, st);
+    radix_sort<uint32_t>(w.vkeys, w.vvals, 4, pairs, w.vis_count, INT64_MAX, w.hist, w.partials, st);
     const uint32_t* sorted_pairs = w.vvals[0];  // 4 passes: result back in buffer 0
     // 3. emit (tile, id) in depth order; n_isect = total
     const int passes = (bits_for(total_tiles) + 7) / 8 > 0 ? (bits_for(total_tiles) + 7) / 8 : 1;
@@ -776,16 +824,14 @@ void launch_bin_sort(const Frame& fr, int64_t n, const float4* rec, const short4
     device_scan(SlotIn{w.r_cnt, aligned16(w.r_cnt)}, SlotOut{w.c_off, w.c_row, w.first_owner, emit_blocks}, capacity, w.n_rows, capacity,
                 w.partials, w.slot_total, st);
     k_slot_totals<<<1, 1, 0, st>>>(w.n_rows, capacity, w.slot_total, n_isect, w.n_owners);
-    if (emit_blocks > 0)
-        k_emit<<<(unsigned)emit_blocks, kEmitThreads, 0, st>>>(w, n_isect, capacity, w.ikeys[0], vals_buf[0], w.hist);
-    // 4. stable sort of the intersections by tile id
-    radix_sort(w.ikeys, vals_buf, passes, capacity, n_isect, capacity, w.hist, w.partials, st, emit_blocks > 0);
-    // 5. per-tile ranges
-    int64_t blocks = (capacity + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    if (blocks > 0)
-        k_tile_ranges<<<(unsigned)blocks, 256, 0, st>>>(w.ikeys[passes & 1], n_isect, capacity, total_tiles,
-                                                        tile_ranges);
+    // 3c.-5. the intersections, their stable sort by tile id and the per-tile ranges, with
+    // 16-bit keys when every tile id fits (the key buffers hold 32 bits per slot either way)
+    if (total_tiles <= 65536) {
+        uint16_t* k16[2] = {reinterpret_cast<uint16_t*>(w.ikeys[0]), reinterpret_cast<uint16_t*>(w.ikeys[1])};
+        tile_stage(w, k16, vals_buf, passes, capacity, emit_blocks, n_isect, total_tiles, tile_ranges, st);
+    } else {
+        tile_stage(w, w.ikeys, vals_buf, passes, capacity, emit_blocks, n_isect, total_tiles, tile_ranges, st);
+    }
 }
 
 }  // namespace splat
