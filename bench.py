@@ -42,6 +42,8 @@ def parse():
     p.add_argument("--workload", choices=["driving", "lidar_heavy", "profile"], default="driving")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--profile-only", action="store_true", help="a few untimed steps (for ncu captures)")
+    p.add_argument("--profile-head", action="store_true",
+                   help="decoder training passes over 1M seeded synthetic rays only (for ncu captures)")
     p.add_argument("--no-serving", action="store_true", help="skip the batched-serving measurement")
     p.add_argument("--no-head", action="store_true", help="skip the learned ray-head measurement")
     p.add_argument("--no-configs", action="store_true",
@@ -853,6 +855,15 @@ def head_bench(args, dev):
     b.record(stream)
     torch.cuda.synchronize()
     infer_ms = a.elapsed_time(b) / 5
+    # the training kernel alone: one pass (loss and gradients, no update) over all the rays
+    head.accumulate(X, YI, YD)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(3):
+        head.accumulate(X, YI, YD)
+    b.record(stream)
+    torch.cuda.synchronize()
+    train_pass_ms = a.elapsed_time(b) / 3
     n_train = X.shape[0]
     del X, YI, YD, out
     torch.cuda.empty_cache()
@@ -952,17 +963,49 @@ def head_bench(args, dev):
             "minibatch": B, "steps": len(starts), "last_loss": loss,
             "infer_ms": infer_ms, "infer_rays_per_s": n_train / (infer_ms * 1e-3),
             "train_tflops": train_tf, "held_out": held, "fused_decode": fused,
-            "roofline": {"bound": "tensor", "kernel": "k_head_train", "achieved": train_tf,
+            "roofline": {"bound": "tensor", "kernel": "k_head_train_umma (tcgen05)", "achieved": train_tf,
                          "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": train_tf / peaks["bf16_tflops"],
-                         "note": "algorithmic flops (37,632 per ray) against the measured BF16 GEMM peak; the split "
-                                 "FP32 operands issue about 2.1x that in MMA work"},
+                         "note": "algorithmic flops (37,632 per ray) of the epoch (minibatches of 65,536 rays, "
+                                 "each with its Adam step) against the measured BF16 GEMM peak; the split FP32 "
+                                 "operands and the padded weight-gradient shapes issue about 2.6x that in MMA work"},
+            "train_pass": {"rays": n_train, "ms": train_pass_ms, "rays_per_s": n_train / (train_pass_ms * 1e-3),
+                           "tflops": n_train * flop_train / (train_pass_ms * 1e-3) / 1e12,
+                           "frac": n_train * flop_train / (train_pass_ms * 1e-3) / 1e12 / peaks["bf16_tflops"],
+                           "note": "one launch of the training kernel over all the rays (loss and gradients)"},
             "infer_roofline": {"bound": "hbm", "kernel": "k_head_fwd", "achieved": infer_gbs, "peak": peaks["hbm_gbs"],
                                "unit": "GB/s", "frac": infer_gbs / peaks["hbm_gbs"],
                                "note": "136 B per ray (32 inputs read, 2 outputs written)"}}
 
 
+def profile_head(dev):
+    """Three training steps of the ray decoder, then ten training passes (loss and
+    gradients) over 1,048,576 seeded synthetic rays, event-timed; prints one JSON line."""
+    import torch
+    from paper_2411_16816_gb300.head import RayHead
+    R = 1 << 20
+    gen = torch.Generator(device="cpu").manual_seed(0)
+    x = torch.randn((R, 32), generator=gen).to(dev)
+    yi = torch.rand(R, generator=gen).to(dev)
+    yd = (torch.rand(R, generator=gen) < 0.2).float().to(dev)
+    head = RayHead(scenes.head_init_params(7), device=dev)
+    for _ in range(3):
+        head.train_step(x, yi, yd)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(10):
+        head.accumulate(x, yi, yd)
+    b.record()
+    torch.cuda.synchronize()
+    print(json.dumps({"profile": "decoder training pass", "rays": R, "ms": a.elapsed_time(b) / 10}))
+
+
 def main():
     args = parse()
+    if args.profile_head:
+        import torch
+        profile_head(torch.device("cuda:0"))
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
