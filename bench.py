@@ -838,13 +838,31 @@ def head_bench(args, dev):
         head.train_step(X[i:i + B], YI[i:i + B], YD[i:i + B])
     stream = torch.cuda.current_stream()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # eager minibatch steps are bound by the host's launches (four per minibatch): one
+    # epoch's steps are captured in a CUDA graph (Adam's step counts advance at capture)
+    # and the epoch is one replay; an eager epoch is timed for comparison first
     torch.cuda.synchronize()
     a.record(stream)
     for i in starts:
         head.train_step(X[i:i + B], YI[i:i + B], YD[i:i + B])
     b.record(stream)
     torch.cuda.synchronize()
+    eager_epoch_ms = a.elapsed_time(b)
+    cap = torch.cuda.Stream(device=dev)
+    cap.wait_stream(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(cap):
+        with torch.cuda.graph(graph, stream=cap):
+            for i in starts:
+                head.train_step(X[i:i + B], YI[i:i + B], YD[i:i + B])
+    stream.wait_stream(cap)
+    torch.cuda.synchronize()
+    a.record(stream)
+    graph.replay()
+    b.record(stream)
+    torch.cuda.synchronize()
     epoch_ms = a.elapsed_time(b)
+    del graph
     loss = float(head.loss.item())
     out = torch.empty((X.shape[0], 2), dtype=torch.float32, device=dev)
     head.forward(X, out)
@@ -868,10 +886,12 @@ def head_bench(args, dev):
     del X, YI, YD, out
     torch.cuda.empty_cache()
 
-    # the decoder-free baseline, the same number of Adam steps as the head's epoch
+    # the decoder-free baseline, the same number of Adam steps as the head took (three
+    # warm-up steps and two epochs: the eager one and the replayed one)
     base = PlainChannels(gd, n_g, dev, lr=0.05)
     frames = {}
-    for step in range(3 + len(starts)):
+    n_steps = 3 + 2 * len(starts)
+    for step in range(n_steps):
         j = step % len(train_sweeps)
         lid, hit, ti, td = train_sweeps[j]
         if j not in frames:
@@ -916,7 +936,7 @@ def head_bench(args, dev):
 
     held = {"sweeps": 4, "all_rays": compare(np.ones(len(yi_), bool)), "hit_rays": compare(hit_),
             "baseline": "per-Gaussian intensity and drop logit channels composited by the rasterizer, fitted "
-                        f"through its backward with Adam for {3 + len(starts)} steps (one sweep each, hit rays), "
+                        f"through its backward with Adam for {n_steps} steps (one sweep each, hit rays), "
                         "the same App. B loss"}
 
     # inference on one more sweep: the decoder fused into the lidar forward's epilogue
@@ -960,6 +980,9 @@ def head_bench(args, dev):
     return {"workload": f"{n_train} lidar rays (128x2048 sweeps at {k} poses) of a 500k-Gaussian scene, "
                         "29 rendered channels + ray direction -> 64 -> 64 -> 2, BF16 weights, FP32 accumulate",
             "train_epoch_ms": epoch_ms, "train_rays_per_s": n_train / (epoch_ms * 1e-3),
+            "train_epoch": "the epoch's minibatch steps (zeroed gradients, training pass, Adam) captured in one CUDA "
+                           "graph, one replay",
+            "eager_epoch_ms": eager_epoch_ms,
             "minibatch": B, "steps": len(starts), "last_loss": loss,
             "infer_ms": infer_ms, "infer_rays_per_s": n_train / (infer_ms * 1e-3),
             "train_tflops": train_tf, "held_out": held, "fused_decode": fused,

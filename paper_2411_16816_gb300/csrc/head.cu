@@ -15,7 +15,7 @@
 // epilogue) on warp-level MMAs (mma.sync m16n8k16): a warp owns 16 rays (one MMA row tile)
 // and a layer's accumulator fragments (rows = rays, columns = units) are exactly the next
 // layer's A-operand fragments, so activations pass from layer to layer in registers.  The
-// training pass runs on the fifth-generation tensor cores (head_train.cu).
+// training pass runs on the fifth-generation tensor cores (head_umma.cu).
 #include <cuda_bf16.h>
 
 #include "head_impl.cuh"

@@ -1,7 +1,7 @@
-// head_train.cu -- training pass of the per-ray lidar decoder (paper Sec. 3.3 decoder, App. B
+// head_umma.cu -- training pass of the per-ray lidar decoder (paper Sec. 3.3 decoder, App. B
 // loss weights) on the fifth-generation tensor cores.
 //
-// One CTA per SM, 512 threads, 128-ray tiles: ray q of a tile is TMEM lane q, and the four
+// Training: one CTA per SM, 512 threads, 128-ray tiles: ray q of a tile is TMEM lane q, and the four
 // warps w, w + 4, w + 8, w + 12 (the warps that may read lane quarter w) share lanes
 // 32 w .. 32 w + 31, each taking 16 of the 64 columns of those rays.  Per tile, in order:
 //   Z1 = X W1, Z2 = H1 W2                    M = 128 products into TMEM
