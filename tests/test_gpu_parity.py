@@ -251,6 +251,29 @@ def test_full_driving_frame_lists(cull):
     assert pairs > (4_000_000 if cull else 5_000_000) and optional < 1e-4 * pairs
 
 
+def test_rig_over_65536_tiles_takes_32_bit_keys_and_three_tile_passes():
+    """Nine 1920 x 1080 cameras and the lidar: 73,440 camera tiles plus the lidar's, more
+    than 16-bit tile keys hold, so the tile sort runs on 32-bit keys in three passes (an
+    odd count: the sorted ids land in the second buffer). 20k Gaussians keep the oracle's
+    lists cheap. Every sensor's list against the oracle's, sampled rays against its
+    renders and the gradients of upstream terms on them."""
+    g = scenes.driving_gaussians(20000, 1017, channels=16, min_radius=2.0)
+    sensors = _cull_cameras(scenes.driving_rig(n_cams=9))
+    total_tiles = sum(oracle.n_tiles_of(s) for s in sensors)
+    assert 65536 < total_tiles < 1 << 24
+    fr, gd, out = U.run(g, sensors)
+    pairs, optional, ties = U.compare_lists(fr, g, sensors)
+    assert pairs > 100_000 and optional < 1e-4 * pairs
+    tiles, _ = fr.intersections()
+    assert tiles.max() >= 65536
+    sel = _sample(sensors, 1500, seed=21)
+    U.check_render(fr, out, g, sensors, sel=sel)
+    grads, per = U.sampled_upstream(fr, sensors, g, sel, seed=22)
+    pg = fr.backward(gd, out, grads)
+    torch.cuda.synchronize()
+    U.check_grads(pg, U.oracle_grads(g, sensors, per))
+
+
 def test_full_lidar_heavy_sampled_parity():
     """1M Gaussians, 128 x 2048 lidar: its whole list, 2,000 rays against the oracle's
     renders and the gradients of upstream terms on them."""
