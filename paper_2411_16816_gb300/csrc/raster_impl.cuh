@@ -1242,6 +1242,12 @@ __global__ void __launch_bounds__(TW* TH / RaysPerThread<CM, true, LIDAR, TW * T
     }
 }
 
+}  // namespace splat
+
+#include "raster_bwd_mma.cuh"   // the 16-channel camera backward on the tensor cores
+
+namespace splat {
+
 // ---------------------------------------------------------------------------------
 // Host launch helpers (instantiated per channel bucket in raster_c*.cu)
 // ---------------------------------------------------------------------------------
@@ -1265,6 +1271,20 @@ template <int CM, int TW, int TH, bool LIDAR>
 static void launch_bwd_t(const Frame& fr, int blocks, const RasterIn& in, const RasterGrad& g, bool recompute,
                          cudaStream_t st) {
     constexpr int NT = TW * TH / RaysPerThread<CM, true, LIDAR, TW * TH>::value;
+    if constexpr (CM == 16 && !LIDAR && TW * TH == 256) {   // 16 channels on 256-ray tiles: tensor cores
+        static_assert(NT == 64, "two warps of 4 rays per thread");
+        constexpr int KB = 16;   // staged entries per batch: 7 blocks of 2 warps per SM
+        if (recompute) {
+            auto k = k_raster_bwd_cam16<TW, TH, true, KB>;
+            set_smem(k, sizeof(cam16::Smem<KB, true>));
+            k<<<blocks, NT, sizeof(cam16::Smem<KB, true>), st>>>(fr, in, g);
+        } else {
+            auto k = k_raster_bwd_cam16<TW, TH, false, KB>;
+            set_smem(k, sizeof(cam16::Smem<KB, false>));
+            k<<<blocks, NT, sizeof(cam16::Smem<KB, false>), st>>>(fr, in, g);
+        }
+        return;
+    }
     using LY = BwdLayout<CM, LIDAR>;
     const size_t sm = sizeof(Stage<CM, NT, LIDAR>) + sizeof(float) * LY::slices(NT / 32) * NT * LY::kRow;
     if (recompute) {
