@@ -321,8 +321,8 @@ __global__ void __launch_bounds__(64, 7)
             }
             __syncwarp();
             // ---- dF = W G: rows of the MMA are channels, columns the group's entries ----
-            // six accumulators (three products x two alternating steps): dependent chains of 4
-            float d[6][4] = {};
+            // one accumulator per product
+            float d[3][4] = {};
 #pragma unroll
             for (int k2 = 0; k2 < 8; k2++) {   // 16 rays per step
                 const int rho = 16 * k2 + ri + 8 * (mi >> 1);
@@ -331,13 +331,12 @@ __global__ void __launch_bounds__(64, 7)
                 ldsm_x4_trans(aL, &s.gl[w][gchunk(rho, mi & 1)]);
                 // B fragments: weights' high parts (rays 16 k2 + 0-7, 8-15), residuals (the same)
                 ldsm_x4(bW, pw + (ri + 8 * (mi >> 1)) * kRowW + 8 * k2 + 4 * (mi & 1));
-                float(&d3)[3][4] = *reinterpret_cast<float(*)[3][4]>(&d[3 * (k2 & 1)][0]);
-                mma16816(d3[0], aH, bW[0], bW[1]);
-                mma16816(d3[1], aL, bW[0], bW[1]);
-                mma16816(d3[2], aH, bW[2], bW[3]);
+                mma16816(d[0], aH, bW[0], bW[1]);
+                mma16816(d[1], aL, bW[0], bW[1]);
+                mma16816(d[2], aH, bW[2], bW[3]);
             }
 #pragma unroll
-            for (int i = 0; i < 4; i++) d[0][i] = ((d[0][i] + d[1][i]) + d[2][i]) + ((d[3][i] + d[4][i]) + d[5][i]);
+            for (int i = 0; i < 4; i++) d[0][i] = (d[0][i] + d[1][i]) + d[2][i];
             // d: (channel g, entry 2 t), (g, 2 t + 1), (g + 8, 2 t), (g + 8, 2 t + 1)
             float* a0 = s.u.b.acc[w][k0 + 2 * t];
             float* a1 = s.u.b.acc[w][k0 + 2 * t + 1];
