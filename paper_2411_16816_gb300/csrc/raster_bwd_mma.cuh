@@ -33,8 +33,8 @@ constexpr int kRow = 24;    // accumulator row: 8 geometric sums, then 16 featur
 // of each row.
 template <int KB>
 struct BwdArea {
-    Stage<16, KB, false> st;   // st.f holds the features as BF16: KB x 16 high parts, then residuals
-    float acc[2][KB][kRow];    // one slice per warp
+    Stage<16, KB, false> st[2];   // per warp; st.f holds the features as BF16: KB x 16 high parts, then residuals
+    float acc[2][KB][kRow];       // per warp: the batch's per-entry sums
 };
 template <int KB, bool RECOMPUTE>
 struct Smem {
@@ -101,7 +101,7 @@ __device__ __forceinline__ void stage_entry(Stage<16, KB, false>& st, const Rast
 }  // namespace cam16
 
 // One block per 256-ray camera tile, 2 warps, 4 rays per thread (pixel threadIdx.x + 64 q);
-// KB staged entries per batch.
+// KB staged entries per batch and warp.
 template <int TW, int TH, bool RECOMPUTE, int KB>
 __global__ void __launch_bounds__(64, 7)
     k_raster_bwd_cam16(const __grid_constant__ Frame fr, RasterIn in, RasterGrad gr) {
@@ -111,7 +111,6 @@ __global__ void __launch_bounds__(64, 7)
     static_assert(KB % kG == 0 && KB <= NT, "whole groups, one staging thread per entry");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem<KB, RECOMPUTE>& s = *reinterpret_cast<Smem<KB, RECOMPUTE>*>(smem_raw);
-    __shared__ int s_max_last[2];
     TileCtx tc;
     RayCtx r[PX];
     if (!block_setup<TW, TH, false, false, PX, NT>(fr, in, tc, r)) return;
@@ -144,7 +143,7 @@ __global__ void __launch_bounds__(64, 7)
             last[q] = r[q].inside ? min(gr.last[r[q].o], len) : 0;   // never past this tile's list
         }
     }
-    for (int i = threadIdx.x; i < 2 * KB * kRow; i += NT) (&s.u.b.acc[0][0][0])[i] = 0.f;
+    for (int i = lane; i < KB * kRow; i += 32) (&s.u.b.acc[w][0][0])[i] = 0.f;
     // this warp's upstream feature gradients, split, into its planes (ray rho = 4 lane + q)
     const int C = in.C;
     float gTT[PX], T[PX], S[PX];
@@ -169,22 +168,22 @@ __global__ void __launch_bounds__(64, 7)
         my_last = max(my_last, last[q]);
     }
     const int wl = __reduce_max_sync(0xffffffffu, (unsigned)my_last);   // this warp's deepest entry
-    if (lane == 0) s_max_last[w] = wl;
-    __syncthreads();
-    const int max_last = max(s_max_last[0], s_max_last[1]);
+    __syncwarp();
     float4* gp0 = gr.grad_proj + rec_index(tc.s, 0, in.n, 0);
     float4* gp1 = gr.grad_proj + rec_index(tc.s, 1, in.n, 0);
-    const bf16* Fh = reinterpret_cast<const bf16*>(s.u.b.st.f);
+    Stage<16, KB, false>& sw = s.u.b.st[w];   // this warp's staging area
+    const bf16* Fh = reinterpret_cast<const bf16*>(sw.f);
     const bf16* Fl = Fh + KB * 16;
     uint32_t* pw = s.pw[w];
     const int g = lane >> 2, t = lane & 3, mi = lane >> 3, ri = lane & 7;   // fragment / ldmatrix roles
     float dtime = 0.f;   // this thread's share of dL/d (camera time offset)
-    for (int end = range.x + max_last; end > range.x; end -= KB) {
+    // The two warps of a tile run independently: each stages the entries its rays reach
+    // (from its own deepest entry up), forms its sums and flushes them, with no barrier.
+    for (int end = range.x + wl; end > range.x; end -= KB) {
         const int cnt = min(KB, end - range.x);
-        __syncthreads();
-        if ((int)threadIdx.x < KB)
-            stage_entry<KB>(s.u.b.st, in, tc.s, end - 1 - (int)threadIdx.x, threadIdx.x, (int)threadIdx.x < cnt, box);
-        __syncthreads();
+        __syncwarp();
+        if (lane < KB) stage_entry<KB>(sw, in, tc.s, end - 1 - lane, lane, lane < cnt, box);
+        __syncwarp();
         for (int k0 = 0; k0 < cnt; k0 += kG) {
             const int n = min(kG, cnt - k0);
             if (end - 1 - (k0 + n - 1) - range.x >= wl) continue;   // every entry deeper than this warp's rays reach
@@ -224,8 +223,8 @@ __global__ void __launch_bounds__(64, 7)
                     uint2* wb = reinterpret_cast<uint2*>(pw + (e + 8) * kRowW + 2 * lane);
                     const int k = k0 + e;
                     const int idx = end - 1 - k - range.x;
-                    const bool act = e < n && idx < wl && s.u.b.st.live[k];
-                    const float4 g0 = s.u.b.st.g0[k], g1 = s.u.b.st.g1[k];
+                    const bool act = e < n && idx < wl && sw.live[k];
+                    const float4 g0 = sw.g0[k], g1 = sw.g1[k];
                     float2 dx2[2], dy2[2], G2[2], a2[2];
                     bool on[PX], cl[PX];
 #pragma unroll
@@ -345,24 +344,12 @@ __global__ void __launch_bounds__(64, 7)
             a0[16 + g] = d[0][2];
             a1[16 + g] = d[0][3];
         }
-        __syncthreads();
-        // one set of vector atomics per (tile, Gaussian): flush this batch's sums
-        if ((int)threadIdx.x < cnt) {
-            const int slot = threadIdx.x;
-            float* a_row = s.u.b.acc[0][slot];
-            float* o_row = s.u.b.acc[1][slot];
-#pragma unroll
-            for (int q = 0; q < kRow; q += 4) {   // fold the second warp's slice into the first
-                float4 x = *reinterpret_cast<float4*>(a_row + q);
-                const float4 y = *reinterpret_cast<float4*>(o_row + q);
-                x.x += y.x;
-                x.y += y.y;
-                x.z += y.z;
-                x.w += y.w;
-                *reinterpret_cast<float4*>(a_row + q) = x;
-                *reinterpret_cast<float4*>(o_row + q) = make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-            const uint32_t id = s.u.b.st.id[slot];
+        __syncwarp();
+        // one set of vector atomics per (warp, Gaussian): flush this batch's sums
+        if (lane < cnt) {
+            const int slot = lane;
+            float* a_row = s.u.b.acc[w][slot];
+            const uint32_t id = sw.id[slot];
             const float4 s0 = *reinterpret_cast<float4*>(a_row);
             const float4 s1 = *reinterpret_cast<float4*>(a_row + 4);
             if (s0.x != 0.f || s0.y != 0.f || s0.z != 0.f || s0.w != 0.f || s1.x != 0.f || s1.y != 0.f ||
