@@ -584,14 +584,20 @@ def run_ours(args):
     peaks = measured_peaks()
     clocks = clk.summary()
     # DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum + write.sum of the
-    # six-camera launch, from the ncu launch list of this benchmark's training step; the
-    # summary and its command are in profiles/driving_frame_launches.md)
-    traffic = {"raster_camera_bwd": 923.13e6 + 0.97e6} if args.workload == "driving" else {}
+    # six-camera k_raster_bwd_cam16 launch, from the ncu launch list of this benchmark's
+    # training step; the summary and its command are in profiles/driving_frame_launches.md)
+    traffic = {"raster_camera_bwd": 923.17e6 + 0.97e6} if args.workload == "driving" else {}
     roofline = frame_roofline(kp, peaks, traffic)
+    if roofline["kernel"] == "raster_camera_bwd":
+        roofline["note"] = ("k_raster_bwd_cam16: the two channel contractions (f.g and w g) run as split-BF16 "
+                            "mma.sync products with FP32 accumulation, the per-ray chain on the FP32 pipes; "
+                            "achieved counts the kernel's algorithmic FP32 flops")
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "precision": ("FP32 arithmetic; the 16-channel camera backward's channel contractions from split-BF16 "
+                          "operands (hi + lo) with FP32 accumulation, about 2^-16 relative per term"),
             "config": dict(desc, l2="explicit 258 MB flush between timed steps (per-step CUDA events)",
                            step="the step's launches captured once in a CUDA graph, one replay per step",
                            intersections=kp["intersections"], evaluated_pairs=kp["evaluated"],
