@@ -260,27 +260,24 @@ __global__ void __launch_bounds__(64, 7)
                         // clamped alpha (o' G > 0.999) passes no gradient to o' and the exponent
                         const float2 dg = make_float2((on[q0] && !cl[q0]) ? dal.x : 0.f, (on[q1] && !cl[q1]) ? dal.y : 0.f);
                         const float2 Pn = __fmul2_rn(dg, aq);   // -dL/dsigma
-                        const float2 Kx = __ffma2_rn(make_float2(g1.x, g1.x), dx2[qp],
-                                                     __fmul2_rn(make_float2(g1.y, g1.y), dy2[qp]));
-                        const float2 Ky = __ffma2_rn(make_float2(g1.y, g1.y), dx2[qp],
-                                                     __fmul2_rn(make_float2(g1.z, g1.z), dy2[qp]));
-                        const float2 nddx = __fmul2_rn(Pn, Kx), nddy = __fmul2_rn(Pn, Ky);   // -ddx, -ddy
+                        // the conic is the entry's own: -ddx = Pn (a dx + b dy), -ddy = Pn (b dx + c dy)
+                        // are formed from the sums of Pn dx and Pn dy when the entry is flushed
                         const float2 hx = __fmul2_rn(Pn, dx2[qp]), hy = __fmul2_rn(Pn, dy2[qp]);
                         const float2 tq = rt[qp];
                         if (qp == 0) {
-                            acc[0] = nddx;
-                            acc[1] = nddy;
-                            acc[2] = __fmul2_rn(nddx, tq);
-                            acc[3] = __fmul2_rn(nddy, tq);
+                            acc[0] = hx;
+                            acc[1] = hy;
+                            acc[2] = __fmul2_rn(hx, tq);
+                            acc[3] = __fmul2_rn(hy, tq);
                             acc[4] = __fmul2_rn(hx, dx2[qp]);
                             acc[5] = __fmul2_rn(hx, dy2[qp]);
                             acc[6] = __fmul2_rn(hy, dy2[qp]);
                             acc[7] = __fmul2_rn(dg, Gq);
                         } else {
-                            acc[0] = __fadd2_rn(acc[0], nddx);
-                            acc[1] = __fadd2_rn(acc[1], nddy);
-                            acc[2] = __ffma2_rn(nddx, tq, acc[2]);
-                            acc[3] = __ffma2_rn(nddy, tq, acc[3]);
+                            acc[0] = __fadd2_rn(acc[0], hx);
+                            acc[1] = __fadd2_rn(acc[1], hy);
+                            acc[2] = __ffma2_rn(hx, tq, acc[2]);
+                            acc[3] = __ffma2_rn(hy, tq, acc[3]);
                             acc[4] = __ffma2_rn(hx, dx2[qp], acc[4]);
                             acc[5] = __ffma2_rn(hx, dy2[qp], acc[5]);
                             acc[6] = __ffma2_rn(hy, dy2[qp], acc[6]);
@@ -292,19 +289,15 @@ __global__ void __launch_bounds__(64, 7)
                     }
                     *wa = make_uint2(whi[0], whi[1]);   // this lane's 4 weights: high parts, then residuals
                     *wb = make_uint2(wlo[0], wlo[1]);
-                    // (-ddx, -ddy, -ddx t, -ddy t, dsig dx^2 / 2, dsig dx dy, dsig dy^2 / 2, dg G) summed
-                    // over this thread's rays; dsig = -Pn
+                    // (Pn dx, Pn dy, Pn dx t, Pn dy t, Pn dx^2, Pn dx dy, Pn dy^2, dg G) summed over
+                    // this thread's rays (Pn = -dL/dsigma); the flush turns them into gradients
                     float v[8];
-                    v[0] = acc[0].x + acc[0].y;
-                    v[1] = acc[1].x + acc[1].y;
-                    v[2] = acc[2].x + acc[2].y;
-                    v[3] = acc[3].x + acc[3].y;
-                    v[4] = -0.5f * (acc[4].x + acc[4].y);
-                    v[5] = -(acc[5].x + acc[5].y);
-                    v[6] = -0.5f * (acc[6].x + acc[6].y);
-                    v[7] = acc[7].x + acc[7].y;
-                    // every pixel time carries the camera time offset; the mean moves by v t
-                    if (gr.dsensor) dtime += v[0] * g0.z + v[1] * g0.w;
+#pragma unroll
+                    for (int j = 0; j < 8; j++) v[j] = acc[j].x + acc[j].y;
+                    // every pixel time carries the camera time offset; the mean moves by v t:
+                    // dL/dt += -ddx vx - ddy vy = v0 (a vx + b vy) + v1 (b vx + c vy)
+                    if (gr.dsensor)
+                        dtime += v[0] * (g1.x * g0.z + g1.y * g0.w) + v[1] * (g1.y * g0.z + g1.z * g0.w);
 #pragma unroll
                     for (int j = 0; j < 8; j++) vv[8 * u + j] = v[j];
                 }
@@ -350,8 +343,14 @@ __global__ void __launch_bounds__(64, 7)
             const int slot = lane;
             float* a_row = s.u.b.acc[w][slot];
             const uint32_t id = sw.id[slot];
-            const float4 s0 = *reinterpret_cast<float4*>(a_row);
-            const float4 s1 = *reinterpret_cast<float4*>(a_row + 4);
+            const float4 q0 = *reinterpret_cast<float4*>(a_row);
+            const float4 q1 = *reinterpret_cast<float4*>(a_row + 4);
+            const float4 cn = sw.g1[slot];   // the entry's conic (a, b, c)
+            // gradients of (mean, mean velocity) and (conic, opacity) record entries: -ddx, -ddy,
+            // -ddx t, -ddy t, dsig dx^2 / 2, dsig dx dy, dsig dy^2 / 2, dg G (dsig = -Pn)
+            const float4 s0 = make_float4(cn.x * q0.x + cn.y * q0.y, cn.y * q0.x + cn.z * q0.y,
+                                          cn.x * q0.z + cn.y * q0.w, cn.y * q0.z + cn.z * q0.w);
+            const float4 s1 = make_float4(-0.5f * q1.x, -q1.y, -0.5f * q1.z, q1.w);
             if (s0.x != 0.f || s0.y != 0.f || s0.z != 0.f || s0.w != 0.f || s1.x != 0.f || s1.y != 0.f ||
                 s1.z != 0.f || s1.w != 0.f) {
                 atomicAdd(gp0 + id, s0);
