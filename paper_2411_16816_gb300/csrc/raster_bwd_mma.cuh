@@ -51,58 +51,83 @@ struct Smem {
 // the eight rows of every ldmatrix, in either operand layout, fall in distinct banks.
 __device__ __forceinline__ int gchunk(int rho, int cb) { return (2 * rho + cb) ^ ((rho >> 2) & 7); }
 
-// Stages list entry j at `slot`: record, id, tile-liveness, split features; a slot past
-// the batch gets zero features and is marked dead.
+// The 16 features of Gaussian `id` (zero past the channel count).
+__device__ __forceinline__ void load_feat16(const RasterIn& in, uint32_t id, float (&f)[16]) {
+    const int C = in.C;
+    const float* fp = in.feat + (int64_t)id * C;
+    if ((C & 3) == 0) {
+#pragma unroll
+        for (int c = 0; c < 16; c += 4) {
+            const float4 v = c < C ? *reinterpret_cast<const float4*>(fp + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            f[c] = v.x;
+            f[c + 1] = v.y;
+            f[c + 2] = v.z;
+            f[c + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < 16; c++) f[c] = c < C ? fp[c] : 0.f;
+    }
+}
+
+// Stages a live list entry (its Gaussian `id`, records g0 g1, features f, list position
+// `pos`) at its packed slot: the records, id, position and split features.
+template <int KB>
+__device__ __forceinline__ void stage_live(Stage<16, KB, false>& st, uint32_t id, float4 g0, float4 g1,
+                                           const float (&f)[16], int slot, int pos) {
+    st.id[slot] = id;
+    st.g0[slot] = g0;
+    st.g1[slot] = g1;
+    st.live[slot] = pos;   // the backward keeps list positions here
+    uint32_t hi[8], lo[8];
+#pragma unroll
+    for (int p = 0; p < 8; p++) split_pair(f[2 * p], f[2 * p + 1], hi[p], lo[p]);
+    uint4* fh = reinterpret_cast<uint4*>(reinterpret_cast<bf16*>(st.f) + slot * 16);
+    uint4* fl = reinterpret_cast<uint4*>(reinterpret_cast<bf16*>(st.f) + KB * 16 + slot * 16);
+    fh[0] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    fh[1] = make_uint4(hi[4], hi[5], hi[6], hi[7]);
+    fl[0] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+    fl[1] = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+}
+
+// Clears a slot past the batch's live entries: zero records and features, so that every
+// term of the chain is finite and zero for it.
+template <int KB>
+__device__ __forceinline__ void stage_empty(Stage<16, KB, false>& st, int slot) {
+    st.g0[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+    st.g1[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+    st.live[slot] = 0;
+    uint4* fh = reinterpret_cast<uint4*>(reinterpret_cast<bf16*>(st.f) + slot * 16);
+    uint4* fl = reinterpret_cast<uint4*>(reinterpret_cast<bf16*>(st.f) + KB * 16 + slot * 16);
+    fh[0] = fh[1] = fl[0] = fl[1] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Stages list entry j at `slot` without packing (lists of culled cameras, where almost
+// every entry is live): records, id, live flag, split features; a slot past the batch
+// gets zero records and features and is marked dead.
 template <int KB>
 __device__ __forceinline__ void stage_entry(Stage<16, KB, false>& st, const RasterIn& in, int s, int64_t j, int slot,
                                             bool valid, const TileBox& box) {
-    bf16* fh = reinterpret_cast<bf16*>(st.f) + slot * 16;
-    bf16* fl = reinterpret_cast<bf16*>(st.f) + KB * 16 + slot * 16;
-    uint32_t hi[8], lo[8];
-    if (valid) {
-        const uint32_t id = load_id(in, j);
-        st.id[slot] = id;
-        const float4 g0 = in.rec[rec_index(s, 0, in.n, id)];
-        const float4 g1 = in.rec[rec_index(s, 1, in.n, id)];
-        st.g0[slot] = g0;
-        st.g1[slot] = g1;
-        st.live[slot] = tile_live(g0, g1, box);
-        const int C = in.C;
-        const float* fp = in.feat + (int64_t)id * C;
-        float f[16];
-        if ((C & 3) == 0) {
-#pragma unroll
-            for (int c = 0; c < 16; c += 4) {
-                const float4 v = c < C ? *reinterpret_cast<const float4*>(fp + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-                f[c] = v.x;
-                f[c + 1] = v.y;
-                f[c + 2] = v.z;
-                f[c + 3] = v.w;
-            }
-        } else {
-#pragma unroll
-            for (int c = 0; c < 16; c++) f[c] = c < C ? fp[c] : 0.f;
-        }
-#pragma unroll
-        for (int p = 0; p < 8; p++) split_pair(f[2 * p], f[2 * p + 1], hi[p], lo[p]);
-    } else {   // zero records: every term of the chain is finite and zero for this slot
-        st.live[slot] = 0;
-        st.g0[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
-        st.g1[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int p = 0; p < 8; p++) hi[p] = lo[p] = 0u;
+    if (!valid) {
+        stage_empty<KB>(st, slot);
+        return;
     }
-    reinterpret_cast<uint4*>(fh)[0] = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-    reinterpret_cast<uint4*>(fh)[1] = make_uint4(hi[4], hi[5], hi[6], hi[7]);
-    reinterpret_cast<uint4*>(fl)[0] = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-    reinterpret_cast<uint4*>(fl)[1] = make_uint4(lo[4], lo[5], lo[6], lo[7]);
+    const uint32_t id = load_id(in, j);
+    const float4 g0 = in.rec[rec_index(s, 0, in.n, id)];
+    const float4 g1 = in.rec[rec_index(s, 1, in.n, id)];
+    float f[16];
+    load_feat16(in, id, f);
+    stage_live<KB>(st, id, g0, g1, f, slot, 0);
+    st.live[slot] = tile_live(g0, g1, box);
 }
 
 }  // namespace cam16
 
 // One block per 256-ray camera tile, 2 warps, 4 rays per thread (pixel threadIdx.x + 64 q);
-// KB staged entries per batch and warp.
-template <int TW, int TH, bool RECOMPUTE, int KB>
+// KB list positions per batch and warp.  COMPACT packs the live entries of each batch (for
+// lists that hold entries dead in their tile); otherwise every position is staged with a
+// live flag.
+template <int TW, int TH, bool RECOMPUTE, int KB, bool COMPACT>
 __global__ void __launch_bounds__(64, 7)
     k_raster_bwd_cam16(const __grid_constant__ Frame fr, RasterIn in, RasterGrad gr) {
     using namespace cam16;
@@ -181,12 +206,39 @@ __global__ void __launch_bounds__(64, 7)
     // (from its own deepest entry up), forms its sums and flushes them, with no barrier.
     for (int end = range.x + wl; end > range.x; end -= KB) {
         const int cnt = min(KB, end - range.x);
+        // the batch's list positions [end - cnt, end), deepest first: only the entries that can
+        // reach alpha >= 1/255 somewhere in the tile are staged, packed in that order, each
+        // with its list position
         __syncwarp();
-        if (lane < KB) stage_entry<KB>(sw, in, tc.s, end - 1 - lane, lane, lane < cnt, box);
+        int n_live = cnt;   // staged slots
+        if constexpr (COMPACT) {
+            const int j = end - 1 - lane;
+            uint32_t id = 0;
+            float4 g0 = make_float4(0.f, 0.f, 0.f, 0.f), g1 = g0;
+            bool lv = false;
+            if (lane < cnt) {
+                id = load_id(in, j);
+                g0 = in.rec[rec_index(tc.s, 0, in.n, id)];
+                g1 = in.rec[rec_index(tc.s, 1, in.n, id)];
+                lv = tile_live(g0, g1, box);
+            }
+            const uint32_t bal = __ballot_sync(0xffffffffu, lv);
+            n_live = __popc(bal);
+            if (lv) {
+                float f[16];
+                load_feat16(in, id, f);
+                stage_live<KB>(sw, id, g0, g1, f, __popc(bal & ((1u << lane) - 1u)), j - range.x);
+            }
+            if (lane >= n_live && lane < KB) stage_empty<KB>(sw, lane);
+        } else {
+            if (lane < KB) stage_entry<KB>(sw, in, tc.s, end - 1 - lane, lane, lane < cnt, box);
+        }
         __syncwarp();
-        for (int k0 = 0; k0 < cnt; k0 += kG) {
-            const int n = min(kG, cnt - k0);
-            if (end - 1 - (k0 + n - 1) - range.x >= wl) continue;   // every entry deeper than this warp's rays reach
+        for (int k0 = 0; k0 < n_live; k0 += kG) {
+            const int n = min(kG, n_live - k0);
+            // the group's shallowest entry is its last
+            const int shallow = COMPACT ? sw.live[k0 + n - 1] : end - 1 - (k0 + n - 1) - range.x;
+            if (shallow >= wl) continue;   // every entry deeper than this warp's rays reach
             // ---- P = F G^T: rows of the MMA are rays, columns the group's entries ----
             __syncwarp();
             uint32_t bF[4];   // B fragments: F high (k 0-7, 8-15), F residual (k 0-7, 8-15)
@@ -210,11 +262,18 @@ __global__ void __launch_bounds__(64, 7)
             }
             __syncwarp();
             // ---- the rays' chains, entry by entry, back to front ----
-            // Without branches: an entry past the batch, deeper than every ray of the warp,
-            // or one no pixel of the tile can blend takes alpha = 0 for every ray, which
-            // leaves T and S bit for bit unchanged and writes zero weights and sums.
+            // Without branches: an entry past the group's staged entries, deeper than every
+            // ray of the warp or dead in the tile takes alpha = 0 for every ray, which leaves T
+            // and S bit for bit unchanged and writes zero weights and sums.
 #pragma unroll 1
             for (int e2 = 0; e2 < kG; e2 += 2) {   // two entries, then their warp sums
+                if (e2 >= n) {   // past the group's live entries (warp-uniform): zero weights
+                    *reinterpret_cast<uint2*>(pw + e2 * kRowW + 2 * lane) = make_uint2(0u, 0u);
+                    *reinterpret_cast<uint2*>(pw + (e2 + 8) * kRowW + 2 * lane) = make_uint2(0u, 0u);
+                    *reinterpret_cast<uint2*>(pw + (e2 + 1) * kRowW + 2 * lane) = make_uint2(0u, 0u);
+                    *reinterpret_cast<uint2*>(pw + (e2 + 9) * kRowW + 2 * lane) = make_uint2(0u, 0u);
+                    continue;
+                }
                 float vv[16];                        // the two entries' 8 geometric values
 #pragma unroll
                 for (int u = 0; u < 2; u++) {
@@ -222,8 +281,8 @@ __global__ void __launch_bounds__(64, 7)
                     uint2* wa = reinterpret_cast<uint2*>(pw + e * kRowW + 2 * lane);
                     uint2* wb = reinterpret_cast<uint2*>(pw + (e + 8) * kRowW + 2 * lane);
                     const int k = k0 + e;
-                    const int idx = end - 1 - k - range.x;
-                    const bool act = e < n && idx < wl && sw.live[k];
+                    const int idx = COMPACT ? sw.live[k] : end - 1 - k - range.x;   // list position
+                    const bool act = e < n && idx < wl && (COMPACT || sw.live[k]);
                     const float4 g0 = sw.g0[k], g1 = sw.g1[k];
                     float2 dx2[2], dy2[2], G2[2], a2[2];
                     bool on[PX], cl[PX];
@@ -339,7 +398,7 @@ __global__ void __launch_bounds__(64, 7)
         }
         __syncwarp();
         // one set of vector atomics per (warp, Gaussian): flush this batch's sums
-        if (lane < cnt) {
+        if (lane < n_live) {
             const int slot = lane;
             float* a_row = s.u.b.acc[w][slot];
             const uint32_t id = sw.id[slot];

@@ -1273,16 +1273,16 @@ static void launch_bwd_t(const Frame& fr, int blocks, const RasterIn& in, const 
     constexpr int NT = TW * TH / RaysPerThread<CM, true, LIDAR, TW * TH>::value;
     if constexpr (CM == 16 && !LIDAR && TW * TH == 256) {   // 16 channels on 256-ray tiles: tensor cores
         static_assert(NT == 64, "two warps of 4 rays per thread");
-        constexpr int KB = 16;   // staged entries per batch: 7 blocks of 2 warps per SM
-        if (recompute) {
-            auto k = k_raster_bwd_cam16<TW, TH, true, KB>;
-            set_smem(k, sizeof(cam16::Smem<KB, true>));
-            k<<<blocks, NT, sizeof(cam16::Smem<KB, true>), st>>>(fr, in, g);
-        } else {
-            auto k = k_raster_bwd_cam16<TW, TH, false, KB>;
-            set_smem(k, sizeof(cam16::Smem<KB, false>));
-            k<<<blocks, NT, sizeof(cam16::Smem<KB, false>), st>>>(fr, in, g);
-        }
+        constexpr int KB = 16;   // list positions per batch: 7 blocks of 2 warps per SM
+        // lists of cameras without the tile cull hold entries dead in their tile: pack the
+        // live ones at staging
+        bool culled = true;
+        for (int c = 0; c < fr.n_cams; c++) culled = culled && (fr.s[fr.cam_sensors[c]].support & 4);
+        auto k = recompute ? (culled ? k_raster_bwd_cam16<TW, TH, true, KB, false> : k_raster_bwd_cam16<TW, TH, true, KB, true>)
+                           : (culled ? k_raster_bwd_cam16<TW, TH, false, KB, false> : k_raster_bwd_cam16<TW, TH, false, KB, true>);
+        const size_t bytes = recompute ? sizeof(cam16::Smem<KB, true>) : sizeof(cam16::Smem<KB, false>);
+        set_smem(k, bytes);
+        k<<<blocks, NT, bytes, st>>>(fr, in, g);
         return;
     }
     using LY = BwdLayout<CM, LIDAR>;
