@@ -253,7 +253,8 @@ __device__ __forceinline__ bool tile_live(const float4 g0, const float4 g1, cons
     return !(m > thr);
 }
 
-template <int CM, int B, bool LIDAR>
+// HALF stages the conic as (a/2, b, c/2, o') for the forward's evaluation.
+template <int CM, int B, bool LIDAR, bool HALF = false>
 __device__ __forceinline__ void stage_load(Stage<CM, B, LIDAR>& sm, const RasterIn& in, int s, int64_t j, int slot,
                                            const TileBox& box) {
     const uint32_t id = load_id(in, j);
@@ -261,7 +262,7 @@ __device__ __forceinline__ void stage_load(Stage<CM, B, LIDAR>& sm, const Raster
     const float4 g0 = in.rec[rec_index(s, 0, in.n, id)];
     const float4 g1 = in.rec[rec_index(s, 1, in.n, id)];
     sm.g0[slot] = g0;
-    sm.g1[slot] = g1;
+    sm.g1[slot] = HALF ? make_float4(__fmul_rn(0.5f, g1.x), g1.y, __fmul_rn(0.5f, g1.z), g1.w) : g1;
     if (!LIDAR) sm.live[slot] = tile_live(g0, g1, box);
     if (LIDAR) {
         const float4 r2 = in.rec[rec_index(s, 2, in.n, id)];
@@ -305,14 +306,17 @@ constexpr float kNegLog2e = -1.4426950408889634f;
 // then agree on every decision):
 //   d = p - (mean + v t),  sigma = d_x (a/2 d_x + b d_y) + (c/2 d_y) d_y,
 //   alpha = min(o' exp(-sigma), 0.999), blended if sigma >= 0 and alpha >= 1/255.
-template <bool LIDAR>
+// HALF: the staged record already holds a/2 and c/2 (the halving is exact, so both forms
+// give the same bits).
+template <bool LIDAR, bool HALF = false>
 __device__ __forceinline__ bool eval_alpha(const float4 g0, const float4 g1, const RayCtx& r, float& dx, float& dy,
                                            float& G, float& alpha, bool& clamped) {
     dx = __fsub_rn(r.pa, __fmaf_rn(g0.z, r.t, g0.x));
     dy = __fsub_rn(r.pb, __fmaf_rn(g0.w, r.t, g0.y));
     if (LIDAR) dx = wrap_pi(dx);
-    const float u = __fmaf_rn(__fmul_rn(0.5f, g1.x), dx, __fmul_rn(g1.y, dy));
-    const float sig = __fmaf_rn(dx, u, __fmul_rn(__fmul_rn(__fmul_rn(0.5f, g1.z), dy), dy));
+    const float ha = HALF ? g1.x : __fmul_rn(0.5f, g1.x), hc = HALF ? g1.z : __fmul_rn(0.5f, g1.z);
+    const float u = __fmaf_rn(ha, dx, __fmul_rn(g1.y, dy));
+    const float sig = __fmaf_rn(dx, u, __fmul_rn(__fmul_rn(hc, dy), dy));
     G = exp2_approx(__fmul_rn(sig, kNegLog2e));
     const float a = __fmul_rn(g1.w, G);
     clamped = a > kAlphaMax;
@@ -322,7 +326,7 @@ __device__ __forceinline__ bool eval_alpha(const float4 g0, const float4 g1, con
 
 // Two rays of one thread against one staged Gaussian in packed FP32 pairs; lane q equals
 // eval_alpha for ray q bit for bit.  pa, pb, t hold the two rays' coordinates and times.
-template <bool LIDAR>
+template <bool LIDAR, bool HALF = false>
 __device__ __forceinline__ void eval_alpha2(const float4 g0, const float4 g1, float2 pa, float2 pb, float2 t,
                                             float2& sig, float2& alpha, float2& dx, float2& dy, float2& G,
                                             float2& a) {
@@ -330,7 +334,7 @@ __device__ __forceinline__ void eval_alpha2(const float4 g0, const float4 g1, fl
     dx = __ffma2_rn(__ffma2_rn(make_float2(g0.z, g0.z), t, make_float2(g0.x, g0.x)), m1, pa);
     dy = __ffma2_rn(__ffma2_rn(make_float2(g0.w, g0.w), t, make_float2(g0.y, g0.y)), m1, pb);
     if (LIDAR) dx = make_float2(wrap_pi(dx.x), wrap_pi(dx.y));
-    const float ha = __fmul_rn(0.5f, g1.x), hc = __fmul_rn(0.5f, g1.z);
+    const float ha = HALF ? g1.x : __fmul_rn(0.5f, g1.x), hc = HALF ? g1.z : __fmul_rn(0.5f, g1.z);
     const float2 u = __ffma2_rn(make_float2(ha, ha), dx, __fmul2_rn(make_float2(g1.y, g1.y), dy));
     sig = __ffma2_rn(dx, u, __fmul2_rn(__fmul2_rn(make_float2(hc, hc), dy), dy));
     const float2 e = __fmul2_rn(sig, make_float2(kNegLog2e, kNegLog2e));
@@ -410,7 +414,7 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
             }
             if (lv) {
                 sm.g0[slot] = g0;
-                sm.g1[slot] = g1;
+                sm.g1[slot] = make_float4(__fmul_rn(0.5f, g1.x), g1.y, __fmul_rn(0.5f, g1.z), g1.w);   // half conic
                 sm.id[slot] = id;
                 sm.live[slot] = j - range.x;
                 const int C = in.C;
@@ -437,7 +441,7 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
             }
         } else {
             if (start + (int)threadIdx.x < range.y) {
-                stage_load<CM, B, LIDAR>(sm, in, tc.s, start + threadIdx.x, threadIdx.x, box);
+                stage_load<CM, B, LIDAR, true>(sm, in, tc.s, start + threadIdx.x, threadIdx.x, box);
             } else {   // past the list: an entry no ray blends (zero opacity, zero features)
                 sm.g0[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
                 sm.g1[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -464,11 +468,11 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
 #pragma unroll
                         for (int qp = 0; qp < PX / 2; qp++) {
                             float2 sig2, a2, dx2, dy2, G2, au2;
-                            eval_alpha2<LIDAR>(g0, g1, rpa[qp], rpb[qp], rt[qp], sig2, a2, dx2, dy2, G2, au2);
+                            eval_alpha2<LIDAR, true>(g0, g1, rpa[qp], rpb[qp], rt[qp], sig2, a2, dx2, dy2, G2, au2);
                             const float2 T2 = make_float2(st[2 * qp].T, st[2 * qp + 1].T);
-                            const float2 Tn2 =
-                                __fmul2_rn(T2, __ffma2_rn(a2, make_float2(-1.f, -1.f), make_float2(1.f, 1.f)));
-                            const float2 w2 = __fmul2_rn(a2, T2);
+                            const float2 w2 = __fmul2_rn(a2, T2);    // blend weight alpha T
+                            // T (1 - alpha) as T - alpha T (one rounding, as __fsub_rn lane by lane)
+                            const float2 Tn2 = __ffma2_rn(w2, make_float2(-1.f, -1.f), T2);
                             av[2 * qp] = a2.x;
                             av[2 * qp + 1] = a2.y;
                             Tnv[2 * qp] = Tn2.x;
@@ -483,9 +487,9 @@ __device__ __forceinline__ int forward_tile(Stage<CM, TW * TH / PX, LIDAR>& sm, 
                         for (int q = 0; q < PX; q++) {
                             float dx, dy, G;
                             bool cl;
-                            ok[q] = eval_alpha<LIDAR>(g0, g1, r[q], dx, dy, G, av[q], cl);
-                            Tnv[q] = st[q].T * (1.f - av[q]);
-                            wv[q] = av[q] * st[q].T;
+                            ok[q] = eval_alpha<LIDAR, true>(g0, g1, r[q], dx, dy, G, av[q], cl);
+                            wv[q] = __fmul_rn(av[q], st[q].T);
+                            Tnv[q] = __fsub_rn(st[q].T, wv[q]);
                         }
                     }
 #pragma unroll
