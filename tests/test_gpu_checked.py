@@ -16,10 +16,11 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2411_16816_gb300 import _lib as L
 from paper_2411_16816_gb300 import scenes
 from paper_2411_16816_gb300.render import Frame, gaussians_to_device
-from tests.test_gpu_parity import _dynamic_tiny, _point_cloud
+from tests.test_gpu_parity import _cull_cameras, _dynamic_tiny, _point_cloud, _small_driving
 
 pytestmark = pytest.mark.gpu
 DEV = torch.device("cuda:0")
@@ -145,3 +146,74 @@ def test_checked_build_reports_a_ray_index_past_the_rays():
         st = lib.splat_sync_status(_stream())
         msg = lib.splat_last_error().decode()
         assert st == L.SPLAT_ERR_BOUNDS and "(site 4)" in msg, (st, msg)
+
+
+def _driving16(cull):
+    """Two 320 x 180 rolling-shutter cameras and the lidar, 16 channels: the camera backward
+    of the 16-channel bucket on 256-ray tiles (tensor cores); with the camera tile cull its
+    unpacked staging, without it the packing one."""
+    g, sensors = _small_driving(n=20000, w=320, h=180, box=30)
+    return g, (_cull_cameras(sensors) if cull else sensors)
+
+
+def _run16(checked, g, sensors):
+    ctx = L.checked_build() if checked else contextlib.nullcontext()
+    with ctx:
+        lib = L.active()
+        assert lib.splat_build_flags() == int(checked)
+        gd = gaussians_to_device(g, DEV)
+        fr = Frame(sensors, len(g["opacities"]), g["features"].shape[1], DEV)
+        out = fr.forward(gd)
+        grads = {k: _seeded_like(out[k], i) for i, k in enumerate(("cam_feat", "lid_feat", "lid_range_exp"))}
+        pg = fr.backward(gd, out, grads)
+        res = {"fwd_" + k: v.clone() for k, v in out.items() if v is not None}
+        res.update({"bwd_" + k: v.clone() for k, v in pg.items() if v is not None})
+        st = lib.splat_sync_status(_stream())
+    return res, st
+
+
+@pytest.mark.parametrize("cull", [False, True])
+def test_checked_build_gives_the_normal_builds_results_with_16_channels(cull):
+    g, sensors = _driving16(cull)
+    a, sa = _run16(False, g, sensors)
+    b, sb = _run16(True, g, sensors)
+    assert sa == L.SPLAT_OK and sb == L.SPLAT_OK
+    assert a.keys() == b.keys()
+    for k in a:
+        if k.startswith("fwd_"):
+            assert torch.equal(a[k], b[k]), k
+        else:
+            # atomic sums in an arbitrary order over many more (tile, Gaussian) terms than the
+            # tiny frame's: the quaternion gradients differ by up to about 1.3e-5 of their
+            # largest element between two builds
+            scale = float(a[k].abs().max()) + 1e-30
+            assert float((a[k] - b[k]).abs().max()) <= 1e-4 * scale, k
+
+
+@pytest.mark.parametrize("cull", [False, True])
+def test_checked_build_reports_a_gaussian_index_past_the_gaussians_in_the_16_channel_backward(cull):
+    with L.checked_build():
+        lib = L.active()
+        assert lib.splat_build_flags() == 1   # the malformed list below goes to the checked build only
+        g, sensors = _driving16(cull)
+        gd = gaussians_to_device(g, DEV)
+        fr = Frame(sensors, len(g["opacities"]), g["features"].shape[1], DEV)
+        out = fr.forward(gd)
+        grads = {k: _seeded_like(out[k], i) for i, k in enumerate(("cam_feat", "lid_feat", "lid_range_exp"))}
+        assert lib.splat_sync_status(_stream()) == L.SPLAT_OK
+        # the longest list of the first camera (its tiles come first)
+        ranges = fr.ranges.clone()
+        n_cam0 = oracle.n_tiles_of(sensors[0])
+        lens = (ranges[:n_cam0, 1] - ranges[:n_cam0, 0]).cpu().numpy()
+        t = int(np.argmax(lens))
+        assert lens[t] > 0
+        j = int(ranges[t, 0])
+        saved = fr.isect_ids[j].clone()
+        fr.isect_ids[j] = fr.n + 7
+        fr.backward(gd, out, grads)
+        st = lib.splat_sync_status(_stream())
+        msg = lib.splat_last_error().decode()
+        assert st == L.SPLAT_ERR_BOUNDS and "(site 2)" in msg, (st, msg)
+        fr.isect_ids[j] = saved
+        fr.backward(gd, out, grads)
+        assert lib.splat_sync_status(_stream()) == L.SPLAT_OK
