@@ -256,9 +256,10 @@ def launches_per_step(fr, n_l1):
     passes = max(1, (bits + 7) // 8)
     scan = 3
     radix_pass = 1 + scan + 1
-    # compaction scan, 4 depth passes, offsets scan, emit (which also writes the first tile
-    # pass's histogram), tile passes, tile ranges
-    bin_sort = scan + 4 * radix_pass + scan + 1 + passes * radix_pass - 1 + 1
+    # compaction scan, 4 depth passes, row-item scan + rows, slot scan + slot totals, emit
+    # (which also writes the first tile pass's histogram), tile passes, tile ranges; on the
+    # driving frame 42 launches, as the ncu launch list of its step shows
+    bin_sort = scan + 4 * radix_pass + (scan + 1) + (scan + 1) + 1 + passes * radix_pass - 1 + 1
     raster = (1 if fr.cam_idx else 0) + (1 if fr.lid_idx else 0)
     return 1 + bin_sort + raster + n_l1 + raster + 1
 
