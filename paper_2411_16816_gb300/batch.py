@@ -131,12 +131,15 @@ class BatchRenderer:
 
     def launches(self) -> int:
         """Kernels one batch launches (stamps, projections, sorts, the persistent launch)."""
-        n = 1
+        n = 1   # the start stamp
         for fr, _, _ in self.groups:
             bits = max(1, int(np.ceil(np.log2(max(fr.total_tiles, 2)))))
             passes = max(1, (bits + 7) // 8)
-            n += 1 + (3 + 4 * 5 + 3 + 1 + passes * 5 + 1)
-        return n + 2
+            # projection; binning: compaction scan, 4 depth passes (histogram, 3-launch
+            # scan, scatter), row-item scan + rows, slot scan + slot totals, emission (with
+            # the first tile pass's histogram), the tile passes, tile ranges
+            n += 1 + (3 + 4 * 5 + 4 + 4 + 1 + passes * 5 - 1 + 1)
+        return n + 2    # the persistent raster launch and its stamp
 
     def run(self):
         st = _stream()
