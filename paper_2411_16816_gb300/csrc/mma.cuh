@@ -21,11 +21,6 @@ __device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint3
     lo = bits2(__floats2bfloat162_rn(a - hf.x, b - hf.y));
 }
 
-__device__ __forceinline__ void split_one(float a, bf16& hi, bf16& lo) {
-    hi = __float2bfloat16_rn(a);
-    lo = __float2bfloat16_rn(a - __bfloat162float(hi));
-}
-
 // d += A (16 x 16, row) * B (16 x 8, col): BF16 operands, FP32 accumulators.  Fragments:
 // g = lane / 4, t = lane % 4; A regs (g, 2t..) (g+8, 2t..) (g, 2t+8..) (g+8, 2t+8..);
 // B regs (k 2t.., n g) (k 2t+8.., n g); d (g, 2t) (g, 2t+1) (g+8, 2t) (g+8, 2t+1).
