@@ -77,7 +77,7 @@ __device__ __forceinline__ void stage_live(Stage<16, KB, false>& st, uint32_t id
                                            const float (&f)[16], int slot, int pos) {
     st.id[slot] = id;
     st.g0[slot] = g0;
-    st.g1[slot] = g1;
+    st.g1[slot] = make_float4(__fmul_rn(0.5f, g1.x), g1.y, __fmul_rn(0.5f, g1.z), g1.w);   // half conic (exact)
     st.live[slot] = pos;   // the backward keeps list positions here
     uint32_t hi[8], lo[8];
 #pragma unroll
@@ -289,7 +289,8 @@ __global__ void __launch_bounds__(64, 7)
 #pragma unroll
                     for (int qp = 0; qp < 2; qp++) {
                         float2 sig2, au2;
-                        eval_alpha2<false>(g0, g1, rpa[qp], rpb[qp], rt[qp], sig2, a2[qp], dx2[qp], dy2[qp], G2[qp], au2);
+                        eval_alpha2<false, true>(g0, g1, rpa[qp], rpb[qp], rt[qp], sig2, a2[qp], dx2[qp], dy2[qp], G2[qp],
+                                                 au2);
                         on[2 * qp] = act && sig2.x >= 0.f && a2[qp].x >= kAlphaMin && idx < last[2 * qp];
                         on[2 * qp + 1] = act && sig2.y >= 0.f && a2[qp].y >= kAlphaMin && idx < last[2 * qp + 1];
                         cl[2 * qp] = au2.x > kAlphaMax;
@@ -355,8 +356,8 @@ __global__ void __launch_bounds__(64, 7)
                     for (int j = 0; j < 8; j++) v[j] = acc[j].x + acc[j].y;
                     // every pixel time carries the camera time offset; the mean moves by v t:
                     // dL/dt += -ddx vx - ddy vy = v0 (a vx + b vy) + v1 (b vx + c vy)
-                    if (gr.dsensor)
-                        dtime += v[0] * (g1.x * g0.z + g1.y * g0.w) + v[1] * (g1.y * g0.z + g1.z * g0.w);
+                    if (gr.dsensor)   // g1 holds (a/2, b, c/2, o')
+                        dtime += v[0] * (2.f * g1.x * g0.z + g1.y * g0.w) + v[1] * (g1.y * g0.z + 2.f * g1.z * g0.w);
 #pragma unroll
                     for (int j = 0; j < 8; j++) vv[8 * u + j] = v[j];
                 }
@@ -404,7 +405,8 @@ __global__ void __launch_bounds__(64, 7)
             const uint32_t id = sw.id[slot];
             const float4 q0 = *reinterpret_cast<float4*>(a_row);
             const float4 q1 = *reinterpret_cast<float4*>(a_row + 4);
-            const float4 cn = sw.g1[slot];   // the entry's conic (a, b, c)
+            const float4 hcn = sw.g1[slot];   // the entry's conic, staged as (a/2, b, c/2)
+            const float4 cn = make_float4(2.f * hcn.x, hcn.y, 2.f * hcn.z, hcn.w);
             // gradients of (mean, mean velocity) and (conic, opacity) record entries: -ddx, -ddy,
             // -ddx t, -ddy t, dsig dx^2 / 2, dsig dx dy, dsig dy^2 / 2, dg G (dsig = -Pn)
             const float4 s0 = make_float4(cn.x * q0.x + cn.y * q0.y, cn.y * q0.x + cn.z * q0.y,
