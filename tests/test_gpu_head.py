@@ -203,7 +203,7 @@ def _bce(p, y):
 
 
 def test_trained_head_beats_plain_composited_channels():
-    """App. B's decoder against the method without it (the hot-path table's baseline):
+    """App. B's decoder against the method without it:
     per-Gaussian intensity and ray-drop logit channels composited by the rasterizer and
     fitted through its own backward with Adam, for the same 1,500 steps and loss.  Scored
     on a held-out sweep: intensity RMSE, drop BCE and the drop decision against the
