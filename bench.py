@@ -400,6 +400,12 @@ def kernel_parts(fr, gd, st_, tgt, flush):
                                           _vp(pgrads["quats"]), _vp(pgrads["opacities"]),
                                           _vp(pgrads["velocities"]), None, st))
     n, C = fr.n, fr.channels
+    # tile sort over the intersections: the emission writes a key and a 4-byte id, each
+    # 8-bit pass reads both, writes both and reads the keys once more for its histogram;
+    # the keys are 16-bit when every tile id fits (32-bit otherwise)
+    key_bytes = 2 if fr.total_tiles <= 65536 else 4
+    tile_passes = max(1, (max(1, int(math.ceil(math.log2(max(fr.total_tiles, 2))))) + 7) // 8)
+    isect_bytes = (key_bytes + 4) + tile_passes * (2 * (key_bytes + 4) + key_bytes)
     work = {
         "raster_camera_fwd": ("alu", ev_cam * (22 + 2 * C) / 1e12, "TFLOP/s"),
         "raster_camera_bwd": ("alu", ev_cam * (50 + 7 * C) / 1e12, "TFLOP/s"),
@@ -407,7 +413,7 @@ def kernel_parts(fr, gd, st_, tgt, flush):
         "raster_lidar_bwd": ("alu", ev_lid * (56 + 7 * C) / 1e12, "TFLOP/s"),
         "project": ("hbm", (n * 56 + S * n * 8 + visible * 56) / 1e9, "GB/s"),
         "project_bwd": ("hbm", (n * 56 + S * n * 4 + visible * 48 + n * 56) / 1e9, "GB/s"),
-        "bin_sort": ("hbm", (S * n * 4 + visible * 64 + n_isect * (8 + 2 * 20) + fr.total_tiles * 8) / 1e9, "GB/s"),
+        "bin_sort": ("hbm", (S * n * 4 + visible * 64 + n_isect * isect_bytes + fr.total_tiles * 8) / 1e9, "GB/s"),
     }
     return {"parts": parts, "work": work, "timed": timed, "cg": cg, "evaluated": {"camera": ev_cam, "lidar": ev_lid},
             "intersections": n_isect}
