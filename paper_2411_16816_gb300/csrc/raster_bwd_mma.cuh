@@ -11,10 +11,17 @@
 // channels, K = the warp's 128 rays).  Each warp forms them per group of 8 staged entries
 // with mma.sync m16n8k16 on split BF16 operands (x = hi + lo, hi = bf16(x), lo = bf16(x -
 // hi); the products hi.hi + hi.lo + lo.hi accumulate in FP32, about 2^-16 relative per
-// term).  The per-ray chain (alpha, transmittance, suffix sum, the 8 geometric terms and
+// term).  The per-ray chain (alpha, transmittance, suffix sum, 8 geometric moments and
 // their warp sums) stays on the CUDA cores, reads P from shared memory and writes the
 // blend weights back in place; the upstream gradients live in shared memory (BF16 high
 // parts and residuals) instead of 64 registers per thread.
+//
+// The two warps of a tile run independently: each stages the entries its own rays reach
+// (16 list positions per batch, deepest first; for lists of uncut cameras only the
+// entries live in the tile, packed), forms its sums and flushes them with its own float4
+// atomics.  The chain sums the moments of Pn dx and Pn dy (Pn = -dL/dsigma); the flush
+// turns them into the mean gradients with the entry's conic, -ddx = Pn (a dx + b dy),
+// -ddy = Pn (b dx + c dy).  The staged conic is (a/2, b, c/2), as the evaluation uses it.
 #pragma once
 
 #include "mma.cuh"
