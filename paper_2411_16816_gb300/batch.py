@@ -142,12 +142,23 @@ class BatchRenderer:
         return n + 2    # the persistent raster launch and its stamp
 
     def run(self):
-        st = _stream()
+        """One batch: the start stamp, every group's projection and binning (the groups are
+        independent and spread over side streams, so that one group's short scan launches
+        overlap another's), then the persistent raster launch over all requests."""
+        cur = torch.cuda.current_stream()
+        st = _stream(cur)
         L.call("splat_stamp", _vp(self.start), st)
-        for fr, sc, _ in self.groups:
+        if not hasattr(self, "_side"):
+            self._side = [torch.cuda.Stream(device=self.device) for _ in range(min(3, len(self.groups)))]
+        for s in self._side:
+            s.wait_stream(cur)
+        for k, (fr, sc, _) in enumerate(self.groups):
+            s = self._side[k % len(self._side)]
             cg = fr.c_gaussians(self.scenes[sc])
-            fr.project(cg)
-            fr.bin_sort()
+            fr.project(cg, stream=s)
+            fr.bin_sort(stream=s)
+        for s in self._side:
+            cur.wait_stream(s)
         L.call("splat_render_batch", _vp(self.table), self.n, self.total_items, self.C, _vp(self.counters),
                _vp(self.stamps), None, st)
 
